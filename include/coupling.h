@@ -1,0 +1,200 @@
+/*
+ * coupling.h -- C ABI of the GB300 (sm_103a) mode-coupling-matrix library.
+ *
+ * The library assembles the pseudo-C_ell mode-coupling matrices of
+ * Kiddier & Gratton, "Fast computation of temperature and polarization
+ * coupling matrices" (arXiv 2602.15605):
+ *
+ *   M^X_{l1 l2} = (2 l2 + 1) Xi_X(l1, l2, W)                       (App. A)
+ *   Xi_X = 1/(4 pi) sum_{l3} (2 l3 + 1) W_{l3} S_X(l1, l2, l3)     (Eqs. K_TT, K_EE)
+ *
+ * for the spectrum kernels
+ *   CPL_TT    S = (l1 l2 l3; 0 0 0)^2                              (Eq. K_TT)
+ *   CPL_TE    S = [L even] (l1 l2 l3; 0 0 0)(l1 l2 l3; -2 2 0)     (Eq. Sig_TE; TB is identical)
+ *   CPL_EE    S = [L even] (l1 l2 l3; -2 2 0)^2                    (Eq. K_EE "+" sign; BB is identical)
+ *   CPL_EEBB  S = [L odd]  (l1 l2 l3; -2 2 0)^2                    (Eq. K_EE "-" sign: the paper's
+ *                                                                  odd-parity "EB" kernel, i.e. the
+ *                                                                  EE <-> BB leakage block)
+ *   CPL_EB    S = S_EE - S_EEBB                                    (the EB -> EB block of the MASTER
+ *                                                                  polarisation system; a
+ *                                                                  convention the paper leaves open)
+ * with L = l1 + l2 + l3 and l3 over the triangle |l1 - l2| .. l1 + l2.
+ * The 3j values are never produced by a per-(l1, l2) recursion: they come
+ * from the lookup table g(p) of Eqs. gdef / g_rec through the closed form of
+ * Eq. 000_sq_main and the (0,-2,2) reduction of Eq. 022_linear (Sec. 3).
+ *
+ * Conventions for every call:
+ *   - Every call returns a cpl_status.  On any status other than CPL_OK the
+ *     output buffers are left untouched and cpl_last_error() returns a
+ *     one-line message (thread-local, valid until the next call on the same
+ *     thread).
+ *   - Device pointers are plain CUDA device addresses on the context's
+ *     device.  The caller owns every input and output buffer; the context
+ *     owns its lookup tables, tile lists and scratch.
+ *   - Calls that take a stream are asynchronous on that stream (a
+ *     cudaStream_t passed as void*; NULL is the legacy default stream).
+ *     Argument errors are reported synchronously.  A device-side fault or
+ *     an exceeded device wait surfaces at the next call on the context or
+ *     at cpl_ctx_sync().
+ *   - A context may be used from one host thread at a time.
+ */
+#ifndef COUPLING_H
+#define COUPLING_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CPL_OK = 0,
+    CPL_ERR_ARG = 1,         /* invalid argument (NULL pointer, bad size, bad combination) */
+    CPL_ERR_RANGE = 2,       /* a size is outside what the library supports */
+    CPL_ERR_OOM = 3,         /* a device or host allocation failed */
+    CPL_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    CPL_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+    CPL_ERR_UNSUPPORTED = 6  /* the request is valid but this build/device cannot run it */
+} cpl_status;
+
+/* Spectrum bits; OR them into cpl_request.spectra.  Outputs are stored in
+ * increasing bit order of the requested set. */
+enum {
+    CPL_TT = 1,
+    CPL_TE = 2,    /* = TB */
+    CPL_EE = 4,    /* = BB */
+    CPL_EEBB = 8,  /* odd-parity kernel */
+    CPL_EB = 16    /* EE - EEBB */
+};
+
+typedef enum {
+    CPL_FP64 = 0,        /* plain FP64 arithmetic throughout (target <= 1e-11 relative) */
+    CPL_MIXED_BF16 = 1   /* l3 contraction on tcgen05 tensor cores with BF16 fixed-point
+                            limbs and exact FP32 partial sums; FP64 tables, scales and
+                            final values (target <= 1e-9 relative) */
+} cpl_precision;
+
+typedef struct cpl_ctx cpl_ctx;
+
+/*
+ * One coupling-matrix request.
+ *
+ *   lmax, lmin   rows and columns run over l = lmin .. lmax.  lmax >= 2 and
+ *                0 <= lmin <= lmax; lmin >= 2 when any polarisation spectrum
+ *                is requested (the (-2 2 0) symbol needs l1, l2 >= 2).
+ *   n_windows    number of windows W stacked in each W_* array (>= 1).
+ *   W_tt/tp/pp   window power spectra, [n_windows][w_len] row-major FP64:
+ *                W_tt feeds CPL_TT, W_tp feeds CPL_TE, W_pp feeds CPL_EE,
+ *                CPL_EEBB and CPL_EB (App. A: the spectrum of the mask pair
+ *                applied to the two maps).  Device pointers for cpl_build /
+ *                cpl_build_batch, host pointers for cpl_build_host.  A
+ *                window that no requested spectrum uses may be NULL.  Passing
+ *                the same pointer for several roles lets the library share
+ *                one l3 sweep between them.
+ *   w_len        entries per window.  The l3 sum needs W_L for L <= 2 lmax
+ *                (Sec. 4); entries beyond w_len - 1 are taken as zero, which
+ *                is exact only for band-limited windows, so w_len < 2 lmax + 1
+ *                requires band_limit.
+ *   band_limit   host array [n_windows] of L_w (last l3 kept), or NULL for
+ *                none.  Terms with l3 > L_w are skipped, which is exact when
+ *                W is zero above L_w (Sec. 4.3).
+ *   spectra      OR of CPL_* bits (non-empty).
+ *   precision    cpl_precision.
+ *   mixed_slices number of BF16 limbs per operand for CPL_MIXED_BF16 (3..6);
+ *                0 selects the default (5).
+ *   bin_edges    host array [n_bins + 1] of increasing multipoles inside
+ *                [lmin, lmax + 1], or NULL for dense output.  Bin b holds
+ *                l in [bin_edges[b], bin_edges[b+1]); the binned matrix is
+ *                M_bb' = (1/|b|) sum_{l1 in b} sum_{l2 in b'} M_{l1 l2}.
+ *   n_bins       number of bins (0 when bin_edges is NULL).
+ */
+typedef struct {
+    int lmax;
+    int lmin;
+    int n_windows;
+    const double *W_tt;
+    const double *W_tp;
+    const double *W_pp;
+    int w_len;
+    const int *band_limit;
+    unsigned spectra;
+    int precision;
+    int mixed_slices;
+    const int *bin_edges;
+    int n_bins;
+} cpl_request;
+
+/* Library version string (static storage). */
+const char *cpl_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *cpl_last_error(void);
+
+/*
+ * Create a context on CUDA device `device` (which must be an sm_103 GPU for
+ * any compute call).  *ctx receives an opaque handle the caller releases
+ * with cpl_ctx_destroy.  Allocates nothing on the device until first use.
+ */
+cpl_status cpl_ctx_create(cpl_ctx **ctx, int device);
+
+/* Synchronise the context's device work and release everything it owns.
+ * NULL is accepted. */
+cpl_status cpl_ctx_destroy(cpl_ctx *ctx);
+
+/* Wait for all work the context queued and report any device-side error
+ * (CPL_ERR_TIMEOUT for an exceeded bounded wait, CPL_ERR_CUDA otherwise). */
+cpl_status cpl_ctx_sync(cpl_ctx *ctx);
+
+/*
+ * Number of doubles the output of `r` occupies:
+ *   dense   n_windows * nspec * n * n,   n = lmax - lmin + 1
+ *   binned  n_windows * nspec * n_bins * n_bins
+ * with nspec the number of bits set in r->spectra.  Validates r.
+ */
+cpl_status cpl_output_size(const cpl_request *r, size_t *n_doubles);
+
+/*
+ * Build the coupling matrices of `r` into `out` (device, caller-owned,
+ * cpl_output_size doubles), asynchronously on `stream`.
+ *
+ * Dense layout: out[w][spec][l1 - lmin][l2 - lmin], spec in increasing bit
+ * order of r->spectra.  Binned layout: out[w][spec][b][b'].  Elements that
+ * the parity selection or the band limit make exactly zero are written as
+ * exactly 0.0.  The W_* pointers are device pointers.
+ */
+cpl_status cpl_build(cpl_ctx *ctx, const cpl_request *r, double *out, void *stream);
+
+/*
+ * The same request with HOST buffers: W_* are host pointers and `out_host`
+ * is a host buffer of cpl_output_size doubles.  The library copies the
+ * windows to the device, builds, copies the result back and returns when
+ * `out_host` is filled (synchronous).  Staging memory is owned by the
+ * context and reused across calls.
+ */
+cpl_status cpl_build_host(cpl_ctx *ctx, const cpl_request *r, double *out_host);
+
+/*
+ * A batch of independent requests (ragged lmax, band limits, window
+ * counts) in one launch sequence: jobs[q] writes outs[q] (device pointers,
+ * each of cpl_output_size(jobs + q) doubles).  All jobs must use the same
+ * precision.  The work items of every job are merged into one cost-ordered
+ * list and executed by one persistent kernel per sweep; the sequence is
+ * captured once into a CUDA graph keyed by the batch shape and replayed on
+ * later calls with the same shape.
+ */
+cpl_status cpl_build_batch(cpl_ctx *ctx, const cpl_request *jobs, int n_jobs,
+                           double *const *outs, void *stream);
+
+/*
+ * Lookup table of Eqs. gdef / g_rec, as the library builds it: out[p] =
+ * g(p) = (2p)! / (2^{2p} (p!)^2) for p = 0 .. pmax, each value the
+ * double-double recurrence g(p) = (p - 1/2)/p g(p-1), g(0) = 1, rounded once
+ * to FP64.  Host-only (no device work); out_host holds pmax + 1 doubles.
+ */
+cpl_status cpl_g_table(int pmax, double *out_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COUPLING_H */

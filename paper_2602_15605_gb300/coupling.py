@@ -1,0 +1,266 @@
+"""Thin ctypes binding of the C ABI in include/coupling.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_build/libcoupling.so``.  There is no CPU fallback -- if the
+library has not been built (``paper_2602_15605_gb300.build_ext.build()``),
+or no sm_103 GPU is present, the calls raise.
+
+PyTorch supplies device memory and the current CUDA stream; the functions
+take and return ``torch.Tensor`` objects (float64, on the context's device).
+"""
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build_ext
+
+TT, TE, EE, EEBB, EB = 1, 2, 4, 8, 16
+SPEC_BITS = (TT, TE, EE, EEBB, EB)
+SPEC_NAMES = {TT: "TT", TE: "TE", EE: "EE", EEBB: "EEBB", EB: "EB"}
+ALL = TT | TE | EE | EEBB | EB
+FP64, MIXED_BF16 = 0, 1
+
+STATUS = {0: "CPL_OK", 1: "CPL_ERR_ARG", 2: "CPL_ERR_RANGE", 3: "CPL_ERR_OOM", 4: "CPL_ERR_CUDA",
+          5: "CPL_ERR_TIMEOUT", 6: "CPL_ERR_UNSUPPORTED"}
+
+
+class CouplingError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_int), ("lmin", ctypes.c_int), ("n_windows", ctypes.c_int),
+                ("W_tt", ctypes.c_void_p), ("W_tp", ctypes.c_void_p), ("W_pp", ctypes.c_void_p),
+                ("w_len", ctypes.c_int), ("band_limit", ctypes.POINTER(ctypes.c_int)),
+                ("spectra", ctypes.c_uint), ("precision", ctypes.c_int), ("mixed_slices", ctypes.c_int),
+                ("bin_edges", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int)]
+
+
+# Every symbol include/coupling.h declares.
+EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
+           "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_g_table")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path():
+    return build_ext.LIB
+
+
+def load():
+    """Load libcoupling.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = build_ext.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library %s is missing: run paper_2602_15605_gb300.build_ext.build() "
+                               "(there is no CPU fallback)" % path)
+        L = ctypes.CDLL(path)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+        L.cpl_version.restype = ctypes.c_char_p
+        L.cpl_last_error.restype = ctypes.c_char_p
+        L.cpl_ctx_create.argtypes = [ctypes.POINTER(vp), ip]
+        L.cpl_ctx_destroy.argtypes = [vp]
+        L.cpl_ctx_sync.argtypes = [vp]
+        L.cpl_output_size.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_size_t)]
+        L.cpl_build.argtypes = [vp, ctypes.POINTER(Request), vp, vp]
+        L.cpl_build_host.argtypes = [vp, ctypes.POINTER(Request), vp]
+        L.cpl_build_batch.argtypes = [vp, ctypes.POINTER(Request), ip, ctypes.POINTER(vp), vp]
+        L.cpl_g_table.argtypes = [ip, dp]
+        for name in EXPORTS:
+            if name not in ("cpl_version", "cpl_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(status):
+    if status != 0:
+        raise CouplingError(status, load().cpl_last_error().decode())
+
+
+def version():
+    return load().cpl_version().decode()
+
+
+def g_table(pmax):
+    """The library's g(p) table (Eq. gdef), host-side, p = 0..pmax."""
+    out = np.zeros(pmax + 1, dtype=np.float64)
+    _check(load().cpl_g_table(int(pmax), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def nspec(spectra):
+    return sum(1 for b in SPEC_BITS if spectra & b)
+
+
+class _Keep:
+    """Holds the ctypes arrays a Request points into."""
+
+    def __init__(self):
+        self.refs = []
+
+
+def _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges, precision, slices,
+                  ptr_of, n_windows, w_len, keep):
+    r = Request()
+    r.lmax, r.lmin, r.n_windows, r.w_len = int(lmax), int(lmin), int(n_windows), int(w_len)
+    r.W_tt, r.W_tp, r.W_pp = ptr_of(W_tt), ptr_of(W_tp), ptr_of(W_pp)
+    r.spectra, r.precision, r.mixed_slices = int(spectra), int(precision), int(slices)
+    if band_limit is not None:
+        bl = np.ascontiguousarray(np.asarray(band_limit, dtype=np.int32).reshape(-1))
+        keep.refs.append(bl)
+        r.band_limit = bl.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    if bin_edges is not None:
+        be = np.ascontiguousarray(np.asarray(bin_edges, dtype=np.int32).reshape(-1))
+        keep.refs.append(be)
+        r.bin_edges = be.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        r.n_bins = be.size - 1
+    return r
+
+
+class Context:
+    """An owned cpl_ctx on one CUDA device."""
+
+    def __init__(self, device=0):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.cpl_ctx_create(ctypes.byref(h), int(device)))
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            load().cpl_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        _check(load().cpl_ctx_sync(self.handle))
+
+    # ------------------------------------------------------------------ device
+    def request(self, lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None,
+                bin_edges=None, precision=FP64, slices=0):
+        """(Request, keepalive, shape) for torch device windows [n_win, w_len]."""
+        import torch
+        ws = [W for W in (W_tt, W_tp, W_pp) if W is not None]
+        if not ws:
+            raise ValueError("no window given")
+        ref = ws[0]
+        n_windows, w_len = (1, ref.shape[0]) if ref.dim() == 1 else tuple(ref.shape)
+        for W in ws:
+            if W.dtype != torch.float64 or not W.is_cuda or not W.is_contiguous():
+                raise ValueError("windows must be contiguous float64 CUDA tensors")
+            if W.numel() != n_windows * w_len:
+                raise ValueError("all windows must have the same shape")
+        keep = _Keep()
+        r = _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges, precision, slices,
+                          lambda W: None if W is None else W.data_ptr(), n_windows, w_len, keep)
+        ns = nspec(spectra)
+        if bin_edges is not None:
+            nb = len(bin_edges) - 1
+            shape = (n_windows, ns, nb, nb)
+        else:
+            n = lmax - lmin + 1
+            shape = (n_windows, ns, n, n)
+        return r, keep, shape
+
+    def build(self, lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None,
+              bin_edges=None, precision=FP64, slices=0, out=None, stream=None):
+        """cpl_build on torch's current stream; returns out [n_win, nspec, n, n] (float64, device)."""
+        import torch
+        r, keep, shape = self.request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges,
+                                      precision, slices)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda:%d" % self.device)
+        elif tuple(out.shape) != shape or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of shape %s" % (shape,))
+        st = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
+        _check(load().cpl_build(self.handle, ctypes.byref(r), ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(st)))
+        del keep
+        return out
+
+    def build_batch(self, jobs, outs=None, stream=None):
+        """cpl_build_batch.  jobs: list of dicts with the keyword arguments of build()."""
+        import torch
+        reqs, keeps, shapes = [], [], []
+        for j in jobs:
+            r, keep, shape = self.request(**j)
+            reqs.append(r)
+            keeps.append(keep)
+            shapes.append(shape)
+        if outs is None:
+            outs = [torch.empty(s, dtype=torch.float64, device="cuda:%d" % self.device) for s in shapes]
+        arr = (Request * len(reqs))(*reqs)
+        ptrs = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        st = torch.cuda.current_stream(self.device).cuda_stream if stream is None else stream
+        _check(load().cpl_build_batch(self.handle, arr, len(reqs), ptrs, ctypes.c_void_p(st)))
+        del keeps
+        return outs
+
+    # ------------------------------------------------------------------ host
+    def build_host(self, lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None,
+                   bin_edges=None, precision=FP64, slices=0, out=None):
+        """cpl_build_host: numpy windows in, numpy matrix out (copies inside the call)."""
+        ws = [np.asarray(W) for W in (W_tt, W_tp, W_pp) if W is not None]
+        ref = ws[0]
+        n_windows, w_len = (1, ref.shape[0]) if ref.ndim == 1 else ref.shape
+        keep = _Keep()
+
+        def ptr(W):
+            if W is None:
+                return None
+            a = np.ascontiguousarray(W, dtype=np.float64)
+            keep.refs.append(a)
+            return a.ctypes.data
+
+        # the same array object for several roles keeps one shared pointer
+        cache = {}
+
+        def ptr_shared(W):
+            if W is None:
+                return None
+            if id(W) not in cache:
+                cache[id(W)] = ptr(W)
+            return cache[id(W)]
+
+        r = _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges, precision, slices,
+                          ptr_shared, n_windows, w_len, keep)
+        ns = nspec(spectra)
+        if bin_edges is not None:
+            nb = len(bin_edges) - 1
+            shape = (n_windows, ns, nb, nb)
+        else:
+            n = lmax - lmin + 1
+            shape = (n_windows, ns, n, n)
+        if out is None:
+            out = np.empty(shape, dtype=np.float64)
+        _check(load().cpl_build_host(self.handle, ctypes.byref(r), ctypes.c_void_p(out.ctypes.data)))
+        del keep
+        return out
+
+
+def output_size(lmax, n_windows, spectra, lmin=2, w_len=None, band_limit=None, bin_edges=None):
+    """cpl_output_size for a request (validates it; needs no GPU)."""
+    keep = _Keep()
+    w_len = 2 * lmax + 1 if w_len is None else w_len
+    fake = 0x1000  # any non-NULL address: output_size never dereferences the windows
+    r = _make_request(lmax, fake if spectra & TT else None, fake if spectra & TE else None,
+                      fake if spectra & (EE | EEBB | EB) else None, spectra, lmin, band_limit, bin_edges,
+                      FP64, 0, lambda W: W, n_windows, w_len, keep)
+    n = ctypes.c_size_t()
+    _check(load().cpl_output_size(ctypes.byref(r), ctypes.byref(n)))
+    return n.value

@@ -1,0 +1,462 @@
+// api.cu -- the C ABI of coupling.h: validation, context, orchestration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+#define CPL_VERSION_STRING "paper_2602_15605_gb300 coupling 0.1 (sm_103a)"
+
+namespace cpl {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+cpl_status fail(cpl_status s, const std::string &msg) {
+    set_error(msg);
+    return s;
+}
+
+int spec_count(unsigned s) {
+    int c = 0;
+    for (int b = 0; b < 5; ++b) c += (s >> b) & 1u;
+    return c;
+}
+
+int spec_slot(unsigned s, unsigned bit) {
+    if (!(s & bit)) return -1;
+    int c = 0;
+    for (unsigned b = 1; b < bit; b <<= 1) c += (s & b) ? 1 : 0;
+    return c;
+}
+
+// A device buffer that only grows.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t cap = 0;
+    cpl_status ensure(size_t bytes, const char *what) {
+        if (bytes <= cap) return CPL_OK;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)256);
+        if (cudaMalloc(&ptr, want) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CPL_ERR_OOM, std::string("device allocation failed for ") + what);
+        }
+        cap = want;
+        return CPL_OK;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(ptr); }
+};
+
+struct TileSet {
+    std::vector<Tile> host;
+    DevBuf dev;
+};
+
+}  // namespace cpl
+
+using namespace cpl;
+
+struct cpl_ctx {
+    int device = 0;
+    int pmax = -1;
+    DevBuf g, h;                 // lookup tables (Sec. 3.1)
+    std::vector<std::unique_ptr<TileSet>> tile_sets;
+    std::vector<std::pair<long long, TileSet *>> tile_index;   // key (lmax, lmin)
+    DevBuf weights;              // A(l3) per role and window
+    DevBuf l3cap;
+    DevBuf items;
+    DevBuf bins_of, bins_inv;
+    DevBuf stage_w, stage_out;   // cpl_build_host staging
+    cudaStream_t own_stream = nullptr;
+    cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams
+};
+
+namespace {
+
+cpl_status select_device(cpl_ctx *c) {
+    CPL_CUDA_TRY(cudaSetDevice(c->device));
+    return CPL_OK;
+}
+
+bool wants_pol(unsigned s) { return (s & (kTE | kEE | kEEBB | kEB)) != 0; }
+
+cpl_status validate(const cpl_request *r, bool device_ptrs) {
+    (void)device_ptrs;
+    if (!r) return fail(CPL_ERR_ARG, "request is NULL");
+    if (r->lmax < 2) return fail(CPL_ERR_ARG, "lmax must be >= 2");
+    if (r->lmax > 32000) return fail(CPL_ERR_RANGE, "lmax above 32000 is not supported");
+    if (r->lmin < 0 || r->lmin > r->lmax) return fail(CPL_ERR_ARG, "lmin must lie in [0, lmax]");
+    if (r->spectra == 0 || (r->spectra & ~31u)) return fail(CPL_ERR_ARG, "spectra must be a non-empty OR of CPL_* bits");
+    if (wants_pol(r->spectra) && r->lmin < 2)
+        return fail(CPL_ERR_ARG, "polarisation spectra need lmin >= 2");
+    if (r->n_windows < 1) return fail(CPL_ERR_ARG, "n_windows must be >= 1");
+    if (r->n_windows > 65535) return fail(CPL_ERR_RANGE, "n_windows above 65535 is not supported");
+    if ((r->spectra & kTT) && !r->W_tt) return fail(CPL_ERR_ARG, "W_tt is NULL but CPL_TT is requested");
+    if ((r->spectra & kTE) && !r->W_tp) return fail(CPL_ERR_ARG, "W_tp is NULL but CPL_TE is requested");
+    if ((r->spectra & (kEE | kEEBB | kEB)) && !r->W_pp)
+        return fail(CPL_ERR_ARG, "W_pp is NULL but a polarisation spectrum is requested");
+    if (r->w_len < 1) return fail(CPL_ERR_ARG, "w_len must be >= 1");
+    const int need = 2 * r->lmax;
+    for (int w = 0; w < r->n_windows; ++w) {
+        int top = need;
+        if (r->band_limit) {
+            if (r->band_limit[w] < 0) return fail(CPL_ERR_ARG, "band_limit entries must be >= 0");
+            top = std::min(top, r->band_limit[w]);
+        }
+        if (r->w_len < top + 1)
+            return fail(CPL_ERR_ARG, "w_len too short: the l3 sum needs W up to min(2 lmax, band_limit)");
+    }
+    if (r->precision != CPL_FP64 && r->precision != CPL_MIXED_BF16)
+        return fail(CPL_ERR_ARG, "unknown precision");
+    if (r->precision == CPL_MIXED_BF16 && r->mixed_slices != 0 &&
+        (r->mixed_slices < 3 || r->mixed_slices > 6))
+        return fail(CPL_ERR_ARG, "mixed_slices must be 0 or in 3..6");
+    if (r->bin_edges) {
+        if (r->n_bins < 1) return fail(CPL_ERR_ARG, "n_bins must be >= 1 with bin_edges");
+        if (r->bin_edges[0] < r->lmin || r->bin_edges[r->n_bins] > r->lmax + 1)
+            return fail(CPL_ERR_ARG, "bin_edges must lie inside [lmin, lmax + 1]");
+        for (int b = 0; b < r->n_bins; ++b)
+            if (r->bin_edges[b + 1] <= r->bin_edges[b]) return fail(CPL_ERR_ARG, "bin_edges must increase");
+    } else if (r->n_bins != 0) {
+        return fail(CPL_ERR_ARG, "n_bins must be 0 without bin_edges");
+    }
+    return CPL_OK;
+}
+
+size_t out_doubles(const cpl_request *r) {
+    const size_t ns = (size_t)spec_count(r->spectra);
+    if (r->bin_edges) return (size_t)r->n_windows * ns * (size_t)r->n_bins * (size_t)r->n_bins;
+    const size_t n = (size_t)(r->lmax - r->lmin + 1);
+    return (size_t)r->n_windows * ns * n * n;
+}
+
+cpl_status ensure_tables(cpl_ctx *c, int lmax) {
+    const int need = 2 * lmax + 2 * (TILE_I + TILE_J) + 16;
+    if (need <= c->pmax) return CPL_OK;
+    const int pmax = std::max(need, 2 * c->pmax);
+    std::vector<double> g, h;
+    build_tables_host(pmax, g, h);
+    cpl_status s;
+    if ((s = c->g.ensure(sizeof(double) * (pmax + 1), "g table")) != CPL_OK) return s;
+    if ((s = c->h.ensure(sizeof(double) * (pmax + 1), "h table")) != CPL_OK) return s;
+    CPL_CUDA_TRY(cudaMemcpy(c->g.ptr, g.data(), sizeof(double) * (pmax + 1), cudaMemcpyHostToDevice));
+    CPL_CUDA_TRY(cudaMemcpy(c->h.ptr, h.data(), sizeof(double) * (pmax + 1), cudaMemcpyHostToDevice));
+    c->pmax = pmax;
+    return CPL_OK;
+}
+
+cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out) {
+    const long long key = (long long)lmax * 65536LL + lmin;
+    for (auto &kv : c->tile_index)
+        if (kv.first == key) {
+            *out = kv.second;
+            return CPL_OK;
+        }
+    auto ts = std::make_unique<TileSet>();
+    make_tiles(lmax, lmin, ts->host);
+    cpl_status s = ts->dev.ensure(sizeof(Tile) * std::max<size_t>(ts->host.size(), 1), "tile list");
+    if (s != CPL_OK) return s;
+    if (!ts->host.empty())
+        CPL_CUDA_TRY(cudaMemcpy(ts->dev.ptr, ts->host.data(), sizeof(Tile) * ts->host.size(),
+                                cudaMemcpyHostToDevice));
+    *out = ts.get();
+    c->tile_index.emplace_back(key, ts.get());
+    c->tile_sets.push_back(std::move(ts));
+    return CPL_OK;
+}
+
+// Work items (window, tile) of one request, heaviest first.  A tile whose
+// smallest |d| exceeds a window's last l3 contributes nothing for that
+// window and is dropped (the output is pre-zeroed in that case).
+void make_items(const std::vector<Tile> &tiles, const std::vector<int> &caps, int lmax, int lmin,
+                bool banded, std::vector<WorkItem> &items) {
+    items.clear();
+    std::vector<std::pair<double, WorkItem>> tmp;
+    const int nw = (int)caps.size();
+    for (int ti = 0; ti < (int)tiles.size(); ++ti) {
+        const Tile &t = tiles[ti];
+        for (int w = 0; w < nw; ++w) {
+            if (banded && 2 * t.i0 + t.pi > caps[w]) continue;
+            WorkItem it{0, w, ti, 0};
+            const double cost = banded ? tile_terms(t, lmax, lmin, caps[w]) : (double)t.cost;
+            tmp.emplace_back(cost, it);
+        }
+    }
+    std::stable_sort(tmp.begin(), tmp.end(),
+                     [](const std::pair<double, WorkItem> &a, const std::pair<double, WorkItem> &b) {
+                         return a.first > b.first;
+                     });
+    items.reserve(tmp.size());
+    for (auto &p : tmp) items.push_back(p.second);
+}
+
+struct Group {
+    const double *W;
+    unsigned spectra;   // spectra this window pointer serves
+};
+
+// The plain FP64 build of one request on `st` (device pointers).
+cpl_status build_fp64(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
+    cpl_status s;
+    if ((s = ensure_tables(c, r->lmax)) != CPL_OK) return s;
+    TileSet *ts = nullptr;
+    if ((s = get_tiles(c, r->lmax, r->lmin, &ts)) != CPL_OK) return s;
+
+    const int nw = r->n_windows;
+    std::vector<int> caps(nw);
+    bool banded = false;
+    for (int w = 0; w < nw; ++w) {
+        int cap = std::min(2 * r->lmax, r->w_len - 1);
+        if (r->band_limit) cap = std::min(cap, r->band_limit[w]);
+        if (cap < 2 * r->lmax) banded = true;
+        caps[w] = cap;
+    }
+    // window roles sharing one pointer share one sweep
+    std::vector<Group> groups;
+    auto add = [&](const double *W, unsigned bits) {
+        if (!(r->spectra & bits)) return;
+        for (auto &g : groups)
+            if (g.W == W) {
+                g.spectra |= (r->spectra & bits);
+                return;
+            }
+        groups.push_back({W, r->spectra & bits});
+    };
+    add(r->W_tt, kTT);
+    add(r->W_tp, kTE);
+    add(r->W_pp, kEE | kEEBB | kEB);
+
+    std::vector<WorkItem> items;
+    make_items(ts->host, caps, r->lmax, r->lmin, banded, items);
+
+    const int a_stride = 2 * r->lmax + 2;
+    if ((s = c->weights.ensure(sizeof(double) * (size_t)a_stride * nw * groups.size(), "weights")) != CPL_OK) return s;
+    if ((s = c->l3cap.ensure(sizeof(int) * nw, "l3 caps")) != CPL_OK) return s;
+    if ((s = c->items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1), "work items")) != CPL_OK) return s;
+
+    const int nb = r->bin_edges ? r->n_bins : 0;
+    std::vector<int> bin_of;
+    std::vector<double> bin_inv;
+    if (nb) {
+        bin_of.assign(r->lmax + 1, -1);
+        bin_inv.assign(nb, 0.0);
+        for (int b = 0; b < nb; ++b) {
+            for (int l = r->bin_edges[b]; l < r->bin_edges[b + 1]; ++l) bin_of[l] = b;
+            bin_inv[b] = 1.0 / (double)(r->bin_edges[b + 1] - r->bin_edges[b]);
+        }
+        if ((s = c->bins_of.ensure(sizeof(int) * bin_of.size(), "bin map")) != CPL_OK) return s;
+        if ((s = c->bins_inv.ensure(sizeof(double) * nb, "bin sizes")) != CPL_OK) return s;
+    }
+
+    CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
+    CPL_CUDA_TRY(cudaMemcpyAsync(c->l3cap.ptr, caps.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, st));
+    if (!items.empty())
+        CPL_CUDA_TRY(cudaMemcpyAsync(c->items.ptr, items.data(), sizeof(WorkItem) * items.size(),
+                                     cudaMemcpyHostToDevice, st));
+    if (nb) {
+        CPL_CUDA_TRY(cudaMemcpyAsync(c->bins_of.ptr, bin_of.data(), sizeof(int) * bin_of.size(),
+                                     cudaMemcpyHostToDevice, st));
+        CPL_CUDA_TRY(cudaMemcpyAsync(c->bins_inv.ptr, bin_inv.data(), sizeof(double) * nb,
+                                     cudaMemcpyHostToDevice, st));
+    }
+    if (nb || banded) CPL_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * out_doubles(r), st));
+
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const Group &G = groups[gi];
+        double *A = c->weights.as<double>() + gi * (size_t)a_stride * nw;
+        CPL_CUDA_TRY(launch_weights(G.W, r->w_len, nw, c->l3cap.as<int>(), A, a_stride, st));
+        PlainArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.g = c->g.as<double>();
+        a.h = c->h.as<double>();
+        a.A = A;
+        a.a_stride = a_stride;
+        a.l3cap = c->l3cap.as<int>();
+        a.tiles = ts->dev.as<Tile>();
+        a.items = c->items.as<WorkItem>();
+        a.n_items = (int)items.size();
+        a.lmax = r->lmax;
+        a.lmin = r->lmin;
+        a.out = out;
+        a.nspec = spec_count(r->spectra);
+        const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
+        for (int q = 0; q < 5; ++q) a.slot[q] = (G.spectra & bits[q]) ? spec_slot(r->spectra, bits[q]) : -1;
+        a.n_bins = nb;
+        a.bin_of = nb ? c->bins_of.as<int>() : nullptr;
+        a.bin_inv = nb ? c->bins_inv.as<double>() : nullptr;
+        int mode;
+        if (G.spectra & (kEE | kEEBB | kEB)) mode = MODE_POL;
+        else if (G.spectra & kTE) mode = MODE_TE;
+        else mode = MODE_TT;
+        CPL_CUDA_TRY(launch_plain(mode, a, st));
+    }
+    CPL_CUDA_TRY(cudaEventRecord(c->done, st));
+    return CPL_OK;
+}
+
+cpl_status build_one(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
+    if (r->precision == CPL_MIXED_BF16)
+        return fail(CPL_ERR_UNSUPPORTED, "the mixed-precision path is not available in this build");
+    return build_fp64(c, r, out, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cpl_version(void) { return CPL_VERSION_STRING; }
+
+const char *cpl_last_error(void) { return g_last_error.c_str(); }
+
+cpl_status cpl_ctx_create(cpl_ctx **ctx, int device) {
+    if (!ctx) return fail(CPL_ERR_ARG, "ctx is NULL");
+    *ctx = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    if (device < 0 || device >= n) return fail(CPL_ERR_ARG, "no such CUDA device");
+    cudaDeviceProp prop;
+    CPL_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(CPL_ERR_UNSUPPORTED, std::string("this library is built for sm_103 (GB300); device is ") +
+                                             prop.name);
+    auto c = new (std::nothrow) cpl_ctx();
+    if (!c) return fail(CPL_ERR_OOM, "host allocation failed");
+    c->device = device;
+    cudaSetDevice(device);
+    if (cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(CPL_ERR_CUDA, "could not create the context's stream / event");
+    }
+    *ctx = c;
+    return CPL_OK;
+}
+
+cpl_status cpl_ctx_destroy(cpl_ctx *c) {
+    if (!c) return CPL_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    c->g.release();
+    c->h.release();
+    for (auto &t : c->tile_sets) t->dev.release();
+    c->weights.release();
+    c->l3cap.release();
+    c->items.release();
+    c->bins_of.release();
+    c->bins_inv.release();
+    c->stage_w.release();
+    c->stage_out.release();
+    if (c->done) cudaEventDestroy(c->done);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+    return CPL_OK;
+}
+
+cpl_status cpl_ctx_sync(cpl_ctx *c) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    cpl_status s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+    return CPL_OK;
+}
+
+cpl_status cpl_output_size(const cpl_request *r, size_t *n_doubles) {
+    if (!n_doubles) return fail(CPL_ERR_ARG, "n_doubles is NULL");
+    cpl_status s = validate(r, true);
+    if (s != CPL_OK) return s;
+    *n_doubles = out_doubles(r);
+    return CPL_OK;
+}
+
+cpl_status cpl_build(cpl_ctx *c, const cpl_request *r, double *out, void *stream) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (!out) return fail(CPL_ERR_ARG, "out is NULL");
+    cpl_status s = validate(r, true);
+    if (s != CPL_OK) return s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    return build_one(c, r, out, (cudaStream_t)stream);
+}
+
+cpl_status cpl_build_host(cpl_ctx *c, const cpl_request *r, double *out_host) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (!out_host) return fail(CPL_ERR_ARG, "out_host is NULL");
+    cpl_status s = validate(r, false);
+    if (s != CPL_OK) return s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    cudaStream_t st = c->own_stream;
+    // stage the distinct windows
+    const double *srcs[3] = {r->W_tt, r->W_tp, r->W_pp};
+    const double *dsts[3] = {nullptr, nullptr, nullptr};
+    const size_t wbytes = sizeof(double) * (size_t)r->n_windows * (size_t)r->w_len;
+    if ((s = c->stage_w.ensure(3 * wbytes, "window staging")) != CPL_OK) return s;
+    int used = 0;
+    for (int q = 0; q < 3; ++q) {
+        if (!srcs[q]) continue;
+        for (int p = 0; p < q; ++p)
+            if (srcs[p] == srcs[q]) dsts[q] = dsts[p];
+        if (dsts[q]) continue;
+        double *d = reinterpret_cast<double *>(static_cast<char *>(c->stage_w.ptr) + used * wbytes);
+        CPL_CUDA_TRY(cudaMemcpyAsync(d, srcs[q], wbytes, cudaMemcpyHostToDevice, st));
+        dsts[q] = d;
+        ++used;
+    }
+    const size_t ob = sizeof(double) * out_doubles(r);
+    if ((s = c->stage_out.ensure(ob, "output staging")) != CPL_OK) return s;
+    cpl_request rd = *r;
+    rd.W_tt = dsts[0];
+    rd.W_tp = dsts[1];
+    rd.W_pp = dsts[2];
+    if ((s = build_one(c, &rd, c->stage_out.as<double>(), st)) != CPL_OK) return s;
+    CPL_CUDA_TRY(cudaMemcpyAsync(out_host, c->stage_out.ptr, ob, cudaMemcpyDeviceToHost, st));
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+    return CPL_OK;
+}
+
+cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, double *const *outs,
+                           void *stream) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (!jobs || !outs || n_jobs < 1) return fail(CPL_ERR_ARG, "jobs / outs must be non-empty");
+    cpl_status s;
+    for (int q = 0; q < n_jobs; ++q) {
+        if ((s = validate(jobs + q, true)) != CPL_OK) return s;
+        if (!outs[q]) return fail(CPL_ERR_ARG, "an output pointer is NULL");
+        if (jobs[q].precision != jobs[0].precision) return fail(CPL_ERR_ARG, "all jobs must use one precision");
+    }
+    if ((s = select_device(c)) != CPL_OK) return s;
+    for (int q = 0; q < n_jobs; ++q)
+        if ((s = build_one(c, jobs + q, outs[q], (cudaStream_t)stream)) != CPL_OK) return s;
+    return CPL_OK;
+}
+
+cpl_status cpl_g_table(int pmax, double *out_host) {
+    if (pmax < 0 || !out_host) return fail(CPL_ERR_ARG, "pmax must be >= 0 and out_host non-NULL");
+    if (pmax > 1 << 24) return fail(CPL_ERR_RANGE, "pmax too large");
+    std::vector<double> g, h;
+    build_tables_host(pmax, g, h);
+    std::memcpy(out_host, g.data(), sizeof(double) * (size_t)(pmax + 1));
+    return CPL_OK;
+}
+
+}  // extern "C"

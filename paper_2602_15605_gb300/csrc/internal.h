@@ -1,0 +1,92 @@
+// internal.h -- shared declarations of the coupling library (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <map>
+#include <tuple>
+
+#include "../../include/coupling.h"
+
+namespace cpl {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+cpl_status fail(cpl_status s, const std::string &msg);
+#define CPL_CUDA_TRY(expr)                                                      \
+    do {                                                                        \
+        cudaError_t e_ = (expr);                                                \
+        if (e_ != cudaSuccess)                                                  \
+            return ::cpl::fail(CPL_ERR_CUDA, std::string(#expr " failed: ") +  \
+                                                 cudaGetErrorString(e_));       \
+    } while (0)
+
+// Spectrum bits as in coupling.h.
+constexpr unsigned kTT = 1u, kTE = 2u, kEE = 4u, kEEBB = 8u, kEB = 16u;
+int spec_slot(unsigned spectra, unsigned bit);   // index of bit in the requested set, -1 if absent
+int spec_count(unsigned spectra);
+
+// ---------------------------------------------------------------- tables
+// g(p) of Eq. gdef and h(p) = 1 / ((2p + 1) g(p)) (the 1/g and 1/(J+1) tables of
+// Sec. 3.1 fused), each built by the recurrence in double-double and rounded once.
+void build_tables_host(int pmax, std::vector<double> &g, std::vector<double> &h);
+
+// ---------------------------------------------------------------- tiles
+// One work item of the separable l3 contraction: a TILE_I x TILE_J block of
+// (i, j) = ((d - pi)/2, (s - pi)/2) in parity class pi, d = l2 - l1, s = l1 + l2.
+struct Tile {
+    int16_t pi;      // parity class of d (and s)
+    int16_t pad;
+    int32_t i0, j0;  // first row / column of the block
+    int32_t cost;    // l3 terms (both sweeps) summed over the block's valid pairs, /1024
+};
+static_assert(sizeof(Tile) == 16, "Tile must be 16 bytes");
+
+// Work item of a batched launch: a tile of one job and one window.
+struct WorkItem {
+    int32_t job;
+    int32_t win;
+    int32_t tile;    // index into the job's tile list
+    int32_t pad;
+};
+
+constexpr int TILE_I = 32;
+constexpr int TILE_J = 32;
+
+// All tiles of the valid region lmin <= l1 <= l2 <= lmax, ordered by cost
+// (largest first).
+void make_tiles(int lmax, int lmin, std::vector<Tile> &tiles);
+// Tiles whose l3 range meets [0, band] (any pair with |d| <= band).
+void filter_tiles_band(const std::vector<Tile> &all, int band, std::vector<Tile> &out);
+double tile_terms(const Tile &t, int lmax, int lmin, int band);  // exact l3 term count (both parities) of a tile
+
+// ---------------------------------------------------------------- plain FP64 kernels
+// Kernel families by which GEMM products they run (see plain_fp64.cu).
+enum PlainMode { MODE_TT = 0, MODE_TE = 1, MODE_POL = 2, MODE_ALL = 3 };
+
+struct PlainArgs {
+    const double *g;        // [pmax + 1]
+    const double *h;        // [pmax + 1]
+    const double *A;        // [n_win][a_stride] weights (2 l3 + 1) W / (4 pi), zero past the band
+    int a_stride;
+    const int *l3cap;       // [n_win] last l3 with nonzero weight
+    const Tile *tiles;       // tile list of the request
+    const WorkItem *items;   // (window, tile) pairs to run, heaviest first
+    int n_items;
+    int lmax, lmin;
+    double *out;            // dense [n_win][nspec][n][n] or binned [n_win][nspec][nb][nb]
+    int nspec;
+    int slot[5];            // output slot of TT, TE, EE, EEBB, EB (-1 = not written)
+    // binning (n_bins == 0: dense)
+    int n_bins;
+    const int *bin_of;      // [lmax + 1] bin index or -1
+    const double *bin_inv;  // [n_bins] 1 / |b|
+};
+
+cudaError_t launch_plain(int mode, const PlainArgs &a, cudaStream_t st);
+cudaError_t launch_weights(const double *W, int w_len, int n_win, const int *l3cap,
+                           double *A, int a_stride, cudaStream_t st);
+
+}  // namespace cpl

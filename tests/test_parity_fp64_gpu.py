@@ -1,0 +1,180 @@
+"""Plain FP64 path vs the CPU oracle, element by element (GPU).
+
+Bar: per-element relative error (against S_abs) <= 1e-11 for every
+spectrum; elements that are zero by parity or band exactly 0.0.  Sizes span
+several 32 x 32 tiles with ragged tails; the full-size l_max = 3000 case is
+checked on sampled pairs, and identities that hold at any size (full sky,
+constant window) are checked on whole matrices.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_15605_gb300 import coupling, windows
+from parity_util import per_spectrum, rel_err, sample_pairs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+ALLN = ["TT", "TE", "EE", "EEBB", "EB"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2602_15605_gb300 import build_ext
+    build_ext.build()
+    c = coupling.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def names(spectra):
+    return [n for b, n in zip(coupling.SPEC_BITS, ALLN) if spectra & b]
+
+
+def check_dense(ctx, lmax, Wt, Wc, Wp, spectra, lmin=2, band_limit=None, tol=TOL, shared=False):
+    if shared:
+        W = dev(Wt)
+        M = ctx.build(lmax, W, W, W, spectra, lmin=lmin, band_limit=band_limit)
+    else:
+        M = ctx.build(lmax, dev(Wt) if Wt is not None else None, dev(Wc) if Wc is not None else None,
+                      dev(Wp) if Wp is not None else None, spectra, lmin=lmin, band_limit=band_limit)
+    got = M.cpu().numpy()
+    ref, sab = oracle.coupling_dense(lmax, Wt, Wc, Wp, spectra, lmin=lmin, band_limit=band_limit)
+    errs = per_spectrum(got, ref, sab, names(spectra))
+    assert max(errs.values()) <= tol, errs
+    return errs
+
+
+def test_tt_512_full_matrix(ctx):
+    # one mask-like window, l_max = 512, l <= 1024, output 511 x 511
+    W = windows.tt_512()
+    errs = check_dense(ctx, 512, W, None, None, coupling.TT)
+    print("TT 512:", errs)
+
+
+def test_full_spin_separate_windows_dense(ctx):
+    lmax = 157   # several tiles and ragged tails in both parities
+    Wt, Wc, Wp = (windows.gaussian_taper(lmax, s) for s in (2, 3, 4))
+    print(check_dense(ctx, lmax, Wt, Wc, Wp, coupling.ALL))
+
+
+def test_full_spin_shared_window_dense(ctx):
+    lmax = 130
+    W = windows.mask_like(lmax, seed=21)
+    print(check_dense(ctx, lmax, W, W, W, coupling.ALL, shared=True))
+
+
+@pytest.mark.parametrize("spectra", [coupling.TT, coupling.TE, coupling.EE, coupling.EEBB, coupling.EB,
+                                     coupling.EE | coupling.EEBB, coupling.TT | coupling.EB,
+                                     coupling.TE | coupling.EEBB])
+def test_spectrum_subsets(ctx, spectra):
+    lmax = 75
+    Wt, Wc, Wp = (windows.gaussian_taper(lmax, s) for s in (5, 6, 7))
+    check_dense(ctx, lmax, Wt, Wc, Wp, spectra)
+
+
+def test_tt_lmin_zero_and_multi_window(ctx):
+    lmax = 97
+    W = np.stack([windows.random_positive(lmax, seed=s) for s in range(3)])
+    check_dense(ctx, lmax, W, None, None, coupling.TT, lmin=0)
+
+
+def test_small_edge_sizes(ctx):
+    for lmax, lmin in [(2, 2), (3, 2), (5, 5), (33, 2), (34, 3), (64, 2), (65, 2)]:
+        W = windows.random_positive(lmax, seed=lmax)
+        check_dense(ctx, lmax, W, W, W, coupling.ALL, lmin=lmin)
+
+
+def test_band_limited_dense(ctx):
+    lmax = 120
+    W = np.stack([windows.random_positive(lmax, seed=s, band=b) for s, b in ((1, 10), (2, 33), (3, 64))])
+    bl = [10, 33, 64]
+    check_dense(ctx, lmax, W, W, W, coupling.ALL, band_limit=bl)
+    # band-limited equals full sweep on the same (zero above L_w) windows
+    Mb = ctx.build(lmax, dev(W), dev(W), dev(W), coupling.ALL, band_limit=bl).cpu().numpy()
+    Mf = ctx.build(lmax, dev(W), dev(W), dev(W), coupling.ALL).cpu().numpy()
+    assert np.array_equal(Mb, Mf)
+
+
+def test_binned(ctx):
+    lmax = 140
+    W = np.stack([windows.random_positive(lmax, seed=s, band=b) for s, b in ((4, 20), (5, 40))])
+    edges = oracle.bin_edges(2, lmax, 25)
+    got = ctx.build(lmax, dev(W), dev(W), dev(W), coupling.ALL, band_limit=[20, 40], bin_edges=edges)
+    ref, sab = oracle.coupling_dense(lmax, W, W, W, coupling.ALL)
+    Rb = oracle.bin_matrix(ref, 2, edges)
+    Sb = oracle.bin_matrix(sab, 2, edges)
+    errs = per_spectrum(got.cpu().numpy(), Rb, Sb, ALLN)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_full_spin_3000_sampled(ctx):
+    # separate W^TT, W^TP, W^PP, l_max = 3000, l <= 6000: sampled pairs
+    lmax = 3000
+    Wt, Wc, Wp = windows.full_spin_3000(lmax)
+    M = ctx.build(lmax, dev(Wt), dev(Wc), dev(Wp), coupling.ALL)
+    l1, l2 = sample_pairs(lmax, n_random=6000)
+    got = M[:, :, l1 - 2, l2 - 2].cpu().numpy()
+    ref, sab = oracle.coupling_pairs(l1, l2, Wt, Wc, Wp, coupling.ALL)
+    errs = per_spectrum(got, ref, sab, ALLN)
+    print("full spin 3000 sampled:", errs)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_full_sky_identity_large(ctx):
+    lmax = 700
+    W = windows.full_sky(lmax)
+    M = ctx.build(lmax, dev(W), dev(W), dev(W), coupling.ALL).cpu().numpy()
+    I = np.eye(lmax - 1)
+    for s, want in enumerate((I, I, I, 0 * I, I)):
+        assert np.max(np.abs(M[0, s] - want)) < 1e-12, ALLN[s]
+
+
+def test_constant_window_large(ctx):
+    lmax = 600
+    W = windows.constant(lmax)
+    M = ctx.build(lmax, dev(W), None, dev(W), coupling.TT | coupling.EE | coupling.EEBB).cpu().numpy()
+    col = (2 * np.arange(2, lmax + 1) + 1)[None, :]
+    assert np.max(np.abs(M[0, 0] / col - 1)) < 1e-11
+    assert np.max(np.abs((M[0, 1] + M[0, 2]) / col - 1)) < 1e-11
+
+
+def test_build_host_matches_device(ctx):
+    lmax = 90
+    Wt, Wc, Wp = (windows.gaussian_taper(lmax, s) for s in (8, 9, 10))
+    Md = ctx.build(lmax, dev(Wt), dev(Wc), dev(Wp), coupling.ALL).cpu().numpy()
+    Mh = ctx.build_host(lmax, Wt, Wc, Wp, coupling.ALL)
+    assert np.array_equal(Md, Mh)
+
+
+def test_batch_matches_single(ctx):
+    jobs = []
+    for lm, s in ((40, 1), (77, 2), (130, 3)):
+        W = dev(windows.mask_like(lm, seed=s))
+        jobs.append(dict(lmax=lm, W_tt=W, W_tp=W, W_pp=W, spectra=coupling.ALL))
+    outs = ctx.build_batch(jobs)
+    for j, o in zip(jobs, outs):
+        single = ctx.build(**j)
+        assert np.array_equal(o.cpu().numpy(), single.cpu().numpy())
+
+
+def test_argument_errors_leave_output_untouched(ctx):
+    import torch
+    lmax = 20
+    W = dev(windows.random_positive(lmax, seed=1))
+    out = torch.full((1, 1, lmax - 1, lmax - 1), 7.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(coupling.CouplingError) as e:
+        ctx.build(lmax, W, None, None, coupling.EE, out=out)   # W_pp missing
+    assert e.value.status == 1
+    with pytest.raises(coupling.CouplingError):
+        ctx.build(lmax, W, None, None, coupling.TT, lmin=-1)
+    torch.cuda.synchronize()
+    assert torch.all(out == 7.0)
