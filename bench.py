@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the coupling-matrix library on GB300.
+
+Workload (one "step"): the full spin-0 / spin-2 set -- TT, TE(=TB),
+EE(=BB), EE->BB and EB -- at l_max = 3000 from three separate synthetic
+windows W^TT, W^TP, W^PP (l <= 6000; power law (l+1)^-a, a ~ U(2,3), times a
+Gaussian taper sigma_l ~ U(200, 800), W_0 = 4 pi fsky^2), plain FP64 path,
+dense 2999 x 2999 output per spectrum.  One step = one cpl_build call.
+
+Printed JSON line (rank 0):
+  value        coupling elements/s = n_windows * n_spectra * 2999^2 / step time,
+               inputs resident in HBM, CUDA events on the launching stream,
+               L2 flushed between steps (outside the timed events)
+  e2e          the same metric through cpl_build_host (host windows in, host
+               matrix out; H2D and D2H copies inside the timed region)
+  roofline     dominant kernel's algorithmic FLOP / its event-timed duration
+               against the FP64 pipe peak (2 FMA/clk/SM x 152 SMs x 2.07 GHz)
+  cpu_baseline the CPU oracle (Schulten-Gordon recursion + direct sum) on a
+               bounded random sample of pairs of the same workload
+Multi-GPU (torchrun): every rank builds an independent problem of the same
+size (weak scaling; no data-path collective), the step time is the max over
+ranks, and value counts the elements of all ranks.
+
+--impl reference times the CPU oracle itself as the reference arm.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "M_l1l2 coupling elements/s (full spin set, plain FP64)"
+UNIT = "elements/s"
+LMAX = 3000
+SPEC_NAMES = ("TT", "TE", "EE", "EEBB", "EB")
+FP64_PEAK_TFLOPS = 2.0 * 2 * 152 * 2.070e9 / 1e12   # 2 FLOP x 2 DFMA/clk/SM x 152 SMs x max clock
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="budget of the CPU-oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lmax", type=int, default=3000,
+                    help="smaller l_max for profiler captures only (the bench line uses 3000)")
+    args = ap.parse_args()
+    global LMAX
+    LMAX = args.lmax
+    return args
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def windows_for_rank(rank):
+    """W^TT, W^TP, W^PP of rank `rank`: seeds 2, 3, 4 on rank 0; independent
+    seeds on the other ranks (each rank builds its own problem)."""
+    from paper_2602_15605_gb300 import windows
+    seeds = (2, 3, 4) if rank == 0 else tuple(1000 + 3 * rank + q for q in range(3))
+    return tuple(windows.gaussian_taper(LMAX, s) for s in seeds)
+
+
+def work_counts(lmax):
+    """Per step: dense elements per spectrum and 3j terms per spectrum kernel
+    (upper triangle l1 <= l2, parity-selected l3 counts)."""
+    n = lmax - 1
+    even = odd = 0
+    for l1 in range(2, lmax + 1):
+        npairs = lmax - l1 + 1
+        # for l1 <= l2 the l3 range has 2 l1 + 1 values: l1 + 1 of even L, l1 of odd L
+        even += npairs * (l1 + 1)
+        odd += npairs * l1
+    terms = {"TT": even, "TE": even, "EE": even, "EEBB": odd, "EB": even + odd}
+    return n * n, terms
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        mhz, maxes, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxes) if maxes else None,
+                "samples": len(mhz), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(Wt, Wc, Wp, seconds, seed=7):
+    """Oracle throughput in elements/s on a random sample of ordered pairs of
+    the workload (uniform over the 2999 x 2999 square, all five spectra).
+    Returns (elements/s, pairs, threads, wall seconds)."""
+    import numpy as np
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+    cal = rng.integers(2, LMAX + 1, size=(max(64, 8 * threads), 2)).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.coupling_pairs(cal[:, 0], cal[:, 1], Wt, Wc, Wp, 31, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(max(cal.shape[0], min(2_000_000, cal.shape[0] * seconds / dt)))
+    P = rng.integers(2, LMAX + 1, size=(n, 2)).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.coupling_pairs(P[:, 0], P[:, 1], Wt, Wc, Wp, 31, threads=threads)
+    wall = time.perf_counter() - t0
+    return 5.0 * n / wall, n, threads, wall
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, timed on this host."""
+    if rank != 0:
+        return
+    Wt, Wc, Wp = windows_for_rank(0)
+    import numpy as np
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    per_step = min(4.0, 120.0 / max(1, args.steps + args.warmup))
+    rng = np.random.default_rng(11)
+    cal = rng.integers(2, LMAX + 1, size=(max(64, 8 * threads), 2)).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.coupling_pairs(cal[:, 0], cal[:, 1], Wt, Wc, Wp, 31, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(max(cal.shape[0], cal.shape[0] * per_step / dt))
+    for _ in range(args.warmup):
+        P = rng.integers(2, LMAX + 1, size=(n, 2)).astype(np.int32)
+        oracle.coupling_pairs(P[:, 0], P[:, 1], Wt, Wc, Wp, 31, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P = rng.integers(2, LMAX + 1, size=(n, 2)).astype(np.int32)
+        oracle.coupling_pairs(P[:, 0], P[:, 1], Wt, Wc, Wp, 31, threads=threads)
+    wall = time.perf_counter() - t0
+    value = 5.0 * n * args.steps / wall
+    sample = "%d random ordered (l1,l2) pairs per step of the l_max=3000 square, all 5 spectra" % n
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(world):
+    return {"workload": "full spin-0/spin-2 set (TT, TE/TB, EE/BB, EE->BB, EB), plain FP64, "
+                        "l_max=%d, separate W^TT/W^TP/W^PP (l<=%d)" % (LMAX, 2 * LMAX),
+            "lmax": LMAX, "lmin": 2, "n_windows": 1, "spectra": list(SPEC_NAMES), "precision": "fp64",
+            "output": "dense 5 x %d x %d FP64 per rank" % (LMAX - 1, LMAX - 1), "parallelism": "independent problem per GPU"
+            if world > 1 else "1 GPU", "l2": "flushed between steps (256 MiB write, outside the timed events)"}
+
+
+# ---------------------------------------------------------------- profiles
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if absent or taken on a different kernel source."""
+    import hashlib
+    path = os.path.join(PROFILE_DIR, "ncu_%s_full_spin_3000.txt" % kernel)
+    src = os.path.join(ROOT, "paper_2602_15605_gb300", "csrc", "plain_fp64.cu")
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha256_16") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2602_15605_gb300 import build_ext, coupling
+
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_ext.build()
+    if world > 1:
+        dist.barrier()
+    ctx = coupling.Context(local)
+    Wt, Wc, Wp = windows_for_rank(rank)
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:%d" % local)
+    dWt, dWc, dWp = dev(Wt), dev(Wc), dev(Wp)
+    n_el, terms = work_counts(LMAX)
+    out = torch.empty((1, 5, LMAX - 1, LMAX - 1), dtype=torch.float64, device="cuda:%d" % local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % local)
+    step = lambda: ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.stats(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for q in range(args.steps):
+        flush.fill_(q & 255)
+        evs[q][0].record()
+        step()
+        evs[q][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    stats = ctx.stats(reset=True)
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda:%d" % local)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+
+    launches = sum(v["launches"] for v in stats.values())
+    dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    achieved = dom["flop"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
+    traffic = recorded_traffic(dom_name)
+    per_launch_ms = dom["ms"] / max(dom["launches"], 1)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom_name,
+                "kernel_ms_per_launch": per_launch_ms,
+                "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.26 TFLOP/s)"}
+    if clk and clk.get("sm_mhz"):
+        at_clock = 2.0 * 2 * 152 * clk["sm_mhz"] * 1e6 / 1e12
+        roofline["frac_at_sampled_clock"] = achieved / at_clock
+
+    # end to end through the public host-buffer call
+    e2e = None
+    if not args.no_e2e:
+        host_out = np.empty((1, 5, LMAX - 1, LMAX - 1), dtype=np.float64)
+        ctx.build_host(LMAX, Wt, Wc, Wp, coupling.ALL, out=host_out)
+        t0 = time.perf_counter()
+        k_e2e = max(3, min(args.steps, 10))
+        for _ in range(k_e2e):
+            ctx.build_host(LMAX, Wt, Wc, Wp, coupling.ALL, out=host_out)
+        dt = (time.perf_counter() - t0) / k_e2e
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda:%d" % local)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * 5 * n_el / dt, "unit": UNIT, "h2d_bytes_per_step": int(3 * Wt.nbytes),
+               "d2h_bytes_per_step": int(host_out.nbytes), "ms_per_step": dt * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, threads, wall = oracle_rate(Wt, Wc, Wp, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d random ordered (l1,l2) pairs of the l_max=3000 square, all 5 spectra, %.1f s"
+                         % (n, wall)}
+
+    if rank == 0:
+        step_s = step_ms * 1e-3
+        value = world * 5 * n_el / step_s
+        total_terms = sum(terms.values())
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(world),
+                "terms_per_s": world * total_terms / step_s,
+                "terms_per_s_by_spectrum": {k: world * v / step_s for k, v in terms.items()},
+                "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches),
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items()},
+                "clocks": clk, "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -186,6 +186,31 @@ cpl_status cpl_build_batch(cpl_ctx *ctx, const cpl_request *jobs, int n_jobs,
                            double *const *outs, void *stream);
 
 /*
+ * Per-kernel accounting (diagnostics).  Every context counts the kernel
+ * launches it issues, per kernel family.  With profiling enabled
+ * (cpl_ctx_profile(ctx, 1)) it also brackets each launch with CUDA events
+ * on the launching stream and records the algorithmic work of the launch:
+ *   flop   floating-point operations the method needs (an FMA counts 2;
+ *          for the mixed path, 2 per window-term per contraction, not the
+ *          limb products actually issued),
+ *   bytes  DRAM bytes the launch must move at minimum (inputs read once,
+ *          outputs written once).
+ * cpl_ctx_stats waits for the recorded events, writes up to `max` entries
+ * to `out` (host), sets *n to the number of kernel families and, when
+ * `reset` is non-zero, clears the counters.
+ */
+typedef struct {
+    char name[40];        /* kernel family */
+    long long launches;   /* launches since the last reset */
+    double ms;            /* summed event-timed duration of those launches (profiling only) */
+    double flop;          /* algorithmic FLOP of the timed launches */
+    double bytes;         /* algorithmic DRAM bytes of the timed launches */
+} cpl_kernel_stat;
+
+cpl_status cpl_ctx_profile(cpl_ctx *ctx, int enable);
+cpl_status cpl_ctx_stats(cpl_ctx *ctx, cpl_kernel_stat *out, int max, int *n, int reset);
+
+/*
  * Lookup table of Eqs. gdef / g_rec, as the library builds it: out[p] =
  * g(p) = (2p)! / (2^{2p} (p!)^2) for p = 0 .. pmax, each value the
  * double-double recurrence g(p) = (p - 1/2)/p g(p-1), g(0) = 1, rounded once

@@ -40,9 +40,15 @@ class Request(ctypes.Structure):
                 ("bin_edges", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("flop", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 # Every symbol include/coupling.h declares.
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
-           "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_g_table")
+           "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_ctx_profile",
+           "cpl_ctx_stats", "cpl_g_table")
 
 _lock = threading.Lock()
 _lib = None
@@ -74,6 +80,8 @@ def load():
         L.cpl_build_host.argtypes = [vp, ctypes.POINTER(Request), vp]
         L.cpl_build_batch.argtypes = [vp, ctypes.POINTER(Request), ip, ctypes.POINTER(vp), vp]
         L.cpl_g_table.argtypes = [ip, dp]
+        L.cpl_ctx_profile.argtypes = [vp, ip]
+        L.cpl_ctx_stats.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]
         for name in EXPORTS:
             if name not in ("cpl_version", "cpl_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -149,6 +157,21 @@ class Context:
 
     def sync(self):
         _check(load().cpl_ctx_sync(self.handle))
+
+    def profile(self, enable=True):
+        """Turn per-launch event timing on or off (cpl_ctx_profile)."""
+        _check(load().cpl_ctx_profile(self.handle, 1 if enable else 0))
+
+    def stats(self, reset=False):
+        """{kernel family: dict(launches, ms, flop, bytes)} (cpl_ctx_stats)."""
+        buf = (KernelStat * 64)()
+        n = ctypes.c_int()
+        _check(load().cpl_ctx_stats(self.handle, buf, 64, ctypes.byref(n), 1 if reset else 0))
+        out = {}
+        for q in range(min(n.value, 64)):
+            k = buf[q]
+            out[k.name.decode()] = dict(launches=k.launches, ms=k.ms, flop=k.flop, bytes=k.bytes)
+        return out
 
     # ------------------------------------------------------------------ device
     def request(self, lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None,

@@ -85,9 +85,73 @@ struct cpl_ctx {
     DevBuf stage_w, stage_out;   // cpl_build_host staging
     cudaStream_t own_stream = nullptr;
     cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams
+    // per-kernel accounting (cpl_ctx_stats)
+    struct KStat {
+        std::string name;
+        long long launches = 0;
+        double ms = 0.0, flop = 0.0, bytes = 0.0;
+    };
+    struct Pending {
+        int idx;
+        cudaEvent_t a, b;
+        double flop, bytes;
+    };
+    bool profiling = false;
+    std::vector<KStat> kstats;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace {
+
+int stat_index(cpl_ctx *c, const char *name) {
+    for (size_t q = 0; q < c->kstats.size(); ++q)
+        if (c->kstats[q].name == name) return (int)q;
+    c->kstats.push_back(cpl_ctx::KStat());
+    c->kstats.back().name = name;
+    return (int)c->kstats.size() - 1;
+}
+
+cudaEvent_t take_event(cpl_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets one kernel launch: counts it and, when profiling, times it with
+// events on the launching stream.
+struct LaunchScope {
+    cpl_ctx *c;
+    int idx;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    LaunchScope(cpl_ctx *c_, const char *name, cudaStream_t st_) : c(c_), idx(stat_index(c_, name)), st(st_) {
+        if (c->profiling) {
+            a = take_event(c);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    void done(double flop, double bytes) {
+        c->kstats[idx].launches++;
+        if (c->profiling && a) {
+            cudaEvent_t b = take_event(c);
+            if (b) {
+                cudaEventRecord(b, st);
+                c->pending.push_back({idx, a, b, flop, bytes});
+                return;
+            }
+            c->ev_pool.push_back(a);
+        }
+    }
+};
 
 cpl_status select_device(cpl_ctx *c) {
     CPL_CUDA_TRY(cudaSetDevice(c->device));
@@ -280,7 +344,11 @@ cpl_status build_fp64(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const Group &G = groups[gi];
         double *A = c->weights.as<double>() + gi * (size_t)a_stride * nw;
-        CPL_CUDA_TRY(launch_weights(G.W, r->w_len, nw, c->l3cap.as<int>(), A, a_stride, st));
+        {
+            LaunchScope ls(c, "window_weights", st);
+            CPL_CUDA_TRY(launch_weights(G.W, r->w_len, nw, c->l3cap.as<int>(), A, a_stride, st));
+            ls.done(0.0, 16.0 * (double)a_stride * nw);
+        }
         PlainArgs a;
         std::memset(&a, 0, sizeof(a));
         a.g = c->g.as<double>();
@@ -304,7 +372,27 @@ cpl_status build_fp64(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_
         if (G.spectra & (kEE | kEEBB | kEB)) mode = MODE_POL;
         else if (G.spectra & kTE) mode = MODE_TE;
         else mode = MODE_TT;
+        int nge;
+        bool odd;
+        plain_variant(mode, a.slot, &nge, &odd);
+        const char *kname = nge == 1 ? "plain_fp64_tt" : nge == 3 ? "plain_fp64_te"
+                          : (nge == 6 && odd) ? "plain_fp64_pol" : nge == 6 ? "plain_fp64_even" : "plain_fp64_odd";
+        double flop = 0.0, bytes = 0.0;
+        if (c->profiling) {
+            // 2 FLOP per FMA: nge FMAs per even-L term, 3 per odd-L term;
+            // bytes: each written spectrum stores both mirror entries once.
+            int nslots = 0;
+            for (int q = 0; q < 5; ++q) nslots += a.slot[q] >= 0;
+            for (const WorkItem &it : items) {
+                double e, o, np;
+                tile_terms_split(ts->host[it.tile], r->lmax, r->lmin, caps[it.win], &e, &o, &np);
+                flop += 2.0 * (nge * e + (odd ? 3.0 : 0.0) * o);
+                bytes += (nb ? 0.0 : 16.0) * nslots * np;
+            }
+        }
+        LaunchScope ls(c, kname, st);
         CPL_CUDA_TRY(launch_plain(mode, a, st));
+        ls.done(flop, bytes);
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));
     return CPL_OK;
@@ -366,6 +454,11 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     c->bins_inv.release();
     c->stage_w.release();
     c->stage_out.release();
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->done) cudaEventDestroy(c->done);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -447,6 +540,44 @@ cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, doub
     if ((s = select_device(c)) != CPL_OK) return s;
     for (int q = 0; q < n_jobs; ++q)
         if ((s = build_one(c, jobs + q, outs[q], (cudaStream_t)stream)) != CPL_OK) return s;
+    return CPL_OK;
+}
+
+cpl_status cpl_ctx_profile(cpl_ctx *c, int enable) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    c->profiling = enable != 0;
+    return CPL_OK;
+}
+
+cpl_status cpl_ctx_stats(cpl_ctx *c, cpl_kernel_stat *out, int max, int *n, int reset) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (max > 0 && !out) return fail(CPL_ERR_ARG, "out is NULL");
+    cpl_status s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    for (auto &p : c->pending) {
+        cudaError_t e = cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("event timing failed: ") + cudaGetErrorString(e));
+        c->kstats[p.idx].ms += ms;
+        c->kstats[p.idx].flop += p.flop;
+        c->kstats[p.idx].bytes += p.bytes;
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->pending.clear();
+    const int nk = (int)c->kstats.size();
+    for (int q = 0; q < nk && q < max; ++q) {
+        std::memset(&out[q], 0, sizeof(cpl_kernel_stat));
+        std::strncpy(out[q].name, c->kstats[q].name.c_str(), sizeof(out[q].name) - 1);
+        out[q].launches = c->kstats[q].launches;
+        out[q].ms = c->kstats[q].ms;
+        out[q].flop = c->kstats[q].flop;
+        out[q].bytes = c->kstats[q].bytes;
+    }
+    if (n) *n = nk;
+    if (reset)
+        for (auto &k : c->kstats) k.launches = 0, k.ms = k.flop = k.bytes = 0.0;
     return CPL_OK;
 }
 

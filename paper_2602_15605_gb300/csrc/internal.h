@@ -86,6 +86,11 @@ struct PlainArgs {
 };
 
 cudaError_t launch_plain(int mode, const PlainArgs &a, cudaStream_t st);
+// Which template variant launch_plain runs: even-sweep contractions (0, 1,
+// 3 or 6) and whether the odd sweep runs.
+void plain_variant(int mode, const int slot[5], int *nge, bool *odd);
+// l3 terms of a tile per parity of L, with l3 <= cap.
+void tile_terms_split(const Tile &t, int lmax, int lmin, int cap, double *even, double *odd, double *pairs);
 cudaError_t launch_weights(const double *W, int w_len, int n_win, const int *l3cap,
                            double *A, int a_stride, cudaStream_t st);
 

@@ -265,25 +265,34 @@ cudaError_t launch_weights(const double *W, int w_len, int n_win, const int *l3c
     return cudaGetLastError();
 }
 
+void plain_variant(int mode, const int slot[5], int *nge, bool *odd) {
+    *odd = slot[3] >= 0 || slot[4] >= 0;
+    if (mode == MODE_TT) {
+        *nge = 1;
+        *odd = false;
+    } else if (mode == MODE_TE) {
+        *nge = 3;
+        *odd = false;
+    } else {
+        const bool even = slot[0] >= 0 || slot[1] >= 0 || slot[2] >= 0 || slot[4] >= 0;
+        *nge = even ? 6 : 0;
+    }
+}
+
 // mode: which contractions run (see PlainMode); the odd sweep runs when
 // slot[EEBB] or slot[EB] is set.
 cudaError_t launch_plain(int mode, const PlainArgs &a, cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
     dim3 grid(a.n_items);
-    const bool odd = a.slot[3] >= 0 || a.slot[4] >= 0;
-    switch (mode) {
-        case MODE_TT: k_plain<1, false><<<grid, NT, 0, st>>>(a); break;
-        case MODE_TE: k_plain<3, false><<<grid, NT, 0, st>>>(a); break;
-        case MODE_POL:
-        case MODE_ALL: {
-            const bool even = a.slot[0] >= 0 || a.slot[1] >= 0 || a.slot[2] >= 0 || a.slot[4] >= 0;
-            if (even && odd) k_plain<6, true><<<grid, NT, 0, st>>>(a);
-            else if (even) k_plain<6, false><<<grid, NT, 0, st>>>(a);
-            else k_plain<0, true><<<grid, NT, 0, st>>>(a);
-            break;
-        }
-        default: return cudaErrorInvalidValue;
-    }
+    int nge;
+    bool odd;
+    plain_variant(mode, a.slot, &nge, &odd);
+    if (nge == 1) k_plain<1, false><<<grid, NT, 0, st>>>(a);
+    else if (nge == 3) k_plain<3, false><<<grid, NT, 0, st>>>(a);
+    else if (nge == 6 && odd) k_plain<6, true><<<grid, NT, 0, st>>>(a);
+    else if (nge == 6) k_plain<6, false><<<grid, NT, 0, st>>>(a);
+    else if (odd) k_plain<0, true><<<grid, NT, 0, st>>>(a);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -40,6 +40,31 @@ double tile_terms(const Tile &t, int lmax, int lmin, int band) {
     return sum;
 }
 
+void tile_terms_split(const Tile &t, int lmax, int lmin, int cap, double *even, double *odd,
+                      double *pairs) {
+    // even l3 = 2k + pi, k in [i, min(j, (cap - pi)/2)];
+    // odd  l3 = 2k + 1 - pi, k in [i + pi, min(j + pi - 1, (cap - 1 + pi)/2)]
+    const int pi = t.pi;
+    const int kce = (cap - pi) >> 1, kco = (cap - 1 + pi) >> 1;
+    double e = 0.0, o = 0.0, np = 0.0;
+    for (int di = 0; di < TILE_I; ++di) {
+        const int i = t.i0 + di;
+        for (int dj = 0; dj < TILE_J; ++dj) {
+            const int j = t.j0 + dj;
+            const int l1 = j - i, l2 = i + j + pi;
+            if (l1 < lmin || l2 > lmax || l1 > l2) continue;
+            np += 1.0;
+            const int ne = std::min(j, kce) - i + 1;
+            const int no = std::min(j + pi - 1, kco) - (i + pi) + 1;
+            if (ne > 0) e += ne;
+            if (no > 0) o += no;
+        }
+    }
+    *even = e;
+    *odd = o;
+    *pairs = np;
+}
+
 void make_tiles(int lmax, int lmin, std::vector<Tile> &tiles) {
     tiles.clear();
     for (int pi = 0; pi < 2; ++pi) {
