@@ -186,6 +186,31 @@ cpl_status cpl_build_batch(cpl_ctx *ctx, const cpl_request *jobs, int n_jobs,
                            double *const *outs, void *stream);
 
 /*
+ * cpl_build_noalloc -- the plain FP64 build of `r` without any device
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc (an application whose own allocator
+ * owns the device memory budget, a pipeline that must not take the device
+ * synchronisation an allocation can cause, or code where allocation calls
+ * are not allowed).
+ *
+ * It computes the same matrices as cpl_build with CPL_FP64 and dense output
+ * into `out` (device, caller-owned, cpl_output_size doubles) on the CURRENT
+ * CUDA device, asynchronously on `stream`.  W_* are device pointers.  It needs
+ * no context: its scratch (lookup tables, window weights, l3 caps) is one
+ * fixed 1 MiB device array inside the library, which every GPU that loads
+ * the library holds until the process exits.  Limits of that array:
+ * lmax <= 4096 and n_windows <= 4; larger requests fail with CPL_ERR_RANGE,
+ * binned output and CPL_MIXED_BF16 with CPL_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents (each
+ *     call rewrites what it reads).  Calls whose GPU work overlaps -- different
+ *     streams without ordering between them, or different host threads --
+ *     race on it and must be serialised by the caller.
+ */
+cpl_status cpl_build_noalloc(const cpl_request *r, double *out, void *stream);
+
+/*
  * Per-kernel accounting (diagnostics).  Every context counts the kernel
  * launches it issues, per kernel family.  With profiling enabled
  * (cpl_ctx_profile(ctx, 1)) it also brackets each launch with CUDA events

@@ -47,8 +47,8 @@ class KernelStat(ctypes.Structure):
 
 # Every symbol include/coupling.h declares.
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
-           "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_ctx_profile",
-           "cpl_ctx_stats", "cpl_g_table")
+           "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
+           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_g_table")
 
 _lock = threading.Lock()
 _lib = None
@@ -274,6 +274,33 @@ class Context:
         _check(load().cpl_build_host(self.handle, ctypes.byref(r), ctypes.c_void_p(out.ctypes.data)))
         del keep
         return out
+
+
+def build_noalloc(lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None, out=None,
+                  stream=None):
+    """cpl_build_noalloc on the current CUDA device and torch's current stream.
+
+    For callers that cannot allocate device memory: the library's fixed
+    1 MiB scratch array replaces the context's buffers (lmax <= 4096, at most
+    4 windows, plain FP64, dense output).  `out` must be supplied by the
+    caller in that setting; here it is allocated with torch when omitted."""
+    import torch
+    L = load()
+    L.cpl_build_noalloc.argtypes = [ctypes.POINTER(Request), ctypes.c_void_p, ctypes.c_void_p]
+    ws = [W for W in (W_tt, W_tp, W_pp) if W is not None]
+    ref = ws[0]
+    n_windows, w_len = (1, ref.shape[0]) if ref.dim() == 1 else tuple(ref.shape)
+    keep = _Keep()
+    r = _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, None, FP64, 0,
+                      lambda W: None if W is None else W.data_ptr(), n_windows, w_len, keep)
+    n = lmax - lmin + 1
+    shape = (n_windows, nspec(spectra), n, n)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float64, device=ref.device)
+    st = torch.cuda.current_stream(ref.device).cuda_stream if stream is None else stream
+    _check(L.cpl_build_noalloc(ctypes.byref(r), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
+    del keep
+    return out
 
 
 def output_size(lmax, n_windows, spectra, lmin=2, w_len=None, band_limit=None, bin_edges=None):
