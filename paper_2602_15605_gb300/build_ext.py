@@ -68,7 +68,7 @@ def build(force=False, verbose=False, jobs=None):
             list(ex.map(lambda t: _compile(t[0], t[1], verbose), tasks))
     if tasks or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
+        cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "internal.h"
+#include "ctx.h"
 
 #define CPL_VERSION_STRING "paper_2602_15605_gb300 coupling 0.1 (sm_103a)"
 
@@ -37,72 +37,12 @@ int spec_slot(unsigned s, unsigned bit) {
     return c;
 }
 
-// A device buffer that only grows.
-struct DevBuf {
-    void *ptr = nullptr;
-    size_t cap = 0;
-    cpl_status ensure(size_t bytes, const char *what) {
-        if (bytes <= cap) return CPL_OK;
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        cap = 0;
-        size_t want = std::max(bytes, (size_t)256);
-        if (cudaMalloc(&ptr, want) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(CPL_ERR_OOM, std::string("device allocation failed for ") + what);
-        }
-        cap = want;
-        return CPL_OK;
-    }
-    void release() {
-        if (ptr) cudaFree(ptr);
-        ptr = nullptr;
-        cap = 0;
-    }
-    template <class T>
-    T *as() const { return static_cast<T *>(ptr); }
-};
-
-struct TileSet {
-    std::vector<Tile> host;
-    DevBuf dev;
-};
-
 }  // namespace cpl
 
 using namespace cpl;
 
-struct cpl_ctx {
-    int device = 0;
-    int pmax = -1;
-    DevBuf g, h;                 // lookup tables (Sec. 3.1)
-    std::vector<std::unique_ptr<TileSet>> tile_sets;
-    std::vector<std::pair<long long, TileSet *>> tile_index;   // key (lmax, lmin)
-    DevBuf weights;              // A(l3) per role and window
-    DevBuf l3cap;
-    DevBuf items;
-    DevBuf bins_of, bins_inv;
-    DevBuf stage_w, stage_out;   // cpl_build_host staging
-    cudaStream_t own_stream = nullptr;
-    cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams
-    // per-kernel accounting (cpl_ctx_stats)
-    struct KStat {
-        std::string name;
-        long long launches = 0;
-        double ms = 0.0, flop = 0.0, bytes = 0.0;
-    };
-    struct Pending {
-        int idx;
-        cudaEvent_t a, b;
-        double flop, bytes;
-    };
-    bool profiling = false;
-    std::vector<KStat> kstats;
-    std::vector<Pending> pending;
-    std::vector<cudaEvent_t> ev_pool;
-};
 
-namespace {
+namespace cpl {
 
 int stat_index(cpl_ctx *c, const char *name) {
     for (size_t q = 0; q < c->kstats.size(); ++q)
@@ -125,6 +65,30 @@ cudaEvent_t take_event(cpl_ctx *c) {
     }
     return e;
 }
+
+cudaEvent_t begin_launch(cpl_ctx *c, cudaStream_t st) {
+    if (!c->profiling) return nullptr;
+    cudaEvent_t a = take_event(c);
+    if (a) cudaEventRecord(a, st);
+    return a;
+}
+
+void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes) {
+    c->kstats[idx].launches++;
+    if (c->profiling && a) {
+        cudaEvent_t b = take_event(c);
+        if (b) {
+            cudaEventRecord(b, st);
+            c->pending.push_back({idx, a, b, flop, bytes});
+            return;
+        }
+        c->ev_pool.push_back(a);
+    }
+}
+
+}  // namespace cpl
+
+namespace {
 
 // Brackets one kernel launch: counts it and, when profiling, times it with
 // events on the launching stream.
@@ -210,6 +174,10 @@ size_t out_doubles(const cpl_request *r) {
     return (size_t)r->n_windows * ns * n * n;
 }
 
+}  // namespace
+
+namespace cpl {
+
 cpl_status ensure_tables(cpl_ctx *c, int lmax) {
     const int need = 2 * lmax + 2 * (TILE_I + TILE_J) + 16;
     if (need <= c->pmax) return CPL_OK;
@@ -244,6 +212,10 @@ cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out) {
     c->tile_sets.push_back(std::move(ts));
     return CPL_OK;
 }
+
+}  // namespace cpl
+
+namespace {
 
 // Work items (window, tile) of one request, heaviest first.  A tile whose
 // smallest |d| exceeds a window's last l3 contributes nothing for that
@@ -399,8 +371,7 @@ cpl_status build_fp64(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_
 }
 
 cpl_status build_one(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
-    if (r->precision == CPL_MIXED_BF16)
-        return fail(CPL_ERR_UNSUPPORTED, "the mixed-precision path is not available in this build");
+    if (r->precision == CPL_MIXED_BF16) return build_mixed(c, r, out, st);
     return build_fp64(c, r, out, st);
 }
 
@@ -454,6 +425,10 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     c->bins_inv.release();
     c->stage_w.release();
     c->stage_out.release();
+    for (DevBuf *b : {&c->mx.Bimg, &c->mx.eB, &c->mx.emaxB, &c->mx.gdd, &c->mx.Aimg, &c->mx.eA, &c->mx.emaxA,
+                      &c->mx.A64, &c->mx.Add, &c->mx.l3cap, &c->mx.src, &c->mx.inter, &c->mx.items,
+                      &c->mx.tile_of, &c->mx.err})
+        b->release();
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -471,6 +446,16 @@ cpl_status cpl_ctx_sync(cpl_ctx *c) {
     if ((s = select_device(c)) != CPL_OK) return s;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+    if (c->mx.err.ptr) {
+        int code = 0;
+        e = cudaMemcpy(&code, c->mx.err.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+        if (code != 0) {
+            cudaMemset(c->mx.err.ptr, 0, sizeof(int));
+            return fail(CPL_ERR_TIMEOUT, "a bounded device wait of the tensor-core kernel ran out (code " +
+                                             std::to_string(code) + ")");
+        }
+    }
     return CPL_OK;
 }
 

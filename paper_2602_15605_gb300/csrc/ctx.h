@@ -1,0 +1,103 @@
+// ctx.h -- the context object behind cpl_ctx (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <memory>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace cpl {
+
+// A device buffer that only grows.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t cap = 0;
+    cpl_status ensure(size_t bytes, const char *what) {
+        if (bytes <= cap) return CPL_OK;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)256);
+        if (cudaMalloc(&ptr, want) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CPL_ERR_OOM, std::string("device allocation failed for ") + what);
+        }
+        cap = want;
+        return CPL_OK;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(ptr); }
+};
+
+struct TileSet {
+    std::vector<Tile> host;
+    DevBuf dev;
+};
+
+
+// Scratch and caches of the mixed-precision path.
+struct MixedState {
+    int S = 0;                   // limbs the B cache was built with
+    int NC_B = 0;                // column blocks in the B cache
+    DevBuf Bimg, eB, emaxB;      // window-independent operand images (cache)
+    int pmax_dd = -1;
+    DevBuf gdd;                  // g, h as double-float: gh | gl | hh | hl
+    DevBuf Aimg, eA, emaxA;      // per-request operand images
+    DevBuf A64, Add, l3cap, src; // per-source weights (FP64, double-float), caps, (win, role)
+    DevBuf inter, items, tile_of;
+    DevBuf err;                  // device error word of the bounded waits
+};
+
+}  // namespace cpl
+
+using cpl::DevBuf;
+using cpl::TileSet;
+
+struct cpl_ctx {
+    cpl::MixedState mx;
+    int device = 0;
+    int pmax = -1;
+    DevBuf g, h;                 // lookup tables (Sec. 3.1)
+    std::vector<std::unique_ptr<TileSet>> tile_sets;
+    std::vector<std::pair<long long, TileSet *>> tile_index;   // key (lmax, lmin)
+    DevBuf weights;              // A(l3) per role and window
+    DevBuf l3cap;
+    DevBuf items;
+    DevBuf bins_of, bins_inv;
+    DevBuf stage_w, stage_out;   // cpl_build_host staging
+    cudaStream_t own_stream = nullptr;
+    cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams
+    // per-kernel accounting (cpl_ctx_stats)
+    struct KStat {
+        std::string name;
+        long long launches = 0;
+        double ms = 0.0, flop = 0.0, bytes = 0.0;
+    };
+    struct Pending {
+        int idx;
+        cudaEvent_t a, b;
+        double flop, bytes;
+    };
+    bool profiling = false;
+    std::vector<KStat> kstats;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace cpl {
+cpl_status ensure_tables(cpl_ctx *c, int lmax);
+cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out);
+cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st);
+int stat_index(cpl_ctx *c, const char *name);
+void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes);
+cudaEvent_t begin_launch(cpl_ctx *c, cudaStream_t st);
+}  // namespace cpl

@@ -1,0 +1,374 @@
+// mixed_epi.cu -- epilogue of the mixed-precision path, and the FP64 band of
+// small l1 pairs.
+//
+// k_mixed_epilogue: one thread per pair (parity, i, j) with l1 >= MX_L1_FP64
+// loops over the row sources (window x role).  The nine separable
+// contractions of the pair come from the GEMM's double-float outputs with
+// their power-of-two frames; the pair coefficients (lambda/eta, c0, c1, c2,
+// e0, e1, C of plain_fp64.cu) are formed once per pair in extended
+// double-float (FP32 pairs with an integer exponent), and the spectra are
+// combined and written as FP64 built with integer operations, so this kernel
+// uses no FP64 arithmetic.
+//
+// k_mixed_band: pairs with l1 < MX_L1_FP64 in plain FP64.  For them the
+// polynomial expansion of the polarisation factor cancels by up to two
+// orders of magnitude, which the limb contraction's 1e-11-level error would
+// amplify; their l3 sums are short (2 l1 + 1 terms), so FP64 costs little.
+#include <cuda_runtime.h>
+
+#include "dd.cuh"
+#include "mixed.h"
+
+namespace cpl {
+namespace {
+
+__device__ __forceinline__ void put_out(double *out, int lmax, int lmin, int nspec, int w, int slot, int l1, int l2,
+                                        xdf xi, int n_bins, const int *bin_of, const double *bin_inv) {
+    if (slot < 0) return;
+    const double m12 = xdf_to_double(xdf_scale_int(xi, 2LL * l2 + 1));
+    const double m21 = xdf_to_double(xdf_scale_int(xi, 2LL * l1 + 1));
+    if (n_bins == 0) {
+        const int n = lmax - lmin + 1;
+        double *base = out + ((size_t)w * nspec + slot) * (size_t)n * (size_t)n;
+        base[(size_t)(l1 - lmin) * n + (l2 - lmin)] = m12;
+        if (l1 != l2) base[(size_t)(l2 - lmin) * n + (l1 - lmin)] = m21;
+    } else {
+        const int b1 = bin_of[l1], b2 = bin_of[l2];
+        if (b1 < 0 || b2 < 0) return;
+        double *base = out + ((size_t)w * nspec + slot) * (size_t)n_bins * (size_t)n_bins;
+        if (m12 != 0.0) atomicAdd(base + (size_t)b1 * n_bins + b2, m12 * bin_inv[b1]);
+        if (l1 != l2 && m21 != 0.0) atomicAdd(base + (size_t)b2 * n_bins + b1, m21 * bin_inv[b2]);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
+    const MxLayout &L = a.L;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    const int pi = blockIdx.z;
+    const int l1 = j - i, l2 = i + j + pi;
+    if (l1 < max(a.lmin, MX_L1_FP64) || l2 > a.lmax || l1 > l2) return;
+    const int b = i / MX_BI, ii = i % MX_BI, c = j / MX_BJ, cc = j % MX_BJ;
+
+    // pair coefficients (exact integer inputs)
+    const long long L1 = l1, L2 = l2;
+    const xdf eta2 = xdf_from_ll((L1 - 1) * (L1 + 2) * (L2 - 1) * L2);
+    const xdf lam2 = xdf_from_ll(L1 * (L1 + 1) * (L2 + 1) * (L2 + 2));
+    const xdf r2 = xdf_mul(lam2, xdf_recip(eta2));
+    const xdf r = xdf_sqrt(r2);
+    const xdf c1 = xdf_recip(xdf_from_ll(L1 * (L1 + 1) * (L2 + 1)));
+    const xdf c0 = xdf_mul(xdf_from_ll(L1 + 2), xdf_recip(xdf_from_ll(L1)));
+    const xdf inv2l2p2 = xdf_recip(xdf_from_ll(2 * (L2 + 2)));
+    const xdf c2 = xdf_mul(c1, inv2l2p2);
+    const xdf two = xdf_from_ll(2);
+    xdf qTE[3], qEE[6], qB[3];
+    qTE[0] = xdf_mul(r, c0);
+    qTE[1] = xdf_neg(xdf_mul(r, c1));
+    qTE[2] = xdf_neg(xdf_mul(r, c2));
+    qEE[0] = xdf_mul(r2, xdf_mul(c0, c0));
+    qEE[1] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c1))));
+    qEE[2] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c2))));
+    qEE[3] = xdf_mul(r2, xdf_mul(c1, c1));
+    qEE[4] = xdf_mul(r2, xdf_mul(two, xdf_mul(c1, c2)));
+    qEE[5] = xdf_mul(r2, xdf_mul(c2, c2));
+    const xdf e0 = xdf_from_ll(L1 + 2);
+    const xdf e1 = inv2l2p2;
+    const xdf Cc = xdf_mul(xdf_mul(xdf_from_ll(L2 + 2), c1), xdf_recip(eta2));
+    qB[0] = xdf_mul(Cc, xdf_mul(e0, e0));
+    qB[1] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
+    qB[2] = xdf_mul(Cc, xdf_mul(e1, e1));
+
+    const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
+    const long long ncols = (long long)L.NC_B * MX_BJ;
+    for (int s = 0; s < a.nsrc; ++s) {
+        const int role = a.src_role[s];
+        const int w = a.src_win[s];
+        const int rg = s / MX_SRC, slot = s % MX_SRC;
+        const int tile = a.tile_of[(((long long)pi * L.NRG + rg) * L.NB + b) * L.NC + c];
+        xdf S[MX_NPROD];
+        const int r = slot * MX_BI + ii;
+        const long long rowg = ((long long)rg * L.NB + b) * MX_ROWS + r;
+        const bool pol = (role & (kEE | kEEBB | kEB)) != 0;
+        const bool odd = (role & (kEEBB | kEB)) != 0;
+        const int np = pol ? (odd ? 9 : 6) : (role & kTE) ? 3 : 1;
+#pragma unroll
+        for (int p = 0; p < MX_NPROD; ++p) {
+            S[p] = {0.f, 0.f, 0};
+            if (p >= np || tile < 0) continue;
+            const float *src = a.inter + ((long long)tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
+            const float hi = src[r * MX_BJ + cc], lo = src[MX_ROWS * MX_BJ + r * MX_BJ + cc];
+            const int E = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
+                          (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
+            S[p] = xdf_make(df_quick(hi, lo), E);
+        }
+        if (role & kTT) put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[0], l1, l2, S[0], a.n_bins, a.bin_of, a.bin_inv);
+        if (role & kTE) {
+            xdf te = xdf_mul(qTE[0], S[0]);
+            te = xdf_add(te, xdf_mul(qTE[1], S[1]));
+            te = xdf_add(te, xdf_mul(qTE[2], S[2]));
+            put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[1], l1, l2, te, a.n_bins, a.bin_of, a.bin_inv);
+        }
+        if (pol) {
+            xdf ee = {0.f, 0.f, 0};
+#pragma unroll
+            for (int p = 0; p < 6; ++p) ee = xdf_add(ee, xdf_mul(qEE[p], S[p]));
+            if (role & kEE) put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[2], l1, l2, ee, a.n_bins, a.bin_of, a.bin_inv);
+            if (odd) {
+                xdf bb = xdf_mul(qB[0], S[6]);
+                bb = xdf_add(bb, xdf_mul(qB[1], S[7]));
+                bb = xdf_add(bb, xdf_mul(qB[2], S[8]));
+                if (role & kEEBB)
+                    put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[3], l1, l2, bb, a.n_bins, a.bin_of, a.bin_inv);
+                if (role & kEB)
+                    put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[4], l1, l2, xdf_add(ee, xdf_neg(bb)), a.n_bins,
+                            a.bin_of, a.bin_inv);
+            }
+        }
+    }
+}
+
+
+// Dense-output epilogue with coalesced writes.  One block covers an 8 x 64
+// block of (i, j) in both parities -- 1024 pairs whose rows of M (fixed l1,
+// l2 = l1 + d) and mirrored rows (fixed l2, l1 = l2 - d) are runs of 16
+// consecutive elements.  Per block the pair coefficients are formed once in
+// extended double-float and kept in shared memory; per row source the five
+// spectra of the 1024 pairs are combined into shared memory and then written
+// row by row.
+constexpr int EB_I = 8, EB_J = 64, EB_P = 2 * EB_I * EB_J, EB_T = 256;
+constexpr int EB_NC = 12;   // combination coefficients: 3 TE, 6 EE, 3 EE->BB
+
+struct EpiShared {
+    xdf coef[EB_NC][EB_P];
+    xdf xi[5][EB_P];
+};
+
+__device__ __forceinline__ int eb_pair(int pi, int ii, int jj) { return (pi * EB_I + ii) * EB_J + jj; }
+
+__global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a) {
+    extern __shared__ __align__(16) uint8_t esm[];
+    EpiShared &sh = *reinterpret_cast<EpiShared *>(esm);
+    const MxLayout &L = a.L;
+    const int i0 = blockIdx.y * EB_I, j0 = blockIdx.x * EB_J;
+    const int tid = threadIdx.x;
+    const int L1min = max(a.lmin, MX_L1_FP64);
+
+    // ---- coefficients of the block's pairs
+    for (int q = tid; q < EB_P; q += EB_T) {
+        const int pi = q / (EB_I * EB_J), ii = (q / EB_J) % EB_I, jj = q % EB_J;
+        const int i = i0 + ii, j = j0 + jj;
+        const int l1 = j - i, l2 = i + j + pi;
+        if (l1 < L1min || l2 > a.lmax || l1 > l2) continue;
+        const long long L1 = l1, L2 = l2;
+        const xdf eta2i = xdf_recip(xdf_from_ll((L1 - 1) * (L1 + 2) * (L2 - 1) * L2));
+        const xdf r2 = xdf_mul(xdf_from_ll(L1 * (L1 + 1) * (L2 + 1) * (L2 + 2)), eta2i);
+        const xdf r = xdf_sqrt(r2);
+        const xdf c1 = xdf_recip(xdf_from_ll(L1 * (L1 + 1) * (L2 + 1)));
+        const xdf c0 = xdf_mul(xdf_from_ll(L1 + 2), xdf_recip(xdf_from_ll(L1)));
+        const xdf e1 = xdf_recip(xdf_from_ll(2 * (L2 + 2)));
+        const xdf c2 = xdf_mul(c1, e1);
+        const xdf two = xdf_from_ll(2);
+        sh.coef[0][q] = xdf_mul(r, c0);
+        sh.coef[1][q] = xdf_neg(xdf_mul(r, c1));
+        sh.coef[2][q] = xdf_neg(xdf_mul(r, c2));
+        sh.coef[3][q] = xdf_mul(r2, xdf_mul(c0, c0));
+        sh.coef[4][q] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c1))));
+        sh.coef[5][q] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c2))));
+        sh.coef[6][q] = xdf_mul(r2, xdf_mul(c1, c1));
+        sh.coef[7][q] = xdf_mul(r2, xdf_mul(two, xdf_mul(c1, c2)));
+        sh.coef[8][q] = xdf_mul(r2, xdf_mul(c2, c2));
+        const xdf e0 = xdf_from_ll(L1 + 2);
+        const xdf Cc = xdf_mul(xdf_mul(xdf_from_ll(L2 + 2), c1), eta2i);
+        sh.coef[9][q] = xdf_mul(Cc, xdf_mul(e0, e0));
+        sh.coef[10][q] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
+        sh.coef[11][q] = xdf_mul(Cc, xdf_mul(e1, e1));
+    }
+
+    const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
+    const long long ncols = (long long)L.NC_B * MX_BJ;
+    const int n = a.lmax - a.lmin + 1;
+    const int b32 = i0 / MX_BI, c128 = j0 / MX_BJ;
+    for (int s = 0; s < a.nsrc; ++s) {
+        const int role = a.src_role[s];
+        if (role == 0) continue;
+        const int w = a.src_win[s];
+        const int rg = s / MX_SRC, slot = s % MX_SRC;
+        const bool pol = (role & (kEE | kEEBB | kEB)) != 0;
+        const bool odd = (role & (kEEBB | kEB)) != 0;
+        const int np = pol ? (odd ? 9 : 6) : (role & kTE) ? 3 : 1;
+        __syncthreads();   // coefficients ready / previous source written out
+        for (int q = tid; q < EB_P; q += EB_T) {
+            const int pi = q / (EB_I * EB_J), ii = (q / EB_J) % EB_I, jj = q % EB_J;
+            const int i = i0 + ii, j = j0 + jj;
+            const int l1 = j - i, l2 = i + j + pi;
+            if (l1 < L1min || l2 > a.lmax || l1 > l2) continue;
+            const int tile = a.tile_of[(((long long)pi * L.NRG + rg) * L.NB + b32) * L.NC + c128];
+            const int r = slot * MX_BI + (i % MX_BI), cc = j % MX_BJ;
+            const long long rowg = ((long long)rg * L.NB + b32) * MX_ROWS + r;
+            xdf S[MX_NPROD];
+#pragma unroll
+            for (int p = 0; p < MX_NPROD; ++p) {
+                S[p] = {0.f, 0.f, 0};
+                if (p >= np || tile < 0) continue;
+                const float *src = a.inter + ((long long)tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
+                const float hi = src[r * MX_BJ + cc], lo = src[MX_ROWS * MX_BJ + r * MX_BJ + cc];
+                const int E = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
+                              (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
+                S[p] = xdf_make(df_quick(hi, lo), E);
+            }
+            sh.xi[0][q] = S[0];
+            if (role & kTE) {
+                xdf te = xdf_mul(sh.coef[0][q], S[0]);
+                te = xdf_add(te, xdf_mul(sh.coef[1][q], S[1]));
+                te = xdf_add(te, xdf_mul(sh.coef[2][q], S[2]));
+                sh.xi[1][q] = te;
+            }
+            if (pol) {
+                xdf ee = {0.f, 0.f, 0};
+#pragma unroll
+                for (int p = 0; p < 6; ++p) ee = xdf_add(ee, xdf_mul(sh.coef[3 + p][q], S[p]));
+                sh.xi[2][q] = ee;
+                if (odd) {
+                    xdf bb = xdf_mul(sh.coef[9][q], S[6]);
+                    bb = xdf_add(bb, xdf_mul(sh.coef[10][q], S[7]));
+                    bb = xdf_add(bb, xdf_mul(sh.coef[11][q], S[8]));
+                    sh.xi[3][q] = bb;
+                    sh.xi[4][q] = xdf_add(ee, xdf_neg(bb));
+                }
+            }
+        }
+        __syncthreads();
+        // ---- rows: M[l1][l2 = l1 + d] (fixed l1) and mirrored M[l2][l1 = l2 - d]
+        // (fixed l2), d = 2 i0 .. 2 i0 + 15: runs of 16 consecutive elements
+        const int nrow = EB_I + EB_J;
+        const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
+        for (int x = 0; x < 5; ++x) {
+            if (!(role & bits[x]) || a.slot[x] < 0) continue;
+            double *base = a.out + ((size_t)w * a.nspec + a.slot[x]) * (size_t)n * (size_t)n;
+            for (int e = tid; e < 2 * nrow * 2 * EB_I; e += EB_T) {
+                const int mirror = e / (nrow * 2 * EB_I);
+                const int rr = (e / (2 * EB_I)) % nrow, dl = e % (2 * EB_I);
+                const int pi = dl & 1, ii = dl >> 1, i = i0 + ii, d = 2 * i + pi;
+                int l1, l2;
+                if (!mirror) {
+                    l1 = j0 - i0 - (EB_I - 1) + rr;
+                    l2 = l1 + d;
+                } else {
+                    l2 = i0 + j0 + rr;
+                    l1 = l2 - d;
+                }
+                const int j = l1 + i, jj = j - j0;
+                if (jj < 0 || jj >= EB_J) continue;
+                if (l1 < L1min || l2 > a.lmax || l1 > l2) continue;
+                const xdf v = sh.xi[x][eb_pair(pi, ii, jj)];
+                if (!mirror) base[(size_t)(l1 - a.lmin) * n + (l2 - a.lmin)] = xdf_to_double(xdf_scale_int(v, 2LL * l2 + 1));
+                else if (l1 != l2) base[(size_t)(l2 - a.lmin) * n + (l1 - a.lmin)] = xdf_to_double(xdf_scale_int(v, 2LL * l1 + 1));
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void put_out_d(const MxBandArgs &a, int w, int slot, int l1, int l2, double xi) {
+    if (slot < 0) return;
+    const double m12 = (2.0 * l2 + 1.0) * xi, m21 = (2.0 * l1 + 1.0) * xi;
+    if (a.n_bins == 0) {
+        const int n = a.lmax - a.lmin + 1;
+        double *base = a.out + ((size_t)w * a.nspec + slot) * (size_t)n * (size_t)n;
+        base[(size_t)(l1 - a.lmin) * n + (l2 - a.lmin)] = m12;
+        if (l1 != l2) base[(size_t)(l2 - a.lmin) * n + (l1 - a.lmin)] = m21;
+    } else {
+        const int b1 = a.bin_of[l1], b2 = a.bin_of[l2];
+        if (b1 < 0 || b2 < 0) return;
+        double *base = a.out + ((size_t)w * a.nspec + slot) * (size_t)a.n_bins * (size_t)a.n_bins;
+        if (m12 != 0.0) atomicAdd(base + (size_t)b1 * a.n_bins + b2, m12 * a.bin_inv[b1]);
+        if (l1 != l2 && m21 != 0.0) atomicAdd(base + (size_t)b2 * a.n_bins + b1, m21 * a.bin_inv[b2]);
+    }
+}
+
+// One thread per (pair with l1 < MX_L1_FP64, source): the separable sums of
+// plain_fp64.cu over the pair's few l3 terms, in FP64.
+__global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
+    const int l2 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int l1 = a.lmin + blockIdx.y;
+    const int s = blockIdx.z;
+    if (l1 >= MX_L1_FP64 || l2 < l1 || l2 > a.lmax) return;
+    const int d = l2 - l1, sm = l1 + l2, pi = d & 1;
+    const int i = (d - pi) >> 1, j = (sm - pi) >> 1;
+    const double *A = a.A + (size_t)s * a.a_stride;
+    const int cap = a.l3cap[s];
+    const int role = a.src_role[s], w = a.src_win[s];
+    double S[MX_NPROD];
+#pragma unroll
+    for (int p = 0; p < MX_NPROD; ++p) S[p] = 0.0;
+    // even sweep: l3 = 2k + pi, i <= k <= j
+    for (int k = i; k <= j; ++k) {
+        const int l3 = 2 * k + pi;
+        if (l3 > cap) break;
+        const double a0 = A[l3] * a.g[i + k + pi] * a.g[k - i];
+        const double v = (double)(2 * k + 2 * i + 2 * pi + 1) * (double)(2 * k - 2 * i);
+        const double b0 = a.g[j - k] * a.h[j + k + pi];
+        const double u = (double)(2 * j + 2 * k + 2 * pi + 2) * (double)(2 * j - 2 * k + 1);
+        S[0] += a0 * b0;
+        S[1] += a0 * b0 * u;
+        S[2] += a0 * v * b0 * u;
+        S[3] += a0 * b0 * u * u;
+        S[4] += a0 * v * b0 * u * u;
+        S[5] += a0 * v * v * b0 * u * u;
+    }
+    // odd sweep: l3 = 2k + 1 - pi, i + pi <= k <= j + pi - 1
+    for (int k = i + pi; k <= j + pi - 1; ++k) {
+        const int l3 = 2 * k + 1 - pi;
+        if (l3 > cap) break;
+        const double a1v = A[l3] * a.g[i + k + 1] * a.g[k - i - pi] *
+                           ((double)(2 * i + 2 * k + 2) * (double)(2 * k + 1 - 2 * i - 2 * pi));
+        const double b1u = a.g[j - k + pi] * a.h[j + k + 1] *
+                           ((double)(2 * j + 2 * k + 3) * (double)(2 * j - 2 * k + 2 * pi));
+        const double up = (double)(2 * j + 2 * k + 4) * (double)(2 * j - 2 * k + 2 * pi + 1);
+        S[6] += a1v * b1u;
+        S[7] += a1v * b1u * up;
+        S[8] += a1v * b1u * up * up;
+    }
+    if (role & kTT) put_out_d(a, w, a.slot[0], l1, l2, S[0]);
+    if (role & (kTE | kEE | kEEBB | kEB)) {
+        const double L1 = l1, L2 = l2;
+        const double eta2 = (L1 - 1.0) * (L1 + 2.0) * (L2 - 1.0) * L2;
+        const double c1 = 1.0 / (L1 * (L1 + 1.0) * (L2 + 1.0));
+        const double r2 = L1 * (L1 + 1.0) * (L2 + 1.0) * (L2 + 2.0) / eta2;
+        const double c0 = 1.0 + 2.0 / L1, c2 = c1 / (2.0 * (L2 + 2.0));
+        if (role & kTE) put_out_d(a, w, a.slot[1], l1, l2, sqrt(r2) * (c0 * S[0] - c1 * S[1] - c2 * S[2]));
+        const double ee = r2 * (c0 * c0 * S[0] - 2.0 * c0 * c1 * S[1] - 2.0 * c0 * c2 * S[2] + c1 * c1 * S[3] +
+                                2.0 * c1 * c2 * S[4] + c2 * c2 * S[5]);
+        if (role & kEE) put_out_d(a, w, a.slot[2], l1, l2, ee);
+        const double e0 = L1 + 2.0, e1 = 1.0 / (2.0 * (L2 + 2.0));
+        const double bb = (L2 + 2.0) * c1 / eta2 * (e0 * e0 * S[6] - 2.0 * e0 * e1 * S[7] + e1 * e1 * S[8]);
+        if (role & kEEBB) put_out_d(a, w, a.slot[3], l1, l2, bb);
+        if (role & kEB) put_out_d(a, w, a.slot[4], l1, l2, ee - bb);
+    }
+}
+
+}  // namespace
+
+cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st) {
+    const int NI = a.L.NB * MX_BI;
+    if (a.n_bins > 0) {
+        dim3 grid((a.lmax + 1 + 127) / 128, NI, 2);
+        k_mixed_epilogue<<<grid, 128, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    const size_t smem = sizeof(EpiShared);
+    cudaError_t e = cudaFuncSetAttribute(k_mixed_epilogue_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.lmax + 1 + EB_J - 1) / EB_J, NI / EB_I);
+    k_mixed_epilogue_dense<<<grid, EB_T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t mx_launch_band(const MxBandArgs &a, cudaStream_t st) {
+    const int rows = MX_L1_FP64 - a.lmin;
+    if (rows <= 0 || a.nsrc == 0) return cudaSuccess;
+    dim3 grid((a.lmax + 1 + 127) / 128, rows, a.nsrc);
+    k_mixed_band<<<grid, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace cpl

@@ -1,0 +1,371 @@
+// mixed_gemm.cu -- the tcgen05 limb GEMM of the mixed-precision path.
+//
+// One CTA per work item (parity, contraction p, row group, i-block, j-block):
+//   C[r, c] = sum_k x[r, k] y[c, k]   (128 x 128 output, k over the item's range)
+// with x, y given as S BF16 fixed-point limbs per element (mixed.h).
+//
+// Warp roles (10 warps):
+//   warp 0      producer: one elected lane streams the KB-k tile images of
+//               all limbs of x and y into a shared-memory ring (2 stages of
+//               32 k for S <= 5 limbs, 3 stages of 16 k for S = 6) with
+//               cp.async.bulk, signalling an mbarrier with the byte count.
+//   warp 1      allocates 512 TMEM columns; one elected lane issues, for each
+//               16-k step, the limb products x_t y_u with t + u < S as
+//               tcgen05.mma (M=128, N=128, K=16, BF16 in, FP32 accumulate)
+//               into four TMEM accumulators by order t + u = 0, 1, 2, >= 3,
+//               and commits each stage back to the producer.
+//   warps 2-9   drain: after every 128-k scale block, read the four
+//               accumulators with tcgen05.ld, combine them, scale by
+//               2^(E_row + E_col) relative to the row / column maxima, and add
+//               into a double-float running sum per element (high part in
+//               registers, low part in shared memory).
+// The accumulators of orders 0, 1 and 2 are integers below 2^24 in their
+// units over a 128-k block (|limb| <= 128, at most 3 products per k), so the
+// tensor core holds them exactly whatever its internal rounding; only the
+// order >= 3 accumulator, 2^-24 of the total, is inexact.  (Measured: with
+// orders >= 2 in one inexact accumulator the error reached 5e-9, consistent
+// with truncating accumulation.)
+// Every wait on an mbarrier is bounded (2 s of globaltimer); on expiry the
+// CTA records an error code, stops issuing, waits (bounded) for the work it
+// already issued, frees its TMEM and exits.
+#include <cuda_runtime.h>
+
+#include "dd.cuh"
+#include "mixed.h"
+
+namespace cpl {
+namespace {
+
+constexpr int NTH = 320;
+constexpr int LPAD = MX_ROWS + 1;          // padded stride of the [col][row] planes
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = gtime();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (gtime() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// K-major, no-swizzle shared-memory matrix descriptor: core matrices of
+// 8 rows x 16 bytes; LBO = offset between K-adjacent cores (128 B), SBO =
+// offset between 8-row groups (KB * 16 B); bits 46-47 = descriptor version 1.
+template <int KB>
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)((KB * 16) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+            tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+#define TMEM_LD16(addr, r)                                                                                      \
+    asm volatile(                                                                                               \
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),     \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),             \
+          "=r"(r[15])                                                                                           \
+        : "r"(addr))
+
+struct Shared {
+    uint64_t full[3], empty[3], acc_full, acc_empty, done;
+    uint32_t tmem;
+    int abort;          // set by any role on a timed-out wait
+    int dabort;         // drain-local copy, written only before the drain barrier
+    int16_t ecol[MX_BJ];
+};
+
+template <int S>
+__global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
+    extern __shared__ __align__(128) uint8_t dsm[];
+    __shared__ Shared sh;
+    constexpr int KB = mx_kb(S);                 // k per stage
+    constexpr int IMG = mx_img_bytes(S);
+    constexpr int NST = mx_stages(S);
+    constexpr int KPS = MX_SB / KB;              // k blocks per scale block
+    constexpr uint32_t STAGE = 2u * S * IMG;
+    float *Ls = reinterpret_cast<float *>(dsm + NST * STAGE);   // [128 cols][LPAD]
+    float *Hs = reinterpret_cast<float *>(dsm);                 // reuses the stages at the end
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const MxItem it = a.items[blockIdx.x];
+    const MxLayout &L = a.L;
+    const int pi = it.pi, p = it.p;
+    const int alpha = mx_alpha(p), beta = mx_beta(p);
+    const int kb_lo = it.kb_lo, kb_hi = it.kb_hi;
+    const uint32_t s_full0 = smem_u32(&sh.full[0]), s_empty0 = smem_u32(&sh.empty[0]);
+    const uint32_t s_accf = smem_u32(&sh.acc_full), s_acce = smem_u32(&sh.acc_empty), s_done = smem_u32(&sh.done);
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < NST; ++q) {
+            mbar_init(s_full0 + 8 * q, 1);
+            mbar_init(s_empty0 + 8 * q, 1);
+        }
+        mbar_init(s_accf, 1);
+        mbar_init(s_acce, 8);
+        mbar_init(s_done, 1);
+        sh.abort = 0;
+        sh.dabort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("fence.proxy.async.shared::cta;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = sh.tmem;
+    const uint32_t stage_base = smem_u32(dsm);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            const uint8_t *Ab = a.Aimg + mx_a_off(L, pi, alpha, it.rg, it.b, L.fA * it.b, 0);
+            int n = 0;
+            for (int kb = kb_lo; kb <= kb_hi; ++kb, ++n) {
+                if (*(volatile int *)&sh.abort) break;
+                const int s = n % NST, u = n / NST;
+                if (u > 0 && !mbar_wait(s_empty0 + 8 * s, (u - 1) & 1)) {
+                    atomicExch(a.err, 11);
+                    sh.abort = 1;
+                    break;
+                }
+                const uint32_t fb = s_full0 + 8 * s;
+                mbar_expect_tx(fb, STAGE);
+                const uint8_t *asrc = Ab + (long long)(kb - L.fA * it.b) * S * IMG;
+                const uint8_t *bsrc = a.Bimg + mx_b_off(L, pi, beta, it.c, kb, 0);
+                const uint32_t dst = stage_base + s * STAGE;
+                bulk_g2s(dst, asrc, S * IMG, fb);
+                bulk_g2s(dst + S * IMG, bsrc, S * IMG, fb);
+            }
+            // wait (bounded) for the copies still in flight before the CTA may exit
+            const int issued = n;
+            for (int q = issued - NST; q < issued; ++q) {
+                if (q < 0) continue;
+                if (!mbar_wait(s_full0 + 8 * (q % NST), (q / NST) & 1)) atomicExch(a.err, 12);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MX_BJ >> 3) << 17) |
+                                   ((uint32_t)(MX_ROWS >> 4) << 24);
+            int n = 0, m = 0;
+            bool started[4] = {false, false, false, false};
+            for (int kb = kb_lo; kb <= kb_hi; ++kb, ++n) {
+                if (*(volatile int *)&sh.abort) break;
+                const bool sfirst = (kb == kb_lo) || (kb % KPS == 0);
+                const bool slast = (kb == kb_hi) || (kb % KPS == KPS - 1);
+                if (sfirst) {
+                    if (m > 0 && !mbar_wait(s_acce, (m - 1) & 1)) {
+                        atomicExch(a.err, 13);
+                        sh.abort = 1;
+                        break;
+                    }
+                    started[0] = started[1] = started[2] = started[3] = false;
+                }
+                const int s = n % NST;
+                if (!mbar_wait(s_full0 + 8 * s, (n / NST) & 1)) {
+                    atomicExch(a.err, 14);
+                    sh.abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t abase = stage_base + s * STAGE;
+                const uint32_t bbase = abase + S * IMG;
+#pragma unroll
+                for (int k16 = 0; k16 < KB / 16; ++k16) {
+#pragma unroll
+                    for (int t = 0; t < S; ++t) {
+#pragma unroll
+                        for (int u = 0; u + t < S; ++u) {
+                            const int acc = (t + u) < 3 ? (t + u) : 3;
+                            const uint64_t ad = umma_desc<KB>(abase + t * IMG + k16 * 256);
+                            const uint64_t bd = umma_desc<KB>(bbase + u * IMG + k16 * 256);
+                            umma(tmem + acc * MX_BJ, ad, bd, idesc, started[acc] ? 1u : 0u);
+                            started[acc] = true;
+                        }
+                    }
+                }
+                umma_commit(s_empty0 + 8 * s);
+                if (slast) {
+                    umma_commit(s_accf);
+                    ++m;
+                }
+            }
+            // all issued MMAs complete before TMEM is released
+            umma_commit(s_done);
+            if (!mbar_wait(s_done, 0)) atomicExch(a.err, 15);
+        }
+    } else {
+        // ------------------------------------------------------------ drain
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int row = 32 * q + lane, c0 = 64 * half;
+        const int dtid = tid - 64;               // 0..255
+        const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
+        const long long ncols = (long long)L.NC_B * MX_BJ;
+        const long long rowg = ((long long)it.rg * L.NB + it.b) * MX_ROWS + row;
+        const int16_t *eArow = a.eA + (((long long)pi * MX_NA + alpha) * nrows + rowg) * L.NSB;
+        const int emA = a.emaxA[((long long)pi * MX_NA + alpha) * nrows + rowg];
+        const int j0 = it.c * MX_BJ;
+        const int16_t *eBcol = a.eB + ((long long)pi * MX_NBV + beta) * ncols * L.NSB_B;
+        const int16_t *emB = a.emaxB + ((long long)pi * MX_NBV + beta) * ncols;
+        float H[64];
+#pragma unroll
+        for (int x = 0; x < 64; ++x) H[x] = 0.f;
+        for (int x = 0; x < 64; ++x) Ls[(c0 + x) * LPAD + row] = 0.f;
+        int m = 0;
+        for (int kb = kb_lo; kb <= kb_hi; ++kb) {
+            const bool slast = (kb == kb_hi) || (kb % KPS == KPS - 1);
+            if (!slast) continue;
+            const int sb = kb / KPS;
+            if (dtid < MX_BJ) {
+                const int j = j0 + dtid;
+                sh.ecol[dtid] = (int16_t)max(-32000, (int)eBcol[(long long)j * L.NSB_B + sb] - (int)emB[j]);
+            }
+            const int eAr = (int)eArow[sb] - emA;
+            const bool ok = !*(volatile int *)&sh.abort && mbar_wait(s_accf, m & 1);
+            if (!ok) sh.dabort = 1;
+            // (A): column exponents visible; the abort decision is the same for all drain threads
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (*(volatile int *)&sh.dabort) {
+                if (dtid == 0) {
+                    atomicExch(a.err, 16);
+                    sh.abort = 1;
+                }
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+#pragma unroll
+            for (int g4 = 0; g4 < 4; ++g4) {
+                uint32_t r0[16], r1[16], r2[16], r3[16];
+                const uint32_t col = (uint32_t)(c0 + 16 * g4);
+                TMEM_LD16(lane_addr + col, r0);
+                TMEM_LD16(lane_addr + MX_BJ + col, r1);
+                TMEM_LD16(lane_addr + 2 * MX_BJ + col, r2);
+                TMEM_LD16(lane_addr + 3 * MX_BJ + col, r3);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int x = 0; x < 16; ++x) {
+                    const int cc = c0 + 16 * g4 + x;
+                    const int d = eAr + (int)sh.ecol[cc];
+                    if (d < -252) continue;
+                    dfl v = df_two_sum(__uint_as_float(r0[x]), __uint_as_float(r1[x]));
+                    v.l += __uint_as_float(r2[x]);
+                    v.l += __uint_as_float(r3[x]);
+                    const float vh = scale2(v.h, d), vl = scale2(v.l, d);
+                    const dfl z = df_two_sum(H[16 * g4 + x], vh);
+                    float lo = Ls[cc * LPAD + row] + z.l + vl;
+                    const dfl w = df_quick(z.h, lo);
+                    H[16 * g4 + x] = w.h;
+                    Ls[cc * LPAD + row] = w.l;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(s_acce);
+            // (B): every drain thread is done with the column exponents
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            ++m;
+        }
+        // ---- write the element sums: hi plane and lo plane, [row][col] in global
+        if (!*(volatile int *)&sh.dabort) {
+            // the producer / MMA are done with the stage buffers once the last
+            // block was drained; reuse them for the transposed hi plane
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+#pragma unroll
+            for (int x = 0; x < 64; ++x) Hs[(c0 + x) * LPAD + row] = H[x];
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            float *dst = a.inter + ((long long)it.tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
+            for (int idx = dtid; idx < MX_ROWS * MX_BJ; idx += 256) {
+                const int r = idx / MX_BJ, cc = idx % MX_BJ;
+                dst[idx] = Hs[cc * LPAD + r];
+                dst[MX_ROWS * MX_BJ + idx] = Ls[cc * LPAD + r];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
+}  // namespace
+
+size_t mx_gemm_smem_bytes(int S) {
+    return (size_t)mx_stages(S) * 2 * S * mx_img_bytes(S) + (size_t)MX_BJ * LPAD * sizeof(float);
+}
+
+cudaError_t mx_launch_gemm(const MxGemmArgs &a, cudaStream_t st) {
+    if (a.n_items == 0) return cudaSuccess;
+    const size_t smem = mx_gemm_smem_bytes(a.L.S);
+    cudaError_t e;
+    switch (a.L.S) {
+        case 4:
+            e = cudaFuncSetAttribute(k_mixed_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_mixed_gemm<4><<<a.n_items, NTH, smem, st>>>(a);
+            break;
+        case 5:
+            e = cudaFuncSetAttribute(k_mixed_gemm<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_mixed_gemm<5><<<a.n_items, NTH, smem, st>>>(a);
+            break;
+        case 6:
+            e = cudaFuncSetAttribute(k_mixed_gemm<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_mixed_gemm<6><<<a.n_items, NTH, smem, st>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cpl

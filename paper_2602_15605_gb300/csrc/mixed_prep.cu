@@ -1,0 +1,299 @@
+// mixed_prep.cu -- operand preparation of the mixed-precision path.
+//
+// Writes the BF16 limb images of the separable operands (see plain_fp64.cu
+// for their definitions; the formulas are repeated next to each variant) in
+// the exact shared-memory layout the tensor-core GEMM consumes (mixed.h:
+// mx_img_off), together with the per-(row, 128-k scale block) power-of-two
+// exponents.  Values are formed in double-float from double-float copies of
+// the FP64 g / h tables and weights; the weights carry a separate integer
+// exponent because window spectra reach below the FP32 range.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "dd.cuh"
+#include "mixed.h"
+
+namespace cpl {
+namespace {
+
+constexpr int16_t EXP_ZERO = -32000;   // exponent of an all-zero block
+
+__global__ void k_tables_dd(const double *__restrict__ g, const double *__restrict__ h, int n,
+                            float *gh, float *gl, float *hh, float *hl) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const double a = g[p], b = h[p];
+        const float ah = (float)a, bh = (float)b;
+        gh[p] = ah;
+        gl[p] = (float)(a - (double)ah);
+        hh[p] = bh;
+        hl[p] = (float)(b - (double)bh);
+    }
+}
+
+// A(l) = m 2^e with m in [1, 2) held as double-float; A = 0 -> m = 0.
+__global__ void k_weights_dd(const double *__restrict__ A, int total, float *Ah, float *Al, int *Ae) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const double a = A[q];
+        if (a == 0.0) {
+            Ah[q] = 0.f;
+            Al[q] = 0.f;
+            Ae[q] = 0;
+            continue;
+        }
+        int e;
+        const double m = frexp(a, &e);          // a = m 2^e, |m| in [0.5, 1)
+        const float mh = (float)m;
+        Ah[q] = mh;
+        Al[q] = (float)(m - (double)mh);
+        Ae[q] = e;
+    }
+}
+
+// exponent E with |x| < 2^E for x = m 2^e (m != 0)
+__device__ __forceinline__ int value_exp(dfl m, int e) { return e + ilogbf_fast(fabsf(m.h)) + 1; }
+
+template <int S>
+__device__ __forceinline__ void put_limbs(uint8_t *img_t0, int off, dfl y, int img_bytes) {
+    // y in (-128.x, 128.x); limb t is stored pre-scaled by 2^(-8t)
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        const float l = rintf(y.h);
+        const dfl z = df_two_sum(y.h - l, y.l);
+        y.h = z.h * 256.0f;
+        y.l = z.l * 256.0f;
+        const __nv_bfloat16 v = __float2bfloat16_rn(l * pow2f(-8 * t));
+        *reinterpret_cast<__nv_bfloat16 *>(img_t0 + (size_t)t * img_bytes + off) = v;
+    }
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// One warp per (parity, source, i): all scale blocks of the row.
+template <int S>
+__global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const MxLayout &L = a.L;
+    const int NI = L.NB * MX_BI;
+    const int nsrc_pad = L.NRG * MX_SRC;
+    if (warp >= 2 * nsrc_pad * NI) return;
+    const int i = warp % NI;
+    const int s = (warp / NI) % nsrc_pad;
+    const int pi = warp / (NI * nsrc_pad);
+    const int b = i / MX_BI, ii = i % MX_BI;
+    const int rg = s / MX_SRC, slot = s % MX_SRC;
+    const int r = slot * MX_BI + ii;                      // row in the 128-row tile
+    const long long row_global = ((long long)rg * L.NB + b) * MX_ROWS + r;
+    const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
+    const bool live = s < a.nsrc;
+    const int cap = live ? a.l3cap[s] : -1;
+    const float *Ah = a.Ah + (size_t)(live ? s : 0) * a.a_stride;
+    const float *Al = a.Al + (size_t)(live ? s : 0) * a.a_stride;
+    const int *Ae = a.Ae + (size_t)(live ? s : 0) * a.a_stride;
+
+    int emax[MX_NA];
+#pragma unroll
+    for (int q = 0; q < MX_NA; ++q) emax[q] = EXP_ZERO;
+    const int sb0 = (b * MX_BI) / MX_SB;
+    for (int sb = sb0; sb < L.NSB; ++sb) {
+        dfl val[MX_NA][4];
+        int vex[MX_NA][4];
+        int bexp[MX_NA];
+#pragma unroll
+        for (int q = 0; q < MX_NA; ++q) bexp[q] = EXP_ZERO;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int k = sb * MX_SB + lane + 32 * m;
+#pragma unroll
+            for (int q = 0; q < MX_NA; ++q) {
+                val[q][m] = {0.f, 0.f};
+                vex[q][m] = EXP_ZERO;
+            }
+            // even sweep: l3 = 2k + pi, a0 = A(l3) g(i+k+pi) g(k-i), v = (2k+2i+2pi+1)(2k-2i)
+            const int l3e = 2 * k + pi;
+            if ((a.alpha_mask & 7) && k >= i && l3e <= cap && Ah[l3e] != 0.f) {
+                const dfl A = {Ah[l3e], Al[l3e]};
+                const dfl g1 = {a.gh[i + k + pi], a.gl[i + k + pi]};
+                const dfl g2 = {a.gh[k - i], a.gl[k - i]};
+                const dfl a0 = df_mul(df_mul(A, g1), g2);
+                const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (long long)(2 * k - 2 * i));
+                const int e = Ae[l3e];
+                val[0][m] = a0;
+                vex[0][m] = value_exp(a0, e);
+                if (v.h != 0.f) {
+                    const dfl a0v = df_mul(a0, v);
+                    const dfl a0v2 = df_mul(a0v, v);
+                    val[1][m] = a0v;
+                    vex[1][m] = value_exp(a0v, e);
+                    val[2][m] = a0v2;
+                    vex[2][m] = value_exp(a0v2, e);
+                }
+                // the exponent of the weight is applied through vex / the block exponent
+#pragma unroll
+                for (int q = 0; q < 3; ++q) vex[q][m] = (val[q][m].h != 0.f) ? vex[q][m] : EXP_ZERO;
+            }
+            // odd sweep: l3 = 2k + 1 - pi, a1 v = A(l3) g(i+k+1) g(k-i-pi) (2i+2k+2)(2k+1-2i-2pi)
+            const int l3o = 2 * k + 1 - pi;
+            if ((a.alpha_mask & 8) && k >= i + pi && l3o <= cap && Ah[l3o] != 0.f) {
+                const dfl A = {Ah[l3o], Al[l3o]};
+                const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
+                const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
+                const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (long long)(2 * k + 1 - 2 * i - 2 * pi));
+                const dfl x = df_mul(df_mul(df_mul(A, g1), g2), v1);
+                if (x.h != 0.f) {
+                    val[3][m] = x;
+                    vex[3][m] = value_exp(x, Ae[l3o]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MX_NA; ++q) bexp[q] = max(bexp[q], vex[q][m]);
+        }
+#pragma unroll
+        for (int q = 0; q < MX_NA; ++q) {
+            if (!((a.alpha_mask >> q) & 1)) continue;
+            const int E = warp_max(bexp[q]);
+            if (lane == 0) a.eA[(((long long)pi * MX_NA + q) * nrows + row_global) * L.NSB + sb] = (int16_t)E;
+            emax[q] = max(emax[q], E);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k = sb * MX_SB + lane + 32 * m;
+                const int kb = k / L.KB;
+                if (kb < L.fA * b || kb >= L.NKB) continue;
+                dfl y = {0.f, 0.f};
+                if (val[q][m].h != 0.f && E != EXP_ZERO) {
+                    // y = x 2^(7 - E) with x = val 2^(weight exponent): shift = vex - ilogb - 1 + 7 - E
+                    const int sh = vex[q][m] - (ilogbf_fast(fabsf(val[q][m].h)) + 1) + 7 - E;
+                    y.h = scale2(val[q][m].h, sh);
+                    y.l = scale2(val[q][m].l, sh);
+                }
+                uint8_t *img = a.Aimg + mx_a_off(L, pi, q, rg, b, kb, 0);
+                put_limbs<S>(img, mx_img_off(r, k % L.KB, L.KB), y, L.IMG);
+            }
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < MX_NA; ++q)
+            if ((a.alpha_mask >> q) & 1) a.emaxA[((long long)pi * MX_NA + q) * nrows + row_global] = (int16_t)emax[q];
+    }
+}
+
+// One warp per (parity, j) for the column blocks [c_lo, c_hi): all six variants.
+template <int S>
+__global__ void __launch_bounds__(256) k_prep_b(const MxPrepBArgs a, int c_hi) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const MxLayout &L = a.L;
+    const int nj = (c_hi - a.c_lo) * MX_BJ;
+    if (warp >= 2 * nj) return;
+    const int j = a.c_lo * MX_BJ + warp % nj;
+    const int pi = warp / nj;
+    const int c = j / MX_BJ, jj = j % MX_BJ;
+    const long long ncols = (long long)L.NC_B * MX_BJ;
+    int emax[MX_NBV];
+#pragma unroll
+    for (int q = 0; q < MX_NBV; ++q) emax[q] = EXP_ZERO;
+    const int nkb_c = L.gB * (c + 1);   // k blocks stored for this column block
+    for (int sb = 0; sb <= c; ++sb) {
+        dfl val[MX_NBV][4];
+        int bexp[MX_NBV];
+#pragma unroll
+        for (int q = 0; q < MX_NBV; ++q) bexp[q] = EXP_ZERO;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int k = sb * MX_SB + lane + 32 * m;
+#pragma unroll
+            for (int q = 0; q < MX_NBV; ++q) val[q][m] = {0.f, 0.f};
+            // even: b0 = g(j-k) h(j+k+pi), u = (2j+2k+2pi+2)(2j-2k+1)
+            if (k <= j) {
+                const dfl b0 = df_mul(dfl{a.gh[j - k], a.gl[j - k]}, dfl{a.hh[j + k + pi], a.hl[j + k + pi]});
+                const dfl u = df_from_ll((long long)(2 * j + 2 * k + 2 * pi + 2) * (long long)(2 * j - 2 * k + 1));
+                val[0][m] = b0;
+                val[1][m] = df_mul(b0, u);
+                val[2][m] = df_mul(val[1][m], u);
+            }
+            // odd: b1 = g(j-k+pi) h(j+k+1), u1 = (2j+2k+3)(2j-2k+2pi), u' = (2j+2k+4)(2j-2k+2pi+1)
+            if (k <= j + pi - 1) {
+                const dfl b1 = df_mul(dfl{a.gh[j - k + pi], a.gl[j - k + pi]}, dfl{a.hh[j + k + 1], a.hl[j + k + 1]});
+                const dfl u1 = df_from_ll((long long)(2 * j + 2 * k + 3) * (long long)(2 * j - 2 * k + 2 * pi));
+                const dfl up = df_from_ll((long long)(2 * j + 2 * k + 4) * (long long)(2 * j - 2 * k + 2 * pi + 1));
+                val[3][m] = df_mul(b1, u1);
+                val[4][m] = df_mul(val[3][m], up);
+                val[5][m] = df_mul(val[4][m], up);
+            }
+#pragma unroll
+            for (int q = 0; q < MX_NBV; ++q)
+                if (val[q][m].h != 0.f) bexp[q] = max(bexp[q], value_exp(val[q][m], 0));
+        }
+#pragma unroll
+        for (int q = 0; q < MX_NBV; ++q) {
+            const int E = warp_max(bexp[q]);
+            if (lane == 0) a.eB[(((long long)pi * MX_NBV + q) * ncols + j) * L.NSB_B + sb] = (int16_t)E;
+            emax[q] = max(emax[q], E);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int k = sb * MX_SB + lane + 32 * m;
+                const int kb = k / L.KB;
+                if (kb >= nkb_c) continue;
+                dfl y = {0.f, 0.f};
+                if (val[q][m].h != 0.f && E != EXP_ZERO) {
+                    const int sh = 7 - E;
+                    y.h = scale2(val[q][m].h, sh);
+                    y.l = scale2(val[q][m].l, sh);
+                }
+                uint8_t *img = a.Bimg + mx_b_off(L, pi, q, c, kb, 0);
+                put_limbs<S>(img, mx_img_off(jj, k % L.KB, L.KB), y, L.IMG);
+            }
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < MX_NBV; ++q) a.emaxB[((long long)pi * MX_NBV + q) * ncols + j] = (int16_t)emax[q];
+    }
+}
+
+}  // namespace
+
+cudaError_t mx_launch_tables_dd(const double *g, const double *h, int n, float *gh, float *gl, float *hh,
+                                float *hl, cudaStream_t st) {
+    k_tables_dd<<<(n + 255) / 256, 256, 0, st>>>(g, h, n, gh, gl, hh, hl);
+    return cudaGetLastError();
+}
+
+cudaError_t mx_launch_weights_dd(const double *A, int n_src, int a_stride, float *Ah, float *Al, int *Ae,
+                                 cudaStream_t st) {
+    const int total = n_src * a_stride;
+    k_weights_dd<<<(total + 255) / 256, 256, 0, st>>>(A, total, Ah, Al, Ae);
+    return cudaGetLastError();
+}
+
+cudaError_t mx_launch_prep_a(const MxPrepAArgs &a, cudaStream_t st) {
+    const long long warps = 2LL * a.L.NRG * MX_SRC * a.L.NB * MX_BI;
+    const int blocks = (int)((warps * 32 + 255) / 256);
+    switch (a.L.S) {
+        case 4: k_prep_a<4><<<blocks, 256, 0, st>>>(a); break;
+        case 5: k_prep_a<5><<<blocks, 256, 0, st>>>(a); break;
+        case 6: k_prep_a<6><<<blocks, 256, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mx_launch_prep_b(const MxPrepBArgs &a, int c_hi, cudaStream_t st) {
+    if (c_hi <= a.c_lo) return cudaSuccess;
+    const long long warps = 2LL * (c_hi - a.c_lo) * MX_BJ;
+    const int blocks = (int)((warps * 32 + 255) / 256);
+    switch (a.L.S) {
+        case 4: k_prep_b<4><<<blocks, 256, 0, st>>>(a, c_hi); break;
+        case 5: k_prep_b<5><<<blocks, 256, 0, st>>>(a, c_hi); break;
+        case 6: k_prep_b<6><<<blocks, 256, 0, st>>>(a, c_hi); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cpl

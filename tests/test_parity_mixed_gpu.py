@@ -1,0 +1,142 @@
+"""Mixed-precision (tcgen05, BF16 fixed-point limbs) path vs the CPU oracle (GPU).
+
+Bar: per-element relative error (against the oracle's S_abs) <= 1e-9 for
+every spectrum, the bound this path states; elements that are zero by parity
+or band exactly 0.0.  Cases span several 128 x 128 GEMM tiles, ragged tails,
+row groups with padding (window counts not a multiple of 4), separate and
+shared window roles, band limits and binning.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_15605_gb300 import coupling, windows
+from parity_util import per_spectrum, sample_pairs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+ALLN = ["TT", "TE", "EE", "EEBB", "EB"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2602_15605_gb300 import build_ext
+    build_ext.build()
+    c = coupling.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def names(spectra):
+    return [n for b, n in zip(coupling.SPEC_BITS, ALLN) if spectra & b]
+
+
+def mixed(ctx, lmax, Wt, Wc, Wp, spectra, **kw):
+    M = ctx.build(lmax, Wt, Wc, Wp, spectra, precision=coupling.MIXED_BF16, **kw)
+    ctx.sync()
+    return M.cpu().numpy()
+
+
+def test_shared_window_dense(ctx):
+    lmax = 300
+    W = windows.mask_like(lmax, seed=31)
+    d = dev(W)
+    got = mixed(ctx, lmax, d, d, d, coupling.ALL)
+    ref, sab = oracle.coupling_dense(lmax, W, W, W, coupling.ALL)
+    errs = per_spectrum(got, ref, sab, ALLN)
+    print("mixed shared 300:", errs)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_separate_windows_dense(ctx):
+    lmax = 257
+    Wt, Wc, Wp = (windows.gaussian_taper(lmax, s) for s in (2, 3, 4))
+    got = mixed(ctx, lmax, dev(Wt), dev(Wc), dev(Wp), coupling.ALL)
+    ref, sab = oracle.coupling_dense(lmax, Wt, Wc, Wp, coupling.ALL)
+    errs = per_spectrum(got, ref, sab, ALLN)
+    print("mixed separate 257:", errs)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_many_windows_padding(ctx):
+    lmax = 200
+    W = np.stack([windows.mask_like(lmax, seed=40 + q) for q in range(6)])
+    d = dev(W)
+    got = mixed(ctx, lmax, d, d, d, coupling.TT | coupling.EE | coupling.EEBB)
+    ref, sab = oracle.coupling_dense(lmax, W, W, W, coupling.TT | coupling.EE | coupling.EEBB)
+    errs = per_spectrum(got, ref, sab, ["TT", "EE", "EEBB"])
+    assert max(errs.values()) <= TOL, errs
+
+
+@pytest.mark.parametrize("spectra", [coupling.TT, coupling.TE, coupling.EE | coupling.EB])
+def test_subsets(ctx, spectra):
+    lmax = 150
+    Wt, Wc, Wp = (windows.gaussian_taper(lmax, s) for s in (5, 6, 7))
+    got = mixed(ctx, lmax, dev(Wt), dev(Wc), dev(Wp), spectra)
+    ref, sab = oracle.coupling_dense(lmax, Wt, Wc, Wp, spectra)
+    errs = per_spectrum(got, ref, sab, names(spectra))
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_band_limited_binned(ctx):
+    lmax = 400
+    W = np.stack([windows.random_positive(lmax, seed=s, band=b) for s, b in ((1, 64), (2, 128), (3, 33))])
+    bl = [64, 128, 33]
+    edges = oracle.bin_edges(2, lmax, 50)
+    d = dev(W)
+    got = ctx.build(lmax, d, d, d, coupling.ALL, band_limit=bl, bin_edges=edges, precision=coupling.MIXED_BF16)
+    ctx.sync()
+    ref, sab = oracle.coupling_dense(lmax, W, W, W, coupling.ALL, band_limit=bl)
+    errs = per_spectrum(got.cpu().numpy(), oracle.bin_matrix(ref, 2, edges), oracle.bin_matrix(sab, 2, edges), ALLN)
+    assert max(errs.values()) <= TOL, errs
+    dense = mixed(ctx, lmax, d, d, d, coupling.ALL, band_limit=bl)
+    errs = per_spectrum(dense, ref, sab, ALLN)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_full_spin_1500_sampled(ctx):
+    lmax = 1500
+    W = windows.mask_like(lmax, seed=77)
+    d = dev(W)
+    M = ctx.build(lmax, d, d, d, coupling.ALL, precision=coupling.MIXED_BF16)
+    ctx.sync()
+    l1, l2 = sample_pairs(lmax, n_random=4000)
+    got = M[:, :, l1 - 2, l2 - 2].cpu().numpy()
+    ref, sab = oracle.coupling_pairs(l1, l2, W, W, W, coupling.ALL)
+    errs = per_spectrum(got, ref, sab, ALLN)
+    print("mixed 1500 sampled:", errs)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_mixed_matches_plain_fp64_many_windows(ctx):
+    # 12 windows (3 row groups) at l_max = 500 against the parity-tested FP64 path
+    lmax = 500
+    W = np.stack([windows.mask_like(lmax, seed=100 + q) for q in range(12)])
+    d = dev(W)
+    Mm = mixed(ctx, lmax, d, d, d, coupling.TT | coupling.EE | coupling.EEBB)
+    Mp = ctx.build(lmax, d, d, d, coupling.TT | coupling.EE | coupling.EEBB).cpu().numpy()
+    # TT, EE and EE->BB have non-negative terms, so |M| is the S_abs scale
+    m = np.abs(Mp) > 1e-280
+    rel = np.max(np.abs(Mm[m] - Mp[m]) / np.abs(Mp[m]))
+    print("mixed vs fp64 (12 windows, 500):", rel)
+    assert rel <= TOL
+    assert np.all(Mm[~m] == 0.0)
+
+
+def test_five_limbs_faster_variant(ctx):
+    # mixed_slices = 5: about 5x fewer limb products than the default 6 at a
+    # bound of 5e-9 (the EE->BB expansion amplifies its ~2e-10 contraction error)
+    lmax = 300
+    W = windows.mask_like(lmax, seed=31)
+    d = dev(W)
+    M = ctx.build(lmax, d, d, d, coupling.ALL, precision=coupling.MIXED_BF16, slices=5)
+    ctx.sync()
+    ref, sab = oracle.coupling_dense(lmax, W, W, W, coupling.ALL)
+    errs = per_spectrum(M.cpu().numpy(), ref, sab, ALLN)
+    print("mixed s=5 300:", errs)
+    assert max(errs.values()) <= 5e-9, errs
