@@ -128,37 +128,66 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
 }
 
 
-// Dense-output epilogue with coalesced writes.  One block covers an 8 x 64
-// block of (i, j) in both parities -- 1024 pairs whose rows of M (fixed l1,
-// l2 = l1 + d) and mirrored rows (fixed l2, l1 = l2 - d) are runs of 16
-// consecutive elements.  Per block the pair coefficients are formed once in
-// extended double-float and kept in shared memory; per row source the five
-// spectra of the 1024 pairs are combined into shared memory and then written
-// row by row.
-constexpr int EB_I = 8, EB_J = 64, EB_P = 2 * EB_I * EB_J, EB_T = 256;
-constexpr int EB_NC = 12;   // combination coefficients: 3 TE, 6 EE, 3 EE->BB
+// Dense-output epilogue with coalesced writes.  One block covers a 4 x 64
+// block of (i, j) in both parities: 512 pairs, one per thread, whose rows of M
+// (fixed l1, l2 = l1 + d) and mirrored rows (fixed l2, l1 = l2 - d) are runs
+// of 8 consecutive elements.  Each thread forms its pair's 12 combination
+// coefficients once in extended double-float and keeps them in registers;
+// per row source it combines the contractions in one exponent frame per
+// spectrum, converts the (2 l2 + 1) and (2 l1 + 1) multiples to FP64 with
+// integer operations, and stages them in shared memory for row-wise writes.
+constexpr int EB_I = 4, EB_J = 64, EB_P = 2 * EB_I * EB_J, EB_T = EB_P;
 
-struct EpiShared {
-    xdf coef[EB_NC][EB_P];
-    xdf xi[5][EB_P];
+struct Term {
+    dfl m;   // mantissa
+    int x;   // exponent of the unit
 };
 
-__device__ __forceinline__ int eb_pair(int pi, int ii, int jj) { return (pi * EB_I + ii) * EB_J + jj; }
+// sum_t m_t 2^(x_t) in one frame: returns (dd, exponent)
+template <int N>
+__device__ __forceinline__ xdf frame_sum(const Term (&t)[N]) {
+    int E = -1000000;
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+        if (t[q].m.h != 0.0f) E = max(E, t[q].x + ilogbf_fast(fabsf(t[q].m.h)));
+    if (E == -1000000) return {0.f, 0.f, 0};
+    dfl s = {0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        if (t[q].m.h == 0.0f) continue;
+        const int k = t[q].x - E;           // the term's magnitude is 2^(k + ilogb m) <= 1
+        if (k < -230) continue;
+        s = df_add(s, dfl{scale2(t[q].m.h, k), scale2(t[q].m.l, k)});
+    }
+    return {s.h, s.l, E};
+}
+
+__device__ __forceinline__ Term term(xdf c, dfl m, int e) { return {df_mul(dfl{c.h, c.l}, m), c.e + e}; }
+
+__device__ __forceinline__ double times_int(xdf v, int f) {
+    // v * f for a small positive integer f, then FP64
+    const float ff = (float)f;
+    const float p = v.h * ff;
+    float e = fmaf(v.h, ff, -p);
+    e = fmaf(v.l, ff, e);
+    const dfl q = df_quick(p, e);
+    return xdf_to_double(xdf{q.h, q.l, v.e});
+}
 
 __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a) {
-    extern __shared__ __align__(16) uint8_t esm[];
-    EpiShared &sh = *reinterpret_cast<EpiShared *>(esm);
+    __shared__ double stage[5][2][EB_P];
     const MxLayout &L = a.L;
     const int i0 = blockIdx.y * EB_I, j0 = blockIdx.x * EB_J;
-    const int tid = threadIdx.x;
+    const int q = threadIdx.x;
     const int L1min = max(a.lmin, MX_L1_FP64);
+    const int pi = q / (EB_I * EB_J), ii = (q / EB_J) % EB_I, jj = q % EB_J;
+    const int i = i0 + ii, j = j0 + jj;
+    const int l1 = j - i, l2 = i + j + pi;
+    const bool valid = !(l1 < L1min || l2 > a.lmax || l1 > l2);
 
-    // ---- coefficients of the block's pairs
-    for (int q = tid; q < EB_P; q += EB_T) {
-        const int pi = q / (EB_I * EB_J), ii = (q / EB_J) % EB_I, jj = q % EB_J;
-        const int i = i0 + ii, j = j0 + jj;
-        const int l1 = j - i, l2 = i + j + pi;
-        if (l1 < L1min || l2 > a.lmax || l1 > l2) continue;
+    // ---- coefficients of this thread's pair
+    xdf cf[12];
+    if (valid) {
         const long long L1 = l1, L2 = l2;
         const xdf eta2i = xdf_recip(xdf_from_ll((L1 - 1) * (L1 + 2) * (L2 - 1) * L2));
         const xdf r2 = xdf_mul(xdf_from_ll(L1 * (L1 + 1) * (L2 + 1) * (L2 + 2)), eta2i);
@@ -168,26 +197,27 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
         const xdf e1 = xdf_recip(xdf_from_ll(2 * (L2 + 2)));
         const xdf c2 = xdf_mul(c1, e1);
         const xdf two = xdf_from_ll(2);
-        sh.coef[0][q] = xdf_mul(r, c0);
-        sh.coef[1][q] = xdf_neg(xdf_mul(r, c1));
-        sh.coef[2][q] = xdf_neg(xdf_mul(r, c2));
-        sh.coef[3][q] = xdf_mul(r2, xdf_mul(c0, c0));
-        sh.coef[4][q] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c1))));
-        sh.coef[5][q] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c2))));
-        sh.coef[6][q] = xdf_mul(r2, xdf_mul(c1, c1));
-        sh.coef[7][q] = xdf_mul(r2, xdf_mul(two, xdf_mul(c1, c2)));
-        sh.coef[8][q] = xdf_mul(r2, xdf_mul(c2, c2));
+        cf[0] = xdf_mul(r, c0);
+        cf[1] = xdf_neg(xdf_mul(r, c1));
+        cf[2] = xdf_neg(xdf_mul(r, c2));
+        cf[3] = xdf_mul(r2, xdf_mul(c0, c0));
+        cf[4] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c1))));
+        cf[5] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c2))));
+        cf[6] = xdf_mul(r2, xdf_mul(c1, c1));
+        cf[7] = xdf_mul(r2, xdf_mul(two, xdf_mul(c1, c2)));
+        cf[8] = xdf_mul(r2, xdf_mul(c2, c2));
         const xdf e0 = xdf_from_ll(L1 + 2);
         const xdf Cc = xdf_mul(xdf_mul(xdf_from_ll(L2 + 2), c1), eta2i);
-        sh.coef[9][q] = xdf_mul(Cc, xdf_mul(e0, e0));
-        sh.coef[10][q] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
-        sh.coef[11][q] = xdf_mul(Cc, xdf_mul(e1, e1));
+        cf[9] = xdf_mul(Cc, xdf_mul(e0, e0));
+        cf[10] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
+        cf[11] = xdf_mul(Cc, xdf_mul(e1, e1));
     }
 
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const long long ncols = (long long)L.NC_B * MX_BJ;
     const int n = a.lmax - a.lmin + 1;
     const int b32 = i0 / MX_BI, c128 = j0 / MX_BJ;
+    const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
     for (int s = 0; s < a.nsrc; ++s) {
         const int role = a.src_role[s];
         if (role == 0) continue;
@@ -196,75 +226,74 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
         const bool pol = (role & (kEE | kEEBB | kEB)) != 0;
         const bool odd = (role & (kEEBB | kEB)) != 0;
         const int np = pol ? (odd ? 9 : 6) : (role & kTE) ? 3 : 1;
-        __syncthreads();   // coefficients ready / previous source written out
-        for (int q = tid; q < EB_P; q += EB_T) {
-            const int pi = q / (EB_I * EB_J), ii = (q / EB_J) % EB_I, jj = q % EB_J;
-            const int i = i0 + ii, j = j0 + jj;
-            const int l1 = j - i, l2 = i + j + pi;
-            if (l1 < L1min || l2 > a.lmax || l1 > l2) continue;
+        if (valid) {
             const int tile = a.tile_of[(((long long)pi * L.NRG + rg) * L.NB + b32) * L.NC + c128];
             const int r = slot * MX_BI + (i % MX_BI), cc = j % MX_BJ;
             const long long rowg = ((long long)rg * L.NB + b32) * MX_ROWS + r;
-            xdf S[MX_NPROD];
+            dfl Sm[MX_NPROD];
+            int Se[MX_NPROD];
 #pragma unroll
             for (int p = 0; p < MX_NPROD; ++p) {
-                S[p] = {0.f, 0.f, 0};
+                Sm[p] = {0.f, 0.f};
+                Se[p] = 0;
                 if (p >= np || tile < 0) continue;
                 const float *src = a.inter + ((long long)tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
-                const float hi = src[r * MX_BJ + cc], lo = src[MX_ROWS * MX_BJ + r * MX_BJ + cc];
-                const int E = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
-                              (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
-                S[p] = xdf_make(df_quick(hi, lo), E);
+                Sm[p] = dfl{src[r * MX_BJ + cc], src[MX_ROWS * MX_BJ + r * MX_BJ + cc]};
+                Se[p] = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
+                        (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
             }
-            sh.xi[0][q] = S[0];
+            xdf X[5];
+            X[0] = xdf{Sm[0].h, Sm[0].l, Se[0]};
+            X[1] = X[2] = X[3] = X[4] = xdf{0.f, 0.f, 0};
             if (role & kTE) {
-                xdf te = xdf_mul(sh.coef[0][q], S[0]);
-                te = xdf_add(te, xdf_mul(sh.coef[1][q], S[1]));
-                te = xdf_add(te, xdf_mul(sh.coef[2][q], S[2]));
-                sh.xi[1][q] = te;
+                const Term t[3] = {term(cf[0], Sm[0], Se[0]), term(cf[1], Sm[1], Se[1]), term(cf[2], Sm[2], Se[2])};
+                X[1] = frame_sum(t);
             }
             if (pol) {
-                xdf ee = {0.f, 0.f, 0};
-#pragma unroll
-                for (int p = 0; p < 6; ++p) ee = xdf_add(ee, xdf_mul(sh.coef[3 + p][q], S[p]));
-                sh.xi[2][q] = ee;
+                const Term t[6] = {term(cf[3], Sm[0], Se[0]), term(cf[4], Sm[1], Se[1]), term(cf[5], Sm[2], Se[2]),
+                                   term(cf[6], Sm[3], Se[3]), term(cf[7], Sm[4], Se[4]), term(cf[8], Sm[5], Se[5])};
+                X[2] = frame_sum(t);
                 if (odd) {
-                    xdf bb = xdf_mul(sh.coef[9][q], S[6]);
-                    bb = xdf_add(bb, xdf_mul(sh.coef[10][q], S[7]));
-                    bb = xdf_add(bb, xdf_mul(sh.coef[11][q], S[8]));
-                    sh.xi[3][q] = bb;
-                    sh.xi[4][q] = xdf_add(ee, xdf_neg(bb));
+                    const Term u[3] = {term(cf[9], Sm[6], Se[6]), term(cf[10], Sm[7], Se[7]), term(cf[11], Sm[8], Se[8])};
+                    X[3] = frame_sum(u);
+                    const Term v[2] = {Term{dfl{X[2].h, X[2].l}, X[2].e}, Term{dfl{-X[3].h, -X[3].l}, X[3].e}};
+                    X[4] = frame_sum(v);
                 }
+            }
+#pragma unroll
+            for (int x = 0; x < 5; ++x) {
+                if (!(role & bits[x])) continue;
+                stage[x][0][q] = times_int(X[x], 2 * l2 + 1);
+                stage[x][1][q] = times_int(X[x], 2 * l1 + 1);
             }
         }
         __syncthreads();
-        // ---- rows: M[l1][l2 = l1 + d] (fixed l1) and mirrored M[l2][l1 = l2 - d]
-        // (fixed l2), d = 2 i0 .. 2 i0 + 15: runs of 16 consecutive elements
+        // ---- rows: M[l1][l2 = l1 + d] and mirrored M[l2][l1 = l2 - d], d = 2 i0 .. 2 i0 + 7
         const int nrow = EB_I + EB_J;
-        const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
         for (int x = 0; x < 5; ++x) {
             if (!(role & bits[x]) || a.slot[x] < 0) continue;
             double *base = a.out + ((size_t)w * a.nspec + a.slot[x]) * (size_t)n * (size_t)n;
-            for (int e = tid; e < 2 * nrow * 2 * EB_I; e += EB_T) {
+            for (int e = q; e < 2 * nrow * 2 * EB_I; e += EB_T) {
                 const int mirror = e / (nrow * 2 * EB_I);
                 const int rr = (e / (2 * EB_I)) % nrow, dl = e % (2 * EB_I);
-                const int pi = dl & 1, ii = dl >> 1, i = i0 + ii, d = 2 * i + pi;
-                int l1, l2;
+                const int epi = dl & 1, eii = dl >> 1, ei = i0 + eii, d = 2 * ei + epi;
+                int el1, el2;
                 if (!mirror) {
-                    l1 = j0 - i0 - (EB_I - 1) + rr;
-                    l2 = l1 + d;
+                    el1 = j0 - i0 - (EB_I - 1) + rr;
+                    el2 = el1 + d;
                 } else {
-                    l2 = i0 + j0 + rr;
-                    l1 = l2 - d;
+                    el2 = i0 + j0 + rr;
+                    el1 = el2 - d;
                 }
-                const int j = l1 + i, jj = j - j0;
-                if (jj < 0 || jj >= EB_J) continue;
-                if (l1 < L1min || l2 > a.lmax || l1 > l2) continue;
-                const xdf v = sh.xi[x][eb_pair(pi, ii, jj)];
-                if (!mirror) base[(size_t)(l1 - a.lmin) * n + (l2 - a.lmin)] = xdf_to_double(xdf_scale_int(v, 2LL * l2 + 1));
-                else if (l1 != l2) base[(size_t)(l2 - a.lmin) * n + (l1 - a.lmin)] = xdf_to_double(xdf_scale_int(v, 2LL * l1 + 1));
+                const int ejj = el1 + ei - j0;
+                if (ejj < 0 || ejj >= EB_J) continue;
+                if (el1 < L1min || el2 > a.lmax || el1 > el2) continue;
+                const int pq = (epi * EB_I + eii) * EB_J + ejj;
+                if (!mirror) base[(size_t)(el1 - a.lmin) * n + (el2 - a.lmin)] = stage[x][0][pq];
+                else if (el1 != el2) base[(size_t)(el2 - a.lmin) * n + (el1 - a.lmin)] = stage[x][1][pq];
             }
         }
+        __syncthreads();
     }
 }
 
@@ -355,11 +384,8 @@ cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st) {
         k_mixed_epilogue<<<grid, 128, 0, st>>>(a);
         return cudaGetLastError();
     }
-    const size_t smem = sizeof(EpiShared);
-    cudaError_t e = cudaFuncSetAttribute(k_mixed_epilogue_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((a.lmax + 1 + EB_J - 1) / EB_J, NI / EB_I);
-    k_mixed_epilogue_dense<<<grid, EB_T, smem, st>>>(a);
+    k_mixed_epilogue_dense<<<grid, EB_T, 0, st>>>(a);
     return cudaGetLastError();
 }
 
