@@ -45,6 +45,16 @@ FP64_PEAK_TFLOPS = 2.0 * 2 * 152 * 2.070e9 / 1e12   # 2 FLOP x 2 DFMA/clk/SM x 1
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 
+def bf16_peak():
+    """Measured dense BF16 tensor peak (TFLOP/s) of this machine, burst figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -57,6 +67,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--lmax", type=int, default=3000,
                     help="smaller l_max for profiler captures only (the bench line uses 3000)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="arm of the headline value (the bench line uses fp64); the other arm is "
+                         "reported in the 'mixed' / 'fp64' sub-object")
+    ap.add_argument("--no-other", action="store_true", help="skip the other precision arm")
     args = ap.parse_args()
     global LMAX
     LMAX = args.lmax
@@ -207,10 +221,11 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(world):
-    return {"workload": "full spin-0/spin-2 set (TT, TE/TB, EE/BB, EE->BB, EB), plain FP64, "
-                        "l_max=%d, separate W^TT/W^TP/W^PP (l<=%d)" % (LMAX, 2 * LMAX),
-            "lmax": LMAX, "lmin": 2, "n_windows": 1, "spectra": list(SPEC_NAMES), "precision": "fp64",
+def workload_config(world, precision="fp64"):
+    return {"workload": "full spin-0/spin-2 set (TT, TE/TB, EE/BB, EE->BB, EB), %s, "
+                        "l_max=%d, separate W^TT/W^TP/W^PP (l<=%d)"
+                        % ("plain FP64" if precision == "fp64" else "mixed BF16 limbs", LMAX, 2 * LMAX),
+            "lmax": LMAX, "lmin": 2, "n_windows": 1, "spectra": list(SPEC_NAMES), "precision": precision,
             "output": "dense 5 x %d x %d FP64 per rank" % (LMAX - 1, LMAX - 1), "parallelism": "independent problem per GPU"
             if world > 1 else "1 GPU", "l2": "flushed between steps (256 MiB write, outside the timed events)"}
 
@@ -260,61 +275,110 @@ def run_ours(args, rank, world, local):
     n_el, terms = work_counts(LMAX)
     out = torch.empty((1, 5, LMAX - 1, LMAX - 1), dtype=torch.float64, device="cuda:%d" % local)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % local)
-    step = lambda: ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=out)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ctx.profile(True)
-    ctx.stats(reset=True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    for q in range(args.steps):
-        flush.fill_(q & 255)
-        evs[q][0].record()
-        step()
-        evs[q][1].record()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
-    step_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    stats = ctx.stats(reset=True)
-    ctx.profile(False)
-    if world > 1:
-        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda:%d" % local)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    def timed_arm(prec, steps, warmup):
+        """Times `steps` builds (L2 flushed between them, outside the events);
+        returns (ms per step, per-kernel stats, sampled clocks, wall seconds)."""
+        step = lambda: ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=out, precision=prec)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        ctx.sync()
+        ctx.profile(True)
+        ctx.stats(reset=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for q in range(steps):
+            flush.fill_(q & 255)
+            evs[q][0].record()
+            step()
+            evs[q][1].record()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t_wall = time.perf_counter() - t_wall
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        st = ctx.stats(reset=True)
+        ctx.profile(False)
+        ctx.sync()
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda:%d" % local)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, st, clk, t_wall
 
-    launches = sum(v["launches"] for v in stats.values())
-    dom_name, dom = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    achieved = dom["flop"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
-    traffic = recorded_traffic(dom_name)
-    per_launch_ms = dom["ms"] / max(dom["launches"], 1)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom_name,
-                "kernel_ms_per_launch": per_launch_ms,
+    def fp64_roofline(stats, clk):
+        dom_name, dom = max(((k, v) for k, v in stats.items() if k.startswith("plain")), key=lambda kv: kv[1]["ms"])
+        achieved = dom["flop"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(dom_name), "kernel": dom_name,
+                "kernel_ms_per_launch": dom["ms"] / max(dom["launches"], 1),
                 "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.26 TFLOP/s)"}
-    if clk and clk.get("sm_mhz"):
-        at_clock = 2.0 * 2 * 152 * clk["sm_mhz"] * 1e6 / 1e12
-        roofline["frac_at_sampled_clock"] = achieved / at_clock
+        if clk and clk.get("sm_mhz"):
+            roof["frac_at_sampled_clock"] = achieved / (2.0 * 2 * 152 * clk["sm_mhz"] * 1e6 / 1e12)
+        return roof
+
+    def mixed_roofline(stats):
+        name, g = max(((k, v) for k, v in stats.items() if k.startswith("mixed_gemm")), key=lambda kv: kv[1]["ms"])
+        peak, src = bf16_peak()
+        issued = g["issued_flop"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
+        algo = g["flop"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
+        return {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak,
+                "traffic": None, "kernel": name, "kernel_ms_per_launch": g["ms"] / max(g["launches"], 1),
+                "algorithmic_tflops": algo, "peak_source": src,
+                "achieved_counts": "BF16 limb-product FLOP issued by the tcgen05 MMAs (21 per contraction term "
+                                   "at 6 limbs) / event-timed kernel duration; algorithmic_tflops counts 2 FLOP "
+                                   "per window-term-contraction"}
+
+    def mixed_error():
+        """Relative error of the mixed arm against the plain FP64 arm on this workload."""
+        ref = torch.empty_like(out)
+        ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=ref)
+        ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=out, precision=coupling.MIXED_BF16)
+        torch.cuda.synchronize()
+        ctx.sync()
+        err = {}
+        for s, nm in enumerate(SPEC_NAMES):
+            a, b = out[0, s], ref[0, s]
+            if nm in ("TT", "EE", "EEBB"):      # non-negative terms: |M| is the absolute-sum scale
+                m = b.abs() > 1e-280
+                err[nm] = float(((a - b).abs()[m] / b.abs()[m]).max())
+            else:                               # signed terms: normwise
+                err[nm + "_normwise"] = float((a - b).abs().max() / b.abs().max())
+        return err
+
+    head_prec = coupling.MIXED_BF16 if args.precision == "mixed" else coupling.FP64
+    step_ms, stats, clk, t_wall = timed_arm(head_prec, args.steps, args.warmup)
+    launches = sum(v["launches"] for v in stats.values())
+    roofline = mixed_roofline(stats) if args.precision == "mixed" else fp64_roofline(stats, clk)
+    other = None
+    if not args.no_other:
+        o_prec = coupling.FP64 if args.precision == "mixed" else coupling.MIXED_BF16
+        o_steps = max(3, min(args.steps, 10))
+        o_ms, o_stats, o_clk, _ = timed_arm(o_prec, o_steps, 2)
+        other = {"value": world * 5 * n_el / (o_ms * 1e-3), "unit": UNIT, "ms_per_step": o_ms, "steps": o_steps,
+                 "precision": "fp64" if args.precision == "mixed" else "mixed_bf16 (6 limbs)",
+                 "roofline": fp64_roofline(o_stats, o_clk) if args.precision == "mixed" else mixed_roofline(o_stats),
+                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in o_stats.items()},
+                 "clocks": o_clk}
+        other["max_rel_err_vs_fp64"] = mixed_error()
 
     # end to end through the public host-buffer call
     e2e = None
     if not args.no_e2e:
         host_out = np.empty((1, 5, LMAX - 1, LMAX - 1), dtype=np.float64)
-        ctx.build_host(LMAX, Wt, Wc, Wp, coupling.ALL, out=host_out)
+        ctx.build_host(LMAX, Wt, Wc, Wp, coupling.ALL, out=host_out, precision=head_prec)
         t0 = time.perf_counter()
         k_e2e = max(3, min(args.steps, 10))
         for _ in range(k_e2e):
-            ctx.build_host(LMAX, Wt, Wc, Wp, coupling.ALL, out=host_out)
+            ctx.build_host(LMAX, Wt, Wc, Wp, coupling.ALL, out=host_out, precision=head_prec)
         dt = (time.perf_counter() - t0) / k_e2e
         if world > 1:
             t = torch.tensor([dt], dtype=torch.float64, device="cuda:%d" % local)
@@ -336,12 +400,15 @@ def run_ours(args, rank, world, local):
         total_terms = sum(terms.values())
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(world),
+                "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16-limbs/f32-acc/f64",
+                "data": "synthetic", "config": workload_config(world, args.precision),
                 "terms_per_s": world * total_terms / step_s,
                 "terms_per_s_by_spectrum": {k: world * v / step_s for k, v in terms.items()},
                 "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches),
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items()},
                 "clocks": clk, "wall_s_timed": t_wall}
+        if other is not None:
+            line["mixed" if args.precision == "fp64" else "fp64"] = other
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

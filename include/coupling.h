@@ -230,6 +230,9 @@ typedef struct {
     double ms;            /* summed event-timed duration of those launches (profiling only) */
     double flop;          /* algorithmic FLOP of the timed launches */
     double bytes;         /* algorithmic DRAM bytes of the timed launches */
+    double issued_flop;   /* floating-point operations the timed launches issue: the
+                             tensor-core limb products for the mixed path, equal to
+                             flop for the FP64 kernels */
 } cpl_kernel_stat;
 
 cpl_status cpl_ctx_profile(cpl_ctx *ctx, int enable);

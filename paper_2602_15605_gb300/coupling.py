@@ -42,7 +42,7 @@ class Request(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
-                ("flop", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("flop", ctypes.c_double), ("bytes", ctypes.c_double), ("issued_flop", ctypes.c_double)]
 
 
 # Every symbol include/coupling.h declares.
@@ -170,7 +170,8 @@ class Context:
         out = {}
         for q in range(min(n.value, 64)):
             k = buf[q]
-            out[k.name.decode()] = dict(launches=k.launches, ms=k.ms, flop=k.flop, bytes=k.bytes)
+            out[k.name.decode()] = dict(launches=k.launches, ms=k.ms, flop=k.flop, bytes=k.bytes,
+                                        issued_flop=k.issued_flop)
         return out
 
     # ------------------------------------------------------------------ device

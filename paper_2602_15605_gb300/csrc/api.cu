@@ -73,13 +73,14 @@ cudaEvent_t begin_launch(cpl_ctx *c, cudaStream_t st) {
     return a;
 }
 
-void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes) {
+void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes, double issued) {
+    if (issued < 0.0) issued = flop;
     c->kstats[idx].launches++;
     if (c->profiling && a) {
         cudaEvent_t b = take_event(c);
         if (b) {
             cudaEventRecord(b, st);
-            c->pending.push_back({idx, a, b, flop, bytes});
+            c->pending.push_back({idx, a, b, flop, bytes, issued});
             return;
         }
         c->ev_pool.push_back(a);
@@ -109,7 +110,7 @@ struct LaunchScope {
             cudaEvent_t b = take_event(c);
             if (b) {
                 cudaEventRecord(b, st);
-                c->pending.push_back({idx, a, b, flop, bytes});
+                c->pending.push_back({idx, a, b, flop, bytes, flop});
                 return;
             }
             c->ev_pool.push_back(a);
@@ -547,6 +548,7 @@ cpl_status cpl_ctx_stats(cpl_ctx *c, cpl_kernel_stat *out, int max, int *n, int 
         c->kstats[p.idx].ms += ms;
         c->kstats[p.idx].flop += p.flop;
         c->kstats[p.idx].bytes += p.bytes;
+        c->kstats[p.idx].issued += p.issued;
         c->ev_pool.push_back(p.a);
         c->ev_pool.push_back(p.b);
     }
@@ -559,10 +561,11 @@ cpl_status cpl_ctx_stats(cpl_ctx *c, cpl_kernel_stat *out, int max, int *n, int 
         out[q].ms = c->kstats[q].ms;
         out[q].flop = c->kstats[q].flop;
         out[q].bytes = c->kstats[q].bytes;
+        out[q].issued_flop = c->kstats[q].issued;
     }
     if (n) *n = nk;
     if (reset)
-        for (auto &k : c->kstats) k.launches = 0, k.ms = k.flop = k.bytes = 0.0;
+        for (auto &k : c->kstats) k.launches = 0, k.ms = k.flop = k.bytes = k.issued = 0.0;
     return CPL_OK;
 }
 

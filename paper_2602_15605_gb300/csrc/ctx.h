@@ -80,12 +80,12 @@ struct cpl_ctx {
     struct KStat {
         std::string name;
         long long launches = 0;
-        double ms = 0.0, flop = 0.0, bytes = 0.0;
+        double ms = 0.0, flop = 0.0, bytes = 0.0, issued = 0.0;
     };
     struct Pending {
         int idx;
         cudaEvent_t a, b;
-        double flop, bytes;
+        double flop, bytes, issued;
     };
     bool profiling = false;
     std::vector<KStat> kstats;
@@ -98,6 +98,7 @@ cpl_status ensure_tables(cpl_ctx *c, int lmax);
 cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out);
 cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st);
 int stat_index(cpl_ctx *c, const char *name);
-void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes);
+void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes,
+                   double issued = -1.0);
 cudaEvent_t begin_launch(cpl_ctx *c, cudaStream_t st);
 }  // namespace cpl

@@ -4,7 +4,7 @@
 //   C[r, c] = sum_k x[r, k] y[c, k]   (128 x 128 output, k over the item's range)
 // with x, y given as S BF16 fixed-point limbs per element (mixed.h).
 //
-// Warp roles (10 warps):
+// Warp roles (18 warps):
 //   warp 0      producer: one elected lane streams the KB-k tile images of
 //               all limbs of x and y into a shared-memory ring (2 stages of
 //               32 k for S <= 5 limbs, 3 stages of 16 k for S = 6) with
@@ -14,11 +14,12 @@
 //               tcgen05.mma (M=128, N=128, K=16, BF16 in, FP32 accumulate)
 //               into four TMEM accumulators by order t + u = 0, 1, 2, >= 3,
 //               and commits each stage back to the producer.
-//   warps 2-9   drain: after every 128-k scale block, read the four
+//   warps 2-17  drain: after every 128-k scale block, read the four
 //               accumulators with tcgen05.ld, combine them, scale by
 //               2^(E_row + E_col) relative to the row / column maxima, and add
 //               into a double-float running sum per element (high part in
-//               registers, low part in shared memory).
+//               registers, low part in shared memory, renormalised once at
+//               the end).
 // The accumulators of orders 0, 1 and 2 are integers below 2^24 in their
 // units over a 128-k block (|limb| <= 128, at most 3 products per k), so the
 // tensor core holds them exactly whatever its internal rounding; only the
@@ -36,7 +37,7 @@
 namespace cpl {
 namespace {
 
-constexpr int NTH = 320;
+constexpr int NTH = 576;                   // 2 control warps + 16 drain warps
 constexpr int LPAD = MX_ROWS + 1;          // padded stride of the [col][row] planes
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
@@ -99,13 +100,11 @@ __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t ad, uint64_t bd, 
         : "memory");
 }
 
-#define TMEM_LD16(addr, r)                                                                                      \
-    asm volatile(                                                                                               \
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),     \
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),             \
-          "=r"(r[15])                                                                                           \
-        : "r"(addr))
+#define TMEM_LD8(addr, r)                                                                    \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"        \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
+                   "=r"(r[7])                                                                      \
+                 : "r"(addr))
 
 struct Shared {
     uint64_t full[3], empty[3], acc_full, acc_empty, done;
@@ -147,7 +146,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             mbar_init(s_empty0 + 8 * q, 1);
         }
         mbar_init(s_accf, 1);
-        mbar_init(s_acce, 8);
+        mbar_init(s_acce, 16);
         mbar_init(s_done, 1);
         sh.abort = 0;
         sh.dabort = 0;
@@ -242,9 +241,12 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
         }
     } else {
         // ------------------------------------------------------------ drain
-        const int q = warp & 3, half = (warp - 2) >> 2;
-        const int row = 32 * q + lane, c0 = 64 * half;
-        const int dtid = tid - 64;               // 0..255
+        // 16 warps: warp (2 + dw) reads TMEM lane quarter (warp & 3) and
+        // columns [32 (dw >> 2), +32); one thread per (row, 32 columns).
+        const int dw = warp - 2;
+        const int q = warp & 3, quarter = dw >> 2;
+        const int row = 32 * q + lane, c0 = 32 * quarter;
+        const int dtid = tid - 64;               // 0..511
         const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
         const long long ncols = (long long)L.NC_B * MX_BJ;
         const long long rowg = ((long long)it.rg * L.NB + it.b) * MX_ROWS + row;
@@ -253,10 +255,12 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
         const int j0 = it.c * MX_BJ;
         const int16_t *eBcol = a.eB + ((long long)pi * MX_NBV + beta) * ncols * L.NSB_B;
         const int16_t *emB = a.emaxB + ((long long)pi * MX_NBV + beta) * ncols;
-        float H[64];
+        // running sum per element: high part in registers, low part (left
+        // unnormalised until the end) in shared memory
+        float H[32];
 #pragma unroll
-        for (int x = 0; x < 64; ++x) H[x] = 0.f;
-        for (int x = 0; x < 64; ++x) Ls[(c0 + x) * LPAD + row] = 0.f;
+        for (int x = 0; x < 32; ++x) H[x] = 0.f;
+        for (int x = 0; x < 32; ++x) Ls[(c0 + x) * LPAD + row] = 0.f;
         int m = 0;
         for (int kb = kb_lo; kb <= kb_hi; ++kb) {
             const bool slast = (kb == kb_hi) || (kb % KPS == KPS - 1);
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             const bool ok = !*(volatile int *)&sh.abort && mbar_wait(s_accf, m & 1);
             if (!ok) sh.dabort = 1;
             // (A): column exponents visible; the abort decision is the same for all drain threads
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            asm volatile("bar.sync 1, 512;" ::: "memory");
             if (*(volatile int *)&sh.dabort) {
                 if (dtid == 0) {
                     atomicExch(a.err, 16);
@@ -281,47 +285,60 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
 #pragma unroll
-            for (int g4 = 0; g4 < 4; ++g4) {
-                uint32_t r0[16], r1[16], r2[16], r3[16];
-                const uint32_t col = (uint32_t)(c0 + 16 * g4);
-                TMEM_LD16(lane_addr + col, r0);
-                TMEM_LD16(lane_addr + MX_BJ + col, r1);
-                TMEM_LD16(lane_addr + 2 * MX_BJ + col, r2);
-                TMEM_LD16(lane_addr + 3 * MX_BJ + col, r3);
+            for (int g = 0; g < 4; ++g) {
+                uint32_t r0[8], r1[8], r2[8], r3[8];
+                const uint32_t col = (uint32_t)(c0 + 8 * g);
+                TMEM_LD8(lane_addr + col, r0);
+                TMEM_LD8(lane_addr + MX_BJ + col, r1);
+                TMEM_LD8(lane_addr + 2 * MX_BJ + col, r2);
+                TMEM_LD8(lane_addr + 3 * MX_BJ + col, r3);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int x = 0; x < 16; ++x) {
-                    const int cc = c0 + 16 * g4 + x;
+                for (int x = 0; x < 8; ++x) {
+                    const int cc = c0 + 8 * g + x;
                     const int d = eAr + (int)sh.ecol[cc];
                     if (d < -252) continue;
+                    // block value: orders 0 and 1 exactly (two-sum), then 2 and >= 3
                     dfl v = df_two_sum(__uint_as_float(r0[x]), __uint_as_float(r1[x]));
                     v.l += __uint_as_float(r2[x]);
                     v.l += __uint_as_float(r3[x]);
-                    const float vh = scale2(v.h, d), vl = scale2(v.l, d);
-                    const dfl z = df_two_sum(H[16 * g4 + x], vh);
-                    float lo = Ls[cc * LPAD + row] + z.l + vl;
-                    const dfl w = df_quick(z.h, lo);
-                    H[16 * g4 + x] = w.h;
-                    Ls[cc * LPAD + row] = w.l;
+                    float vh, vl;
+                    if (d >= -126) {
+                        const float f = pow2f(d);
+                        vh = v.h * f;
+                        vl = v.l * f;
+                    } else {
+                        vh = scale2(v.h, d);
+                        vl = scale2(v.l, d);
+                    }
+                    const dfl z = df_two_sum(H[8 * g + x], vh);
+                    H[8 * g + x] = z.h;
+                    Ls[cc * LPAD + row] += z.l + vl;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) mbar_arrive(s_acce);
             // (B): every drain thread is done with the column exponents
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            asm volatile("bar.sync 1, 512;" ::: "memory");
             ++m;
         }
         // ---- write the element sums: hi plane and lo plane, [row][col] in global
         if (!*(volatile int *)&sh.dabort) {
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+                const dfl w = df_quick(H[x], Ls[(c0 + x) * LPAD + row]);
+                H[x] = w.h;
+                Ls[(c0 + x) * LPAD + row] = w.l;
+            }
             // the producer / MMA are done with the stage buffers once the last
             // block was drained; reuse them for the transposed hi plane
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            asm volatile("bar.sync 1, 512;" ::: "memory");
 #pragma unroll
-            for (int x = 0; x < 64; ++x) Hs[(c0 + x) * LPAD + row] = H[x];
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            for (int x = 0; x < 32; ++x) Hs[(c0 + x) * LPAD + row] = H[x];
+            asm volatile("bar.sync 1, 512;" ::: "memory");
             float *dst = a.inter + ((long long)it.tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
-            for (int idx = dtid; idx < MX_ROWS * MX_BJ; idx += 256) {
+            for (int idx = dtid; idx < MX_ROWS * MX_BJ; idx += 512) {
                 const int r = idx / MX_BJ, cc = idx % MX_BJ;
                 dst[idx] = Hs[cc * LPAD + r];
                 dst[MX_ROWS * MX_BJ + idx] = Ls[cc * LPAD + r];

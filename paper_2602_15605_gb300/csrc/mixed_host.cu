@@ -299,8 +299,12 @@ cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream
         ga.inter = M.inter.as<float>();
         ga.err = M.err.as<int>();
         ga.L = L;
-        double flop = 0.0;
+        double flop = 0.0, issued = 0.0;
         if (c->profiling) {
+            // issued: 2 x 128 x 128 x k x (limb products) per item
+            const double nlp = (double)S * (S + 1) / 2;
+            for (const MxItem &it : items)
+                issued += 2.0 * MX_ROWS * MX_BJ * (double)(it.kb_hi - it.kb_lo + 1) * L.KB * nlp;
             // algorithmic work: 2 FLOP per (source, l3 term, contraction) over the pairs the GEMM serves
             for (const TileRec &t : tiles)
                 for (int q = 0; q < MX_SRC; ++q) {
@@ -320,7 +324,7 @@ cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream
         const int idx = stat_index(c, S == 6 ? "mixed_gemm_s6" : S == 5 ? "mixed_gemm_s5" : "mixed_gemm_s4");
         cudaEvent_t ev = begin_launch(c, st);
         CPL_CUDA_TRY(mx_launch_gemm(ga, st));
-        record_launch(c, idx, ev, st, flop, 0.0);
+        record_launch(c, idx, ev, st, flop, 0.0, issued);
     }
 
     // ---- epilogue and FP64 band
