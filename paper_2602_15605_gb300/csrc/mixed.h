@@ -23,9 +23,7 @@
 
 namespace cpl {
 
-constexpr int MX_ROWS = 128;        // GEMM tile rows: MX_SRC sources x MX_BI i-values
-constexpr int MX_SRC = 4;           // row sources (window x role) per row group
-constexpr int MX_BI = 32;           // i per row block
+constexpr int MX_ROWS = 128;        // GEMM tile rows: SRC sources x BI i-values (MxLayout)
 constexpr int MX_BJ = 128;          // j per column block (GEMM N)
 constexpr int MX_SB = 128;          // k per scale block (drain period)
 // k per tile image / pipeline stage: 32 for up to 5 limbs, 16 for 6 limbs
@@ -47,14 +45,16 @@ struct MxLayout {
     int S;          // limbs per operand
     int KB;         // k per tile image (mx_kb(S))
     int IMG;        // bytes per tile image
-    int fA;         // k blocks per 32-row i block (32 / KB)
+    int fA;         // k blocks per i block (BI / KB)
     int gB;         // k blocks per 128-column j block (128 / KB)
     int lmax, lmin;
-    int NB;         // row blocks (32 i) per parity
+    int NB;         // row blocks (BI i) per parity
     int NC;         // column blocks (128 j) of this request
     int NKB;        // k blocks (KB k) of this request
     int NSB;        // scale blocks of this request
-    int NRG;        // row groups of MX_SRC sources
+    int SRC;        // row sources (window x role) per row group: 1, 2 or 4
+    int BI;         // i per row block: 128 / SRC
+    int NRG;        // row groups of SRC sources
     long long a_rg_bytes;   // bytes of one (pi, alpha, rg) slab of A images
     // B cache geometry (independent of the request except through its size)
     int NC_B;       // column blocks the B cache holds

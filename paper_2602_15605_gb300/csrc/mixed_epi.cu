@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
     const int pi = blockIdx.z;
     const int l1 = j - i, l2 = i + j + pi;
     if (l1 < max(a.lmin, MX_L1_FP64) || l2 > a.lmax || l1 > l2) return;
-    const int b = i / MX_BI, ii = i % MX_BI, c = j / MX_BJ, cc = j % MX_BJ;
+    const int b = i / L.BI, ii = i % L.BI, c = j / MX_BJ, cc = j % MX_BJ;
 
     // pair coefficients (exact integer inputs)
     const long long L1 = l1, L2 = l2;
@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
     for (int s = 0; s < a.nsrc; ++s) {
         const int role = a.src_role[s];
         const int w = a.src_win[s];
-        const int rg = s / MX_SRC, slot = s % MX_SRC;
+        const int rg = s / L.SRC, slot = s % L.SRC;
         const int tile = a.tile_of[(((long long)pi * L.NRG + rg) * L.NB + b) * L.NC + c];
         xdf S[MX_NPROD];
-        const int r = slot * MX_BI + ii;
+        const int r = slot * L.BI + ii;
         const long long rowg = ((long long)rg * L.NB + b) * MX_ROWS + r;
         const bool pol = (role & (kEE | kEEBB | kEB)) != 0;
         const bool odd = (role & (kEEBB | kEB)) != 0;
@@ -216,19 +216,19 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const long long ncols = (long long)L.NC_B * MX_BJ;
     const int n = a.lmax - a.lmin + 1;
-    const int b32 = i0 / MX_BI, c128 = j0 / MX_BJ;
+    const int b32 = i0 / L.BI, c128 = j0 / MX_BJ;
     const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
     for (int s = 0; s < a.nsrc; ++s) {
         const int role = a.src_role[s];
         if (role == 0) continue;
         const int w = a.src_win[s];
-        const int rg = s / MX_SRC, slot = s % MX_SRC;
+        const int rg = s / L.SRC, slot = s % L.SRC;
         const bool pol = (role & (kEE | kEEBB | kEB)) != 0;
         const bool odd = (role & (kEEBB | kEB)) != 0;
         const int np = pol ? (odd ? 9 : 6) : (role & kTE) ? 3 : 1;
         if (valid) {
             const int tile = a.tile_of[(((long long)pi * L.NRG + rg) * L.NB + b32) * L.NC + c128];
-            const int r = slot * MX_BI + (i % MX_BI), cc = j % MX_BJ;
+            const int r = slot * L.BI + (i % L.BI), cc = j % MX_BJ;
             const long long rowg = ((long long)rg * L.NB + b32) * MX_ROWS + r;
             dfl Sm[MX_NPROD];
             int Se[MX_NPROD];
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
 }  // namespace
 
 cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st) {
-    const int NI = a.L.NB * MX_BI;
+    const int NI = a.L.NB * a.L.BI;
     if (a.n_bins > 0) {
         dim3 grid((a.lmax + 1 + 127) / 128, NI, 2);
         k_mixed_epilogue<<<grid, 128, 0, st>>>(a);

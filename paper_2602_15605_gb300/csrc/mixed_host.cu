@@ -82,12 +82,16 @@ cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream
     add(r->W_tt, kTT);
     add(r->W_tp, kTE);
     add(r->W_pp, kEE | kEEBB | kEB);
+    // rows of a GEMM tile: SRC sources x BI i-values, SRC the smallest power
+    // of two >= the windows per role (at most 4), so few windows waste no rows
+    const int SRC = nw >= 3 ? 4 : nw == 2 ? 2 : 1;
+    const int BI = MX_ROWS / SRC;
     std::vector<Source> src;
     std::vector<int> group_start;
     for (auto &g : groups) {
         group_start.push_back((int)src.size());
         for (int w = 0; w < nw; ++w) src.push_back({g.W, w, g.spectra});
-        while (src.size() % MX_SRC) src.push_back({nullptr, -1, 0u});   // pad the row group
+        while (src.size() % SRC) src.push_back({nullptr, -1, 0u});   // pad the row group
     }
     const int nsrc = (int)src.size();
 
@@ -108,17 +112,19 @@ cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream
     MxLayout L;
     std::memset(&L, 0, sizeof(L));
     L.S = S;
+    L.SRC = SRC;
+    L.BI = BI;
     L.KB = mx_kb(S);
     L.IMG = mx_img_bytes(S);
-    L.fA = MX_BI / L.KB;
+    L.fA = L.BI / L.KB;
     L.gB = MX_BJ / L.KB;
     L.lmax = lmax;
     L.lmin = lmin;
-    L.NB = (lmax - lmin) / 2 / MX_BI + 1;
+    L.NB = (lmax - lmin) / 2 / L.BI + 1;
     L.NC = (lmax + 1 + MX_BJ - 1) / MX_BJ;
     L.NKB = lmax / L.KB + 1;
     L.NSB = (L.NKB + 3) / 4;
-    L.NRG = nsrc / MX_SRC;
+    L.NRG = nsrc / L.SRC;
     L.a_rg_bytes = ((long long)L.NB * L.NKB - (long long)L.fA * L.NB * (L.NB - 1) / 2) * S * L.IMG;
     if (M.S != S || M.NC_B < L.NC) {
         M.S = S;
@@ -237,13 +243,13 @@ cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream
     for (int pi = 0; pi < 2; ++pi)
         for (int b = 0; b < L.NB; ++b)
             for (int cb = 0; cb < L.NC; ++cb) {
-                const int i0 = b * MX_BI;
+                const int i0 = b * L.BI;
                 const int ja = std::max(cb * MX_BJ, i0 + L1min), jb = std::min(cb * MX_BJ + MX_BJ - 1, lmax - pi - i0);
                 if (ja > jb) continue;
                 for (int rg = 0; rg < L.NRG; ++rg) {
                     int kcap = -1;
-                    for (int q = 0; q < MX_SRC; ++q) {
-                        const int cap = src_cap[rg * MX_SRC + q];
+                    for (int q = 0; q < L.SRC; ++q) {
+                        const int cap = src_cap[rg * L.SRC + q];
                         if (cap < 0) continue;
                         kcap = std::max(kcap, std::max((cap - pi) >> 1, (cap - 1 + pi) >> 1));
                     }
@@ -260,7 +266,7 @@ cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream
             for (const TileRec &t : tiles) {
                 if (t.pi != pi) continue;
                 int need = 0;
-                for (int q = 0; q < MX_SRC; ++q) need = std::max(need, products_for(src[t.rg * MX_SRC + q].role));
+                for (int q = 0; q < L.SRC; ++q) need = std::max(need, products_for(src[t.rg * L.SRC + q].role));
                 if (p >= need) continue;
                 MxItem it;
                 it.pi = (int16_t)pi;
@@ -307,16 +313,16 @@ cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream
                 issued += 2.0 * MX_ROWS * MX_BJ * (double)(it.kb_hi - it.kb_lo + 1) * L.KB * nlp;
             // algorithmic work: 2 FLOP per (source, l3 term, contraction) over the pairs the GEMM serves
             for (const TileRec &t : tiles)
-                for (int q = 0; q < MX_SRC; ++q) {
-                    const Source &sr = src[t.rg * MX_SRC + q];
+                for (int q = 0; q < L.SRC; ++q) {
+                    const Source &sr = src[t.rg * L.SRC + q];
                     if (sr.win < 0) continue;
                     const int np = products_for(sr.role);
                     const int n_even = std::min(np, 6), n_odd = np > 6 ? 3 : 0;
                     double e = 0, o = 0;
-                    for (int di = 0; di < MX_BI; ++di) {
-                        const int i = t.b * MX_BI + di;
+                    for (int di = 0; di < L.BI; ++di) {
+                        const int i = t.b * L.BI + di;
                         const int ja = std::max(t.c * MX_BJ, i + L1min), jb = std::min(t.c * MX_BJ + MX_BJ - 1, lmax - t.pi - i);
-                        if (ja <= jb) row_terms(i, ja, jb, t.pi, src_cap[t.rg * MX_SRC + q], &e, &o);
+                        if (ja <= jb) row_terms(i, ja, jb, t.pi, src_cap[t.rg * L.SRC + q], &e, &o);
                     }
                     flop += 2.0 * (n_even * e + n_odd * o);
                 }

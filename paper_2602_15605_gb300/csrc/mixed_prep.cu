@@ -78,15 +78,15 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const MxLayout &L = a.L;
-    const int NI = L.NB * MX_BI;
-    const int nsrc_pad = L.NRG * MX_SRC;
+    const int NI = L.NB * L.BI;
+    const int nsrc_pad = L.NRG * L.SRC;
     if (warp >= 2 * nsrc_pad * NI) return;
     const int i = warp % NI;
     const int s = (warp / NI) % nsrc_pad;
     const int pi = warp / (NI * nsrc_pad);
-    const int b = i / MX_BI, ii = i % MX_BI;
-    const int rg = s / MX_SRC, slot = s % MX_SRC;
-    const int r = slot * MX_BI + ii;                      // row in the 128-row tile
+    const int b = i / L.BI, ii = i % L.BI;
+    const int rg = s / L.SRC, slot = s % L.SRC;
+    const int r = slot * L.BI + ii;                      // row in the 128-row tile
     const long long row_global = ((long long)rg * L.NB + b) * MX_ROWS + r;
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const bool live = s < a.nsrc;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     int emax[MX_NA];
 #pragma unroll
     for (int q = 0; q < MX_NA; ++q) emax[q] = EXP_ZERO;
-    const int sb0 = (b * MX_BI) / MX_SB;
+    const int sb0 = (b * L.BI) / MX_SB;
     for (int sb = sb0; sb < L.NSB; ++sb) {
         dfl val[MX_NA][4];
         int vex[MX_NA][4];
@@ -272,7 +272,7 @@ cudaError_t mx_launch_weights_dd(const double *A, int n_src, int a_stride, float
 }
 
 cudaError_t mx_launch_prep_a(const MxPrepAArgs &a, cudaStream_t st) {
-    const long long warps = 2LL * a.L.NRG * MX_SRC * a.L.NB * MX_BI;
+    const long long warps = 2LL * a.L.NRG * a.L.SRC * a.L.NB * a.L.BI;
     const int blocks = (int)((warps * 32 + 255) / 256);
     switch (a.L.S) {
         case 4: k_prep_a<4><<<blocks, 256, 0, st>>>(a); break;

@@ -140,3 +140,14 @@ def test_five_limbs_faster_variant(ctx):
     errs = per_spectrum(M.cpu().numpy(), ref, sab, ALLN)
     print("mixed s=5 300:", errs)
     assert max(errs.values()) <= 5e-9, errs
+
+
+def test_two_windows_row_shape(ctx):
+    # two windows per role: GEMM tiles of 2 sources x 64 i-values
+    lmax = 333
+    W = np.stack([windows.mask_like(lmax, seed=60 + q) for q in range(2)])
+    d = dev(W)
+    got = mixed(ctx, lmax, d, d, d, coupling.ALL)
+    ref, sab = oracle.coupling_dense(lmax, W, W, W, coupling.ALL)
+    errs = per_spectrum(got, ref, sab, ALLN)
+    assert max(errs.values()) <= TOL, errs
