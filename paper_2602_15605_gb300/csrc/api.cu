@@ -426,10 +426,10 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     c->bins_inv.release();
     c->stage_w.release();
     c->stage_out.release();
-    for (DevBuf *b : {&c->mx.Bimg, &c->mx.eB, &c->mx.emaxB, &c->mx.gdd, &c->mx.Aimg, &c->mx.eA, &c->mx.emaxA,
-                      &c->mx.A64, &c->mx.Add, &c->mx.l3cap, &c->mx.src, &c->mx.inter, &c->mx.items,
-                      &c->mx.tile_of, &c->mx.err})
+    c->mx.plans.clear();
+    for (DevBuf *b : {&c->mx.Bimg, &c->mx.eB, &c->mx.emaxB, &c->mx.gdd, &c->mx.arena, &c->mx.ticket, &c->mx.err})
         b->release();
+    if (c->mx.cap_stream) cudaStreamDestroy(c->mx.cap_stream);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -524,6 +524,8 @@ cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, doub
         if (jobs[q].precision != jobs[0].precision) return fail(CPL_ERR_ARG, "all jobs must use one precision");
     }
     if ((s = select_device(c)) != CPL_OK) return s;
+    if (jobs[0].precision == CPL_MIXED_BF16)
+        return cpl::build_mixed_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream, true);
     for (int q = 0; q < n_jobs; ++q)
         if ((s = build_one(c, jobs + q, outs[q], (cudaStream_t)stream)) != CPL_OK) return s;
     return CPL_OK;

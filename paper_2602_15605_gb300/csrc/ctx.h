@@ -44,6 +44,11 @@ struct TileSet {
 };
 
 
+struct MxPlan;                    // a planned batch (mixed_host.cu)
+struct MxPlanDeleter {
+    void operator()(MxPlan *p) const;
+};
+
 // Scratch and caches of the mixed-precision path.
 struct MixedState {
     int S = 0;                   // limbs the B cache was built with
@@ -51,10 +56,13 @@ struct MixedState {
     DevBuf Bimg, eB, emaxB;      // window-independent operand images (cache)
     int pmax_dd = -1;
     DevBuf gdd;                  // g, h as double-float: gh | gl | hh | hl
-    DevBuf Aimg, eA, emaxA;      // per-request operand images
-    DevBuf A64, Add, l3cap, src; // per-source weights (FP64, double-float), caps, (win, role)
-    DevBuf inter, items, tile_of;
+    DevBuf arena;                // per-job scratch of the running chunk (A images, weights, GEMM output)
+    DevBuf ticket;               // work-item ticket of the persistent GEMM
     DevBuf err;                  // device error word of the bounded waits
+    std::vector<std::unique_ptr<MxPlan, MxPlanDeleter>> plans;   // cached plans (LRU)
+    unsigned long long clock = 0;
+    int nsm = 0;
+    cudaStream_t cap_stream = nullptr;   // stream used only for graph capture
 };
 
 }  // namespace cpl
@@ -97,6 +105,8 @@ namespace cpl {
 cpl_status ensure_tables(cpl_ctx *c, int lmax);
 cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out);
 cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st);
+cpl_status build_mixed_batch(cpl_ctx *c, const cpl_request *reqs, double *const *outs, int n, cudaStream_t st,
+                             bool use_graph);
 int stat_index(cpl_ctx *c, const char *name);
 void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes,
                    double issued = -1.0);

@@ -82,21 +82,28 @@ __host__ __device__ inline int mx_img_off(int r, int kk, int KB) {
 struct MxItem {
     int16_t pi, p;
     int16_t kb_lo, kb_hi;
-    int32_t tile;      // index into the intermediate buffer
+    int32_t tile;      // index into the job's intermediate buffer
     int16_t rg, b;
-    int16_t c, pad;
+    int16_t c, job;
 };
 static_assert(sizeof(MxItem) == 20, "MxItem layout");
 
-struct MxGemmArgs {
-    const uint8_t *Aimg, *Bimg;
-    const int16_t *eA, *emaxA;     // [pi][alpha][row_global][NSB], [pi][alpha][row_global]
-    const int16_t *eB, *emaxB;     // [pi][beta][j][NSB_B], [pi][beta][j]
-    const MxItem *items;
-    int n_items;
-    float *inter;                  // [tile][9][2][128 cols][128 rows]: hi then lo planes
-    int *err;                      // device error word (bounded waits)
+// Per-request data of one GEMM launch (a launch may serve a batch of requests).
+struct MxJob {
     MxLayout L;
+    const uint8_t *Aimg;
+    const int16_t *eA, *emaxA;     // [pi][alpha][row_global][NSB], [pi][alpha][row_global]
+    float *inter;                  // [tile][9][2 planes (hi, lo)][128 cols][128 rows], column-major
+};
+
+struct MxGemmArgs {
+    const MxJob *jobs;
+    const uint8_t *Bimg;           // shared, window-independent B images (one cache for all jobs)
+    const int16_t *eB, *emaxB;     // [pi][beta][j][NSB_B], [pi][beta][j]
+    const MxItem *items;           // in ticket order (see mixed_host.cu)
+    int n_items;
+    int *ticket;                   // next item to take; zero before the launch
+    int *err;                      // device error word (bounded waits)
 };
 
 struct MxPrepAArgs {
@@ -158,9 +165,10 @@ cudaError_t mx_launch_weights_dd(const double *A, int n_src, int a_stride, float
                                  cudaStream_t st);
 cudaError_t mx_launch_prep_a(const MxPrepAArgs &a, cudaStream_t st);
 cudaError_t mx_launch_prep_b(const MxPrepBArgs &a, int c_hi, cudaStream_t st);
-cudaError_t mx_launch_gemm(const MxGemmArgs &a, cudaStream_t st);
+cudaError_t mx_launch_gemm(const MxGemmArgs &a, int S, int grid, cudaStream_t st);
 cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st);
 cudaError_t mx_launch_band(const MxBandArgs &a, cudaStream_t st);
 size_t mx_gemm_smem_bytes(int S);
+cudaError_t mx_gemm_prepare(int S);   // shared-memory attribute; call before launching (not under capture)
 
 }  // namespace cpl

@@ -41,10 +41,12 @@ __device__ __forceinline__ void put_out(double *out, int lmax, int lmin, int nsp
     }
 }
 
+// i runs fastest across the threads of a block so that the reads of the
+// column-major GEMM output ([col][row]) are coalesced.
 __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
     const MxLayout &L = a.L;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
     const int pi = blockIdx.z;
     const int l1 = j - i, l2 = i + j + pi;
     if (l1 < max(a.lmin, MX_L1_FP64) || l2 > a.lmax || l1 > l2) return;
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
             S[p] = {0.f, 0.f, 0};
             if (p >= np || tile < 0) continue;
             const float *src = a.inter + ((long long)tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
-            const float hi = src[r * MX_BJ + cc], lo = src[MX_ROWS * MX_BJ + r * MX_BJ + cc];
+            const float hi = src[cc * MX_ROWS + r], lo = src[MX_ROWS * MX_BJ + cc * MX_ROWS + r];
             const int E = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
                           (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
             S[p] = xdf_make(df_quick(hi, lo), E);
@@ -128,15 +130,16 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
 }
 
 
-// Dense-output epilogue with coalesced writes.  One block covers a 4 x 64
-// block of (i, j) in both parities: 512 pairs, one per thread, whose rows of M
-// (fixed l1, l2 = l1 + d) and mirrored rows (fixed l2, l1 = l2 - d) are runs
-// of 8 consecutive elements.  Each thread forms its pair's 12 combination
+// Dense-output epilogue with coalesced writes.  One block covers an 8 x 32
+// block of (i, j) in both parities: 512 pairs, one per thread, i fastest (the
+// GEMM output is column-major, so 8 consecutive i are one 32-byte sector),
+// whose rows of M (fixed l1, l2 = l1 + d) and mirrored rows (fixed l2,
+// l1 = l2 - d) are runs of 16 consecutive elements.  Each thread forms its pair's 12 combination
 // coefficients once in extended double-float and keeps them in registers;
 // per row source it combines the contractions in one exponent frame per
 // spectrum, converts the (2 l2 + 1) and (2 l1 + 1) multiples to FP64 with
 // integer operations, and stages them in shared memory for row-wise writes.
-constexpr int EB_I = 4, EB_J = 64, EB_P = 2 * EB_I * EB_J, EB_T = EB_P;
+constexpr int EB_I = 8, EB_J = 32, EB_P = 2 * EB_I * EB_J, EB_T = EB_P;
 
 struct Term {
     dfl m;   // mantissa
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
     const int i0 = blockIdx.y * EB_I, j0 = blockIdx.x * EB_J;
     const int q = threadIdx.x;
     const int L1min = max(a.lmin, MX_L1_FP64);
-    const int pi = q / (EB_I * EB_J), ii = (q / EB_J) % EB_I, jj = q % EB_J;
+    const int pi = q / (EB_I * EB_J), jj = (q / EB_I) % EB_J, ii = q % EB_I;
     const int i = i0 + ii, j = j0 + jj;
     const int l1 = j - i, l2 = i + j + pi;
     const bool valid = !(l1 < L1min || l2 > a.lmax || l1 > l2);
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
                 Se[p] = 0;
                 if (p >= np || tile < 0) continue;
                 const float *src = a.inter + ((long long)tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
-                Sm[p] = dfl{src[r * MX_BJ + cc], src[MX_ROWS * MX_BJ + r * MX_BJ + cc]};
+                Sm[p] = dfl{src[cc * MX_ROWS + r], src[MX_ROWS * MX_BJ + cc * MX_ROWS + r]};
                 Se[p] = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
                         (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
             }
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
             }
         }
         __syncthreads();
-        // ---- rows: M[l1][l2 = l1 + d] and mirrored M[l2][l1 = l2 - d], d = 2 i0 .. 2 i0 + 7
+        // ---- rows: M[l1][l2 = l1 + d] and mirrored M[l2][l1 = l2 - d], d = 2 i0 .. 2 i0 + 2 EB_I - 1
         const int nrow = EB_I + EB_J;
         for (int x = 0; x < 5; ++x) {
             if (!(role & bits[x]) || a.slot[x] < 0) continue;
@@ -288,7 +291,7 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
                 const int ejj = el1 + ei - j0;
                 if (ejj < 0 || ejj >= EB_J) continue;
                 if (el1 < L1min || el2 > a.lmax || el1 > el2) continue;
-                const int pq = (epi * EB_I + eii) * EB_J + ejj;
+                const int pq = (epi * EB_J + ejj) * EB_I + eii;
                 if (!mirror) base[(size_t)(el1 - a.lmin) * n + (el2 - a.lmin)] = stage[x][0][pq];
                 else if (el1 != el2) base[(size_t)(el2 - a.lmin) * n + (el1 - a.lmin)] = stage[x][1][pq];
             }
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
 cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st) {
     const int NI = a.L.NB * a.L.BI;
     if (a.n_bins > 0) {
-        dim3 grid((a.lmax + 1 + 127) / 128, NI, 2);
+        dim3 grid((NI + 127) / 128, a.lmax + 1, 2);
         k_mixed_epilogue<<<grid, 128, 0, st>>>(a);
         return cudaGetLastError();
     }

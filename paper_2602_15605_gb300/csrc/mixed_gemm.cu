@@ -1,8 +1,14 @@
 // mixed_gemm.cu -- the tcgen05 limb GEMM of the mixed-precision path.
 //
-// One CTA per work item (parity, contraction p, row group, i-block, j-block):
+// A work item is one (job, parity, contraction p, row group, i-block, j-block):
 //   C[r, c] = sum_k x[r, k] y[c, k]   (128 x 128 output, k over the item's range)
-// with x, y given as S BF16 fixed-point limbs per element (mixed.h).
+// with x, y given as S BF16 fixed-point limbs per element (mixed.h).  The
+// kernel is persistent: each CTA takes the next item of a list with an
+// atomic ticket (the producer lane draws it and passes it to the MMA and
+// drain roles through a 4-slot ring in shared memory), keeps one TMEM
+// allocation and carries its pipeline counters across items, so one launch
+// serves a whole batch of requests (MxJob) and the write-out of an item
+// overlaps the MMAs of the next.
 //
 // Warp roles (18 warps):
 //   warp 0      producer: one elected lane streams the KB-k tile images of
@@ -106,8 +112,12 @@ __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t ad, uint64_t bd, 
                    "=r"(r[7])                                                                      \
                  : "r"(addr))
 
+constexpr int TQ = 4;                      // ticket ring slots
+
 struct Shared {
     uint64_t full[3], empty[3], acc_full, acc_empty, done;
+    uint64_t tfull[TQ], tempty[TQ];
+    int tick[TQ];
     uint32_t tmem;
     int abort;          // set by any role on a timed-out wait
     int dabort;         // drain-local copy, written only before the drain barrier
@@ -124,14 +134,8 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
     constexpr int KPS = MX_SB / KB;              // k blocks per scale block
     constexpr uint32_t STAGE = 2u * S * IMG;
     float *Ls = reinterpret_cast<float *>(dsm + NST * STAGE);   // [128 cols][LPAD]
-    float *Hs = reinterpret_cast<float *>(dsm);                 // reuses the stages at the end
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const MxItem it = a.items[blockIdx.x];
-    const MxLayout &L = a.L;
-    const int pi = it.pi, p = it.p;
-    const int alpha = mx_alpha(p), beta = mx_beta(p);
-    const int kb_lo = it.kb_lo, kb_hi = it.kb_hi;
     const uint32_t s_full0 = smem_u32(&sh.full[0]), s_empty0 = smem_u32(&sh.empty[0]);
     const uint32_t s_accf = smem_u32(&sh.acc_full), s_acce = smem_u32(&sh.acc_empty), s_done = smem_u32(&sh.done);
 
@@ -148,6 +152,10 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
         mbar_init(s_accf, 1);
         mbar_init(s_acce, 16);
         mbar_init(s_done, 1);
+        for (int q = 0; q < TQ; ++q) {
+            mbar_init(smem_u32(&sh.tfull[q]), 1);
+            mbar_init(smem_u32(&sh.tempty[q]), 2);   // MMA lane + drain
+        }
         sh.abort = 0;
         sh.dabort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -159,30 +167,49 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
     const uint32_t tmem = sh.tmem;
     const uint32_t stage_base = smem_u32(dsm);
 
+    // Every role takes the items in ticket order and keeps its pipeline
+    // counters running across items, so the mbarrier phases stay in step.
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            const uint8_t *Ab = a.Aimg + mx_a_off(L, pi, alpha, it.rg, it.b, L.fA * it.b, 0);
             int n = 0;
-            for (int kb = kb_lo; kb <= kb_hi; ++kb, ++n) {
-                if (*(volatile int *)&sh.abort) break;
-                const int s = n % NST, u = n / NST;
-                if (u > 0 && !mbar_wait(s_empty0 + 8 * s, (u - 1) & 1)) {
-                    atomicExch(a.err, 11);
+            for (int nt = 0; !*(volatile int *)&sh.abort; ++nt) {
+                // draw a ticket and publish it
+                const int ts = nt % TQ;
+                if (nt >= TQ && !mbar_wait(smem_u32(&sh.tempty[ts]), ((nt / TQ) - 1) & 1)) {
+                    atomicExch(a.err, 17);
                     sh.abort = 1;
                     break;
                 }
-                const uint32_t fb = s_full0 + 8 * s;
-                mbar_expect_tx(fb, STAGE);
-                const uint8_t *asrc = Ab + (long long)(kb - L.fA * it.b) * S * IMG;
-                const uint8_t *bsrc = a.Bimg + mx_b_off(L, pi, beta, it.c, kb, 0);
-                const uint32_t dst = stage_base + s * STAGE;
-                bulk_g2s(dst, asrc, S * IMG, fb);
-                bulk_g2s(dst + S * IMG, bsrc, S * IMG, fb);
+                int w = atomicAdd(a.ticket, 1);
+                if (w >= a.n_items) w = -1;
+                sh.tick[ts] = w;
+                mbar_arrive(smem_u32(&sh.tfull[ts]));
+                if (w < 0) break;
+                const MxItem it = a.items[w];
+                const MxJob &J = a.jobs[it.job];
+                const MxLayout &L = J.L;
+                const int alpha = mx_alpha(it.p), beta = mx_beta(it.p);
+                const uint8_t *Ab = J.Aimg + mx_a_off(L, it.pi, alpha, it.rg, it.b, L.fA * it.b, 0);
+                for (int kb = it.kb_lo; kb <= it.kb_hi; ++kb, ++n) {
+                    if (*(volatile int *)&sh.abort) break;
+                    const int s = n % NST, u = n / NST;
+                    if (u > 0 && !mbar_wait(s_empty0 + 8 * s, (u - 1) & 1)) {
+                        atomicExch(a.err, 11);
+                        sh.abort = 1;
+                        break;
+                    }
+                    const uint32_t fb = s_full0 + 8 * s;
+                    mbar_expect_tx(fb, STAGE);
+                    const uint8_t *asrc = Ab + (long long)(kb - L.fA * it.b) * S * IMG;
+                    const uint8_t *bsrc = a.Bimg + mx_b_off(L, it.pi, beta, it.c, kb, 0);
+                    const uint32_t dst = stage_base + s * STAGE;
+                    bulk_g2s(dst, asrc, S * IMG, fb);
+                    bulk_g2s(dst + S * IMG, bsrc, S * IMG, fb);
+                }
             }
             // wait (bounded) for the copies still in flight before the CTA may exit
-            const int issued = n;
-            for (int q = issued - NST; q < issued; ++q) {
+            for (int q = n - NST; q < n; ++q) {
                 if (q < 0) continue;
                 if (!mbar_wait(s_full0 + 8 * (q % NST), (q / NST) & 1)) atomicExch(a.err, 12);
             }
@@ -194,45 +221,57 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                                    ((uint32_t)(MX_ROWS >> 4) << 24);
             int n = 0, m = 0;
             bool started[4] = {false, false, false, false};
-            for (int kb = kb_lo; kb <= kb_hi; ++kb, ++n) {
-                if (*(volatile int *)&sh.abort) break;
-                const bool sfirst = (kb == kb_lo) || (kb % KPS == 0);
-                const bool slast = (kb == kb_hi) || (kb % KPS == KPS - 1);
-                if (sfirst) {
-                    if (m > 0 && !mbar_wait(s_acce, (m - 1) & 1)) {
-                        atomicExch(a.err, 13);
-                        sh.abort = 1;
-                        break;
-                    }
-                    started[0] = started[1] = started[2] = started[3] = false;
-                }
-                const int s = n % NST;
-                if (!mbar_wait(s_full0 + 8 * s, (n / NST) & 1)) {
-                    atomicExch(a.err, 14);
+            for (int nt = 0; !*(volatile int *)&sh.abort; ++nt) {
+                const int ts = nt % TQ;
+                if (!mbar_wait(smem_u32(&sh.tfull[ts]), (nt / TQ) & 1)) {
+                    atomicExch(a.err, 18);
                     sh.abort = 1;
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t abase = stage_base + s * STAGE;
-                const uint32_t bbase = abase + S * IMG;
+                const int w = *(volatile int *)&sh.tick[ts];
+                mbar_arrive(smem_u32(&sh.tempty[ts]));
+                if (w < 0) break;
+                const MxItem it = a.items[w];
+                for (int kb = it.kb_lo; kb <= it.kb_hi; ++kb, ++n) {
+                    if (*(volatile int *)&sh.abort) break;
+                    const bool sfirst = (kb == it.kb_lo) || (kb % KPS == 0);
+                    const bool slast = (kb == it.kb_hi) || (kb % KPS == KPS - 1);
+                    if (sfirst) {
+                        if (m > 0 && !mbar_wait(s_acce, (m - 1) & 1)) {
+                            atomicExch(a.err, 13);
+                            sh.abort = 1;
+                            break;
+                        }
+                        started[0] = started[1] = started[2] = started[3] = false;
+                    }
+                    const int s = n % NST;
+                    if (!mbar_wait(s_full0 + 8 * s, (n / NST) & 1)) {
+                        atomicExch(a.err, 14);
+                        sh.abort = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t abase = stage_base + s * STAGE;
+                    const uint32_t bbase = abase + S * IMG;
 #pragma unroll
-                for (int k16 = 0; k16 < KB / 16; ++k16) {
+                    for (int k16 = 0; k16 < KB / 16; ++k16) {
 #pragma unroll
-                    for (int t = 0; t < S; ++t) {
+                        for (int t = 0; t < S; ++t) {
 #pragma unroll
-                        for (int u = 0; u + t < S; ++u) {
-                            const int acc = (t + u) < 3 ? (t + u) : 3;
-                            const uint64_t ad = umma_desc<KB>(abase + t * IMG + k16 * 256);
-                            const uint64_t bd = umma_desc<KB>(bbase + u * IMG + k16 * 256);
-                            umma(tmem + acc * MX_BJ, ad, bd, idesc, started[acc] ? 1u : 0u);
-                            started[acc] = true;
+                            for (int u = 0; u + t < S; ++u) {
+                                const int acc = (t + u) < 3 ? (t + u) : 3;
+                                const uint64_t ad = umma_desc<KB>(abase + t * IMG + k16 * 256);
+                                const uint64_t bd = umma_desc<KB>(bbase + u * IMG + k16 * 256);
+                                umma(tmem + acc * MX_BJ, ad, bd, idesc, started[acc] ? 1u : 0u);
+                                started[acc] = true;
+                            }
                         }
                     }
-                }
-                umma_commit(s_empty0 + 8 * s);
-                if (slast) {
-                    umma_commit(s_accf);
-                    ++m;
+                    umma_commit(s_empty0 + 8 * s);
+                    if (slast) {
+                        umma_commit(s_accf);
+                        ++m;
+                    }
                 }
             }
             // all issued MMAs complete before TMEM is released
@@ -247,101 +286,116 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
         const int q = warp & 3, quarter = dw >> 2;
         const int row = 32 * q + lane, c0 = 32 * quarter;
         const int dtid = tid - 64;               // 0..511
-        const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
-        const long long ncols = (long long)L.NC_B * MX_BJ;
-        const long long rowg = ((long long)it.rg * L.NB + it.b) * MX_ROWS + row;
-        const int16_t *eArow = a.eA + (((long long)pi * MX_NA + alpha) * nrows + rowg) * L.NSB;
-        const int emA = a.emaxA[((long long)pi * MX_NA + alpha) * nrows + rowg];
-        const int j0 = it.c * MX_BJ;
-        const int16_t *eBcol = a.eB + ((long long)pi * MX_NBV + beta) * ncols * L.NSB_B;
-        const int16_t *emB = a.emaxB + ((long long)pi * MX_NBV + beta) * ncols;
-        // running sum per element: high part in registers, low part (left
-        // unnormalised until the end) in shared memory
-        float H[32];
-#pragma unroll
-        for (int x = 0; x < 32; ++x) H[x] = 0.f;
-        for (int x = 0; x < 32; ++x) Ls[(c0 + x) * LPAD + row] = 0.f;
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
         int m = 0;
-        for (int kb = kb_lo; kb <= kb_hi; ++kb) {
-            const bool slast = (kb == kb_hi) || (kb % KPS == KPS - 1);
-            if (!slast) continue;
-            const int sb = kb / KPS;
-            if (dtid < MX_BJ) {
-                const int j = j0 + dtid;
-                sh.ecol[dtid] = (int16_t)max(-32000, (int)eBcol[(long long)j * L.NSB_B + sb] - (int)emB[j]);
-            }
-            const int eAr = (int)eArow[sb] - emA;
-            const bool ok = !*(volatile int *)&sh.abort && mbar_wait(s_accf, m & 1);
-            if (!ok) sh.dabort = 1;
-            // (A): column exponents visible; the abort decision is the same for all drain threads
+        for (int nt = 0;; ++nt) {
+            const int ts = nt % TQ;
+            const bool tok = !*(volatile int *)&sh.abort && mbar_wait(smem_u32(&sh.tfull[ts]), (nt / TQ) & 1);
+            if (!tok) sh.dabort = 1;
+            const int w = *(volatile int *)&sh.tick[ts];
+            // (T): every drain thread has read the ticket; the abort decision is uniform
             asm volatile("bar.sync 1, 512;" ::: "memory");
             if (*(volatile int *)&sh.dabort) {
                 if (dtid == 0) {
-                    atomicExch(a.err, 16);
+                    atomicExch(a.err, 19);
                     sh.abort = 1;
                 }
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+            if (w < 0) break;
+            if (dtid == 0) mbar_arrive(smem_u32(&sh.tempty[ts]));
+            bool stop = false;
+            const MxItem it = a.items[w];
+            const MxJob &J = a.jobs[it.job];
+            const MxLayout &L = J.L;
+            const int alpha = mx_alpha(it.p), beta = mx_beta(it.p);
+            const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
+            const long long ncols = (long long)L.NC_B * MX_BJ;
+            const long long rowg = ((long long)it.rg * L.NB + it.b) * MX_ROWS + row;
+            const int16_t *eArow = J.eA + (((long long)it.pi * MX_NA + alpha) * nrows + rowg) * L.NSB;
+            const int emA = J.emaxA[((long long)it.pi * MX_NA + alpha) * nrows + rowg];
+            const int j0 = it.c * MX_BJ;
+            const int16_t *eBcol = a.eB + ((long long)it.pi * MX_NBV + beta) * ncols * L.NSB_B;
+            const int16_t *emB = a.emaxB + ((long long)it.pi * MX_NBV + beta) * ncols;
+            // running sum per element: high part in registers, low part (left
+            // unnormalised until the end) in shared memory; each thread owns
+            // its 32 cells of Ls, so no barrier is needed around the reset
+            float H[32];
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                uint32_t r0[8], r1[8], r2[8], r3[8];
-                const uint32_t col = (uint32_t)(c0 + 8 * g);
-                TMEM_LD8(lane_addr + col, r0);
-                TMEM_LD8(lane_addr + MX_BJ + col, r1);
-                TMEM_LD8(lane_addr + 2 * MX_BJ + col, r2);
-                TMEM_LD8(lane_addr + 3 * MX_BJ + col, r3);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int x = 0; x < 8; ++x) {
-                    const int cc = c0 + 8 * g + x;
-                    const int d = eAr + (int)sh.ecol[cc];
-                    if (d < -252) continue;
-                    // block value: orders 0 and 1 exactly (two-sum), then 2 and >= 3
-                    dfl v = df_two_sum(__uint_as_float(r0[x]), __uint_as_float(r1[x]));
-                    v.l += __uint_as_float(r2[x]);
-                    v.l += __uint_as_float(r3[x]);
-                    float vh, vl;
-                    if (d >= -126) {
-                        const float f = pow2f(d);
-                        vh = v.h * f;
-                        vl = v.l * f;
-                    } else {
-                        vh = scale2(v.h, d);
-                        vl = scale2(v.l, d);
-                    }
-                    const dfl z = df_two_sum(H[8 * g + x], vh);
-                    H[8 * g + x] = z.h;
-                    Ls[cc * LPAD + row] += z.l + vl;
+            for (int x = 0; x < 32; ++x) H[x] = 0.f;
+            for (int x = 0; x < 32; ++x) Ls[(c0 + x) * LPAD + row] = 0.f;
+            for (int kb = it.kb_lo; kb <= it.kb_hi; ++kb) {
+                const bool slast = (kb == it.kb_hi) || (kb % KPS == KPS - 1);
+                if (!slast) continue;
+                const int sb = kb / KPS;
+                if (dtid < MX_BJ) {
+                    const int j = j0 + dtid;
+                    sh.ecol[dtid] = (int16_t)max(-32000, (int)eBcol[(long long)j * L.NSB_B + sb] - (int)emB[j]);
                 }
+                const int eAr = (int)eArow[sb] - emA;
+                const bool ok = !*(volatile int *)&sh.abort && mbar_wait(s_accf, m & 1);
+                if (!ok) sh.dabort = 1;
+                // (A): column exponents visible; the abort decision is the same for all drain threads
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                if (*(volatile int *)&sh.dabort) {
+                    if (dtid == 0) {
+                        atomicExch(a.err, 16);
+                        sh.abort = 1;
+                    }
+                    stop = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t r0[8], r1[8], r2[8], r3[8];
+                    const uint32_t col = (uint32_t)(c0 + 8 * g);
+                    TMEM_LD8(lane_addr + col, r0);
+                    TMEM_LD8(lane_addr + MX_BJ + col, r1);
+                    TMEM_LD8(lane_addr + 2 * MX_BJ + col, r2);
+                    TMEM_LD8(lane_addr + 3 * MX_BJ + col, r3);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) {
+                        const int cc = c0 + 8 * g + x;
+                        const int d = eAr + (int)sh.ecol[cc];
+                        if (d < -252) continue;
+                        // block value: orders 0 and 1 exactly (two-sum), then 2 and >= 3
+                        dfl v = df_two_sum(__uint_as_float(r0[x]), __uint_as_float(r1[x]));
+                        v.l += __uint_as_float(r2[x]);
+                        v.l += __uint_as_float(r3[x]);
+                        float vh, vl;
+                        if (d >= -126) {
+                            const float f = pow2f(d);
+                            vh = v.h * f;
+                            vl = v.l * f;
+                        } else {
+                            vh = scale2(v.h, d);
+                            vl = scale2(v.l, d);
+                        }
+                        const dfl z = df_two_sum(H[8 * g + x], vh);
+                        H[8 * g + x] = z.h;
+                        Ls[cc * LPAD + row] += z.l + vl;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(s_acce);
+                // (B): every drain thread is done with the column exponents
+                asm volatile("bar.sync 1, 512;" ::: "memory");
+                ++m;
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(s_acce);
-            // (B): every drain thread is done with the column exponents
-            asm volatile("bar.sync 1, 512;" ::: "memory");
-            ++m;
-        }
-        // ---- write the element sums: hi plane and lo plane, [row][col] in global
-        if (!*(volatile int *)&sh.dabort) {
+            if (stop) break;
+            // ---- write the element sums, column-major: [plane][col][row]; per
+            // column the 32 lanes of a warp store 32 consecutive rows.  The
+            // accumulators are already released, so the MMA of the next item
+            // runs meanwhile.
+            float *dst = J.inter + ((long long)it.tile * MX_NPROD + it.p) * 2 * (MX_ROWS * MX_BJ);
 #pragma unroll
             for (int x = 0; x < 32; ++x) {
-                const dfl w = df_quick(H[x], Ls[(c0 + x) * LPAD + row]);
-                H[x] = w.h;
-                Ls[(c0 + x) * LPAD + row] = w.l;
-            }
-            // the producer / MMA are done with the stage buffers once the last
-            // block was drained; reuse them for the transposed hi plane
-            asm volatile("bar.sync 1, 512;" ::: "memory");
-#pragma unroll
-            for (int x = 0; x < 32; ++x) Hs[(c0 + x) * LPAD + row] = H[x];
-            asm volatile("bar.sync 1, 512;" ::: "memory");
-            float *dst = a.inter + ((long long)it.tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
-            for (int idx = dtid; idx < MX_ROWS * MX_BJ; idx += 512) {
-                const int r = idx / MX_BJ, cc = idx % MX_BJ;
-                dst[idx] = Hs[cc * LPAD + r];
-                dst[MX_ROWS * MX_BJ + idx] = Ls[cc * LPAD + r];
+                const dfl v = df_quick(H[x], Ls[(c0 + x) * LPAD + row]);
+                dst[(c0 + x) * MX_ROWS + row] = v.h;
+                dst[MX_ROWS * MX_BJ + (c0 + x) * MX_ROWS + row] = v.l;
             }
         }
     }
@@ -359,28 +413,25 @@ size_t mx_gemm_smem_bytes(int S) {
     return (size_t)mx_stages(S) * 2 * S * mx_img_bytes(S) + (size_t)MX_BJ * LPAD * sizeof(float);
 }
 
-cudaError_t mx_launch_gemm(const MxGemmArgs &a, cudaStream_t st) {
+cudaError_t mx_gemm_prepare(int S) {
+    const int smem = (int)mx_gemm_smem_bytes(S);
+    switch (S) {
+        case 4: return cudaFuncSetAttribute(k_mixed_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 5: return cudaFuncSetAttribute(k_mixed_gemm<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        case 6: return cudaFuncSetAttribute(k_mixed_gemm<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t mx_launch_gemm(const MxGemmArgs &a, int S, int grid, cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
-    const size_t smem = mx_gemm_smem_bytes(a.L.S);
-    cudaError_t e;
-    switch (a.L.S) {
-        case 4:
-            e = cudaFuncSetAttribute(k_mixed_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            k_mixed_gemm<4><<<a.n_items, NTH, smem, st>>>(a);
-            break;
-        case 5:
-            e = cudaFuncSetAttribute(k_mixed_gemm<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            k_mixed_gemm<5><<<a.n_items, NTH, smem, st>>>(a);
-            break;
-        case 6:
-            e = cudaFuncSetAttribute(k_mixed_gemm<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            k_mixed_gemm<6><<<a.n_items, NTH, smem, st>>>(a);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+    if (grid <= 0 || grid > a.n_items) grid = a.n_items;
+    const size_t smem = mx_gemm_smem_bytes(S);
+    switch (S) {
+        case 4: k_mixed_gemm<4><<<grid, NTH, smem, st>>>(a); break;
+        case 5: k_mixed_gemm<5><<<grid, NTH, smem, st>>>(a); break;
+        case 6: k_mixed_gemm<6><<<grid, NTH, smem, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
