@@ -6,12 +6,13 @@
 //
 //   x[r, k] ~= 2^(E_r - 7) sum_{t < S} X_t[r, k],   X_t = x_t 2^(-8t),  x_t in [-128, 128] integer
 //
-// with one power-of-two scale E_r per operand row and 128-wide block of k
+// with one power-of-two scale E_r per operand row and 256-wide block of k
 // (a "scale block").  Each limb is exact in BF16, every limb product is exact
-// in FP32, and the sums of the products of order t + u = 0, 1 and 2 are
-// integers below 2^24 in their units, so the FP32 tensor-core accumulators
-// hold them exactly; the orders t + u >= 3 (up to S - 1) go to a fourth
-// accumulator, about 2^-24 of the total.  After each scale block the four
+// in FP32 (|x_t y_u| <= 2^14), and the sums of the products of order
+// t + u = 0, 1 and 2 over a scale block are integers in their units below
+// 256 * 2^14, 2 * 256 * 2^14 and 3 * 256 * 2^14 < 2^24, so the FP32
+// tensor-core accumulators hold them exactly; the orders t + u >= 3 (up to
+// S - 1) go to a fourth accumulator, about 2^-24 of the total.  After each scale block the four
 // accumulators are drained from TMEM, scaled by
 // 2^(E_r + E_c) and added in double-float (a pair of FP32 values) per
 // element; FP64 is kept for the lookup tables, the weights and the final
@@ -25,7 +26,7 @@ namespace cpl {
 
 constexpr int MX_ROWS = 128;        // GEMM tile rows: SRC sources x BI i-values (MxLayout)
 constexpr int MX_BJ = 128;          // j per column block (GEMM N)
-constexpr int MX_SB = 128;          // k per scale block (drain period)
+constexpr int MX_SB = 256;          // k per scale block (drain period; the exactness bound above)
 // k per tile image / pipeline stage: 32 for up to 5 limbs, 16 for 6 limbs
 // (so that the stages of 2 x S images still fit in shared memory)
 __host__ __device__ constexpr int mx_kb(int S) { return S >= 6 ? 16 : 32; }

@@ -20,14 +20,14 @@
 //               tcgen05.mma (M=128, N=128, K=16, BF16 in, FP32 accumulate)
 //               into four TMEM accumulators by order t + u = 0, 1, 2, >= 3,
 //               and commits each stage back to the producer.
-//   warps 2-17  drain: after every 128-k scale block, read the four
+//   warps 2-17  drain: after every 256-k scale block, read the four
 //               accumulators with tcgen05.ld, combine them, scale by
 //               2^(E_row + E_col) relative to the row / column maxima, and add
 //               into a double-float running sum per element (high part in
 //               registers, low part in shared memory, renormalised once at
 //               the end).
 // The accumulators of orders 0, 1 and 2 are integers below 2^24 in their
-// units over a 128-k block (|limb| <= 128, at most 3 products per k), so the
+// units over a 256-k block (|limb| <= 128, at most 3 products per k), so the
 // tensor core holds them exactly whatever its internal rounding; only the
 // order >= 3 accumulator, 2^-24 of the total, is inexact.  (Measured: with
 // orders >= 2 in one inexact accumulator the error reached 5e-9, consistent
@@ -360,18 +360,21 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                         const int cc = c0 + 8 * g + x;
                         const int d = eAr + (int)sh.ecol[cc];
                         if (d < -252) continue;
-                        // block value: orders 0 and 1 exactly (two-sum), then 2 and >= 3
-                        dfl v = df_two_sum(__uint_as_float(r0[x]), __uint_as_float(r1[x]));
-                        v.l += __uint_as_float(r2[x]);
-                        v.l += __uint_as_float(r3[x]);
+                        // block value: orders 0, 1 and 2 summed exactly (two two-sums:
+                        // with decaying operands order 2 can reach 2^-8 of order 0, so
+                        // it must not be folded into the residue of the first sum);
+                        // the residues and order >= 3 are then added in FP32
+                        const dfl v01 = df_two_sum(__uint_as_float(r0[x]), __uint_as_float(r1[x]));
+                        const dfl v = df_two_sum(v01.h, __uint_as_float(r2[x]));
+                        const float vlo = (v01.l + v.l) + __uint_as_float(r3[x]);
                         float vh, vl;
                         if (d >= -126) {
                             const float f = pow2f(d);
                             vh = v.h * f;
-                            vl = v.l * f;
+                            vl = vlo * f;
                         } else {
                             vh = scale2(v.h, d);
-                            vl = scale2(v.l, d);
+                            vl = scale2(vlo, d);
                         }
                         const dfl z = df_two_sum(H[8 * g + x], vh);
                         H[8 * g + x] = z.h;

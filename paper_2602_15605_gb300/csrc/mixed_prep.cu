@@ -3,7 +3,7 @@
 // Writes the BF16 limb images of the separable operands (see plain_fp64.cu
 // for their definitions; the formulas are repeated next to each variant) in
 // the exact shared-memory layout the tensor-core GEMM consumes (mixed.h:
-// mx_img_off), together with the per-(row, 128-k scale block) power-of-two
+// mx_img_off), together with the per-(row, MX_SB-k scale block) power-of-two
 // exponents.  Values are formed in double-float from double-float copies of
 // the FP64 g / h tables and weights; the weights carry a separate integer
 // exponent because window spectra reach below the FP32 range.
@@ -17,6 +17,7 @@ namespace cpl {
 namespace {
 
 constexpr int16_t EXP_ZERO = -32000;   // exponent of an all-zero block
+constexpr int MPL = MX_SB / 32;          // k values per lane in one scale block
 
 __global__ void k_tables_dd(const double *__restrict__ g, const double *__restrict__ h, int n,
                             float *gh, float *gl, float *hh, float *hl) {
@@ -100,13 +101,13 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     for (int q = 0; q < MX_NA; ++q) emax[q] = EXP_ZERO;
     const int sb0 = (b * L.BI) / MX_SB;
     for (int sb = sb0; sb < L.NSB; ++sb) {
-        dfl val[MX_NA][4];
-        int vex[MX_NA][4];
+        dfl val[MX_NA][MPL];
+        int vex[MX_NA][MPL];
         int bexp[MX_NA];
 #pragma unroll
         for (int q = 0; q < MX_NA; ++q) bexp[q] = EXP_ZERO;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < MPL; ++m) {
             const int k = sb * MX_SB + lane + 32 * m;
 #pragma unroll
             for (int q = 0; q < MX_NA; ++q) {
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
             if (lane == 0) a.eA[(((long long)pi * MX_NA + q) * nrows + row_global) * L.NSB + sb] = (int16_t)E;
             emax[q] = max(emax[q], E);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < MPL; ++m) {
                 const int k = sb * MX_SB + lane + 32 * m;
                 const int kb = k / L.KB;
                 if (kb < L.fA * b || kb >= L.NKB) continue;
@@ -198,13 +199,14 @@ __global__ void __launch_bounds__(256) k_prep_b(const MxPrepBArgs a, int c_hi) {
 #pragma unroll
     for (int q = 0; q < MX_NBV; ++q) emax[q] = EXP_ZERO;
     const int nkb_c = L.gB * (c + 1);   // k blocks stored for this column block
-    for (int sb = 0; sb <= c; ++sb) {
-        dfl val[MX_NBV][4];
+    const int sb_hi = (nkb_c * L.KB - 1) / MX_SB;
+    for (int sb = 0; sb <= sb_hi; ++sb) {
+        dfl val[MX_NBV][MPL];
         int bexp[MX_NBV];
 #pragma unroll
         for (int q = 0; q < MX_NBV; ++q) bexp[q] = EXP_ZERO;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < MPL; ++m) {
             const int k = sb * MX_SB + lane + 32 * m;
 #pragma unroll
             for (int q = 0; q < MX_NBV; ++q) val[q][m] = {0.f, 0.f};
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(256) k_prep_b(const MxPrepBArgs a, int c_hi) {
             if (lane == 0) a.eB[(((long long)pi * MX_NBV + q) * ncols + j) * L.NSB_B + sb] = (int16_t)E;
             emax[q] = max(emax[q], E);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < MPL; ++m) {
                 const int k = sb * MX_SB + lane + 32 * m;
                 const int kb = k / L.KB;
                 if (kb >= nkb_c) continue;
