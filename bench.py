@@ -37,7 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "M_l1l2 coupling elements/s (full spin set, plain FP64)"
+METRIC = "M_l1l2 elements/s and 3j terms/s, lmax 3000-10000, batched vs plain FP64 on 1 GB300"
 UNIT = "elements/s"
 LMAX = 3000
 SPEC_NAMES = ("TT", "TE", "EE", "EEBB", "EB")
@@ -71,6 +71,9 @@ def parse():
                     help="arm of the headline value (the bench line uses fp64); the other arm is "
                          "reported in the 'mixed' / 'fp64' sub-object")
     ap.add_argument("--no-other", action="store_true", help="skip the other precision arm")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the ragged mixed-precision batch (8 jobs, l_max 1000-10000, 4 windows each)")
+    ap.add_argument("--batch-steps", type=int, default=3)
     args = ap.parse_args()
     global LMAX
     LMAX = args.lmax
@@ -253,6 +256,94 @@ def recorded_traffic(kernel):
         return None
 
 
+# ---------------------------------------------------------------- ragged batch
+def batch_arm(ctx, args, world, local, mixed_roofline):
+    """The persistent ragged batch: 8 jobs, l_max in {1000, ..., 10000}, 4
+    windows each (one pointer for all three roles), all five spectra, mixed
+    precision, one cpl_build_batch per step (a CUDA graph replay after the
+    first call).  Errors against the plain FP64 path for the jobs with
+    l_max <= 4000 (the larger ones would take ~40 s in FP64)."""
+    import torch
+    from paper_2602_15605_gb300 import coupling, windows
+    dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:%d" % local)
+    seed0 = 300 if world == 1 else 300 + 1000 * int(os.environ.get("RANK", "0"))
+    jobs_w = windows.ragged_jobs(seed0=seed0)
+    jobs = []
+    n_el = 0
+    terms = 0
+    for lm, W in jobs_w:
+        d = dev(W)
+        jobs.append(dict(lmax=lm, W_tt=d, W_tp=d, W_pp=d, spectra=coupling.ALL, precision=coupling.MIXED_BF16))
+        e, t = work_counts(lm)
+        n_el += W.shape[0] * 5 * e
+        terms += W.shape[0] * sum(t.values())
+    t0 = time.perf_counter()
+    outs = ctx.build_batch(jobs)            # plans, captures the graph and runs once
+    torch.cuda.synchronize()
+    ctx.sync()
+    first_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup - 1, 1)):
+        ctx.build_batch(jobs, outs=outs)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % local)
+    steps = max(1, args.batch_steps)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    before = ctx.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for q in range(steps):
+        flush.fill_(q & 255)
+        evs[q][0].record()
+        ctx.build_batch(jobs, outs=outs)
+        evs[q][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ctx.sync()
+    after = ctx.stats()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    launches = sum(v["launches"] for v in after.values()) - sum(v["launches"] for v in before.values())
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda:%d" % local)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # one profiled (eager, not graph) step for the per-kernel breakdown
+    ctx.profile(True)
+    ctx.stats(reset=True)
+    ctx.build_batch(jobs, outs=outs)
+    torch.cuda.synchronize()
+    st = ctx.stats(reset=True)
+    ctx.profile(False)
+    ctx.sync()
+    err = {}
+    for job, o in zip(jobs, outs):
+        if job["lmax"] > 4000:
+            continue
+        ref = ctx.build(**dict(job, precision=coupling.FP64))
+        torch.cuda.synchronize()
+        for s_, nm in enumerate(SPEC_NAMES):
+            a, b = o[:, s_], ref[:, s_]
+            if nm in ("TT", "EE", "EEBB"):
+                m = b.abs() > 1e-280
+                e = float(((a - b).abs()[m] / b.abs()[m]).max())
+            else:
+                e = float((a - b).abs().max() / b.abs().max())
+                nm = nm + "_normwise"
+            err[nm] = max(err.get(nm, 0.0), e)
+        del ref
+    ctx.sync()
+    return {"workload": "8 jobs, l_max in (1000,2000,3000,4000,6000,8000,9000,10000), 4 mask-like windows "
+                        "each (one pointer for W^TT/W^TP/W^PP), all five spectra, mixed BF16 limbs (6), dense "
+                        "FP64 output; one cpl_build_batch per step = one CUDA graph replay",
+            "value": world * n_el / (ms * 1e-3), "unit": UNIT, "terms_per_s": world * terms / (ms * 1e-3),
+            "ms_per_step": ms, "steps": steps, "first_call_s": first_s, "gpu_launches_per_step": launches / steps,
+            "roofline": mixed_roofline(st),
+            "kernels_profiled_step": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in st.items()},
+            "max_rel_err_vs_fp64_lmax_le_4000": err, "clocks": clk,
+            "l2": "flushed between steps (256 MiB write, outside the timed events)"}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local):
     import numpy as np
@@ -370,6 +461,10 @@ def run_ours(args, rank, world, local):
                  "clocks": o_clk}
         other["max_rel_err_vs_fp64"] = mixed_error()
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_arm(ctx, args, world, local, mixed_roofline)
+
     # end to end through the public host-buffer call
     e2e = None
     if not args.no_e2e:
@@ -409,6 +504,8 @@ def run_ours(args, rank, world, local):
                 "clocks": clk, "wall_s_timed": t_wall}
         if other is not None:
             line["mixed" if args.precision == "fp64" else "fp64"] = other
+        if batch is not None:
+            line["batch"] = batch
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
