@@ -176,11 +176,16 @@ def oracle_rate(Wt, Wc, Wp, seconds, seed=7):
     import oracle
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(seed)
-    cal = rng.integers(2, LMAX + 1, size=(max(64, 8 * threads), 2)).astype(np.int32)
-    t0 = time.perf_counter()
-    oracle.coupling_pairs(cal[:, 0], cal[:, 1], Wt, Wc, Wp, 31, threads=threads)
-    dt = max(time.perf_counter() - t0, 1e-6)
-    n = int(max(cal.shape[0], min(2_000_000, cal.shape[0] * seconds / dt)))
+    # two calibration passes (the first also pays for thread start-up, the
+    # second runs about a second), then a sample sized for `seconds`
+    def rate_of(n):
+        cal = rng.integers(2, LMAX + 1, size=(n, 2)).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.coupling_pairs(cal[:, 0], cal[:, 1], Wt, Wc, Wp, 31, threads=threads)
+        return n / max(time.perf_counter() - t0, 1e-6)
+    r = rate_of(max(64, 8 * threads))
+    r = rate_of(int(min(6_000_000, max(64, r * 1.0))))
+    n = int(min(6_000_000, max(64, r * seconds)))
     P = rng.integers(2, LMAX + 1, size=(n, 2)).astype(np.int32)
     t0 = time.perf_counter()
     oracle.coupling_pairs(P[:, 0], P[:, 1], Wt, Wc, Wp, 31, threads=threads)

@@ -52,6 +52,8 @@ struct MxLayout {
     int NB;         // row blocks (BI i) per parity
     int NC;         // column blocks (128 j) of this request
     int NKB;        // k blocks (KB k) of this request
+    int NBA;        // row blocks that can hold nonzero A values (i <= l3 cap / 2)
+    int NKBA;       // k blocks stored per A row (k <= l3 cap / 2)
     int NSB;        // scale blocks of this request
     int SRC;        // row sources (window x role) per row group: 1, 2 or 4
     int BI;         // i per row block: 128 / SRC
@@ -63,10 +65,12 @@ struct MxLayout {
     long long b_var_bytes;  // bytes of one (pi, beta) slab of B images
 };
 
-// Offsets (bytes) of one tile image.  Row block b stores k blocks
-// kb = fA b .. NKB - 1; column block c stores kb = 0 .. gB (c + 1) - 1.
+// Offsets (bytes) of one tile image.  Row block b < NBA stores k blocks
+// kb = fA b .. NKBA - 1; column block c stores kb = 0 .. gB (c + 1) - 1.
+// (With band-limited windows, A rows and k beyond the largest l3 cap are
+// zero and are neither stored nor read.)
 __host__ __device__ inline long long mx_a_off(const MxLayout &L, int pi, int alpha, int rg, int b, int kb, int t) {
-    const long long blk = (long long)b * L.NKB - (long long)L.fA * b * (b - 1) / 2 + (kb - (long long)L.fA * b);
+    const long long blk = (long long)b * L.NKBA - (long long)L.fA * b * (b - 1) / 2 + (kb - (long long)L.fA * b);
     return ((long long)(pi * MX_NA + alpha) * L.NRG + rg) * L.a_rg_bytes + (blk * L.S + t) * L.IMG;
 }
 __host__ __device__ inline long long mx_b_off(const MxLayout &L, int pi, int beta, int c, int kb, int t) {
@@ -133,6 +137,7 @@ struct MxEpiArgs {
     const int32_t *tile_of;        // [pi][NRG][NB][NC] -> tile index or -1
     const int16_t *emaxA, *emaxB;
     const int *src_win, *src_role; // per source: window index and role bits (CPL_* spectra it feeds)
+    const int *l3cap;              // per source: last l3 with a nonzero weight
     int nsrc;
     int lmax, lmin;
     double *out;

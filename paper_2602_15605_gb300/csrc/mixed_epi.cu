@@ -1,18 +1,19 @@
 // mixed_epi.cu -- epilogue of the mixed-precision path, and the FP64 band of
 // small l1 pairs.
 //
-// k_mixed_epilogue: one thread per pair (parity, i, j) with l1 >= MX_L1_FP64
-// loops over the row sources (window x role).  The nine separable
-// contractions of the pair come from the GEMM's double-float outputs with
-// their power-of-two frames; the pair coefficients (lambda/eta, c0, c1, c2,
-// e0, e1, C of plain_fp64.cu) are formed once per pair in extended
-// double-float (FP32 pairs with an integer exponent), and the spectra are
-// combined and written as FP64 built with integer operations, so this kernel
-// uses no FP64 arithmetic.
+// k_mixed_epilogue (binned output) and k_mixed_epilogue_dense: one thread per
+// pair (parity, i, j) with l1 >= MX_L1_FP64 loops over the row sources
+// (window x role).  The nine separable contractions of the pair come from
+// the GEMM's double-float outputs with their power-of-two frames; the pair
+// coefficients (lambda/eta, c0, c1, c2, e0, e1, C of plain_fp64.cu) are
+// formed once per pair in extended double-float (FP32 pairs with an integer
+// exponent), and the spectra are combined in that form and converted to
+// FP64 with integer operations (the binned variant then applies the
+// (2l+1) / |bin| weights in FP64).
 //
 // k_mixed_band: pairs with l1 < MX_L1_FP64 in plain FP64.  For them the
 // polynomial expansion of the polarisation factor cancels by up to two
-// orders of magnitude, which the limb contraction's 1e-11-level error would
+// orders of magnitude, which the limb contraction's 1e-10-level error would
 // amplify; their l3 sums are short (2 l1 + 1 terms), so FP64 costs little.
 #include <cuda_runtime.h>
 
@@ -22,37 +23,9 @@
 namespace cpl {
 namespace {
 
-__device__ __forceinline__ void put_out(double *out, int lmax, int lmin, int nspec, int w, int slot, int l1, int l2,
-                                        xdf xi, int n_bins, const int *bin_of, const double *bin_inv) {
-    if (slot < 0) return;
-    const double m12 = xdf_to_double(xdf_scale_int(xi, 2LL * l2 + 1));
-    const double m21 = xdf_to_double(xdf_scale_int(xi, 2LL * l1 + 1));
-    if (n_bins == 0) {
-        const int n = lmax - lmin + 1;
-        double *base = out + ((size_t)w * nspec + slot) * (size_t)n * (size_t)n;
-        base[(size_t)(l1 - lmin) * n + (l2 - lmin)] = m12;
-        if (l1 != l2) base[(size_t)(l2 - lmin) * n + (l1 - lmin)] = m21;
-    } else {
-        const int b1 = bin_of[l1], b2 = bin_of[l2];
-        if (b1 < 0 || b2 < 0) return;
-        double *base = out + ((size_t)w * nspec + slot) * (size_t)n_bins * (size_t)n_bins;
-        if (m12 != 0.0) atomicAdd(base + (size_t)b1 * n_bins + b2, m12 * bin_inv[b1]);
-        if (l1 != l2 && m21 != 0.0) atomicAdd(base + (size_t)b2 * n_bins + b1, m21 * bin_inv[b2]);
-    }
-}
-
-// i runs fastest across the threads of a block so that the reads of the
-// column-major GEMM output ([col][row]) are coalesced.
-__global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
-    const MxLayout &L = a.L;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    const int pi = blockIdx.z;
-    const int l1 = j - i, l2 = i + j + pi;
-    if (l1 < max(a.lmin, MX_L1_FP64) || l2 > a.lmax || l1 > l2) return;
-    const int b = i / L.BI, ii = i % L.BI, c = j / MX_BJ, cc = j % MX_BJ;
-
-    // pair coefficients (exact integer inputs)
+// Pair coefficients of the spectra (exact integer inputs), in the order
+// TE[0..2], EE[0..5], EE->BB[0..2] (see plain_fp64.cu for the formulas).
+__device__ __forceinline__ void pair_coeffs(int l1, int l2, xdf (&qTE)[3], xdf (&qEE)[6], xdf (&qB)[3]) {
     const long long L1 = l1, L2 = l2;
     const xdf eta2 = xdf_from_ll((L1 - 1) * (L1 + 2) * (L2 - 1) * L2);
     const xdf lam2 = xdf_from_ll(L1 * (L1 + 1) * (L2 + 1) * (L2 + 2));
@@ -63,7 +36,6 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
     const xdf inv2l2p2 = xdf_recip(xdf_from_ll(2 * (L2 + 2)));
     const xdf c2 = xdf_mul(c1, inv2l2p2);
     const xdf two = xdf_from_ll(2);
-    xdf qTE[3], qEE[6], qB[3];
     qTE[0] = xdf_mul(r, c0);
     qTE[1] = xdf_neg(xdf_mul(r, c1));
     qTE[2] = xdf_neg(xdf_mul(r, c2));
@@ -79,14 +51,38 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
     qB[0] = xdf_mul(Cc, xdf_mul(e0, e0));
     qB[1] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
     qB[2] = xdf_mul(Cc, xdf_mul(e1, e1));
+}
 
+// Binned-output epilogue.  One thread per pair (parity, i, j), i fastest
+// across the block (the GEMM output is column-major, so the reads coalesce);
+// each pair's band-power contributions are added to the output with FP64
+// atomics.  Sources whose band limit L_w < |l2 - l1| contribute nothing to
+// the pair and are skipped.
+__global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
+    const MxLayout &L = a.L;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    const int pi = blockIdx.z;
+    const int l1 = j - i, l2 = i + j + pi;
+    if (l1 < max(a.lmin, MX_L1_FP64) || l2 > a.lmax || l1 > l2) return;
+    const int b1 = a.bin_of[l1], b2 = a.bin_of[l2];
+    if (b1 < 0 || b2 < 0) return;
+
+    xdf qTE[3], qEE[6], qB[3];
+    pair_coeffs(l1, l2, qTE, qEE, qB);
+    const int b = i / L.BI, ii = i % L.BI, c = j / MX_BJ, cc = j % MX_BJ;
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const long long ncols = (long long)L.NC_B * MX_BJ;
+    const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
+    const double f12 = (2.0 * l2 + 1.0) * a.bin_inv[b1];
+    const double f21 = (2.0 * l1 + 1.0) * a.bin_inv[b2];
     for (int s = 0; s < a.nsrc; ++s) {
         const int role = a.src_role[s];
+        if (role == 0 || l2 - l1 > a.l3cap[s]) continue;
         const int w = a.src_win[s];
         const int rg = s / L.SRC, slot = s % L.SRC;
         const int tile = a.tile_of[(((long long)pi * L.NRG + rg) * L.NB + b) * L.NC + c];
+        if (tile < 0) continue;
         xdf S[MX_NPROD];
         const int r = slot * L.BI + ii;
         const long long rowg = ((long long)rg * L.NB + b) * MX_ROWS + r;
@@ -96,35 +92,39 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
 #pragma unroll
         for (int p = 0; p < MX_NPROD; ++p) {
             S[p] = {0.f, 0.f, 0};
-            if (p >= np || tile < 0) continue;
+            if (p >= np) continue;
             const float *src = a.inter + ((long long)tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
             const float hi = src[cc * MX_ROWS + r], lo = src[MX_ROWS * MX_BJ + cc * MX_ROWS + r];
             const int E = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
                           (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
             S[p] = xdf_make(df_quick(hi, lo), E);
         }
-        if (role & kTT) put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[0], l1, l2, S[0], a.n_bins, a.bin_of, a.bin_inv);
+        xdf X[5];
+        X[0] = S[0];
+        X[1] = X[2] = X[3] = X[4] = xdf{0.f, 0.f, 0};
         if (role & kTE) {
-            xdf te = xdf_mul(qTE[0], S[0]);
-            te = xdf_add(te, xdf_mul(qTE[1], S[1]));
-            te = xdf_add(te, xdf_mul(qTE[2], S[2]));
-            put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[1], l1, l2, te, a.n_bins, a.bin_of, a.bin_inv);
+            X[1] = xdf_mul(qTE[0], S[0]);
+            X[1] = xdf_add(X[1], xdf_mul(qTE[1], S[1]));
+            X[1] = xdf_add(X[1], xdf_mul(qTE[2], S[2]));
         }
         if (pol) {
-            xdf ee = {0.f, 0.f, 0};
 #pragma unroll
-            for (int p = 0; p < 6; ++p) ee = xdf_add(ee, xdf_mul(qEE[p], S[p]));
-            if (role & kEE) put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[2], l1, l2, ee, a.n_bins, a.bin_of, a.bin_inv);
+            for (int p = 0; p < 6; ++p) X[2] = xdf_add(X[2], xdf_mul(qEE[p], S[p]));
             if (odd) {
-                xdf bb = xdf_mul(qB[0], S[6]);
-                bb = xdf_add(bb, xdf_mul(qB[1], S[7]));
-                bb = xdf_add(bb, xdf_mul(qB[2], S[8]));
-                if (role & kEEBB)
-                    put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[3], l1, l2, bb, a.n_bins, a.bin_of, a.bin_inv);
-                if (role & kEB)
-                    put_out(a.out, a.lmax, a.lmin, a.nspec, w, a.slot[4], l1, l2, xdf_add(ee, xdf_neg(bb)), a.n_bins,
-                            a.bin_of, a.bin_inv);
+                X[3] = xdf_mul(qB[0], S[6]);
+                X[3] = xdf_add(X[3], xdf_mul(qB[1], S[7]));
+                X[3] = xdf_add(X[3], xdf_mul(qB[2], S[8]));
+                X[4] = xdf_add(X[2], xdf_neg(X[3]));
             }
+        }
+#pragma unroll
+        for (int x = 0; x < 5; ++x) {
+            if (!(role & bits[x]) || a.slot[x] < 0) continue;
+            const double v = xdf_to_double(X[x]);
+            if (v == 0.0) continue;
+            double *base = a.out + ((size_t)w * a.nspec + a.slot[x]) * (size_t)a.n_bins * (size_t)a.n_bins;
+            atomicAdd(base + (size_t)b1 * a.n_bins + b2, v * f12);
+            if (l1 != l2) atomicAdd(base + (size_t)b2 * a.n_bins + b1, v * f21);
         }
     }
 }
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
 }  // namespace
 
 cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st) {
-    const int NI = a.L.NB * a.L.BI;
+    const int NI = a.L.NBA * a.L.BI;   // rows beyond hold no nonzero value (band limit)
     if (a.n_bins > 0) {
         dim3 grid((NI + 127) / 128, a.lmax + 1, 2);
         k_mixed_epilogue<<<grid, 128, 0, st>>>(a);

@@ -193,7 +193,13 @@ void plan_job(const cpl_request *r, double *out, int S, MxJobPlan &J) {
     L.NKB = lmax / L.KB + 1;
     L.NSB = (L.NKB * L.KB + MX_SB - 1) / MX_SB;
     L.NRG = J.nsrc / L.SRC;
-    L.a_rg_bytes = ((long long)L.NB * L.NKB - (long long)L.fA * L.NB * (L.NB - 1) / 2) * S * L.IMG;
+    // A values a(i, k) vanish unless k >= i and l3 = 2k + pi or 2k + 1 - pi <= cap
+    int cap_max = 0;
+    for (int q = 0; q < J.nsrc; ++q) cap_max = std::max(cap_max, J.src_cap[q]);
+    const int kA = cap_max >> 1;
+    L.NKBA = std::min(L.NKB, kA / L.KB + 1);
+    L.NBA = std::min(L.NB, kA / L.BI + 1);
+    L.a_rg_bytes = ((long long)L.NBA * L.NKBA - (long long)L.fA * L.NBA * (L.NBA - 1) / 2) * S * L.IMG;
     J.a_stride = 2 * lmax + 2;
 
     unsigned role_union = 0;
@@ -515,6 +521,11 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             if (J.nb) {
                 const size_t n_out = (size_t)J.r.n_windows * nspec * J.nb * J.nb;
                 CPL_CUDA_TRY(cudaMemsetAsync(J.out, 0, sizeof(double) * n_out, st));
+            } else if (J.L.NBA < J.L.NB) {
+                // band-limited dense output: pairs beyond the band are zero and the
+                // epilogue covers only the row blocks that hold nonzero values
+                const size_t n = (size_t)(J.r.lmax - J.r.lmin + 1);
+                CPL_CUDA_TRY(cudaMemsetAsync(J.out, 0, sizeof(double) * J.r.n_windows * nspec * n * n, st));
             }
             MxEpiArgs ea;
             std::memset(&ea, 0, sizeof(ea));
@@ -524,6 +535,7 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             ea.emaxB = M.emaxB.as<int16_t>();
             ea.src_win = srcp;
             ea.src_role = srcp + J.nsrc;
+            ea.l3cap = reinterpret_cast<const int *>(meta + J.m_cap);
             ea.nsrc = J.nsrc;
             ea.lmax = J.r.lmax;
             ea.lmin = J.r.lmin;

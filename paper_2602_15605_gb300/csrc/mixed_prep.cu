@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const MxLayout &L = a.L;
-    const int NI = L.NB * L.BI;
+    const int NI = L.NBA * L.BI;
     const int nsrc_pad = L.NRG * L.SRC;
     if (warp >= 2 * nsrc_pad * NI) return;
     const int i = warp % NI;
@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
 #pragma unroll
     for (int q = 0; q < MX_NA; ++q) emax[q] = EXP_ZERO;
     const int sb0 = (b * L.BI) / MX_SB;
-    for (int sb = sb0; sb < L.NSB; ++sb) {
+    const int sb_end = (L.NKBA * L.KB + MX_SB - 1) / MX_SB;
+    for (int sb = sb0; sb < sb_end; ++sb) {
         dfl val[MX_NA][MPL];
         int vex[MX_NA][MPL];
         int bexp[MX_NA];
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
             for (int m = 0; m < MPL; ++m) {
                 const int k = sb * MX_SB + lane + 32 * m;
                 const int kb = k / L.KB;
-                if (kb < L.fA * b || kb >= L.NKB) continue;
+                if (kb < L.fA * b || kb >= L.NKBA) continue;
                 dfl y = {0.f, 0.f};
                 if (val[q][m].h != 0.f && E != EXP_ZERO) {
                     // y = x 2^(7 - E) with x = val 2^(weight exponent): shift = vex - ilogb - 1 + 7 - E
@@ -274,7 +275,7 @@ cudaError_t mx_launch_weights_dd(const double *A, int n_src, int a_stride, float
 }
 
 cudaError_t mx_launch_prep_a(const MxPrepAArgs &a, cudaStream_t st) {
-    const long long warps = 2LL * a.L.NRG * a.L.SRC * a.L.NB * a.L.BI;
+    const long long warps = 2LL * a.L.NRG * a.L.SRC * a.L.NBA * a.L.BI;
     const int blocks = (int)((warps * 32 + 255) / 256);
     switch (a.L.S) {
         case 4: k_prep_a<4><<<blocks, 256, 0, st>>>(a); break;
