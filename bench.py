@@ -365,6 +365,11 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.barrier()
     ctx = coupling.Context(local)
+    # the mixed path's tile shapes come from the autotuner (measured on the
+    # first request of each shape, outside every timed region)
+    import tempfile
+    tune_file = os.path.join(tempfile.mkdtemp(prefix="cpl_tune_"), "tune.jsonl")
+    ctx.tune(True, tune_file)
     Wt, Wc, Wp = windows_for_rank(rank)
     dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:%d" % local)
     dWt, dWc, dWp = dev(Wt), dev(Wc), dev(Wp)
@@ -511,6 +516,11 @@ def run_ours(args, rank, world, local):
             line["mixed" if args.precision == "fp64" else "fp64"] = other
         if batch is not None:
             line["batch"] = batch
+        try:
+            line["tuner"] = [dict(lmax=e["key"][1], n_windows=e["key"][3], src=e["src"], order=e["order"],
+                                  ms=e["ms"]) for e in map(json.loads, open(tune_file).read().splitlines())]
+        except (OSError, ValueError, KeyError, IndexError):
+            line["tuner"] = None
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

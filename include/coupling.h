@@ -239,6 +239,33 @@ cpl_status cpl_ctx_profile(cpl_ctx *ctx, int enable);
 cpl_status cpl_ctx_stats(cpl_ctx *ctx, cpl_kernel_stat *out, int max, int *n, int reset);
 
 /*
+ * Tile-shape autotuner of the mixed-precision path (the persistent batched
+ * scheduler's tile choice).  The tuned parameters are the row shape of a
+ * tensor-core tile (1, 2 or 4 row sources x 128, 64 or 32 values of i) and
+ * the order in which the persistent kernel takes a job's work items
+ * (grouped by contraction or by tile).  They change the speed only: every
+ * candidate computes bit-identical matrices.
+ *
+ *   mode CPL_TUNE_OFF      built-in choice (row sources = window count
+ *                          rounded up to 1, 2 or 4; order by contraction);
+ *   mode CPL_TUNE_MEASURE  on the first request of a shape (l_max, l_min,
+ *                          window count, window-role grouping, spectra,
+ *                          l3 caps, binning, mixed_slices) every candidate
+ *                          runs the request's full launch sequence on its
+ *                          own buffers, timed with CUDA events, and the
+ *                          fastest is kept for that shape.  The first call
+ *                          of a shape therefore blocks until the candidates
+ *                          have run (about 2 x 6 builds).
+ *
+ * With a non-NULL `cache_path` the choices are also read from and appended
+ * to that file (one JSON object per line: {"key": [...], "src": n,
+ * "order": n, "ms": t}); unreadable lines are ignored.  Returns
+ * CPL_ERR_ARG for an unknown mode.
+ */
+typedef enum { CPL_TUNE_OFF = 0, CPL_TUNE_MEASURE = 1 } cpl_tune_mode;
+cpl_status cpl_ctx_tune(cpl_ctx *ctx, int mode, const char *cache_path);
+
+/*
  * Lookup table of Eqs. gdef / g_rec, as the library builds it: out[p] =
  * g(p) = (2p)! / (2^{2p} (p!)^2) for p = 0 .. pmax, each value the
  * double-double recurrence g(p) = (p - 1/2)/p g(p-1), g(0) = 1, rounded once

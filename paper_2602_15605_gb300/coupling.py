@@ -21,6 +21,7 @@ SPEC_BITS = (TT, TE, EE, EEBB, EB)
 SPEC_NAMES = {TT: "TT", TE: "TE", EE: "EE", EEBB: "EEBB", EB: "EB"}
 ALL = TT | TE | EE | EEBB | EB
 FP64, MIXED_BF16 = 0, 1
+TUNE_OFF, TUNE_MEASURE = 0, 1
 
 STATUS = {0: "CPL_OK", 1: "CPL_ERR_ARG", 2: "CPL_ERR_RANGE", 3: "CPL_ERR_OOM", 4: "CPL_ERR_CUDA",
           5: "CPL_ERR_TIMEOUT", 6: "CPL_ERR_UNSUPPORTED"}
@@ -48,7 +49,7 @@ class KernelStat(ctypes.Structure):
 # Every symbol include/coupling.h declares.
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
-           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_g_table")
+           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_g_table")
 
 _lock = threading.Lock()
 _lib = None
@@ -81,6 +82,7 @@ def load():
         L.cpl_build_batch.argtypes = [vp, ctypes.POINTER(Request), ip, ctypes.POINTER(vp), vp]
         L.cpl_g_table.argtypes = [ip, dp]
         L.cpl_ctx_profile.argtypes = [vp, ip]
+        L.cpl_ctx_tune.argtypes = [vp, ip, ctypes.c_char_p]
         L.cpl_ctx_stats.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]
         for name in EXPORTS:
             if name not in ("cpl_version", "cpl_last_error"):
@@ -161,6 +163,14 @@ class Context:
     def profile(self, enable=True):
         """Turn per-launch event timing on or off (cpl_ctx_profile)."""
         _check(load().cpl_ctx_profile(self.handle, 1 if enable else 0))
+
+    def tune(self, mode=True, cache_path=None):
+        """Mixed-path tile-shape autotuner (cpl_ctx_tune): True / TUNE_MEASURE
+        measures candidates on the first request of each shape, False / TUNE_OFF
+        uses the built-in choice; cache_path persists the choices."""
+        m = TUNE_MEASURE if mode is True else TUNE_OFF if mode is False else int(mode)
+        path = None if cache_path is None else os.fsencode(str(cache_path))
+        _check(load().cpl_ctx_tune(self.handle, m, path))
 
     def stats(self, reset=False):
         """{kernel family: dict(launches, ms, flop, bytes)} (cpl_ctx_stats)."""

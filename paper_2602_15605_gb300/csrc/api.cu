@@ -531,6 +531,12 @@ cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, doub
     return CPL_OK;
 }
 
+cpl_status cpl_ctx_tune(cpl_ctx *c, int mode, const char *cache_path) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (mode != CPL_TUNE_OFF && mode != CPL_TUNE_MEASURE) return fail(CPL_ERR_ARG, "unknown tuning mode");
+    return cpl::set_tuning(c, mode, cache_path);
+}
+
 cpl_status cpl_ctx_profile(cpl_ctx *c, int enable) {
     if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
     c->profiling = enable != 0;

@@ -49,6 +49,14 @@ struct MxPlanDeleter {
     void operator()(MxPlan *p) const;
 };
 
+// One autotuner decision: the key describes a request shape (mixed_host.cu
+// tune_key), src / order the chosen row shape and item order.
+struct TuneEntry {
+    std::vector<long long> key;
+    int src = 0, order = 0;
+    double ms = 0.0;
+};
+
 // Scratch and caches of the mixed-precision path.
 struct MixedState {
     int S = 0;                   // limbs the B cache was built with
@@ -63,6 +71,9 @@ struct MixedState {
     unsigned long long clock = 0;
     int nsm = 0;
     cudaStream_t cap_stream = nullptr;   // stream used only for graph capture
+    int tune_mode = 0;                   // cpl_tune_mode
+    std::string tune_path;               // persisted choices ("" = none)
+    std::vector<TuneEntry> tuned;
 };
 
 }  // namespace cpl
@@ -107,6 +118,7 @@ cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out);
 cpl_status build_mixed(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st);
 cpl_status build_mixed_batch(cpl_ctx *c, const cpl_request *reqs, double *const *outs, int n, cudaStream_t st,
                              bool use_graph);
+cpl_status set_tuning(cpl_ctx *c, int mode, const char *path);
 int stat_index(cpl_ctx *c, const char *name);
 void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes,
                    double issued = -1.0);

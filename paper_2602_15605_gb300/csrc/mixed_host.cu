@@ -79,6 +79,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+// Tunable shape of one job: row sources per tile (0 = built-in choice) and
+// the order of its work items (0: by contraction, 1: by tile).
+struct MxParams {
+    int src = 0;
+    int order = 0;
+};
+
 // The host-side plan of one request.
 struct MxJobPlan {
     cpl_request r;                     // copy; its host arrays are not read after planning
@@ -136,7 +143,7 @@ struct MxPlan {
 namespace {
 
 // Row sources, caps, geometry, tiles and items of one request.
-void plan_job(const cpl_request *r, double *out, int S, MxJobPlan &J) {
+void plan_job(const cpl_request *r, double *out, int S, MxParams prm, MxJobPlan &J) {
     J.r = *r;
     J.out = out;
     const int lmax = r->lmax, lmin = r->lmin, nw = r->n_windows;
@@ -154,7 +161,7 @@ void plan_job(const cpl_request *r, double *out, int S, MxJobPlan &J) {
     add(r->W_pp, kEE | kEEBB | kEB);
     // rows of a GEMM tile: SRC sources x BI i-values, SRC the smallest power
     // of two >= the windows per role (at most 4), so few windows waste no rows
-    const int SRC = nw >= 3 ? 4 : nw == 2 ? 2 : 1;
+    const int SRC = prm.src ? prm.src : nw >= 3 ? 4 : nw == 2 ? 2 : 1;
     const int BI = MX_ROWS / SRC;
     for (auto &g : J.groups) {
         J.group_start.push_back((int)J.src.size());
@@ -231,32 +238,41 @@ void plan_job(const cpl_request *r, double *out, int S, MxJobPlan &J) {
                     J.tiles.push_back({pi, rg, b, cb, kb_lo, kb_hi});
                 }
             }
-    // order: parity, contraction, row block, column block, row group -- a
+    // order 0: parity, contraction, row block, column block, row group -- a
     // run of consecutive items shares its A images (same row block) and its
     // B images (same column block) through L2, and the cost of the items of
     // one (parity, contraction) segment falls with the row block, so each
-    // segment ends with its lightest items
-    for (int pi = 0; pi < 2; ++pi)
-        for (int p = 0; p < MX_NPROD; ++p)
-            for (size_t t = 0; t < J.tiles.size(); ++t) {
-                const TileRec &T = J.tiles[t];
-                if (T.pi != pi) continue;
-                int need = 0;
-                for (int q = 0; q < L.SRC; ++q) need = std::max(need, products_for(J.src[T.rg * L.SRC + q].role));
-                if (p >= need) continue;
-                MxItem it;
-                it.pi = (int16_t)pi;
-                it.p = (int16_t)p;
-                it.kb_lo = (int16_t)T.kb_lo;
-                it.kb_hi = (int16_t)T.kb_hi;
-                it.tile = (int32_t)t;
-                it.rg = (int16_t)T.rg;
-                it.b = (int16_t)T.b;
-                it.c = (int16_t)T.c;
-                it.job = 0;
-                J.items.push_back(it);
-                J.kblocks += (double)(T.kb_hi - T.kb_lo + 1);
-            }
+    // segment ends with its lightest items.  order 1: parity, tile, then the
+    // contractions of the tile (the same A and B tiles in all their variants).
+    auto push = [&](int pi, int p, size_t t) {
+        const TileRec &T = J.tiles[t];
+        int need = 0;
+        for (int q = 0; q < L.SRC; ++q) need = std::max(need, products_for(J.src[T.rg * L.SRC + q].role));
+        if (p >= need) return;
+        MxItem it;
+        it.pi = (int16_t)pi;
+        it.p = (int16_t)p;
+        it.kb_lo = (int16_t)T.kb_lo;
+        it.kb_hi = (int16_t)T.kb_hi;
+        it.tile = (int32_t)t;
+        it.rg = (int16_t)T.rg;
+        it.b = (int16_t)T.b;
+        it.c = (int16_t)T.c;
+        it.job = 0;
+        J.items.push_back(it);
+        J.kblocks += (double)(T.kb_hi - T.kb_lo + 1);
+    };
+    for (int pi = 0; pi < 2; ++pi) {
+        if (prm.order == 0) {
+            for (int p = 0; p < MX_NPROD; ++p)
+                for (size_t t = 0; t < J.tiles.size(); ++t)
+                    if (J.tiles[t].pi == pi) push(pi, p, t);
+        } else {
+            for (size_t t = 0; t < J.tiles.size(); ++t)
+                if (J.tiles[t].pi == pi)
+                    for (int p = 0; p < MX_NPROD; ++p) push(pi, p, t);
+        }
+    }
     const double nlp = (double)S * (S + 1) / 2;
     J.gemm_issued = 2.0 * MX_ROWS * MX_BJ * J.kblocks * L.KB * nlp;
 
@@ -423,7 +439,6 @@ cpl_status materialize(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
     cpl_status s;
     if ((s = P.meta.ensure(std::max<size_t>(host.size(), 256), "mixed plan metadata")) != CPL_OK) return s;
     CPL_CUDA_TRY(cudaMemcpyAsync(P.meta.ptr, host.data(), host.size(), cudaMemcpyHostToDevice, st));
-    P.baked = baked_ptrs(c);
     if (P.exec) {
         cudaGraphExecDestroy(P.exec);
         P.exec = nullptr;
@@ -656,6 +671,178 @@ static cpl_status ensure_common(cpl_ctx *c, int S, int nc_max, size_t scratch, c
     return CPL_OK;
 }
 
+// Make the shared state fit the plan and (re)write its metadata if a device
+// pointer or the B-cache geometry it depends on has changed.
+static cpl_status prepare_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
+    MixedState &M = c->mx;
+    cpl_status s;
+    int nc_max = 0;
+    for (const MxJobPlan &J : P.jobs) nc_max = std::max(nc_max, J.L.NC);
+    if ((s = ensure_common(c, P.S, nc_max, P.scratch, st)) != CPL_OK) return s;
+    std::vector<const void *> baked = baked_ptrs(c);
+    baked.push_back(reinterpret_cast<const void *>((uintptr_t)M.NC_B));
+    baked.push_back(reinterpret_cast<const void *>((uintptr_t)c->pmax));
+    if (baked != P.baked) {
+        for (MxJobPlan &J : P.jobs) {   // the B geometry of every job follows the (possibly grown) cache
+            J.L.NC_B = M.NC_B;
+            J.L.NSB_B = M.NC_B;
+            J.L.b_var_bytes = (long long)J.L.gB * M.NC_B * (M.NC_B + 1) / 2 * P.S * J.L.IMG;
+        }
+        if ((s = materialize(c, P, st)) != CPL_OK) return s;
+        P.baked = baked;
+    }
+    return CPL_OK;
+}
+
+namespace {
+
+// Shape of a request as the tuner sees it: everything that changes the
+// work items or their costs, but no pointer values.
+std::vector<long long> tune_key(const cpl_request *r, int S) {
+    std::vector<long long> k = {S, r->lmax, r->lmin, r->n_windows, (long long)r->spectra,
+                                r->bin_edges ? r->n_bins : 0};
+    const double *W[3] = {r->W_tt, r->W_tp, r->W_pp};
+    const unsigned bits[3] = {kTT, kTE, kEE | kEEBB | kEB};
+    int shared = 0;   // which requested roles share one window pointer
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            shared = 2 * shared + ((r->spectra & bits[a]) && (r->spectra & bits[b]) && W[a] == W[b] ? 1 : 0);
+    k.push_back(shared);
+    for (int w = 0; w < r->n_windows; ++w) {
+        int cap = std::min(2 * r->lmax, r->w_len - 1);
+        if (r->band_limit) cap = std::min(cap, r->band_limit[w]);
+        k.push_back(cap);
+    }
+    return k;
+}
+
+void append_tune_file(const std::string &path, const TuneEntry &e) {
+    if (path.empty()) return;
+    FILE *f = std::fopen(path.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "{\"key\": [");
+    for (size_t q = 0; q < e.key.size(); ++q) std::fprintf(f, "%s%lld", q ? ", " : "", e.key[q]);
+    std::fprintf(f, "], \"src\": %d, \"order\": %d, \"ms\": %.4f}\n", e.src, e.order, e.ms);
+    std::fclose(f);
+}
+
+bool parse_tune_line(const std::string &ln, TuneEntry &e) {
+    const size_t k0 = ln.find("\"key\""), b0 = ln.find('[', k0 == std::string::npos ? 0 : k0);
+    const size_t b1 = ln.find(']', b0 == std::string::npos ? 0 : b0);
+    const size_t s0 = ln.find("\"src\""), o0 = ln.find("\"order\""), m0 = ln.find("\"ms\"");
+    if (k0 == std::string::npos || b0 == std::string::npos || b1 == std::string::npos || s0 == std::string::npos ||
+        o0 == std::string::npos)
+        return false;
+    e.key.clear();
+    const char *p = ln.c_str() + b0 + 1, *end = ln.c_str() + b1;
+    while (p < end) {
+        char *q = nullptr;
+        const long long v = std::strtoll(p, &q, 10);
+        if (q == p) {
+            ++p;
+            continue;
+        }
+        e.key.push_back(v);
+        p = q;
+    }
+    e.src = std::atoi(ln.c_str() + ln.find(':', s0) + 1);
+    e.order = std::atoi(ln.c_str() + ln.find(':', o0) + 1);
+    e.ms = m0 == std::string::npos ? 0.0 : std::atof(ln.c_str() + ln.find(':', m0) + 1);
+    return !e.key.empty() && (e.src == 1 || e.src == 2 || e.src == 4) && (e.order == 0 || e.order == 1);
+}
+
+// The tuned parameters of one request: from the cache, or measured now by
+// running every candidate's full launch sequence on the request's own
+// buffers (all candidates compute identical results).
+cpl_status tune_job(cpl_ctx *c, const cpl_request *r, double *out, int S, cudaStream_t st, MxParams *best) {
+    MixedState &M = c->mx;
+    *best = MxParams{};
+    if (M.tune_mode != CPL_TUNE_MEASURE) return CPL_OK;
+    const std::vector<long long> key = tune_key(r, S);
+    for (const TuneEntry &e : M.tuned)
+        if (e.key == key) {
+            best->src = e.src;
+            best->order = e.order;
+            return CPL_OK;
+        }
+    std::vector<MxParams> cand;
+    for (int src : {1, 2, 4})
+        if (src < 2 * std::max(1, r->n_windows))
+            for (int order : {0, 1}) cand.push_back(MxParams{src, order});
+    // tuning runs are not part of the caller's accounting
+    const bool prof = c->profiling;
+    c->profiling = false;
+    std::vector<long long> launches(c->kstats.size());
+    for (size_t q = 0; q < launches.size(); ++q) launches[q] = c->kstats[q].launches;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cpl_status s = CPL_OK;
+    double best_ms = 1e300;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        s = fail(CPL_ERR_CUDA, "event creation failed");
+    }
+    for (size_t q = 0; q < cand.size() && s == CPL_OK; ++q) {
+        MxPlan P;
+        P.S = S;
+        P.jobs.resize(1);
+        plan_job(r, out, S, cand[q], P.jobs[0]);
+        make_chunks(P, scratch_budget(M.arena));
+        if ((s = prepare_plan(c, P, st)) != CPL_OK) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && s == CPL_OK; ++rep) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) s = fail(CPL_ERR_CUDA, "event record failed");
+            if (s == CPL_OK) s = run_plan(c, P, st);
+            if (s == CPL_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                s = fail(CPL_ERR_CUDA, std::string("tuning run failed: ") + cudaGetErrorString(cudaGetLastError()));
+        }
+        if (s == CPL_OK && ms < best_ms) {
+            best_ms = ms;
+            *best = cand[q];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c->profiling = prof;
+    for (size_t q = 0; q < c->kstats.size(); ++q) c->kstats[q].launches = q < launches.size() ? launches[q] : 0;
+    if (s != CPL_OK) return s;
+    TuneEntry e;
+    e.key = key;
+    e.src = best->src;
+    e.order = best->order;
+    e.ms = best_ms;
+    M.tuned.push_back(e);
+    append_tune_file(M.tune_path, e);
+    return CPL_OK;
+}
+
+}  // namespace
+
+cpl_status set_tuning(cpl_ctx *c, int mode, const char *path) {
+    MixedState &M = c->mx;
+    M.tune_mode = mode;
+    M.tune_path = path ? path : "";
+    if (!M.tune_path.empty()) {
+        FILE *f = std::fopen(M.tune_path.c_str(), "r");
+        if (f) {
+            char buf[1 << 16];
+            while (std::fgets(buf, sizeof(buf), f)) {
+                TuneEntry e;
+                if (!parse_tune_line(buf, e)) continue;
+                bool dup = false;
+                for (TuneEntry &o : M.tuned)
+                    if (o.key == e.key) {
+                        o = e;
+                        dup = true;
+                    }
+                if (!dup) M.tuned.push_back(e);
+            }
+            std::fclose(f);
+        }
+    }
+    return CPL_OK;
+}
+
 // Build a batch of mixed-precision requests on `st`.  With use_graph (and
 // profiling off) the launch sequence is captured once per plan into a CUDA
 // graph and replayed.
@@ -685,7 +872,13 @@ cpl_status build_mixed_batch(cpl_ctx *c, const cpl_request *reqs, double *const 
         np->sig = sig;
         np->S = S;
         np->jobs.resize(n);
-        for (int q = 0; q < n; ++q) plan_job(reqs + q, outs[q], S, np->jobs[q]);
+        cpl_status ts;
+        for (int q = 0; q < n; ++q) {
+            MxParams prm;
+            CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
+            if ((ts = tune_job(c, reqs + q, outs[q], S, st, &prm)) != CPL_OK) return ts;
+            plan_job(reqs + q, outs[q], S, prm, np->jobs[q]);
+        }
         make_chunks(*np, scratch_budget(M.arena));
         P = np.get();
         M.plans.push_back(std::move(np));
@@ -694,22 +887,7 @@ cpl_status build_mixed_batch(cpl_ctx *c, const cpl_request *reqs, double *const 
 
     cpl_status s;
     CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
-    int nc_max = 0;
-    for (const MxJobPlan &J : P->jobs) nc_max = std::max(nc_max, J.L.NC);
-    if ((s = ensure_common(c, S, nc_max, P->scratch, st)) != CPL_OK) return s;
-    // the B geometry of every job follows the (possibly grown) cache
-    std::vector<const void *> baked = baked_ptrs(c);
-    baked.push_back(reinterpret_cast<const void *>((uintptr_t)M.NC_B));
-    baked.push_back(reinterpret_cast<const void *>((uintptr_t)c->pmax));
-    if (baked != P->baked) {
-        for (MxJobPlan &J : P->jobs) {
-            J.L.NC_B = M.NC_B;
-            J.L.NSB_B = M.NC_B;
-            J.L.b_var_bytes = (long long)J.L.gB * M.NC_B * (M.NC_B + 1) / 2 * S * J.L.IMG;
-        }
-        if ((s = materialize(c, *P, st)) != CPL_OK) return s;
-        P->baked = baked;
-    }
+    if ((s = prepare_plan(c, *P, st)) != CPL_OK) return s;
 
     if (use_graph && !c->profiling) {
         if (!P->exec) {

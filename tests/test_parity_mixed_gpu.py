@@ -234,3 +234,50 @@ def test_batch_graph_replay_sees_new_window_values(ctx):
     g0 = before.get("mixed_gemm_s6", {}).get("launches", 0)
     g1 = after.get("mixed_gemm_s6", {}).get("launches", 0)
     assert g1 == g0 + 1   # one persistent GEMM launch for the whole batch
+
+
+def test_autotuner_is_exact_and_cached(tmp_path):
+    # every tuner candidate computes the same matrices: the tuned build equals
+    # the built-in one bit for bit, the choice is cached per shape and
+    # persisted, and a new context reads it back instead of measuring again
+    import json
+    path = tmp_path / "tune.jsonl"
+    lmax = 333
+    W = np.stack([windows.mask_like(lmax, seed=70 + q) for q in range(3)])
+    plain = coupling.Context(0)
+    d = dev(W)
+    ref = plain.build(lmax, d, d, d, coupling.ALL, precision=coupling.MIXED_BF16).cpu().numpy()
+    plain.close()
+    t = coupling.Context(0)
+    t.tune(True, path)
+    got = t.build(lmax, d, d, d, coupling.ALL, precision=coupling.MIXED_BF16).cpu().numpy()
+    t.sync()
+    assert np.array_equal(got, ref)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) == 1 and lines[0]["src"] in (1, 2, 4) and lines[0]["order"] in (0, 1)
+    assert lines[0]["key"][1] == lmax and lines[0]["ms"] > 0
+    t.build(lmax, d, d, d, coupling.ALL, precision=coupling.MIXED_BF16)   # cached: no new measurement
+    t.sync()
+    assert len(path.read_text().splitlines()) == 1
+    t.close()
+    u = coupling.Context(0)
+    u.tune(True, path)
+    again = u.build(lmax, d, d, d, coupling.ALL, precision=coupling.MIXED_BF16).cpu().numpy()
+    u.sync()
+    assert np.array_equal(again, ref)
+    assert len(path.read_text().splitlines()) == 1   # read from the file
+    with pytest.raises(coupling.CouplingError):
+        u.tune(7)
+    u.close()
+
+
+def test_autotuned_batch_matches_untuned(ctx):
+    jobs, host = _ragged_jobs()
+    ref = [o.cpu().numpy() for o in ctx.build_batch(jobs)]
+    t = coupling.Context(0)
+    t.tune(True)
+    outs = t.build_batch(jobs)
+    t.sync()
+    for o, r, h in zip(outs, ref, host):
+        _same(o.cpu().numpy(), r, h["bin_edges"] is not None)
+    t.close()
