@@ -95,6 +95,27 @@ def windows_for_rank(rank):
     return tuple(windows.gaussian_taper(LMAX, s) for s in seeds)
 
 
+def ragged_seed0(rank):
+    """First window seed of rank `rank`'s ragged batch (independent per rank)."""
+    return 300 if rank == 0 else 300 + 1000 * rank
+
+
+def max_over_ranks(x, world, device):
+    """Max of a float over all ranks (the slowest rank's step time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, step_s):
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return world * units_per_rank / step_s
+
+
 def work_counts(lmax):
     """Per step: dense elements per spectrum and 3j terms per spectrum kernel
     (upper triangle l1 <= l2, parity-selected l3 counts)."""
@@ -271,8 +292,7 @@ def batch_arm(ctx, args, world, local, mixed_roofline):
     import torch
     from paper_2602_15605_gb300 import coupling, windows
     dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:%d" % local)
-    seed0 = 300 if world == 1 else 300 + 1000 * int(os.environ.get("RANK", "0"))
-    jobs_w = windows.ragged_jobs(seed0=seed0)
+    jobs_w = windows.ragged_jobs(seed0=ragged_seed0(int(os.environ.get("RANK", "0"))))
     jobs = []
     n_el = 0
     terms = 0
@@ -308,11 +328,7 @@ def batch_arm(ctx, args, world, local, mixed_roofline):
     after = ctx.stats()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     launches = sum(v["launches"] for v in after.values()) - sum(v["launches"] for v in before.values())
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda:%d" % local)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, "cuda:%d" % local)
     # one profiled (eager, not graph) step for the per-kernel breakdown
     ctx.profile(True)
     ctx.stats(reset=True)
@@ -341,7 +357,8 @@ def batch_arm(ctx, args, world, local, mixed_roofline):
     return {"workload": "8 jobs, l_max in (1000,2000,3000,4000,6000,8000,9000,10000), 4 mask-like windows "
                         "each (one pointer for W^TT/W^TP/W^PP), all five spectra, mixed BF16 limbs (6), dense "
                         "FP64 output; one cpl_build_batch per step = one CUDA graph replay",
-            "value": world * n_el / (ms * 1e-3), "unit": UNIT, "terms_per_s": world * terms / (ms * 1e-3),
+            "value": job_value(world, n_el, ms * 1e-3), "unit": UNIT,
+            "terms_per_s": job_value(world, terms, ms * 1e-3),
             "ms_per_step": ms, "steps": steps, "first_call_s": first_s, "gpu_launches_per_step": launches / steps,
             "roofline": mixed_roofline(st),
             "kernels_profiled_step": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in st.items()},
@@ -409,10 +426,7 @@ def run_ours(args, rank, world, local):
         st = ctx.stats(reset=True)
         ctx.profile(False)
         ctx.sync()
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda:%d" % local)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world, "cuda:%d" % local)
         return ms, st, clk, t_wall
 
     def fp64_roofline(stats, clk):
@@ -464,7 +478,7 @@ def run_ours(args, rank, world, local):
         o_prec = coupling.FP64 if args.precision == "mixed" else coupling.MIXED_BF16
         o_steps = max(3, min(args.steps, 10))
         o_ms, o_stats, o_clk, _ = timed_arm(o_prec, o_steps, 2)
-        other = {"value": world * 5 * n_el / (o_ms * 1e-3), "unit": UNIT, "ms_per_step": o_ms, "steps": o_steps,
+        other = {"value": job_value(world, 5 * n_el, o_ms * 1e-3), "unit": UNIT, "ms_per_step": o_ms, "steps": o_steps,
                  "precision": "fp64" if args.precision == "mixed" else "mixed_bf16 (6 limbs)",
                  "roofline": fp64_roofline(o_stats, o_clk) if args.precision == "mixed" else mixed_roofline(o_stats),
                  "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in o_stats.items()},
@@ -484,12 +498,8 @@ def run_ours(args, rank, world, local):
         k_e2e = max(3, min(args.steps, 10))
         for _ in range(k_e2e):
             ctx.build_host(LMAX, Wt, Wc, Wp, coupling.ALL, out=host_out, precision=head_prec)
-        dt = (time.perf_counter() - t0) / k_e2e
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda:%d" % local)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * 5 * n_el / dt, "unit": UNIT, "h2d_bytes_per_step": int(3 * Wt.nbytes),
+        dt = max_over_ranks((time.perf_counter() - t0) / k_e2e, world, "cuda:%d" % local)
+        e2e = {"value": job_value(world, 5 * n_el, dt), "unit": UNIT, "h2d_bytes_per_step": int(3 * Wt.nbytes),
                "d2h_bytes_per_step": int(host_out.nbytes), "ms_per_step": dt * 1e3}
 
     cpu = None
@@ -501,7 +511,7 @@ def run_ours(args, rank, world, local):
 
     if rank == 0:
         step_s = step_ms * 1e-3
-        value = world * 5 * n_el / step_s
+        value = job_value(world, 5 * n_el, step_s)
         total_terms = sum(terms.values())
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
