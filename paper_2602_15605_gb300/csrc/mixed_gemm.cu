@@ -43,7 +43,7 @@
 namespace cpl {
 namespace {
 
-constexpr int NTH = 576;                   // 2 control warps + 16 drain warps
+constexpr int NTH = 576;                   // 2 control warps + 16 drain warps (96 registers each)
 constexpr int LPAD = MX_ROWS + 1;          // padded stride of the [col][row] planes
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
@@ -114,6 +114,30 @@ __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t ad, uint64_t bd, 
 
 constexpr int TQ = 4;                      // ticket ring slots
 
+// Packed FP32 pairs (sm_100+ f32x2 instructions): the drain handles two
+// adjacent columns of a row per instruction.
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
+    return *reinterpret_cast<float2 *>(&r);
+}
+struct dfl2 {
+    float2 h, l;
+};
+// error-free sum of two packed pairs (Knuth two-sum, lane-wise)
+__device__ __forceinline__ dfl2 two_sum2(float2 a, float2 b) {
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = f2sub(s, a);
+    const float2 e = __fadd2_rn(f2sub(a, f2sub(s, bb)), f2sub(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) { return make_float2(__uint_as_float(a), __uint_as_float(b)); }
+// 2^e as a float for the scale factors of a block: 0 below 2^-126 (such a
+// block is below 2^-126 of the element's largest block)
+__device__ __forceinline__ float pow2_or_zero(int e) { return e < -126 ? 0.0f : pow2f(min(e, 0)); }
+
 struct Shared {
     uint64_t full[3], empty[3], acc_full, acc_empty, done;
     uint64_t tfull[TQ], tempty[TQ];
@@ -121,7 +145,7 @@ struct Shared {
     uint32_t tmem;
     int abort;          // set by any role on a timed-out wait
     int dabort;         // drain-local copy, written only before the drain barrier
-    int16_t ecol[MX_BJ];
+    float2 fcol[MX_BJ / 2];   // per column pair: 2^(E_col(block) - E_col(max)), or 0
 };
 
 template <int S>
@@ -133,7 +157,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
     constexpr int NST = mx_stages(S);
     constexpr int KPS = MX_SB / KB;              // k blocks per scale block
     constexpr uint32_t STAGE = 2u * S * IMG;
-    float *Ls = reinterpret_cast<float *>(dsm + NST * STAGE);   // [128 cols][LPAD]
+    float2 *Ls = reinterpret_cast<float2 *>(dsm + NST * STAGE);   // [64 column pairs][LPAD]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s_full0 = smem_u32(&sh.full[0]), s_empty0 = smem_u32(&sh.empty[0]);
@@ -320,19 +344,21 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             // running sum per element: high part in registers, low part (left
             // unnormalised until the end) in shared memory; each thread owns
             // its 32 cells of Ls, so no barrier is needed around the reset
-            float H[32];
+            float2 H[16];
 #pragma unroll
-            for (int x = 0; x < 32; ++x) H[x] = 0.f;
-            for (int x = 0; x < 32; ++x) Ls[(c0 + x) * LPAD + row] = 0.f;
+            for (int x = 0; x < 16; ++x) H[x] = make_float2(0.f, 0.f);
+            for (int x = 0; x < 16; ++x) Ls[(c0 / 2 + x) * LPAD + row] = make_float2(0.f, 0.f);
             for (int kb = it.kb_lo; kb <= it.kb_hi; ++kb) {
                 const bool slast = (kb == it.kb_hi) || (kb % KPS == KPS - 1);
                 if (!slast) continue;
                 const int sb = kb / KPS;
                 if (dtid < MX_BJ) {
                     const int j = j0 + dtid;
-                    sh.ecol[dtid] = (int16_t)max(-32000, (int)eBcol[(long long)j * L.NSB_B + sb] - (int)emB[j]);
+                    reinterpret_cast<float *>(sh.fcol)[dtid] =
+                        pow2_or_zero((int)eBcol[(long long)j * L.NSB_B + sb] - (int)emB[j]);
                 }
-                const int eAr = (int)eArow[sb] - emA;
+                const float fa = pow2_or_zero((int)eArow[sb] - emA);
+                const float2 fa2 = make_float2(fa, fa);
                 const bool ok = !*(volatile int *)&sh.abort && mbar_wait(s_accf, m & 1);
                 if (!ok) sh.dabort = 1;
                 // (A): column exponents visible; the abort decision is the same for all drain threads
@@ -356,29 +382,21 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                     TMEM_LD8(lane_addr + 3 * MX_BJ + col, r3);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int x = 0; x < 8; ++x) {
-                        const int cc = c0 + 8 * g + x;
-                        const int d = eAr + (int)sh.ecol[cc];
-                        if (d < -252) continue;
+                    for (int x = 0; x < 8; x += 2) {
+                        const int cp = (c0 + 8 * g + x) / 2;   // column pair
+                        // scale of this block relative to the element's frame (0 if negligible)
+                        const float2 F = __fmul2_rn(fa2, sh.fcol[cp]);
                         // block value: orders 0, 1 and 2 summed exactly (two two-sums:
                         // with decaying operands order 2 can reach 2^-8 of order 0, so
                         // it must not be folded into the residue of the first sum);
                         // the residues and order >= 3 are then added in FP32
-                        const dfl v01 = df_two_sum(__uint_as_float(r0[x]), __uint_as_float(r1[x]));
-                        const dfl v = df_two_sum(v01.h, __uint_as_float(r2[x]));
-                        const float vlo = (v01.l + v.l) + __uint_as_float(r3[x]);
-                        float vh, vl;
-                        if (d >= -126) {
-                            const float f = pow2f(d);
-                            vh = v.h * f;
-                            vl = vlo * f;
-                        } else {
-                            vh = scale2(v.h, d);
-                            vl = scale2(vlo, d);
-                        }
-                        const dfl z = df_two_sum(H[8 * g + x], vh);
-                        H[8 * g + x] = z.h;
-                        Ls[cc * LPAD + row] += z.l + vl;
+                        const dfl2 v01 = two_sum2(u2f2(r0[x], r0[x + 1]), u2f2(r1[x], r1[x + 1]));
+                        const dfl2 v = two_sum2(v01.h, u2f2(r2[x], r2[x + 1]));
+                        const float2 vlo = __fadd2_rn(__fadd2_rn(v01.l, v.l), u2f2(r3[x], r3[x + 1]));
+                        const dfl2 z = two_sum2(H[4 * g + x / 2], __fmul2_rn(v.h, F));
+                        H[4 * g + x / 2] = z.h;
+                        float2 &ls = Ls[cp * LPAD + row];
+                        ls = __fadd2_rn(ls, __fadd2_rn(z.l, __fmul2_rn(vlo, F)));
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
@@ -395,10 +413,13 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             // runs meanwhile.
             float *dst = J.inter + ((long long)it.tile * MX_NPROD + it.p) * 2 * (MX_ROWS * MX_BJ);
 #pragma unroll
-            for (int x = 0; x < 32; ++x) {
-                const dfl v = df_quick(H[x], Ls[(c0 + x) * LPAD + row]);
-                dst[(c0 + x) * MX_ROWS + row] = v.h;
-                dst[MX_ROWS * MX_BJ + (c0 + x) * MX_ROWS + row] = v.l;
+            for (int x = 0; x < 16; ++x) {
+                const float2 lo = Ls[(c0 / 2 + x) * LPAD + row];
+                const dfl v0 = df_quick(H[x].x, lo.x), v1 = df_quick(H[x].y, lo.y);
+                dst[(c0 + 2 * x) * MX_ROWS + row] = v0.h;
+                dst[(c0 + 2 * x + 1) * MX_ROWS + row] = v1.h;
+                dst[MX_ROWS * MX_BJ + (c0 + 2 * x) * MX_ROWS + row] = v0.l;
+                dst[MX_ROWS * MX_BJ + (c0 + 2 * x + 1) * MX_ROWS + row] = v1.l;
             }
         }
     }
@@ -413,7 +434,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
 }  // namespace
 
 size_t mx_gemm_smem_bytes(int S) {
-    return (size_t)mx_stages(S) * 2 * S * mx_img_bytes(S) + (size_t)MX_BJ * LPAD * sizeof(float);
+    return (size_t)mx_stages(S) * 2 * S * mx_img_bytes(S) + (size_t)(MX_BJ / 2) * LPAD * sizeof(float2);
 }
 
 cudaError_t mx_gemm_prepare(int S) {
