@@ -73,21 +73,109 @@ __device__ __forceinline__ int warp_max(int v) {
     return v;
 }
 
-// One warp per (parity, source, i): all scale blocks of the row.
+// The four A-side values x_q(i, k) of one (source, i, k), as double-float
+// mantissas with an exponent (the weight keeps its own exponent because
+// window spectra reach below the FP32 range): x = val 2^(e - ilogb(val) - 1)
+// relative to value_exp.  vex[q] = EXP_ZERO for a zero value.
+__device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, const float *Al, const int *Ae,
+                                         int cap, int i, int k, int pi, dfl (&val)[MX_NA], int (&vex)[MX_NA]) {
+#pragma unroll
+    for (int q = 0; q < MX_NA; ++q) {
+        val[q] = {0.f, 0.f};
+        vex[q] = EXP_ZERO;
+    }
+    // even sweep: l3 = 2k + pi, a0 = A(l3) g(i+k+pi) g(k-i), v = (2k+2i+2pi+1)(2k-2i)
+    const int l3e = 2 * k + pi;
+    if ((a.alpha_mask & 7) && k >= i && l3e <= cap && Ah[l3e] != 0.f) {
+        const dfl A = {Ah[l3e], Al[l3e]};
+        const dfl g1 = {a.gh[i + k + pi], a.gl[i + k + pi]};
+        const dfl g2 = {a.gh[k - i], a.gl[k - i]};
+        const dfl a0 = df_mul(df_mul(A, g1), g2);
+        const int e = Ae[l3e];
+        val[0] = a0;
+        vex[0] = a0.h != 0.f ? value_exp(a0, e) : EXP_ZERO;
+        if (k > i && (a.alpha_mask & 6)) {
+            const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (long long)(2 * k - 2 * i));
+            const dfl a0v = df_mul(a0, v);
+            const dfl a0v2 = df_mul(a0v, v);
+            val[1] = a0v;
+            vex[1] = a0v.h != 0.f ? value_exp(a0v, e) : EXP_ZERO;
+            val[2] = a0v2;
+            vex[2] = a0v2.h != 0.f ? value_exp(a0v2, e) : EXP_ZERO;
+        }
+    }
+    // odd sweep: l3 = 2k + 1 - pi, a1 v = A(l3) g(i+k+1) g(k-i-pi) (2i+2k+2)(2k+1-2i-2pi)
+    const int l3o = 2 * k + 1 - pi;
+    if ((a.alpha_mask & 8) && k >= i + pi && l3o <= cap && Ah[l3o] != 0.f) {
+        const dfl A = {Ah[l3o], Al[l3o]};
+        const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
+        const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
+        const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (long long)(2 * k + 1 - 2 * i - 2 * pi));
+        const dfl x = df_mul(df_mul(df_mul(A, g1), g2), v1);
+        if (x.h != 0.f) {
+            val[3] = x;
+            vex[3] = value_exp(x, Ae[l3o]);
+        }
+    }
+}
+
+// Variant q alone (same definitions as a_values).
+__device__ __forceinline__ dfl a_value(const MxPrepAArgs &a, const float *Ah, const float *Al, const int *Ae,
+                                       int cap, int i, int k, int pi, int q, int *vex) {
+    *vex = EXP_ZERO;
+    if (q < 3) {
+        const int l3e = 2 * k + pi;
+        if (!(k >= i && l3e <= cap && Ah[l3e] != 0.f) || (q > 0 && k == i)) return {0.f, 0.f};
+        const dfl A = {Ah[l3e], Al[l3e]};
+        const dfl g1 = {a.gh[i + k + pi], a.gl[i + k + pi]};
+        const dfl g2 = {a.gh[k - i], a.gl[k - i]};
+        dfl x = df_mul(df_mul(A, g1), g2);
+        if (q > 0) {
+            const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (long long)(2 * k - 2 * i));
+            x = df_mul(x, v);
+            if (q > 1) x = df_mul(x, v);
+        }
+        if (x.h != 0.f) *vex = value_exp(x, Ae[l3e]);
+        return x;
+    }
+    const int l3o = 2 * k + 1 - pi;
+    if (!(k >= i + pi && l3o <= cap && Ah[l3o] != 0.f)) return {0.f, 0.f};
+    const dfl A = {Ah[l3o], Al[l3o]};
+    const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
+    const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
+    const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (long long)(2 * k + 1 - 2 * i - 2 * pi));
+    const dfl x = df_mul(df_mul(df_mul(A, g1), g2), v1);
+    if (x.h != 0.f) *vex = value_exp(x, Ae[l3o]);
+    return x;
+}
+
+// One block per (parity, row group, row block, octet of 8 tile rows): the 8
+// rows belong to one source (BI >= 8) and are 8 consecutive values of i.
+// Thread (warp w, lane) owns tile row 8 o + (lane & 7) and the 8 consecutive
+// k = sb MX_SB + 32 w + 8 (lane >> 3) + 0..7 of each scale block sb, so that
+// for every limb it writes one 16-byte core-matrix row and each warp writes
+// whole 128-byte core matrices.  Pass 1 finds the row maxima of the
+// exponents (shuffles over the 4 lanes of a row, then shared memory over the
+// 8 warps), pass 2 recomputes the values and writes the limbs.
 template <int S>
 __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    constexpr int NW = 256 / 32;
+    static_assert(MX_SB == 32 * NW, "one scale block per pass of the block");
+    __shared__ int wmax[2][NW][8][MX_NA];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int q8 = lane & 7, kg = lane >> 3;
     const MxLayout &L = a.L;
-    const int NI = L.NBA * L.BI;
-    const int nsrc_pad = L.NRG * L.SRC;
-    if (warp >= 2 * nsrc_pad * NI) return;
-    const int i = warp % NI;
-    const int s = (warp / NI) % nsrc_pad;
-    const int pi = warp / (NI * nsrc_pad);
-    const int b = i / L.BI, ii = i % L.BI;
-    const int rg = s / L.SRC, slot = s % L.SRC;
-    const int r = slot * L.BI + ii;                      // row in the 128-row tile
+    int blk = blockIdx.x;
+    const int o = blk % (MX_ROWS / 8);
+    blk /= MX_ROWS / 8;
+    const int b = blk % L.NBA;
+    blk /= L.NBA;
+    const int rg = blk % L.NRG;
+    const int pi = blk / L.NRG;
+    const int r = 8 * o + q8;                            // row in the 128-row tile
+    const int slot = r / L.BI, ii = r % L.BI;
+    const int s = rg * L.SRC + slot;
+    const int i = b * L.BI + ii;
     const long long row_global = ((long long)rg * L.NB + b) * MX_ROWS + r;
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const bool live = s < a.nsrc;
@@ -102,82 +190,73 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     const int sb0 = (b * L.BI) / MX_SB;
     const int sb_end = (L.NKBA * L.KB + MX_SB - 1) / MX_SB;
     for (int sb = sb0; sb < sb_end; ++sb) {
-        dfl val[MX_NA][MPL];
-        int vex[MX_NA][MPL];
-        int bexp[MX_NA];
+        const int k0 = sb * MX_SB + 32 * w + 8 * kg;
+        // ---- pass 1: maxima of the value exponents over the row's scale block
+        int bmax[MX_NA];
 #pragma unroll
-        for (int q = 0; q < MX_NA; ++q) bexp[q] = EXP_ZERO;
+        for (int q = 0; q < MX_NA; ++q) bmax[q] = EXP_ZERO;
+#pragma unroll 1
+        for (int m = 0; m < 8; ++m) {
+            dfl val[MX_NA];
+            int vex[MX_NA];
+            a_values(a, Ah, Al, Ae, cap, i, k0 + m, pi, val, vex);
 #pragma unroll
-        for (int m = 0; m < MPL; ++m) {
-            const int k = sb * MX_SB + lane + 32 * m;
-#pragma unroll
-            for (int q = 0; q < MX_NA; ++q) {
-                val[q][m] = {0.f, 0.f};
-                vex[q][m] = EXP_ZERO;
-            }
-            // even sweep: l3 = 2k + pi, a0 = A(l3) g(i+k+pi) g(k-i), v = (2k+2i+2pi+1)(2k-2i)
-            const int l3e = 2 * k + pi;
-            if ((a.alpha_mask & 7) && k >= i && l3e <= cap && Ah[l3e] != 0.f) {
-                const dfl A = {Ah[l3e], Al[l3e]};
-                const dfl g1 = {a.gh[i + k + pi], a.gl[i + k + pi]};
-                const dfl g2 = {a.gh[k - i], a.gl[k - i]};
-                const dfl a0 = df_mul(df_mul(A, g1), g2);
-                const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (long long)(2 * k - 2 * i));
-                const int e = Ae[l3e];
-                val[0][m] = a0;
-                vex[0][m] = value_exp(a0, e);
-                if (v.h != 0.f) {
-                    const dfl a0v = df_mul(a0, v);
-                    const dfl a0v2 = df_mul(a0v, v);
-                    val[1][m] = a0v;
-                    vex[1][m] = value_exp(a0v, e);
-                    val[2][m] = a0v2;
-                    vex[2][m] = value_exp(a0v2, e);
-                }
-                // the exponent of the weight is applied through vex / the block exponent
-#pragma unroll
-                for (int q = 0; q < 3; ++q) vex[q][m] = (val[q][m].h != 0.f) ? vex[q][m] : EXP_ZERO;
-            }
-            // odd sweep: l3 = 2k + 1 - pi, a1 v = A(l3) g(i+k+1) g(k-i-pi) (2i+2k+2)(2k+1-2i-2pi)
-            const int l3o = 2 * k + 1 - pi;
-            if ((a.alpha_mask & 8) && k >= i + pi && l3o <= cap && Ah[l3o] != 0.f) {
-                const dfl A = {Ah[l3o], Al[l3o]};
-                const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
-                const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
-                const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (long long)(2 * k + 1 - 2 * i - 2 * pi));
-                const dfl x = df_mul(df_mul(df_mul(A, g1), g2), v1);
-                if (x.h != 0.f) {
-                    val[3][m] = x;
-                    vex[3][m] = value_exp(x, Ae[l3o]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < MX_NA; ++q) bexp[q] = max(bexp[q], vex[q][m]);
+            for (int q = 0; q < MX_NA; ++q) bmax[q] = max(bmax[q], vex[q]);
         }
+        const int buf = sb & 1;
+#pragma unroll
+        for (int q = 0; q < MX_NA; ++q) {
+            int v = max(bmax[q], __shfl_xor_sync(0xffffffffu, bmax[q], 8));
+            v = max(v, __shfl_xor_sync(0xffffffffu, v, 16));
+            if (kg == 0) wmax[buf][w][q8][q] = v;
+        }
+        __syncthreads();
+        int E[MX_NA];
+#pragma unroll
+        for (int q = 0; q < MX_NA; ++q) {
+            E[q] = EXP_ZERO;
+#pragma unroll
+            for (int x = 0; x < NW; ++x) E[q] = max(E[q], wmax[buf][x][q8][q]);
+            emax[q] = max(emax[q], E[q]);
+            if (w == 0 && kg == 0 && ((a.alpha_mask >> q) & 1))
+                a.eA[(((long long)pi * MX_NA + q) * nrows + row_global) * L.NSB + sb] = (int16_t)E[q];
+        }
+        // ---- pass 2: limbs of the 8 values, one 16-byte store per limb and variant
+        const int kb = k0 / L.KB;
+        if (kb < L.fA * b || kb >= L.NKBA) continue;
 #pragma unroll
         for (int q = 0; q < MX_NA; ++q) {
             if (!((a.alpha_mask >> q) & 1)) continue;
-            const int E = warp_max(bexp[q]);
-            if (lane == 0) a.eA[(((long long)pi * MX_NA + q) * nrows + row_global) * L.NSB + sb] = (int16_t)E;
-            emax[q] = max(emax[q], E);
+            uint32_t pk[S][4];
 #pragma unroll
-            for (int m = 0; m < MPL; ++m) {
-                const int k = sb * MX_SB + lane + 32 * m;
-                const int kb = k / L.KB;
-                if (kb < L.fA * b || kb >= L.NKBA) continue;
+            for (int m = 0; m < 8; ++m) {
+                int vex;
+                const dfl val = a_value(a, Ah, Al, Ae, cap, i, k0 + m, pi, q, &vex);
                 dfl y = {0.f, 0.f};
-                if (val[q][m].h != 0.f && E != EXP_ZERO) {
+                if (vex != EXP_ZERO && E[q] != EXP_ZERO) {
                     // y = x 2^(7 - E) with x = val 2^(weight exponent): shift = vex - ilogb - 1 + 7 - E
-                    const int sh = vex[q][m] - (ilogbf_fast(fabsf(val[q][m].h)) + 1) + 7 - E;
-                    y.h = scale2(val[q][m].h, sh);
-                    y.l = scale2(val[q][m].l, sh);
+                    const int sh = vex - (ilogbf_fast(fabsf(val.h)) + 1) + 7 - E[q];
+                    y.h = scale2(val.h, sh);
+                    y.l = scale2(val.l, sh);
                 }
-                uint8_t *img = a.Aimg + mx_a_off(L, pi, q, rg, b, kb, 0);
-                put_limbs<S>(img, mx_img_off(r, k % L.KB, L.KB), y, L.IMG);
+#pragma unroll
+                for (int t = 0; t < S; ++t) {
+                    const float l = rintf(y.h);
+                    const dfl z = df_two_sum(y.h - l, y.l);
+                    y.h = z.h * 256.0f;
+                    y.l = z.l * 256.0f;
+                    const uint32_t bits = __bfloat16_as_ushort(__float2bfloat16_rn(l * pow2f(-8 * t)));
+                    if (m & 1) pk[t][m >> 1] |= bits << 16;
+                    else pk[t][m >> 1] = bits;
+                }
             }
+            uint8_t *img = a.Aimg + mx_a_off(L, pi, q, rg, b, kb, 0) + mx_img_off(r, k0 % L.KB, L.KB);
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+                *reinterpret_cast<uint4 *>(img + (size_t)t * L.IMG) = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
         }
     }
-    if (lane == 0) {
+    if (w == 0 && kg == 0) {
 #pragma unroll
         for (int q = 0; q < MX_NA; ++q)
             if ((a.alpha_mask >> q) & 1) a.emaxA[((long long)pi * MX_NA + q) * nrows + row_global] = (int16_t)emax[q];
@@ -275,8 +354,10 @@ cudaError_t mx_launch_weights_dd(const double *A, int n_src, int a_stride, float
 }
 
 cudaError_t mx_launch_prep_a(const MxPrepAArgs &a, cudaStream_t st) {
-    const long long warps = 2LL * a.L.NRG * a.L.SRC * a.L.NBA * a.L.BI;
-    const int blocks = (int)((warps * 32 + 255) / 256);
+    const long long octets = 2LL * a.L.NRG * a.L.NBA * (MX_ROWS / 8);
+    if (octets == 0) return cudaSuccess;
+    if (a.L.BI < 8 || a.L.KB % 8 != 0) return cudaErrorInvalidValue;
+    const int blocks = (int)octets;
     switch (a.L.S) {
         case 4: k_prep_a<4><<<blocks, 256, 0, st>>>(a); break;
         case 5: k_prep_a<5><<<blocks, 256, 0, st>>>(a); break;
