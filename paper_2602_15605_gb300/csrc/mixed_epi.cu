@@ -23,6 +23,11 @@
 namespace cpl {
 namespace {
 
+// Whether A variant v feeds one of the first np contractions.
+__device__ __forceinline__ bool mx_alpha_used(int v, int np) {
+    return v == 0 || (v == 1 && np > 2) || (v == 2 && np > 4) || (v == 3 && np > 6);
+}
+
 // Pair coefficients of the spectra (exact integer inputs), in the order
 // TE[0..2], EE[0..5], EE->BB[0..2] (see plain_fp64.cu for the formulas).
 __device__ __forceinline__ void pair_coeffs(int l1, int l2, xdf (&qTE)[3], xdf (&qEE)[6], xdf (&qB)[3]) {
@@ -130,8 +135,8 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
 }
 
 
-// Dense-output epilogue with coalesced writes.  One block covers an 8 x 32
-// block of (i, j) in both parities: 512 pairs, one per thread, i fastest (the
+// Dense-output epilogue with coalesced writes.  One block covers an 8 x 16
+// block of (i, j) in both parities: 256 pairs, one per thread, i fastest (the
 // GEMM output is column-major, so 8 consecutive i are one 32-byte sector),
 // whose rows of M (fixed l1, l2 = l1 + d) and mirrored rows (fixed l2,
 // l1 = l2 - d) are runs of 16 consecutive elements.  Each thread forms its pair's 12 combination
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
 // per row source it combines the contractions in one exponent frame per
 // spectrum, converts the (2 l2 + 1) and (2 l1 + 1) multiples to FP64 with
 // integer operations, and stages them in shared memory for row-wise writes.
-constexpr int EB_I = 8, EB_J = 32, EB_P = 2 * EB_I * EB_J, EB_T = EB_P;
+constexpr int EB_I = 8, EB_J = 16, EB_P = 2 * EB_I * EB_J, EB_T = EB_P;
 
 struct Term {
     dfl m;   // mantissa
@@ -177,8 +182,17 @@ __device__ __forceinline__ double times_int(xdf v, int f) {
     return xdf_to_double(xdf{q.h, q.l, v.e});
 }
 
+// Shared memory of one block: the staged rows of M, and the pair
+// coefficients (kept out of registers so that more blocks fit an SM).
+struct EpiSmem {
+    double stage[5][2][EB_P];
+    float cfh[12][EB_T], cfl[12][EB_T];
+    int cfe[12][EB_T];
+};
+
 __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a) {
-    __shared__ double stage[5][2][EB_P];
+    extern __shared__ __align__(16) uint8_t epi_smem[];
+    EpiSmem &sm = *reinterpret_cast<EpiSmem *>(epi_smem);
     const MxLayout &L = a.L;
     const int i0 = blockIdx.y * EB_I, j0 = blockIdx.x * EB_J;
     const int q = threadIdx.x;
@@ -188,32 +202,18 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
     const int l1 = j - i, l2 = i + j + pi;
     const bool valid = !(l1 < L1min || l2 > a.lmax || l1 > l2);
 
-    // ---- coefficients of this thread's pair
-    xdf cf[12];
+    // ---- coefficients of this thread's pair (TE[0..2], EE[3..8], EE->BB[9..11])
     if (valid) {
-        const long long L1 = l1, L2 = l2;
-        const xdf eta2i = xdf_recip(xdf_from_ll((L1 - 1) * (L1 + 2) * (L2 - 1) * L2));
-        const xdf r2 = xdf_mul(xdf_from_ll(L1 * (L1 + 1) * (L2 + 1) * (L2 + 2)), eta2i);
-        const xdf r = xdf_sqrt(r2);
-        const xdf c1 = xdf_recip(xdf_from_ll(L1 * (L1 + 1) * (L2 + 1)));
-        const xdf c0 = xdf_mul(xdf_from_ll(L1 + 2), xdf_recip(xdf_from_ll(L1)));
-        const xdf e1 = xdf_recip(xdf_from_ll(2 * (L2 + 2)));
-        const xdf c2 = xdf_mul(c1, e1);
-        const xdf two = xdf_from_ll(2);
-        cf[0] = xdf_mul(r, c0);
-        cf[1] = xdf_neg(xdf_mul(r, c1));
-        cf[2] = xdf_neg(xdf_mul(r, c2));
-        cf[3] = xdf_mul(r2, xdf_mul(c0, c0));
-        cf[4] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c1))));
-        cf[5] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c2))));
-        cf[6] = xdf_mul(r2, xdf_mul(c1, c1));
-        cf[7] = xdf_mul(r2, xdf_mul(two, xdf_mul(c1, c2)));
-        cf[8] = xdf_mul(r2, xdf_mul(c2, c2));
-        const xdf e0 = xdf_from_ll(L1 + 2);
-        const xdf Cc = xdf_mul(xdf_mul(xdf_from_ll(L2 + 2), c1), eta2i);
-        cf[9] = xdf_mul(Cc, xdf_mul(e0, e0));
-        cf[10] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
-        cf[11] = xdf_mul(Cc, xdf_mul(e1, e1));
+        xdf qTE[3], qEE[6], qB[3];
+        pair_coeffs(l1, l2, qTE, qEE, qB);
+        const xdf *c[12] = {&qTE[0], &qTE[1], &qTE[2], &qEE[0], &qEE[1], &qEE[2],
+                            &qEE[3], &qEE[4], &qEE[5], &qB[0], &qB[1], &qB[2]};
+#pragma unroll
+        for (int x = 0; x < 12; ++x) {
+            sm.cfh[x][q] = c[x]->h;
+            sm.cfl[x][q] = c[x]->l;
+            sm.cfe[x][q] = c[x]->e;
+        }
     }
 
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
@@ -221,6 +221,36 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
     const int n = a.lmax - a.lmin + 1;
     const int b32 = i0 / L.BI, c128 = j0 / MX_BJ;
     const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
+    // this thread's share of the row writes, the same for every source and
+    // spectrum: output offset and index into the staged [2][EB_P] values
+    // (rows M[l1][l2 = l1 + d] and mirrored M[l2][l1 = l2 - d], d = 2 i0 .. 2 i0 + 2 EB_I - 1)
+    constexpr int NROW = EB_I + EB_J, NWR = (2 * NROW * 2 * EB_I + EB_T - 1) / EB_T;
+    long long woff[NWR];
+    int widx[NWR];
+#pragma unroll
+    for (int k = 0; k < NWR; ++k) {
+        widx[k] = -1;
+        woff[k] = 0;
+        const int e = q + k * EB_T;
+        if (e >= 2 * NROW * 2 * EB_I) continue;
+        const int mirror = e / (NROW * 2 * EB_I);
+        const int rr = (e / (2 * EB_I)) % NROW, dl = e % (2 * EB_I);
+        const int epi = dl & 1, eii = dl >> 1, ei = i0 + eii, d = 2 * ei + epi;
+        const int el1 = mirror ? i0 + j0 + rr - d : j0 - i0 - (EB_I - 1) + rr;
+        const int el2 = el1 + d;
+        const int ejj = el1 + ei - j0;
+        if (ejj < 0 || ejj >= EB_J) continue;
+        if (el1 < L1min || el2 > a.lmax || el1 > el2) continue;
+        if (mirror && el1 == el2) continue;
+        const int pq = (epi * EB_J + ejj) * EB_I + eii;
+        widx[k] = mirror * EB_P + pq;
+        woff[k] = mirror ? (long long)(el2 - a.lmin) * n + (el1 - a.lmin) : (long long)(el1 - a.lmin) * n + (el2 - a.lmin);
+    }
+    // column frames of the six B variants: the same for every source
+    int eBv[MX_NBV];
+#pragma unroll
+    for (int v = 0; v < MX_NBV; ++v)
+        eBv[v] = valid ? (int)a.emaxB[((long long)pi * MX_NBV + v) * ncols + j] : 0;
     for (int s = 0; s < a.nsrc; ++s) {
         const int role = a.src_role[s];
         if (role == 0) continue;
@@ -233,31 +263,37 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
             const int tile = a.tile_of[(((long long)pi * L.NRG + rg) * L.NB + b32) * L.NC + c128];
             const int r = slot * L.BI + (i % L.BI), cc = j % MX_BJ;
             const long long rowg = ((long long)rg * L.NB + b32) * MX_ROWS + r;
-            dfl Sm[MX_NPROD];
-            int Se[MX_NPROD];
+            int eAv[MX_NA];
 #pragma unroll
-            for (int p = 0; p < MX_NPROD; ++p) {
-                Sm[p] = {0.f, 0.f};
-                Se[p] = 0;
-                if (p >= np || tile < 0) continue;
-                const float *src = a.inter + ((long long)tile * MX_NPROD + p) * 2 * (MX_ROWS * MX_BJ);
-                Sm[p] = dfl{src[cc * MX_ROWS + r], src[MX_ROWS * MX_BJ + cc * MX_ROWS + r]};
-                Se[p] = (int)a.emaxA[((long long)pi * MX_NA + mx_alpha(p)) * nrows + rowg] +
-                        (int)a.emaxB[((long long)pi * MX_NBV + mx_beta(p)) * ncols + j] - 14;
-            }
+            for (int v = 0; v < MX_NA; ++v)
+                eAv[v] = (tile >= 0 && mx_alpha_used(v, np)) ? (int)a.emaxA[((long long)pi * MX_NA + v) * nrows + rowg] : 0;
+            const float *src0 = a.inter + (long long)(tile < 0 ? 0 : tile) * MX_NPROD * 2 * (MX_ROWS * MX_BJ) +
+                                cc * MX_ROWS + r;
+            // contraction p of this pair as (mantissa, exponent); zero where the tile is empty
+            auto S = [&](int p) -> Term {
+                if (tile < 0) return Term{dfl{0.f, 0.f}, 0};
+                const float *sp = src0 + (long long)p * 2 * (MX_ROWS * MX_BJ);
+                return Term{dfl{sp[0], sp[MX_ROWS * MX_BJ]}, eAv[mx_alpha(p)] + eBv[mx_beta(p)] - 14};
+            };
+            auto T = [&](int c, int p) -> Term {
+                const Term t = S(p);
+                return term(xdf{sm.cfh[c][q], sm.cfl[c][q], sm.cfe[c][q]}, t.m, t.x);
+            };
             xdf X[5];
-            X[0] = xdf{Sm[0].h, Sm[0].l, Se[0]};
+            {
+                const Term t0 = S(0);
+                X[0] = xdf{t0.m.h, t0.m.l, t0.x};
+            }
             X[1] = X[2] = X[3] = X[4] = xdf{0.f, 0.f, 0};
             if (role & kTE) {
-                const Term t[3] = {term(cf[0], Sm[0], Se[0]), term(cf[1], Sm[1], Se[1]), term(cf[2], Sm[2], Se[2])};
+                const Term t[3] = {T(0, 0), T(1, 1), T(2, 2)};
                 X[1] = frame_sum(t);
             }
             if (pol) {
-                const Term t[6] = {term(cf[3], Sm[0], Se[0]), term(cf[4], Sm[1], Se[1]), term(cf[5], Sm[2], Se[2]),
-                                   term(cf[6], Sm[3], Se[3]), term(cf[7], Sm[4], Se[4]), term(cf[8], Sm[5], Se[5])};
+                const Term t[6] = {T(3, 0), T(4, 1), T(5, 2), T(6, 3), T(7, 4), T(8, 5)};
                 X[2] = frame_sum(t);
                 if (odd) {
-                    const Term u[3] = {term(cf[9], Sm[6], Se[6]), term(cf[10], Sm[7], Se[7]), term(cf[11], Sm[8], Se[8])};
+                    const Term u[3] = {T(9, 6), T(10, 7), T(11, 8)};
                     X[3] = frame_sum(u);
                     const Term v[2] = {Term{dfl{X[2].h, X[2].l}, X[2].e}, Term{dfl{-X[3].h, -X[3].l}, X[3].e}};
                     X[4] = frame_sum(v);
@@ -266,35 +302,18 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
 #pragma unroll
             for (int x = 0; x < 5; ++x) {
                 if (!(role & bits[x])) continue;
-                stage[x][0][q] = times_int(X[x], 2 * l2 + 1);
-                stage[x][1][q] = times_int(X[x], 2 * l1 + 1);
+                sm.stage[x][0][q] = times_int(X[x], 2 * l2 + 1);
+                sm.stage[x][1][q] = times_int(X[x], 2 * l1 + 1);
             }
         }
         __syncthreads();
-        // ---- rows: M[l1][l2 = l1 + d] and mirrored M[l2][l1 = l2 - d], d = 2 i0 .. 2 i0 + 2 EB_I - 1
-        const int nrow = EB_I + EB_J;
         for (int x = 0; x < 5; ++x) {
             if (!(role & bits[x]) || a.slot[x] < 0) continue;
             double *base = a.out + ((size_t)w * a.nspec + a.slot[x]) * (size_t)n * (size_t)n;
-            for (int e = q; e < 2 * nrow * 2 * EB_I; e += EB_T) {
-                const int mirror = e / (nrow * 2 * EB_I);
-                const int rr = (e / (2 * EB_I)) % nrow, dl = e % (2 * EB_I);
-                const int epi = dl & 1, eii = dl >> 1, ei = i0 + eii, d = 2 * ei + epi;
-                int el1, el2;
-                if (!mirror) {
-                    el1 = j0 - i0 - (EB_I - 1) + rr;
-                    el2 = el1 + d;
-                } else {
-                    el2 = i0 + j0 + rr;
-                    el1 = el2 - d;
-                }
-                const int ejj = el1 + ei - j0;
-                if (ejj < 0 || ejj >= EB_J) continue;
-                if (el1 < L1min || el2 > a.lmax || el1 > el2) continue;
-                const int pq = (epi * EB_J + ejj) * EB_I + eii;
-                if (!mirror) base[(size_t)(el1 - a.lmin) * n + (el2 - a.lmin)] = stage[x][0][pq];
-                else if (el1 != el2) base[(size_t)(el2 - a.lmin) * n + (el1 - a.lmin)] = stage[x][1][pq];
-            }
+            const double *stg = &sm.stage[x][0][0];
+#pragma unroll
+            for (int k = 0; k < NWR; ++k)
+                if (widx[k] >= 0) base[woff[k]] = stg[widx[k]];
         }
         __syncthreads();
     }
@@ -388,7 +407,14 @@ cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st) {
         return cudaGetLastError();
     }
     dim3 grid((a.lmax + 1 + EB_J - 1) / EB_J, NI / EB_I);
-    k_mixed_epilogue_dense<<<grid, EB_T, 0, st>>>(a);
+    static bool attr = false;   // the attribute is per function; set once per process
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_mixed_epilogue_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(EpiSmem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_mixed_epilogue_dense<<<grid, EB_T, sizeof(EpiSmem), st>>>(a);
     return cudaGetLastError();
 }
 
