@@ -260,12 +260,12 @@ def workload_config(world, precision="fp64"):
 
 
 # ---------------------------------------------------------------- profiles
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+def recorded_traffic(summary, source, key):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, or
     None if absent or taken on a different kernel source."""
     import hashlib
-    path = os.path.join(PROFILE_DIR, "ncu_%s_full_spin_3000.txt" % kernel)
-    src = os.path.join(ROOT, "paper_2602_15605_gb300", "csrc", "plain_fp64.cu")
+    path = os.path.join(PROFILE_DIR, summary)
+    src = os.path.join(ROOT, "paper_2602_15605_gb300", "csrc", source)
     if not os.path.exists(path) or not os.path.exists(src):
         return None
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -277,8 +277,8 @@ def recorded_traffic(kernel):
     if vals.get("source_sha256_16") != digest:
         return None
     try:
-        return float(vals["dram_bytes_per_launch_full_size"])
-    except (KeyError, ValueError):
+        return float(vals[key].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
 
 
@@ -432,21 +432,25 @@ def run_ours(args, rank, world, local):
     def fp64_roofline(stats, clk):
         dom_name, dom = max(((k, v) for k, v in stats.items() if k.startswith("plain")), key=lambda kv: kv[1]["ms"])
         achieved = dom["flop"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
+        traffic = recorded_traffic("ncu_%s_full_spin_3000.txt" % dom_name, "plain_fp64.cu",
+                                   "dram_bytes_per_launch_full_size") if LMAX == 3000 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(dom_name), "kernel": dom_name,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom_name,
                 "kernel_ms_per_launch": dom["ms"] / max(dom["launches"], 1),
                 "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.26 TFLOP/s)"}
         if clk and clk.get("sm_mhz"):
             roof["frac_at_sampled_clock"] = achieved / (2.0 * 2 * 152 * clk["sm_mhz"] * 1e6 / 1e12)
         return roof
 
-    def mixed_roofline(stats):
+    def mixed_roofline(stats, traffic_summary=None):
         name, g = max(((k, v) for k, v in stats.items() if k.startswith("mixed_gemm")), key=lambda kv: kv[1]["ms"])
+        traffic = (recorded_traffic(traffic_summary, "mixed_gemm.cu", "dram_bytes_per_launch")
+                   if traffic_summary and LMAX == 3000 else None)
         peak, src = bf16_peak()
         issued = g["issued_flop"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
         algo = g["flop"] / (g["ms"] * 1e-3) / 1e12 if g["ms"] > 0 else 0.0
         return {"bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak,
-                "traffic": None, "kernel": name, "kernel_ms_per_launch": g["ms"] / max(g["launches"], 1),
+                "traffic": traffic, "kernel": name, "kernel_ms_per_launch": g["ms"] / max(g["launches"], 1),
                 "algorithmic_tflops": algo, "peak_source": src,
                 "achieved_counts": "BF16 limb-product FLOP issued by the tcgen05 MMAs (21 per contraction term "
                                    "at 6 limbs) / event-timed kernel duration; algorithmic_tflops counts 2 FLOP "
@@ -472,7 +476,8 @@ def run_ours(args, rank, world, local):
     head_prec = coupling.MIXED_BF16 if args.precision == "mixed" else coupling.FP64
     step_ms, stats, clk, t_wall = timed_arm(head_prec, args.steps, args.warmup)
     launches = sum(v["launches"] for v in stats.values())
-    roofline = mixed_roofline(stats) if args.precision == "mixed" else fp64_roofline(stats, clk)
+    MIXED_SUMMARY = "ncu_mixed_gemm_s6_full_spin_3000.txt"
+    roofline = mixed_roofline(stats, MIXED_SUMMARY) if args.precision == "mixed" else fp64_roofline(stats, clk)
     other = None
     if not args.no_other:
         o_prec = coupling.FP64 if args.precision == "mixed" else coupling.MIXED_BF16
@@ -480,7 +485,7 @@ def run_ours(args, rank, world, local):
         o_ms, o_stats, o_clk, _ = timed_arm(o_prec, o_steps, 2)
         other = {"value": job_value(world, 5 * n_el, o_ms * 1e-3), "unit": UNIT, "ms_per_step": o_ms, "steps": o_steps,
                  "precision": "fp64" if args.precision == "mixed" else "mixed_bf16 (6 limbs)",
-                 "roofline": fp64_roofline(o_stats, o_clk) if args.precision == "mixed" else mixed_roofline(o_stats),
+                 "roofline": fp64_roofline(o_stats, o_clk) if args.precision == "mixed" else mixed_roofline(o_stats, MIXED_SUMMARY),
                  "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in o_stats.items()},
                  "clocks": o_clk}
         other["max_rel_err_vs_fp64"] = mixed_error()
