@@ -175,12 +175,22 @@ cpl_status cpl_build_host(cpl_ctx *ctx, const cpl_request *r, double *out_host);
 
 /*
  * A batch of independent requests (ragged lmax, band limits, window
- * counts) in one launch sequence: jobs[q] writes outs[q] (device pointers,
- * each of cpl_output_size(jobs + q) doubles).  All jobs must use the same
- * precision.  The work items of every job are merged into one cost-ordered
- * list and executed by one persistent kernel per sweep; the sequence is
- * captured once into a CUDA graph keyed by the batch shape and replayed on
- * later calls with the same shape.
+ * counts, bins): jobs[q] writes outs[q] (device pointers, each of
+ * cpl_output_size(jobs + q) doubles).  All jobs must use the same precision
+ * (and, for CPL_MIXED_BF16, the same mixed_slices).  The work items of all
+ * jobs are merged:
+ *   CPL_MIXED_BF16  one persistent tensor-core GEMM launch takes the items of
+ *                   every job by an atomic ticket (jobs that do not fit the
+ *                   scratch budget together run as several such chunks); the
+ *                   batch is planned once per signature (every field of every
+ *                   request, pointers included, and the contents of the
+ *                   band-limit and bin-edge arrays), its launch sequence is
+ *                   captured into a CUDA graph on the first call and replayed
+ *                   on later calls with the same signature;
+ *   CPL_FP64        one launch per kernel variant over the items of every
+ *                   job, heaviest first.
+ * Results equal those of cpl_build on each job (bit for bit for dense
+ * output; binned sums are accumulated in no fixed order).
  */
 cpl_status cpl_build_batch(cpl_ctx *ctx, const cpl_request *jobs, int n_jobs,
                            double *const *outs, void *stream);

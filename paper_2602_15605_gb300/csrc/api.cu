@@ -218,29 +218,21 @@ cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out) {
 
 namespace {
 
-// Work items (window, tile) of one request, heaviest first.  A tile whose
-// smallest |d| exceeds a window's last l3 contributes nothing for that
-// window and is dropped (the output is pre-zeroed in that case).
+// Work items (window, tile) of one request with their costs (l3 terms).  A
+// tile whose smallest |d| exceeds a window's last l3 contributes nothing for
+// that window and is dropped (the output is pre-zeroed in that case).
 void make_items(const std::vector<Tile> &tiles, const std::vector<int> &caps, int lmax, int lmin,
-                bool banded, std::vector<WorkItem> &items) {
+                bool banded, std::vector<std::pair<double, WorkItem>> &items) {
     items.clear();
-    std::vector<std::pair<double, WorkItem>> tmp;
     const int nw = (int)caps.size();
     for (int ti = 0; ti < (int)tiles.size(); ++ti) {
         const Tile &t = tiles[ti];
         for (int w = 0; w < nw; ++w) {
             if (banded && 2 * t.i0 + t.pi > caps[w]) continue;
-            WorkItem it{0, w, ti, 0};
             const double cost = banded ? tile_terms(t, lmax, lmin, caps[w]) : (double)t.cost;
-            tmp.emplace_back(cost, it);
+            items.emplace_back(cost, WorkItem{0, w, ti, 0});
         }
     }
-    std::stable_sort(tmp.begin(), tmp.end(),
-                     [](const std::pair<double, WorkItem> &a, const std::pair<double, WorkItem> &b) {
-                         return a.first > b.first;
-                     });
-    items.reserve(tmp.size());
-    for (auto &p : tmp) items.push_back(p.second);
 }
 
 struct Group {
@@ -248,127 +240,217 @@ struct Group {
     unsigned spectra;   // spectra this window pointer serves
 };
 
-// The plain FP64 build of one request on `st` (device pointers).
-cpl_status build_fp64(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The plain FP64 build of a batch of requests on `st` (device pointers).
+// Every request's window-role groups become sweeps (PlainJob); the work
+// items of all sweeps that run the same kernel variant are merged into one
+// list, heaviest first, and run by one launch.
+cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *outs, int n, cudaStream_t st) {
     cpl_status s;
-    if ((s = ensure_tables(c, r->lmax)) != CPL_OK) return s;
-    TileSet *ts = nullptr;
-    if ((s = get_tiles(c, r->lmax, r->lmin, &ts)) != CPL_OK) return s;
+    int lmax_all = 2;
+    for (int q = 0; q < n; ++q) lmax_all = std::max(lmax_all, reqs[q].lmax);
+    if ((s = ensure_tables(c, lmax_all)) != CPL_OK) return s;
 
-    const int nw = r->n_windows;
-    std::vector<int> caps(nw);
-    bool banded = false;
-    for (int w = 0; w < nw; ++w) {
-        int cap = std::min(2 * r->lmax, r->w_len - 1);
-        if (r->band_limit) cap = std::min(cap, r->band_limit[w]);
-        if (cap < 2 * r->lmax) banded = true;
-        caps[w] = cap;
-    }
-    // window roles sharing one pointer share one sweep
-    std::vector<Group> groups;
-    auto add = [&](const double *W, unsigned bits) {
-        if (!(r->spectra & bits)) return;
-        for (auto &g : groups)
-            if (g.W == W) {
-                g.spectra |= (r->spectra & bits);
-                return;
-            }
-        groups.push_back({W, r->spectra & bits});
+    struct JobInfo {
+        TileSet *ts = nullptr;
+        std::vector<int> caps;
+        bool banded = false;
+        int nb = 0;
+        std::vector<int> bin_of;
+        std::vector<double> bin_inv;
+        std::vector<std::pair<double, WorkItem>> items;
+        size_t o_cap = 0, o_binof = 0, o_bininv = 0;
     };
-    add(r->W_tt, kTT);
-    add(r->W_tp, kTE);
-    add(r->W_pp, kEE | kEEBB | kEB);
-
-    std::vector<WorkItem> items;
-    make_items(ts->host, caps, r->lmax, r->lmin, banded, items);
-
-    const int a_stride = 2 * r->lmax + 2;
-    if ((s = c->weights.ensure(sizeof(double) * (size_t)a_stride * nw * groups.size(), "weights")) != CPL_OK) return s;
-    if ((s = c->l3cap.ensure(sizeof(int) * nw, "l3 caps")) != CPL_OK) return s;
-    if ((s = c->items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1), "work items")) != CPL_OK) return s;
-
-    const int nb = r->bin_edges ? r->n_bins : 0;
-    std::vector<int> bin_of;
-    std::vector<double> bin_inv;
-    if (nb) {
-        bin_of.assign(r->lmax + 1, -1);
-        bin_inv.assign(nb, 0.0);
-        for (int b = 0; b < nb; ++b) {
-            for (int l = r->bin_edges[b]; l < r->bin_edges[b + 1]; ++l) bin_of[l] = b;
-            bin_inv[b] = 1.0 / (double)(r->bin_edges[b + 1] - r->bin_edges[b]);
+    struct Sweep {
+        int job;
+        Group G;
+        int slot[5];
+        int nge;
+        bool odd;
+        size_t a_off;   // doubles into the weights buffer
+    };
+    std::vector<JobInfo> jobs(n);
+    std::vector<Sweep> sweeps;
+    const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
+    size_t a_total = 0;
+    for (int q = 0; q < n; ++q) {
+        const cpl_request *r = reqs + q;
+        JobInfo &J = jobs[q];
+        if ((s = get_tiles(c, r->lmax, r->lmin, &J.ts)) != CPL_OK) return s;
+        const int nw = r->n_windows;
+        J.caps.resize(nw);
+        for (int w = 0; w < nw; ++w) {
+            int cap = std::min(2 * r->lmax, r->w_len - 1);
+            if (r->band_limit) cap = std::min(cap, r->band_limit[w]);
+            if (cap < 2 * r->lmax) J.banded = true;
+            J.caps[w] = cap;
         }
-        if ((s = c->bins_of.ensure(sizeof(int) * bin_of.size(), "bin map")) != CPL_OK) return s;
-        if ((s = c->bins_inv.ensure(sizeof(double) * nb, "bin sizes")) != CPL_OK) return s;
+        J.nb = r->bin_edges ? r->n_bins : 0;
+        if (J.nb) {
+            J.bin_of.assign(r->lmax + 1, -1);
+            J.bin_inv.assign(J.nb, 0.0);
+            for (int b = 0; b < J.nb; ++b) {
+                for (int l = r->bin_edges[b]; l < r->bin_edges[b + 1]; ++l) J.bin_of[l] = b;
+                J.bin_inv[b] = 1.0 / (double)(r->bin_edges[b + 1] - r->bin_edges[b]);
+            }
+        }
+        make_items(J.ts->host, J.caps, r->lmax, r->lmin, J.banded, J.items);
+        // window roles sharing one pointer share one sweep
+        std::vector<Group> groups;
+        auto add = [&](const double *W, unsigned b) {
+            if (!(r->spectra & b)) return;
+            for (auto &g : groups)
+                if (g.W == W) {
+                    g.spectra |= (r->spectra & b);
+                    return;
+                }
+            groups.push_back({W, r->spectra & b});
+        };
+        add(r->W_tt, kTT);
+        add(r->W_tp, kTE);
+        add(r->W_pp, kEE | kEEBB | kEB);
+        const int a_stride = 2 * r->lmax + 2;
+        for (const Group &G : groups) {
+            Sweep sw;
+            sw.job = q;
+            sw.G = G;
+            for (int x = 0; x < 5; ++x) sw.slot[x] = (G.spectra & bits[x]) ? spec_slot(r->spectra, bits[x]) : -1;
+            const int mode = (G.spectra & (kEE | kEEBB | kEB)) ? MODE_POL : (G.spectra & kTE) ? MODE_TE : MODE_TT;
+            plain_variant(mode, sw.slot, &sw.nge, &sw.odd);
+            sw.a_off = a_total;
+            a_total += (size_t)a_stride * nw;
+            sweeps.push_back(sw);
+        }
     }
+
+    // ---- items per kernel variant, heaviest first
+    auto vkey = [](int nge, bool odd) { return nge * 2 + (odd ? 1 : 0); };
+    std::vector<int> keys;
+    for (const Sweep &sw : sweeps)
+        if (std::find(keys.begin(), keys.end(), vkey(sw.nge, sw.odd)) == keys.end()) keys.push_back(vkey(sw.nge, sw.odd));
+    std::vector<std::vector<WorkItem>> vitems(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) {
+        std::vector<std::pair<double, WorkItem>> tmp;
+        for (size_t x = 0; x < sweeps.size(); ++x) {
+            if (vkey(sweeps[x].nge, sweeps[x].odd) != keys[k]) continue;
+            for (auto it : jobs[sweeps[x].job].items) {
+                it.second.job = (int32_t)x;
+                tmp.push_back(it);
+            }
+        }
+        std::stable_sort(tmp.begin(), tmp.end(), [](const std::pair<double, WorkItem> &a,
+                                                    const std::pair<double, WorkItem> &b) { return a.first > b.first; });
+        vitems[k].reserve(tmp.size());
+        for (auto &p : tmp) vitems[k].push_back(p.second);
+    }
+
+    // ---- one metadata buffer: sweep table, caps, bins, items
+    size_t o = 0;
+    const size_t o_jobs = o;
+    o = align256(o + sizeof(PlainJob) * sweeps.size());
+    for (JobInfo &J : jobs) {
+        J.o_cap = o;
+        o = align256(o + sizeof(int) * J.caps.size());
+        J.o_binof = o;
+        o = align256(o + sizeof(int) * J.bin_of.size());
+        J.o_bininv = o;
+        o = align256(o + sizeof(double) * J.bin_inv.size());
+    }
+    std::vector<size_t> o_items(keys.size());
+    for (size_t k = 0; k < keys.size(); ++k) {
+        o_items[k] = o;
+        o = align256(o + sizeof(WorkItem) * vitems[k].size());
+    }
+    if ((s = c->items.ensure(std::max<size_t>(o, 256), "work items")) != CPL_OK) return s;
+    if ((s = c->weights.ensure(sizeof(double) * std::max<size_t>(a_total, 1), "weights")) != CPL_OK) return s;
+    uint8_t *dmeta = c->items.as<uint8_t>();
+    double *dA = c->weights.as<double>();
+    std::vector<uint8_t> host(o, 0);
+    for (size_t x = 0; x < sweeps.size(); ++x) {
+        const Sweep &sw = sweeps[x];
+        const cpl_request *r = reqs + sw.job;
+        const JobInfo &J = jobs[sw.job];
+        PlainJob pj;
+        std::memset(&pj, 0, sizeof(pj));
+        pj.A = dA + sw.a_off;
+        pj.a_stride = 2 * r->lmax + 2;
+        pj.l3cap = reinterpret_cast<const int *>(dmeta + J.o_cap);
+        pj.tiles = J.ts->dev.as<Tile>();
+        pj.lmax = r->lmax;
+        pj.lmin = r->lmin;
+        pj.out = outs[sw.job];
+        pj.nspec = spec_count(r->spectra);
+        for (int q = 0; q < 5; ++q) pj.slot[q] = sw.slot[q];
+        pj.n_bins = J.nb;
+        pj.bin_of = J.nb ? reinterpret_cast<const int *>(dmeta + J.o_binof) : nullptr;
+        pj.bin_inv = J.nb ? reinterpret_cast<const double *>(dmeta + J.o_bininv) : nullptr;
+        std::memcpy(host.data() + o_jobs + x * sizeof(PlainJob), &pj, sizeof(pj));
+    }
+    for (const JobInfo &J : jobs) {
+        std::memcpy(host.data() + J.o_cap, J.caps.data(), sizeof(int) * J.caps.size());
+        if (J.nb) {
+            std::memcpy(host.data() + J.o_binof, J.bin_of.data(), sizeof(int) * J.bin_of.size());
+            std::memcpy(host.data() + J.o_bininv, J.bin_inv.data(), sizeof(double) * J.bin_inv.size());
+        }
+    }
+    for (size_t k = 0; k < keys.size(); ++k)
+        if (!vitems[k].empty())
+            std::memcpy(host.data() + o_items[k], vitems[k].data(), sizeof(WorkItem) * vitems[k].size());
 
     CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
-    CPL_CUDA_TRY(cudaMemcpyAsync(c->l3cap.ptr, caps.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, st));
-    if (!items.empty())
-        CPL_CUDA_TRY(cudaMemcpyAsync(c->items.ptr, items.data(), sizeof(WorkItem) * items.size(),
-                                     cudaMemcpyHostToDevice, st));
-    if (nb) {
-        CPL_CUDA_TRY(cudaMemcpyAsync(c->bins_of.ptr, bin_of.data(), sizeof(int) * bin_of.size(),
-                                     cudaMemcpyHostToDevice, st));
-        CPL_CUDA_TRY(cudaMemcpyAsync(c->bins_inv.ptr, bin_inv.data(), sizeof(double) * nb,
-                                     cudaMemcpyHostToDevice, st));
+    CPL_CUDA_TRY(cudaMemcpyAsync(dmeta, host.data(), o, cudaMemcpyHostToDevice, st));
+    for (int q = 0; q < n; ++q)
+        if (jobs[q].nb || jobs[q].banded) CPL_CUDA_TRY(cudaMemsetAsync(outs[q], 0, sizeof(double) * out_doubles(reqs + q), st));
+    for (const Sweep &sw : sweeps) {
+        const cpl_request *r = reqs + sw.job;
+        const int a_stride = 2 * r->lmax + 2;
+        LaunchScope ls(c, "window_weights", st);
+        CPL_CUDA_TRY(launch_weights(sw.G.W, r->w_len, r->n_windows,
+                                    reinterpret_cast<const int *>(dmeta + jobs[sw.job].o_cap), dA + sw.a_off, a_stride,
+                                    st));
+        ls.done(0.0, 16.0 * (double)a_stride * r->n_windows);
     }
-    if (nb || banded) CPL_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * out_doubles(r), st));
-
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        const Group &G = groups[gi];
-        double *A = c->weights.as<double>() + gi * (size_t)a_stride * nw;
-        {
-            LaunchScope ls(c, "window_weights", st);
-            CPL_CUDA_TRY(launch_weights(G.W, r->w_len, nw, c->l3cap.as<int>(), A, a_stride, st));
-            ls.done(0.0, 16.0 * (double)a_stride * nw);
-        }
+    for (size_t k = 0; k < keys.size(); ++k) {
         PlainArgs a;
         std::memset(&a, 0, sizeof(a));
         a.g = c->g.as<double>();
         a.h = c->h.as<double>();
-        a.A = A;
-        a.a_stride = a_stride;
-        a.l3cap = c->l3cap.as<int>();
-        a.tiles = ts->dev.as<Tile>();
-        a.items = c->items.as<WorkItem>();
-        a.n_items = (int)items.size();
-        a.lmax = r->lmax;
-        a.lmin = r->lmin;
-        a.out = out;
-        a.nspec = spec_count(r->spectra);
-        const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
-        for (int q = 0; q < 5; ++q) a.slot[q] = (G.spectra & bits[q]) ? spec_slot(r->spectra, bits[q]) : -1;
-        a.n_bins = nb;
-        a.bin_of = nb ? c->bins_of.as<int>() : nullptr;
-        a.bin_inv = nb ? c->bins_inv.as<double>() : nullptr;
-        int mode;
-        if (G.spectra & (kEE | kEEBB | kEB)) mode = MODE_POL;
-        else if (G.spectra & kTE) mode = MODE_TE;
-        else mode = MODE_TT;
-        int nge;
-        bool odd;
-        plain_variant(mode, a.slot, &nge, &odd);
-        const char *kname = nge == 1 ? "plain_fp64_tt" : nge == 3 ? "plain_fp64_te"
-                          : (nge == 6 && odd) ? "plain_fp64_pol" : nge == 6 ? "plain_fp64_even" : "plain_fp64_odd";
+        a.jobs = reinterpret_cast<const PlainJob *>(dmeta + o_jobs);
+        a.items = reinterpret_cast<const WorkItem *>(dmeta + o_items[k]);
+        a.n_items = (int)vitems[k].size();
+        a.nge = keys[k] / 2;
+        a.odd = keys[k] & 1;
+        const bool odd = a.odd != 0;
+        const char *kname = a.nge == 1 ? "plain_fp64_tt" : a.nge == 3 ? "plain_fp64_te"
+                          : (a.nge == 6 && odd) ? "plain_fp64_pol" : a.nge == 6 ? "plain_fp64_even" : "plain_fp64_odd";
         double flop = 0.0, bytes = 0.0;
         if (c->profiling) {
             // 2 FLOP per FMA: nge FMAs per even-L term, 3 per odd-L term;
             // bytes: each written spectrum stores both mirror entries once.
-            int nslots = 0;
-            for (int q = 0; q < 5; ++q) nslots += a.slot[q] >= 0;
-            for (const WorkItem &it : items) {
-                double e, o, np;
-                tile_terms_split(ts->host[it.tile], r->lmax, r->lmin, caps[it.win], &e, &o, &np);
-                flop += 2.0 * (nge * e + (odd ? 3.0 : 0.0) * o);
-                bytes += (nb ? 0.0 : 16.0) * nslots * np;
+            for (const WorkItem &it : vitems[k]) {
+                const Sweep &sw = sweeps[it.job];
+                const cpl_request *r = reqs + sw.job;
+                const JobInfo &J = jobs[sw.job];
+                int nslots = 0;
+                for (int q = 0; q < 5; ++q) nslots += sw.slot[q] >= 0;
+                double e, od, np;
+                tile_terms_split(J.ts->host[it.tile], r->lmax, r->lmin, J.caps[it.win], &e, &od, &np);
+                flop += 2.0 * (a.nge * e + (odd ? 3.0 : 0.0) * od);
+                bytes += (J.nb ? 0.0 : 16.0) * nslots * np;
             }
         }
         LaunchScope ls(c, kname, st);
-        CPL_CUDA_TRY(launch_plain(mode, a, st));
+        CPL_CUDA_TRY(launch_plain(a, st));
         ls.done(flop, bytes);
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));
     return CPL_OK;
+}
+
+cpl_status build_fp64(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
+    double *outs[1] = {out};
+    return build_fp64_batch(c, r, outs, 1, st);
 }
 
 cpl_status build_one(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
@@ -526,9 +608,7 @@ cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, doub
     if ((s = select_device(c)) != CPL_OK) return s;
     if (jobs[0].precision == CPL_MIXED_BF16)
         return cpl::build_mixed_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream, true);
-    for (int q = 0; q < n_jobs; ++q)
-        if ((s = build_one(c, jobs + q, outs[q], (cudaStream_t)stream)) != CPL_OK) return s;
-    return CPL_OK;
+    return build_fp64_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream);
 }
 
 cpl_status cpl_ctx_tune(cpl_ctx *c, int mode, const char *cache_path) {

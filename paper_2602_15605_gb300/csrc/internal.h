@@ -44,11 +44,11 @@ struct Tile {
 };
 static_assert(sizeof(Tile) == 16, "Tile must be 16 bytes");
 
-// Work item of a batched launch: a tile of one job and one window.
+// Work item of a launch: a tile of one sweep (PlainJob) and one window.
 struct WorkItem {
-    int32_t job;
+    int32_t job;     // index into PlainArgs::jobs
     int32_t win;
-    int32_t tile;    // index into the job's tile list
+    int32_t tile;    // index into the sweep's tile list
     int32_t pad;
 };
 
@@ -66,15 +66,14 @@ double tile_terms(const Tile &t, int lmax, int lmin, int band);  // exact l3 ter
 // Kernel families by which GEMM products they run (see plain_fp64.cu).
 enum PlainMode { MODE_TT = 0, MODE_TE = 1, MODE_POL = 2, MODE_ALL = 3 };
 
-struct PlainArgs {
-    const double *g;        // [pmax + 1]
-    const double *h;        // [pmax + 1]
+// One sweep: the window-role group of one request (the windows of one
+// pointer and the spectra they feed).  A launch runs the items of any
+// number of sweeps of the same kernel variant.
+struct PlainJob {
     const double *A;        // [n_win][a_stride] weights (2 l3 + 1) W / (4 pi), zero past the band
     int a_stride;
     const int *l3cap;       // [n_win] last l3 with nonzero weight
-    const Tile *tiles;       // tile list of the request
-    const WorkItem *items;   // (window, tile) pairs to run, heaviest first
-    int n_items;
+    const Tile *tiles;      // tile list of the request
     int lmax, lmin;
     double *out;            // dense [n_win][nspec][n][n] or binned [n_win][nspec][nb][nb]
     int nspec;
@@ -85,7 +84,17 @@ struct PlainArgs {
     const double *bin_inv;  // [n_bins] 1 / |b|
 };
 
-cudaError_t launch_plain(int mode, const PlainArgs &a, cudaStream_t st);
+struct PlainArgs {
+    const double *g;        // [pmax + 1]
+    const double *h;        // [pmax + 1]
+    const PlainJob *jobs;   // sweeps (device)
+    const WorkItem *items;  // (sweep, window, tile) triples to run, heaviest first
+    int n_items;
+    int nge;                // even-sweep contractions of the variant (0, 1, 3 or 6)
+    int odd;                // whether the odd sweep runs
+};
+
+cudaError_t launch_plain(const PlainArgs &a, cudaStream_t st);   // variant from a.nge / a.odd
 // Which template variant launch_plain runs: even-sweep contractions (0, 1,
 // 3 or 6) and whether the odd sweep runs.
 void plain_variant(int mode, const int slot[5], int *nge, bool *odd);

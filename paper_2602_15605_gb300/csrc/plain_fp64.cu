@@ -60,7 +60,7 @@ struct Shape {
     static constexpr int NG = NGE + (ODD ? 3 : 0);
 };
 
-__device__ __forceinline__ void write_out(const PlainArgs &p, int win, int slot, int l1, int l2,
+__device__ __forceinline__ void write_out(const PlainJob &p, int win, int slot, int l1, int l2,
                                           double xi) {
     if (slot < 0) return;
     const double m12 = (2.0 * l2 + 1.0) * xi;   // M[l1][l2] = (2 l2 + 1) Xi
@@ -81,18 +81,19 @@ __device__ __forceinline__ void write_out(const PlainArgs &p, int win, int slot,
 }
 
 template <int NGE, bool ODD>
-__global__ void __launch_bounds__(NT) k_plain(const PlainArgs p) {
+__global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
     using S = Shape<NGE, ODD>;
     __shared__ double sa[S::NA > 0 ? S::NA : 1][KC][TILE_I];
     __shared__ double sb[S::NB > 0 ? S::NB : 1][KC][TILE_J];
 
-    const WorkItem it = p.items[blockIdx.x];
+    const WorkItem it = pa.items[blockIdx.x];
+    const PlainJob &p = pa.jobs[it.job];
     const int win = it.win;
     const Tile t = p.tiles[it.tile];
     const int pi = t.pi, i0 = t.i0, j0 = t.j0;
     const double *__restrict__ A = p.A + (size_t)win * p.a_stride;
-    const double *__restrict__ g = p.g;
-    const double *__restrict__ h = p.h;
+    const double *__restrict__ g = pa.g;
+    const double *__restrict__ h = pa.h;
     const int cap = p.l3cap[win];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -279,14 +280,13 @@ void plain_variant(int mode, const int slot[5], int *nge, bool *odd) {
     }
 }
 
-// mode: which contractions run (see PlainMode); the odd sweep runs when
-// slot[EEBB] or slot[EB] is set.
-cudaError_t launch_plain(int mode, const PlainArgs &a, cudaStream_t st) {
+// One CTA per work item; the variant (even contractions, odd sweep) is the
+// same for every sweep of the launch (plain_variant of each sweep).
+cudaError_t launch_plain(const PlainArgs &a, cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
     dim3 grid(a.n_items);
-    int nge;
-    bool odd;
-    plain_variant(mode, a.slot, &nge, &odd);
+    const int nge = a.nge;
+    const bool odd = a.odd != 0;
     if (nge == 1) k_plain<1, false><<<grid, NT, 0, st>>>(a);
     else if (nge == 3) k_plain<3, false><<<grid, NT, 0, st>>>(a);
     else if (nge == 6 && odd) k_plain<6, true><<<grid, NT, 0, st>>>(a);

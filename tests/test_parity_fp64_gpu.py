@@ -178,3 +178,29 @@ def test_argument_errors_leave_output_untouched(ctx):
         ctx.build(lmax, W, None, None, coupling.TT, lmin=-1)
     torch.cuda.synchronize()
     assert torch.all(out == 7.0)
+
+
+def test_batch_mixed_variants_band_and_bins(ctx):
+    # one launch per kernel variant over the items of all jobs: a TT-only
+    # job, a full spin set with separate windows, a band-limited binned job
+    jobs = []
+    W1 = dev(windows.mask_like(88, seed=11))
+    jobs.append(dict(lmax=88, W_tt=W1, spectra=coupling.TT))
+    Wt, Wc, Wp = (dev(windows.gaussian_taper(121, s)) for s in (12, 13, 14))
+    jobs.append(dict(lmax=121, W_tt=Wt, W_tp=Wc, W_pp=Wp, spectra=coupling.ALL))
+    Wb = np.stack([windows.random_positive(150, seed=15 + q, band=b) for q, b in enumerate((40, 90))])
+    jobs.append(dict(lmax=150, W_tt=dev(Wb), W_tp=dev(Wb), W_pp=dev(Wb), spectra=coupling.TE | coupling.EEBB,
+                     band_limit=[40, 90], bin_edges=oracle.bin_edges(2, 150, 20)))
+    outs = ctx.build_batch(jobs)
+    ctx.sync()
+    for q, (j, o) in enumerate(zip(jobs, outs)):
+        single = ctx.build(**j).cpu().numpy()
+        if "bin_edges" in j:
+            assert np.allclose(o.cpu().numpy(), single, rtol=1e-14, atol=0.0)
+        else:
+            assert np.array_equal(o.cpu().numpy(), single)
+    # and the band-limited binned job against the oracle
+    ref, sab = oracle.coupling_dense(150, Wb, Wb, Wb, coupling.TE | coupling.EEBB, band_limit=[40, 90])
+    e = oracle.bin_edges(2, 150, 20)
+    errs = per_spectrum(outs[2].cpu().numpy(), oracle.bin_matrix(ref, 2, e), oracle.bin_matrix(sab, 2, e), ["TE", "EEBB"])
+    assert max(errs.values()) <= 1e-11, errs
