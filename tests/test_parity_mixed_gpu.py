@@ -281,3 +281,21 @@ def test_autotuned_batch_matches_untuned(ctx):
     for o, r, h in zip(outs, ref, host):
         _same(o.cpu().numpy(), r, h["bin_edges"] is not None)
     t.close()
+
+
+def test_batch_split_into_chunks_matches(ctx, monkeypatch):
+    # a scratch budget smaller than any job puts every job in its own chunk
+    # (one persistent GEMM launch each); the results must not change
+    jobs, host = _ragged_jobs()
+    ref = [o.cpu().numpy() for o in ctx.build_batch(jobs)]
+    monkeypatch.setenv("CPL_MIXED_SCRATCH_GB", "0.000001")
+    c = coupling.Context(0)
+    c.profile(True)
+    c.stats(reset=True)
+    outs = c.build_batch(jobs)    # profiling on: eager launches, counted
+    c.sync()
+    st = c.stats()
+    assert st["mixed_gemm_s6"]["launches"] == len(jobs)
+    for o, r, h in zip(outs, ref, host):
+        _same(o.cpu().numpy(), r, h["bin_edges"] is not None)
+    c.close()
