@@ -314,14 +314,15 @@ def build_noalloc(lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, ban
     return out
 
 
-def output_size(lmax, n_windows, spectra, lmin=2, w_len=None, band_limit=None, bin_edges=None):
+def output_size(lmax, n_windows, spectra, lmin=2, w_len=None, band_limit=None, bin_edges=None,
+                precision=FP64, slices=0):
     """cpl_output_size for a request (validates it; needs no GPU)."""
     keep = _Keep()
     w_len = 2 * lmax + 1 if w_len is None else w_len
     fake = 0x1000  # any non-NULL address: output_size never dereferences the windows
     r = _make_request(lmax, fake if spectra & TT else None, fake if spectra & TE else None,
                       fake if spectra & (EE | EEBB | EB) else None, spectra, lmin, band_limit, bin_edges,
-                      FP64, 0, lambda W: W, n_windows, w_len, keep)
+                      precision, slices, lambda W: W, n_windows, w_len, keep)
     n = ctypes.c_size_t()
     _check(load().cpl_output_size(ctypes.byref(r), ctypes.byref(n)))
     return n.value

@@ -154,8 +154,8 @@ cpl_status validate(const cpl_request *r, bool device_ptrs) {
     if (r->precision != CPL_FP64 && r->precision != CPL_MIXED_BF16)
         return fail(CPL_ERR_ARG, "unknown precision");
     if (r->precision == CPL_MIXED_BF16 && r->mixed_slices != 0 &&
-        (r->mixed_slices < 3 || r->mixed_slices > 6))
-        return fail(CPL_ERR_ARG, "mixed_slices must be 0 or in 3..6");
+        (r->mixed_slices < 4 || r->mixed_slices > 6))
+        return fail(CPL_ERR_ARG, "mixed_slices must be 0 or in 4..6");
     if (r->bin_edges) {
         if (r->n_bins < 1) return fail(CPL_ERR_ARG, "n_bins must be >= 1 with bin_edges");
         if (r->bin_edges[0] < r->lmin || r->bin_edges[r->n_bins] > r->lmax + 1)
@@ -502,10 +502,7 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     c->h.release();
     for (auto &t : c->tile_sets) t->dev.release();
     c->weights.release();
-    c->l3cap.release();
     c->items.release();
-    c->bins_of.release();
-    c->bins_inv.release();
     c->stage_w.release();
     c->stage_out.release();
     c->mx.plans.clear();

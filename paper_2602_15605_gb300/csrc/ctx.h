@@ -88,10 +88,8 @@ struct cpl_ctx {
     DevBuf g, h;                 // lookup tables (Sec. 3.1)
     std::vector<std::unique_ptr<TileSet>> tile_sets;
     std::vector<std::pair<long long, TileSet *>> tile_index;   // key (lmax, lmin)
-    DevBuf weights;              // A(l3) per role and window
-    DevBuf l3cap;
-    DevBuf items;
-    DevBuf bins_of, bins_inv;
+    DevBuf weights;              // FP64 path: A(l3) per sweep and window
+    DevBuf items;                // FP64 path: sweep table, caps, bins and work items of the last build
     DevBuf stage_w, stage_out;   // cpl_build_host staging
     cudaStream_t own_stream = nullptr;
     cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams

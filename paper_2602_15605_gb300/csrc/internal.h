@@ -58,8 +58,6 @@ constexpr int TILE_J = 32;
 // All tiles of the valid region lmin <= l1 <= l2 <= lmax, ordered by cost
 // (largest first).
 void make_tiles(int lmax, int lmin, std::vector<Tile> &tiles);
-// Tiles whose l3 range meets [0, band] (any pair with |d| <= band).
-void filter_tiles_band(const std::vector<Tile> &all, int band, std::vector<Tile> &out);
 double tile_terms(const Tile &t, int lmax, int lmin, int band);  // exact l3 term count (both parities) of a tile
 
 // ---------------------------------------------------------------- plain FP64 kernels

@@ -91,12 +91,5 @@ void make_tiles(int lmax, int lmin, std::vector<Tile> &tiles) {
                      [](const Tile &a, const Tile &b) { return a.cost > b.cost; });
 }
 
-void filter_tiles_band(const std::vector<Tile> &all, int band, std::vector<Tile> &out) {
-    out.clear();
-    for (const Tile &t : all) {
-        // smallest |d| in the block is 2 i0 + pi; the l3 range starts at |d|
-        if (2 * t.i0 + t.pi <= band) out.push_back(t);
-    }
-}
 
 }  // namespace cpl

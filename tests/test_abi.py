@@ -81,6 +81,12 @@ def test_output_size_and_validation(lib):
     assert _status(lambda: coupling.output_size(10, 1, coupling.TT, bin_edges=[1, 5])) == 1
     assert _status(lambda: coupling.output_size(10, 1, coupling.TT, bin_edges=[2, 12])) == 1
     assert _status(lambda: coupling.output_size(40000, 1, coupling.TT)) == 2
+    # mixed precision: 4..6 limbs (0 = default 6)
+    for sl in (0, 4, 5, 6):
+        assert coupling.output_size(10, 1, coupling.TT, precision=coupling.MIXED_BF16, slices=sl) == 81
+    for sl in (3, 7, -1):
+        assert _status(lambda: coupling.output_size(10, 1, coupling.TT, precision=coupling.MIXED_BF16, slices=sl)) == 1
+    assert _status(lambda: coupling.output_size(10, 1, coupling.TT, precision=2)) == 1
 
 
 def test_ctx_create_without_gpu_fails_cleanly(lib):
