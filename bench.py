@@ -95,6 +95,42 @@ def windows_for_rank(rank):
     return tuple(windows.gaussian_taper(LMAX, s) for s in seeds)
 
 
+def oracle_batch_extrapolation(jobs_w, seconds, seed=13):
+    """The oracle on a sample of upper-triangle pairs of each ragged job (all
+    its windows, all five spectra): 3j terms/s per job and the full-batch
+    time extrapolated as terms / rate."""
+    import numpy as np
+    import oracle
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(seed)
+
+    def run(n):
+        rates, wall = [], 0.0
+        for lm, W in jobs_w:
+            P = np.sort(rng.integers(2, lm + 1, size=(n, 2)), axis=1).astype(np.int32)
+            t0 = time.perf_counter()
+            oracle.coupling_pairs(P[:, 0], P[:, 1], W, W, W, 31, threads=threads)
+            dt = max(time.perf_counter() - t0, 1e-6)
+            m = P[:, 0].astype(np.float64)   # l3 range: m + 1 even-L and m odd-L terms
+            terms = W.shape[0] * float(np.sum(4.0 * (m + 1) + 2.0 * m))
+            rates.append(terms / dt)
+            wall += dt
+        return rates, wall
+
+    n = 16 * threads
+    _, w = run(n)                                        # also pays for thread start-up
+    n = int(max(16 * threads, n * 0.25 * seconds / max(w, 1e-3)))
+    _, w = run(n)
+    n = int(max(16 * threads, n * seconds / max(w, 1e-3)))
+    rates, wall = run(n)
+    total_s = 0.0
+    for (lm, W), r in zip(jobs_w, rates):
+        _, t = work_counts(lm)
+        total_s += W.shape[0] * sum(t.values()) / r
+    return {"kind": "oracle", "cores": threads, "sample": "%d upper-triangle pairs per job, %.1f s" % (n, wall),
+            "terms_per_s_by_job": rates, "extrapolated_batch_s": total_s, "label": "extrapolated"}
+
+
 def ragged_seed0(rank):
     """First window seed of rank `rank`'s ragged batch (independent per rank)."""
     return 300 if rank == 0 else 300 + 1000 * rank
@@ -326,7 +362,8 @@ def batch_arm(ctx, args, world, local, mixed_roofline):
     clk = clocks.stop()
     ctx.sync()
     after = ctx.stats()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    per = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(per) / steps
     launches = sum(v["launches"] for v in after.values()) - sum(v["launches"] for v in before.values())
     ms = max_over_ranks(ms, world, "cuda:%d" % local)
     # one profiled (eager, not graph) step for the per-kernel breakdown
@@ -363,6 +400,9 @@ def batch_arm(ctx, args, world, local, mixed_roofline):
             "roofline": mixed_roofline(st),
             "kernels_profiled_step": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in st.items()},
             "max_rel_err_vs_fp64_lmax_le_4000": err, "clocks": clk,
+            "spread": {"ms_median": statistics.median(per), "ms_min": min(per), "ms_max": max(per)},
+            "cpu_extrapolated": (oracle_batch_extrapolation(jobs_w, args.cpu_seconds / 2)
+                                 if world == 1 and not args.no_cpu_baseline else None),
             "l2": "flushed between steps (256 MiB write, outside the timed events)"}
 
 
@@ -398,8 +438,18 @@ def run_ours(args, rank, world, local):
         """Times `steps` builds (L2 flushed between them, outside the events);
         returns (ms per step, per-kernel stats, sampled clocks, wall seconds)."""
         step = lambda: ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=out, precision=prec)
-        for _ in range(warmup):
-            step()
+        first_ms = None
+        for w in range(warmup):
+            if w == 0:
+                # the first call of this precision in the context: table build,
+                # B-image cache and the autotuner's candidate runs included
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                step()
+                torch.cuda.synchronize()
+                first_ms = (time.perf_counter() - t0) * 1e3
+            else:
+                step()
         torch.cuda.synchronize()
         ctx.sync()
         ctx.profile(True)
@@ -422,12 +472,15 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         t_wall = time.perf_counter() - t_wall
         clk = clocks.stop()
-        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        per = [a.elapsed_time(b) for a, b in evs]
+        ms = sum(per) / steps
         st = ctx.stats(reset=True)
         ctx.profile(False)
         ctx.sync()
         ms = max_over_ranks(ms, world, "cuda:%d" % local)
-        return ms, st, clk, t_wall
+        spread = {"ms_median": statistics.median(per), "ms_min": min(per), "ms_max": max(per),
+                  "first_call_ms": first_ms}
+        return ms, st, clk, t_wall, spread
 
     def fp64_roofline(stats, clk):
         dom_name, dom = max(((k, v) for k, v in stats.items() if k.startswith("plain")), key=lambda kv: kv[1]["ms"])
@@ -474,7 +527,7 @@ def run_ours(args, rank, world, local):
         return err
 
     head_prec = coupling.MIXED_BF16 if args.precision == "mixed" else coupling.FP64
-    step_ms, stats, clk, t_wall = timed_arm(head_prec, args.steps, args.warmup)
+    step_ms, stats, clk, t_wall, spread = timed_arm(head_prec, args.steps, args.warmup)
     launches = sum(v["launches"] for v in stats.values())
     MIXED_SUMMARY = "ncu_mixed_gemm_s6_full_spin_3000.txt"
     roofline = mixed_roofline(stats, MIXED_SUMMARY) if args.precision == "mixed" else fp64_roofline(stats, clk)
@@ -482,12 +535,12 @@ def run_ours(args, rank, world, local):
     if not args.no_other:
         o_prec = coupling.FP64 if args.precision == "mixed" else coupling.MIXED_BF16
         o_steps = max(3, min(args.steps, 10))
-        o_ms, o_stats, o_clk, _ = timed_arm(o_prec, o_steps, 2)
+        o_ms, o_stats, o_clk, _, o_spread = timed_arm(o_prec, o_steps, 2)
         other = {"value": job_value(world, 5 * n_el, o_ms * 1e-3), "unit": UNIT, "ms_per_step": o_ms, "steps": o_steps,
                  "precision": "fp64" if args.precision == "mixed" else "mixed_bf16 (6 limbs)",
                  "roofline": fp64_roofline(o_stats, o_clk) if args.precision == "mixed" else mixed_roofline(o_stats, MIXED_SUMMARY),
                  "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in o_stats.items()},
-                 "clocks": o_clk}
+                 "clocks": o_clk, "spread": o_spread}
         other["max_rel_err_vs_fp64"] = mixed_error()
 
     batch = None
@@ -526,7 +579,7 @@ def run_ours(args, rank, world, local):
                 "terms_per_s_by_spectrum": {k: world * v / step_s for k, v in terms.items()},
                 "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches),
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items()},
-                "clocks": clk, "wall_s_timed": t_wall}
+                "clocks": clk, "wall_s_timed": t_wall, "spread": spread}
         if other is not None:
             line["mixed" if args.precision == "fp64" else "fp64"] = other
         if batch is not None:

@@ -277,6 +277,16 @@ typedef enum { CPL_TUNE_OFF = 0, CPL_TUNE_MEASURE = 1 } cpl_tune_mode;
 cpl_status cpl_ctx_tune(cpl_ctx *ctx, int mode, const char *cache_path);
 
 /*
+ * Test hook (host-side fault injection; the paper has no counterpart): the
+ * n-th device allocation that the context makes from now on fails with
+ * CPL_ERR_OOM, exactly as if cudaMalloc had failed (n = 0 disables).  The
+ * failing call returns the status with the output untouched, and the
+ * context stays usable: caches whose buffers the failure freed are rebuilt
+ * by the next call.  CPL_ERR_ARG for n < 0.
+ */
+cpl_status cpl_ctx_inject_alloc_failure(cpl_ctx *ctx, int n);
+
+/*
  * Lookup table of Eqs. gdef / g_rec, as the library builds it: out[p] =
  * g(p) = (2p)! / (2^{2p} (p!)^2) for p = 0 .. pmax, each value the
  * double-double recurrence g(p) = (p - 1/2)/p g(p-1), g(0) = 1, rounded once

@@ -49,7 +49,7 @@ class KernelStat(ctypes.Structure):
 # Every symbol include/coupling.h declares.
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
-           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_g_table")
+           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_inject_alloc_failure", "cpl_g_table")
 
 _lock = threading.Lock()
 _lib = None
@@ -83,6 +83,7 @@ def load():
         L.cpl_g_table.argtypes = [ip, dp]
         L.cpl_ctx_profile.argtypes = [vp, ip]
         L.cpl_ctx_tune.argtypes = [vp, ip, ctypes.c_char_p]
+        L.cpl_ctx_inject_alloc_failure.argtypes = [vp, ip]
         L.cpl_ctx_stats.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]
         for name in EXPORTS:
             if name not in ("cpl_version", "cpl_last_error"):
@@ -171,6 +172,10 @@ class Context:
         m = TUNE_MEASURE if mode is True else TUNE_OFF if mode is False else int(mode)
         path = None if cache_path is None else os.fsencode(str(cache_path))
         _check(load().cpl_ctx_tune(self.handle, m, path))
+
+    def inject_alloc_failure(self, n):
+        """Test hook: the n-th device allocation from now on fails (0 disables)."""
+        _check(load().cpl_ctx_inject_alloc_failure(self.handle, int(n)))
 
     def stats(self, reset=False):
         """{kernel family: dict(launches, ms, flop, bytes)} (cpl_ctx_stats)."""

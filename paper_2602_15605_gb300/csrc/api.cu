@@ -19,6 +19,8 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+thread_local int *t_alloc_fault = nullptr;
+
 cpl_status fail(cpl_status s, const std::string &msg) {
     set_error(msg);
     return s;
@@ -119,6 +121,7 @@ struct LaunchScope {
 };
 
 cpl_status select_device(cpl_ctx *c) {
+    t_alloc_fault = &c->alloc_fault;   // allocations of this call count against the context's hook
     CPL_CUDA_TRY(cudaSetDevice(c->device));
     return CPL_OK;
 }
@@ -186,6 +189,7 @@ cpl_status ensure_tables(cpl_ctx *c, int lmax) {
     std::vector<double> g, h;
     build_tables_host(pmax, g, h);
     cpl_status s;
+    c->pmax = -1;   // invalid until both tables are rebuilt (a failed reallocation frees them)
     if ((s = c->g.ensure(sizeof(double) * (pmax + 1), "g table")) != CPL_OK) return s;
     if ((s = c->h.ensure(sizeof(double) * (pmax + 1), "h table")) != CPL_OK) return s;
     CPL_CUDA_TRY(cudaMemcpy(c->g.ptr, g.data(), sizeof(double) * (pmax + 1), cudaMemcpyHostToDevice));
@@ -496,6 +500,7 @@ cpl_status cpl_ctx_create(cpl_ctx **ctx, int device) {
 
 cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     if (!c) return CPL_OK;
+    if (t_alloc_fault == &c->alloc_fault) t_alloc_fault = nullptr;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     c->g.release();
@@ -606,6 +611,13 @@ cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, doub
     if (jobs[0].precision == CPL_MIXED_BF16)
         return cpl::build_mixed_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream, true);
     return build_fp64_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream);
+}
+
+cpl_status cpl_ctx_inject_alloc_failure(cpl_ctx *c, int n) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (n < 0) return fail(CPL_ERR_ARG, "n must be >= 0");
+    c->alloc_fault = n;
+    return CPL_OK;
 }
 
 cpl_status cpl_ctx_tune(cpl_ctx *c, int mode, const char *cache_path) {

@@ -12,6 +12,11 @@
 
 namespace cpl {
 
+// Allocation-failure hook of the calling thread's current context
+// (cpl_ctx_inject_alloc_failure): when it counts down to zero, the
+// allocation fails as if cudaMalloc had.
+extern thread_local int *t_alloc_fault;
+
 // A device buffer that only grows.
 struct DevBuf {
     void *ptr = nullptr;
@@ -21,6 +26,8 @@ struct DevBuf {
         if (ptr) cudaFree(ptr);
         ptr = nullptr;
         cap = 0;
+        if (t_alloc_fault && *t_alloc_fault > 0 && --*t_alloc_fault == 0)
+            return fail(CPL_ERR_OOM, std::string("device allocation failed for ") + what + " (injected)");
         size_t want = std::max(bytes, (size_t)256);
         if (cudaMalloc(&ptr, want) != cudaSuccess) {
             cudaGetLastError();
@@ -104,6 +111,7 @@ struct cpl_ctx {
         cudaEvent_t a, b;
         double flop, bytes, issued;
     };
+    int alloc_fault = 0;         // cpl_ctx_inject_alloc_failure countdown (0 = off)
     bool profiling = false;
     std::vector<KStat> kstats;
     std::vector<Pending> pending;

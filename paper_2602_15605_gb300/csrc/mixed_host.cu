@@ -640,10 +640,11 @@ static cpl_status ensure_common(cpl_ctx *c, int S, int nc_max, size_t scratch, c
         L.NSB_B = M.NC_B;
         L.b_var_bytes = (long long)L.gB * L.NC_B * (L.NC_B + 1) / 2 * S * L.IMG;
         const long long ncols_B = (long long)L.NC_B * MX_BJ;
-        if ((s = M.Bimg.ensure((size_t)2 * MX_NBV * L.b_var_bytes, "mixed B images")) != CPL_OK) return s;
+        // the cache counts as built only when all three buffers exist (Bimg set)
         if ((s = M.eB.ensure(sizeof(int16_t) * 2 * MX_NBV * ncols_B * L.NSB_B, "mixed B exponents")) != CPL_OK)
             return s;
         if ((s = M.emaxB.ensure(sizeof(int16_t) * 2 * MX_NBV * ncols_B, "mixed B maxima")) != CPL_OK) return s;
+        if ((s = M.Bimg.ensure((size_t)2 * MX_NBV * L.b_var_bytes, "mixed B images")) != CPL_OK) return s;
         const float *gh = M.gdd.as<float>();
         MxPrepBArgs pb;
         std::memset(&pb, 0, sizeof(pb));
@@ -658,7 +659,11 @@ static cpl_status ensure_common(cpl_ctx *c, int S, int nc_max, size_t scratch, c
         pb.L = L;
         const int idx = stat_index(c, "mixed_prep_b");
         cudaEvent_t ev = begin_launch(c, st);
-        CPL_CUDA_TRY(mx_launch_prep_b(pb, L.NC_B, st));
+        const cudaError_t le = mx_launch_prep_b(pb, L.NC_B, st);
+        if (le != cudaSuccess) {
+            M.Bimg.release();
+            return fail(CPL_ERR_CUDA, std::string("mx_launch_prep_b failed: ") + cudaGetErrorString(le));
+        }
         record_launch(c, idx, ev, st, 0.0, (double)2 * MX_NBV * L.b_var_bytes);
     }
     if ((s = M.arena.ensure(std::max<size_t>(scratch, 256), "mixed scratch arena")) != CPL_OK) return s;
