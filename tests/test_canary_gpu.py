@@ -1,0 +1,60 @@
+"""Unwritten or mis-mirrored outputs (GPU): the output buffer is prefilled
+with a NaN canary, so every element either path leaves unwritten shows up;
+the lower and upper triangles must agree, (2 l1 + 1) M[l1][l2] =
+(2 l2 + 1) M[l2][l1] (only Xi is symmetric)."""
+import numpy as np
+import pytest
+
+from paper_2602_15605_gb300 import coupling, windows
+
+pytestmark = pytest.mark.gpu
+CASES = [
+    dict(lmax=203, spectra=coupling.ALL, sep=True, band=None, lmin=2),
+    dict(lmax=150, spectra=coupling.TT | coupling.EEBB, sep=False, band=[60, 33], lmin=2),
+    dict(lmax=77, spectra=coupling.TT, sep=False, band=None, lmin=0),
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = coupling.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("precision", [coupling.FP64, coupling.MIXED_BF16])
+def test_every_element_written_and_mirrors_agree(ctx, case, precision):
+    import torch
+    cs = CASES[case]
+    if precision == coupling.MIXED_BF16 and cs["lmin"] < 2 and (cs["spectra"] & ~coupling.TT):
+        pytest.skip("spin-2 needs lmin >= 2")
+    lmax = cs["lmax"]
+    nw = 1 if cs["band"] is None else len(cs["band"])
+    if cs["band"] is None:
+        W = [np.stack([windows.mask_like(lmax, seed=s + q) for q in range(nw)]) for s in (20, 30, 40)]
+    else:
+        W = [np.stack([windows.random_positive(lmax, seed=s + q, band=b) for q, b in enumerate(cs["band"])])
+             for s in (20, 30, 40)]
+    Wd = [dev(w) for w in W]
+    if not cs["sep"]:
+        Wd = [Wd[0]] * 3
+    args = dict(spectra=cs["spectra"], lmin=cs["lmin"], band_limit=cs["band"], precision=precision)
+    _, _, shape = ctx.request(lmax, *Wd, **args)
+    out = torch.full(shape, float("nan"), dtype=torch.float64, device="cuda")
+    ctx.build(lmax, *Wd, out=out, **args)
+    ctx.sync()
+    M = out.cpu().numpy()
+    assert np.all(np.isfinite(M)), int(np.sum(~np.isfinite(M)))
+    ls = np.arange(cs["lmin"], lmax + 1, dtype=np.float64)
+    w1 = (2 * ls + 1)[:, None]
+    w2 = (2 * ls + 1)[None, :]
+    a = M * w1                      # (2 l1 + 1) M[l1][l2]
+    b = np.swapaxes(M, -1, -2) * w2  # (2 l2 + 1) M[l2][l1]
+    scale = np.max(np.abs(a), axis=(-1, -2), keepdims=True) + 1e-300
+    assert np.max(np.abs(a - b) / scale) <= 1e-14

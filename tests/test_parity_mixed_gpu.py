@@ -299,3 +299,14 @@ def test_batch_split_into_chunks_matches(ctx, monkeypatch):
     for o, r, h in zip(outs, ref, host):
         _same(o.cpu().numpy(), r, h["bin_edges"] is not None)
     c.close()
+
+
+def test_tt_lmin_zero_two_windows(ctx):
+    # l1 from 0 (TT only): the FP64 band covers l1 < 32, the GEMM the rest
+    lmax = 111
+    W = np.stack([windows.mask_like(lmax, seed=80), windows.mask_like(lmax, seed=81)])
+    d = dev(W)
+    got = mixed(ctx, lmax, d, None, None, coupling.TT, lmin=0)
+    ref, sab = oracle.coupling_dense(lmax, W, spectra=coupling.TT, lmin=0)
+    errs = per_spectrum(got, ref, sab, ["TT"])
+    assert max(errs.values()) <= TOL, errs
