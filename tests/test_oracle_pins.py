@@ -213,6 +213,49 @@ def test_oracle_pol_large_l_vs_paper_appendix_b():
     assert worst < 1e-12
 
 
+def _paper_011(j1, j2, j3):
+    """(j1 j2 j3; 0 -1 1) from the paper's Appendix B at 40 digits: Eq. joneeven
+    (two (0 0 0) symbols) for even J, Eq. joneodd for odd J."""
+    J = j1 + j2 + j3
+    Jm, Jp, Jq = -j1 + j2 + j3, j1 - j2 + j3, j1 + j2 - j3
+    den = mp.mpf(j2 * (j2 + 1) * j3 * (j3 + 1))
+    if J % 2 == 0:
+        return (mp.sqrt(mp.mpf((j2 + 1) * (j3 + 1)) / (j2 * j3)) * _mp000(j1, j2, j3)
+                + mp.sqrt(mp.mpf((J + 2) * (J + 3) * (Jm + 1) * (Jm + 2)) / den) / 2 * _mp000(j1, j2 + 1, j3 + 1))
+    return -mp.sqrt(mp.mpf((J + 2) * (Jm + 1) * (Jp + 1) * Jq) / den) / 2 * _mp000(j1, j2, j3 + 1)
+
+
+def test_oracle_m11_vs_racah_all_small():
+    # the (0,-1,1) configuration of the lensing / aberration weights
+    worst = 0.0
+    for j2 in range(1, 21):
+        for j3 in range(1, 21):
+            jmin, col = oracle.threej_column(j2, j3, 0, -1, 1)
+            for k, j1 in enumerate(range(jmin, j2 + j3 + 1)):
+                worst = max(worst, abs(col[k] - racah.threej_float(j1, j2, j3, 0, -1, 1)))
+    assert worst < 1e-14
+
+
+def test_paper_m11_helper_matches_racah():
+    mp.mp.dps = 40
+    for (j1, j2, j3) in [(0, 1, 1), (1, 1, 1), (2, 1, 1), (3, 2, 4), (4, 2, 4), (5, 7, 3), (9, 6, 8), (12, 10, 5)]:
+        assert abs(float(_paper_011(j1, j2, j3)) - racah.threej_float(j1, j2, j3, 0, -1, 1)) < 1e-15
+
+
+def test_oracle_m11_large_l_vs_paper_appendix_b():
+    mp.mp.dps = 40
+    rnd = random.Random(23)
+    worst = 0.0
+    for _ in range(8):
+        j2, j3 = rnd.randint(300, 3000), rnd.randint(300, 3000)
+        jmin, col = oracle.threej_column(j2, j3, 0, -1, 1)
+        for j1 in rnd.sample(range(jmin, j2 + j3 + 1), 4):
+            ref = _paper_011(j1, j2, j3)
+            scale = float(mp.sqrt(1 / mp.mpf(2 * max(j2, j3) + 1)))
+            worst = max(worst, abs(col[j1 - jmin] - float(ref)) / scale)
+    assert worst < 1e-12
+
+
 # ---------------------------------------------------------------- matrices
 def _dense(lmax, W, spectra, lmin=2, **kw):
     return oracle.coupling_dense(lmax, W, W, W, spectra, lmin=lmin, **kw)
