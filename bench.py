@@ -55,6 +55,16 @@ def bf16_peak():
         return 1900.0, "fallback 1.9 PFLOP/s"
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s) of this machine."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,6 +553,39 @@ def run_ours(args, rank, world, local):
                  "clocks": o_clk, "spread": o_spread}
         other["max_rel_err_vs_fp64"] = mixed_error()
 
+    # (j1 j2 j3; 0 -1 1) columns: 4096 pairs with j2, j3 in [1000, 3000]
+    threej = None
+    if not args.no_batch:
+        rng = np.random.default_rng(31)
+        j2 = rng.integers(1000, 3001, size=4096)
+        j3 = rng.integers(1000, 3001, size=4096)
+        stride = int(2 * np.minimum(j2, j3).max() + 1)
+        tout = torch.empty((4096, stride), dtype=torch.float64, device="cuda:%d" % local)
+        for _ in range(3):
+            ctx.threej_m11(j2, j3, out=tout, stride=stride)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a, b in ev:
+            flush.fill_(1)
+            a.record()
+            ctx.threej_m11(j2, j3, out=tout, stride=stride)
+            b.record()
+        torch.cuda.synchronize()
+        ctx.sync()
+        tms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        nsym = int(np.sum(2 * np.minimum(j2, j3) + 1))
+        peak = hbm_peak()
+        gbs = 4096 * stride * 8 / (tms * 1e-3) / 1e9
+        threej = {"workload": "4096 (j2, j3) pairs, j2, j3 uniform in [1000, 3000], rows padded to %d" % stride,
+                  "symbols_per_s": nsym / (tms * 1e-3), "ms": tms,
+                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak[0], "unit": "GB/s",
+                               "frac": gbs / peak[0], "traffic": None, "peak_source": peak[1],
+                               "achieved_counts": "bytes of the written rows / median event time; the kernel "
+                                                  "is instruction-issue bound (about 100 FP32/INT instructions "
+                                                  "per symbol: double-float products and the integer FP64 "
+                                                  "assembly), not DRAM bound"}}
+        del tout
+
     batch = None
     if not args.no_batch:
         batch = batch_arm(ctx, args, world, local, mixed_roofline)
@@ -584,6 +627,8 @@ def run_ours(args, rank, world, local):
             line["mixed" if args.precision == "fp64" else "fp64"] = other
         if batch is not None:
             line["batch"] = batch
+        if threej is not None:
+            line["threej_m11"] = threej
         try:
             line["tuner"] = [dict(lmax=e["key"][1], n_windows=e["key"][3], src=e["src"], order=e["order"],
                                   ms=e["ms"]) for e in map(json.loads, open(tune_file).read().splitlines())]

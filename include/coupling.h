@@ -287,6 +287,28 @@ cpl_status cpl_ctx_tune(cpl_ctx *ctx, int mode, const char *cache_path);
 cpl_status cpl_ctx_inject_alloc_failure(cpl_ctx *ctx, int n);
 
 /*
+ * cpl_threej_m11 -- the Wigner symbols (j1 j2 j3; 0 -1 1) for every j1 of
+ * each given (j2, j3): the (0,-1,1) configuration that appears in the
+ * lensing quadratic-estimator and aberration weights (Sec. 1; App. B,
+ * "Obtaining J(-1,1) symbols").  They come from the g table like the
+ * coupling matrices: for even J = j1 + j2 + j3 from the (0 0 0) symbol of
+ * the same triple (Eq. joneevensimp), for odd J from the (0 0 0) symbol of
+ * (j1, j2, j3 + 1) (Eq. joneodd); no recursion.
+ *
+ *   j2, j3      host arrays [n] with 1 <= j2, j3 and j2 + j3 <= CPL_THREEJ_JMAX
+ *               (m = -1, 1 needs j >= 1);
+ *   out         device array [n][out_stride] FP64 (caller-owned): row q holds
+ *               j1 = |j2 - j3| .. j2 + j3 at out[q * out_stride + j1 - |j2 - j3|]
+ *               and zeros in the rest of the row;
+ *   out_stride  >= 2 min(j2, j3) + 1 for every q.
+ * Asynchronous on `stream`.
+ * CPL_ERR_ARG / CPL_ERR_RANGE for invalid arguments (output untouched).
+ */
+#define CPL_THREEJ_JMAX 200000
+cpl_status cpl_threej_m11(cpl_ctx *ctx, const int *j2, const int *j3, int n, double *out, long long out_stride,
+                          void *stream);
+
+/*
  * Lookup table of Eqs. gdef / g_rec, as the library builds it: out[p] =
  * g(p) = (2p)! / (2^{2p} (p!)^2) for p = 0 .. pmax, each value the
  * double-double recurrence g(p) = (p - 1/2)/p g(p-1), g(0) = 1, rounded once

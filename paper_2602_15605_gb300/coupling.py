@@ -49,7 +49,8 @@ class KernelStat(ctypes.Structure):
 # Every symbol include/coupling.h declares.
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
-           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_inject_alloc_failure", "cpl_g_table")
+           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
+           "cpl_g_table")
 
 _lock = threading.Lock()
 _lib = None
@@ -84,6 +85,8 @@ def load():
         L.cpl_ctx_profile.argtypes = [vp, ip]
         L.cpl_ctx_tune.argtypes = [vp, ip, ctypes.c_char_p]
         L.cpl_ctx_inject_alloc_failure.argtypes = [vp, ip]
+        L.cpl_threej_m11.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, vp,
+                                     ctypes.c_longlong, vp]
         L.cpl_ctx_stats.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]
         for name in EXPORTS:
             if name not in ("cpl_version", "cpl_last_error"):
@@ -172,6 +175,27 @@ class Context:
         m = TUNE_MEASURE if mode is True else TUNE_OFF if mode is False else int(mode)
         path = None if cache_path is None else os.fsencode(str(cache_path))
         _check(load().cpl_ctx_tune(self.handle, m, path))
+
+    def threej_m11(self, j2, j3, out=None, stride=None):
+        """cpl_threej_m11: rows of (j1 j2 j3; 0 -1 1) for j1 = |j2 - j3| .. j2 + j3
+        (zero-padded to `stride`), one row per (j2, j3) pair; a float64 CUDA
+        tensor [n, stride] on torch's current stream."""
+        import torch
+        a = np.ascontiguousarray(np.asarray(j2, dtype=np.int32).reshape(-1))
+        b = np.ascontiguousarray(np.asarray(j3, dtype=np.int32).reshape(-1))
+        if a.size != b.size:
+            raise ValueError("j2 and j3 must have the same length")
+        if stride is None:
+            stride = int(2 * np.minimum(a, b).max() + 1) if a.size else 1
+        if out is None:
+            out = torch.empty((a.size, stride), dtype=torch.float64, device="cuda:%d" % self.device)
+        elif tuple(out.shape) != (a.size, stride) or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of shape %s" % ((a.size, stride),))
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        ip = ctypes.POINTER(ctypes.c_int)
+        _check(load().cpl_threej_m11(self.handle, a.ctypes.data_as(ip), b.ctypes.data_as(ip), int(a.size),
+                                     ctypes.c_void_p(out.data_ptr()), int(stride), ctypes.c_void_p(st)))
+        return out
 
     def inject_alloc_failure(self, n):
         """Test hook: the n-th device allocation from now on fails (0 disables)."""

@@ -510,6 +510,8 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     c->items.release();
     c->stage_w.release();
     c->stage_out.release();
+    c->threej_idx.release();
+    c->sqrt_tab.release();
     c->mx.plans.clear();
     for (DevBuf *b : {&c->mx.Bimg, &c->mx.eB, &c->mx.emaxB, &c->mx.gdd, &c->mx.arena, &c->mx.ticket, &c->mx.err})
         b->release();
@@ -611,6 +613,49 @@ cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, doub
     if (jobs[0].precision == CPL_MIXED_BF16)
         return cpl::build_mixed_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream, true);
     return build_fp64_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream);
+}
+
+cpl_status cpl_threej_m11(cpl_ctx *c, const int *j2, const int *j3, int n, double *out, long long out_stride,
+                          void *stream) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (n < 0 || (n > 0 && (!j2 || !j3 || !out))) return fail(CPL_ERR_ARG, "j2, j3 and out must be non-NULL");
+    if (n == 0) return CPL_OK;
+    int smax = 0;
+    for (int q = 0; q < n; ++q) {
+        if (j2[q] < 1 || j3[q] < 1) return fail(CPL_ERR_ARG, "j2 and j3 must be >= 1 for m = -1, 1");
+        if ((long long)j2[q] + j3[q] > CPL_THREEJ_JMAX) return fail(CPL_ERR_RANGE, "j2 + j3 exceeds CPL_THREEJ_JMAX");
+        if (out_stride < 2LL * std::min(j2[q], j3[q]) + 1) return fail(CPL_ERR_ARG, "out_stride too small");
+        smax = std::max(smax, j2[q] + j3[q]);
+    }
+    cpl_status s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    if ((s = ensure_tables(c, smax + 1)) != CPL_OK) return s;
+    if ((s = c->threej_idx.ensure(sizeof(int) * 2 * (size_t)n, "3j indices")) != CPL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d = c->threej_idx.as<int>();
+    CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
+    // square roots of the tables and of the integers up to 2 (j2 + j3) + 4
+    const int nn = 2 * smax + 4;
+    if (c->sq_pmax != c->pmax || c->sq_nn < nn) {
+        const int np1 = c->pmax + 1, nn_b = std::max(nn, 2 * CPL_THREEJ_JMAX / 8);
+        c->sq_pmax = -1;
+        if ((s = c->sqrt_tab.ensure(sizeof(float2) * (2 * (size_t)np1 + nn_b), "square-root tables")) != CPL_OK)
+            return s;
+        float2 *sg = c->sqrt_tab.as<float2>();
+        CPL_CUDA_TRY(launch_sqrt_tables(c->g.as<double>(), c->h.as<double>(), np1, nn_b, sg, sg + np1, sg + 2 * np1, st));
+        c->sq_pmax = c->pmax;
+        c->sq_nn = nn_b;
+    }
+    const float2 *sg = c->sqrt_tab.as<float2>(), *sh = sg + (c->pmax + 1), *sn = sg + 2 * (c->pmax + 1);
+    CPL_CUDA_TRY(cudaMemcpyAsync(d, j2, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    CPL_CUDA_TRY(cudaMemcpyAsync(d + n, j3, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    {
+        LaunchScope ls(c, "threej_m11", st);
+        CPL_CUDA_TRY(launch_threej_m11(sg, sh, sn, d, d + n, n, out, out_stride, st));
+        ls.done(0.0, 8.0 * (double)n * (double)out_stride);
+    }
+    CPL_CUDA_TRY(cudaEventRecord(c->done, st));
+    return CPL_OK;
 }
 
 cpl_status cpl_ctx_inject_alloc_failure(cpl_ctx *c, int n) {

@@ -98,6 +98,9 @@ struct cpl_ctx {
     DevBuf weights;              // FP64 path: A(l3) per sweep and window
     DevBuf items;                // FP64 path: sweep table, caps, bins and work items of the last build
     DevBuf stage_w, stage_out;   // cpl_build_host staging
+    DevBuf threej_idx;           // cpl_threej_m11: (j2, j3) of the last call
+    DevBuf sqrt_tab;             // cpl_threej_m11: sqrt g | sqrt h (pmax + 1 each) | sqrt n (sq_nn), FP32 pairs
+    int sq_pmax = -1, sq_nn = 0;
     cudaStream_t own_stream = nullptr;
     cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams
     // per-kernel accounting (cpl_ctx_stats)

@@ -100,5 +100,11 @@ void plain_variant(int mode, const int slot[5], int *nge, bool *odd);
 void tile_terms_split(const Tile &t, int lmax, int lmin, int cap, double *even, double *odd, double *pairs);
 cudaError_t launch_weights(const double *W, int w_len, int n_win, const int *l3cap,
                            double *A, int a_stride, cudaStream_t st);
+// (j1 j2 j3; 0 -1 1) rows for device arrays j2, j3 from sqrt g, sqrt h, sqrt n
+// held as double-float (threej.cu)
+cudaError_t launch_sqrt_tables(const double *g, const double *h, int np1, int nn, float2 *sg, float2 *sh, float2 *sn,
+                               cudaStream_t st);
+cudaError_t launch_threej_m11(const float2 *sg, const float2 *sh, const float2 *sn, const int *j2, const int *j3,
+                              int n, double *out, long long stride, cudaStream_t st);
 
 }  // namespace cpl
