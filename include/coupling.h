@@ -309,6 +309,50 @@ cpl_status cpl_threej_m11(cpl_ctx *ctx, const int *j2, const int *j3, int n, dou
                           void *stream);
 
 /*
+ * cpl_decouple -- mode decoupling: the underlying spectra C from measured
+ * pseudo-spectra by solving the linear systems of Eq. pseudo_cl (Sec. 2;
+ * kernels of App. A) for every window and right-hand side:
+ *
+ *   TT:     K^TT C^TT = pcl^TT            TE: K^TE C^TE = pcl^TE (TB alike)
+ *   EE/BB:  K^EE C^EE + K^EEBB C^BB = pcl^EE,  K^EEBB C^EE + K^EE C^BB = pcl^BB
+ *   EB:     K^EB C^EB = pcl^EB,  K^EB = K^EE - K^EEBB (the CPL_EB block)
+ *
+ * K[l1][l2] is a cpl_build output block (row l1 = pseudo-spectrum
+ * multipole).  For binned output the same equations hold for the band powers
+ * pcl_b = (1/|b|) sum_{l in b} pcl_l, exactly when C is constant inside
+ * each bin.
+ *
+ *   n          block size: lmax - lmin + 1 (dense) or n_bins (binned),
+ *              1 <= n <= CPL_DECOUPLE_NMAX.
+ *   n_windows  windows stacked in M (>= 1).
+ *   spectra    the spectrum set M was built with.  CPL_EE and CPL_EEBB must
+ *              come together (the EE/BB system couples through EE->BB).
+ *   M          device, [n_windows][nspec][n][n] FP64, the cpl_build layout
+ *              (spectra in increasing bit order); read only.
+ *   pcl        device, [n_windows][n_rhs][n_fields][n] FP64: the fields TT,
+ *              TE, EE, BB, EB of the requested set in that order (EE and BB
+ *              both present with CPL_EE); read only.
+ *   n_rhs      pseudo-spectra per window (e.g. simulations),
+ *              1 <= n_rhs <= CPL_DECOUPLE_RHS_MAX.
+ *   out        device, layout of pcl (caller-owned, must not overlap M or
+ *              pcl): the decoupled spectra.
+ *   info       device int [n_windows][n_systems] or NULL; systems per window
+ *              in the order TT, TE, EE+EEBB, EE-EEBB, EB (present ones
+ *              only).  0 on success; k + 1 when the k-th pivot of that system
+ *              was zero or not finite, in which case its outputs are NaN.
+ *   stream     cudaStream_t or NULL.
+ *
+ * Each system is solved in FP64 by Gaussian elimination with partial
+ * pivoting; the EE/BB system is split exactly into (K^EE +- K^EEBB) systems.
+ * Results are deterministic.  Asynchronous on `stream`; CPL_ERR_ARG /
+ * CPL_ERR_RANGE for invalid arguments (output untouched).
+ */
+#define CPL_DECOUPLE_NMAX 1024
+#define CPL_DECOUPLE_RHS_MAX 4096
+cpl_status cpl_decouple(cpl_ctx *ctx, int n, int n_windows, unsigned spectra, const double *M, const double *pcl,
+                        int n_rhs, double *out, int *info, void *stream);
+
+/*
  * Lookup table of Eqs. gdef / g_rec, as the library builds it: out[p] =
  * g(p) = (2p)! / (2^{2p} (p!)^2) for p = 0 .. pmax, each value the
  * double-double recurrence g(p) = (p - 1/2)/p g(p-1), g(0) = 1, rounded once

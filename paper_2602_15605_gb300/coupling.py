@@ -47,10 +47,20 @@ class KernelStat(ctypes.Structure):
 
 
 # Every symbol include/coupling.h declares.
+def decouple_fields(spectra):
+    """Pseudo-spectrum fields per right-hand side of cpl_decouple: TT, TE, EE, BB, EB."""
+    return (bool(spectra & TT) + bool(spectra & TE) + 2 * bool(spectra & EE) + bool(spectra & EB))
+
+
+def decouple_systems(spectra):
+    """Linear systems per window of cpl_decouple: TT, TE, EE+EEBB, EE-EEBB, EB."""
+    return (bool(spectra & TT) + bool(spectra & TE) + 2 * bool(spectra & EE) + bool(spectra & EB))
+
+
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
            "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
-           "cpl_g_table")
+           "cpl_decouple", "cpl_g_table")
 
 _lock = threading.Lock()
 _lib = None
@@ -87,6 +97,7 @@ def load():
         L.cpl_ctx_inject_alloc_failure.argtypes = [vp, ip]
         L.cpl_threej_m11.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, vp,
                                      ctypes.c_longlong, vp]
+        L.cpl_decouple.argtypes = [vp, ip, ip, ctypes.c_uint, vp, vp, ip, vp, vp, vp]
         L.cpl_ctx_stats.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]
         for name in EXPORTS:
             if name not in ("cpl_version", "cpl_last_error"):
@@ -195,6 +206,35 @@ class Context:
         ip = ctypes.POINTER(ctypes.c_int)
         _check(load().cpl_threej_m11(self.handle, a.ctypes.data_as(ip), b.ctypes.data_as(ip), int(a.size),
                                      ctypes.c_void_p(out.data_ptr()), int(stride), ctypes.c_void_p(st)))
+        return out
+
+    def decouple(self, M, pcl, spectra, info=None, out=None):
+        """cpl_decouple: underlying spectra from pseudo-spectra (Eq. pseudo_cl).
+        M: float64 CUDA tensor [n_windows, nspec, n, n] (cpl_build layout);
+        pcl: [n_windows, n_rhs, n_fields, n] with fields TT, TE, EE, BB, EB of
+        `spectra`; info: optional int32 CUDA tensor [n_windows, n_systems].
+        Returns `out` (layout of pcl) on torch's current stream."""
+        import torch
+        if M.dim() != 4 or M.shape[-1] != M.shape[-2] or M.dtype != torch.float64 or not M.is_contiguous():
+            raise ValueError("M must be a contiguous float64 tensor [n_windows, nspec, n, n]")
+        if pcl.dim() != 4 or pcl.dtype != torch.float64 or not pcl.is_contiguous():
+            raise ValueError("pcl must be a contiguous float64 tensor [n_windows, n_rhs, n_fields, n]")
+        nw, _, n, _ = M.shape
+        if pcl.shape[0] != nw or pcl.shape[-1] != n or pcl.shape[2] != decouple_fields(spectra):
+            raise ValueError("pcl shape %s does not match M %s and the spectrum set" % (tuple(pcl.shape), tuple(M.shape)))
+        if out is None:
+            out = torch.empty_like(pcl)
+        elif out.shape != pcl.shape or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor shaped like pcl")
+        ip_ = 0
+        if info is not None:
+            if info.dtype != torch.int32 or not info.is_contiguous() or info.numel() != nw * decouple_systems(spectra):
+                raise ValueError("info must be a contiguous int32 tensor [n_windows, n_systems]")
+            ip_ = info.data_ptr()
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        _check(load().cpl_decouple(self.handle, int(n), int(nw), int(spectra), ctypes.c_void_p(M.data_ptr()),
+                                   ctypes.c_void_p(pcl.data_ptr()), int(pcl.shape[1]), ctypes.c_void_p(out.data_ptr()),
+                                   ctypes.c_void_p(ip_), ctypes.c_void_p(st)))
         return out
 
     def inject_alloc_failure(self, n):

@@ -658,6 +658,79 @@ cpl_status cpl_threej_m11(cpl_ctx *c, const int *j2, const int *j3, int n, doubl
     return CPL_OK;
 }
 
+cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, const double *M, const double *pcl,
+                        int n_rhs, double *out, int *info, void *stream) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (!M || !pcl || !out) return fail(CPL_ERR_ARG, "M, pcl and out must be non-NULL");
+    if (n < 1 || n > CPL_DECOUPLE_NMAX) return fail(CPL_ERR_RANGE, "n must be in 1 .. CPL_DECOUPLE_NMAX");
+    if (n_windows < 1) return fail(CPL_ERR_ARG, "n_windows must be >= 1");
+    if (n_rhs < 1 || n_rhs > CPL_DECOUPLE_RHS_MAX) return fail(CPL_ERR_RANGE, "n_rhs must be in 1 .. CPL_DECOUPLE_RHS_MAX");
+    if (spectra == 0 || (spectra & ~31u)) return fail(CPL_ERR_ARG, "spectra must be a non-empty set of CPL_* bits");
+    if (!(spectra & kEE) != !(spectra & kEEBB))
+        return fail(CPL_ERR_ARG, "CPL_EE and CPL_EEBB must be decoupled together (the EE/BB system)");
+    DecoupleArgs a{};
+    a.M = M;
+    a.pcl = pcl;
+    a.out = out;
+    a.info = info;
+    a.n = n;
+    a.n_rhs = n_rhs;
+    a.ld = (n + n_rhs) | 1;
+    a.nspec = spec_count(spectra);
+    // fields TT, TE, EE, BB, EB of the requested set, systems TT, TE, EE+EEBB, EE-EEBB, EB
+    int nf = 0, fTT = -1, fTE = -1, fEE = -1, fBB = -1, fEB = -1;
+    if (spectra & kTT) fTT = nf++;
+    if (spectra & kTE) fTE = nf++;
+    if (spectra & kEE) { fEE = nf++; fBB = nf++; }
+    if (spectra & kEB) fEB = nf++;
+    a.n_fields = nf;
+    int q = 0;
+    auto add = [&](int kind, int s1, int s2, int f1, int f2) {
+        a.kind[q] = kind; a.slot1[q] = s1; a.slot2[q] = s2; a.field1[q] = f1; a.field2[q] = f2; ++q;
+    };
+    if (fTT >= 0) add(0, spec_slot(spectra, kTT), spec_slot(spectra, kTT), fTT, fTT);
+    if (fTE >= 0) add(0, spec_slot(spectra, kTE), spec_slot(spectra, kTE), fTE, fTE);
+    if (fEE >= 0) {
+        add(1, spec_slot(spectra, kEE), spec_slot(spectra, kEEBB), fEE, fBB);
+        add(2, spec_slot(spectra, kEE), spec_slot(spectra, kEEBB), fEE, fBB);
+    }
+    if (fEB >= 0) add(0, spec_slot(spectra, kEB), spec_slot(spectra, kEB), fEB, fEB);
+    a.sys_per_window = q;
+    a.n_sys = (long long)q * n_windows;
+
+    cpl_status s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int nsm = 0;
+    CPL_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    const size_t sys_bytes = sizeof(double) * (size_t)n * a.ld;
+    size_t smem = 0;
+    int grid;
+    if (sys_bytes <= (size_t)decouple_smem_limit()) {
+        smem = sys_bytes;
+        int bps = 0;
+        CPL_CUDA_TRY(decouple_blocks_per_sm(smem, &bps));
+        grid = (int)std::min<long long>(a.n_sys, (long long)nsm * std::max(bps, 1));
+    } else {
+        grid = (int)std::min<long long>(a.n_sys, nsm);
+        a.ws_stride = (size_t)n * a.ld;
+        CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
+        if ((s = c->dec_ws.ensure(sys_bytes * grid, "decoupling workspace")) != CPL_OK) return s;
+        a.ws = c->dec_ws.as<double>();
+    }
+    if (fEE >= 0)
+        CPL_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)n_windows * n_rhs * nf * n, st));
+    {
+        LaunchScope ls(c, "decouple", st);
+        CPL_CUDA_TRY(launch_decouple(a, grid, smem, st));
+        const double nn = n, R = n_rhs;
+        const double flop = (double)a.n_sys * ((nn - 1) * nn * (2 * nn - 1) / 3.0 + 2.0 * R * nn * (nn - 1));
+        ls.done(flop, 8.0 * (double)a.n_sys * (nn * nn + 2.0 * R * nn));
+    }
+    if (a.ws) CPL_CUDA_TRY(cudaEventRecord(c->done, st));
+    return CPL_OK;
+}
+
 cpl_status cpl_ctx_inject_alloc_failure(cpl_ctx *c, int n) {
     if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
     if (n < 0) return fail(CPL_ERR_ARG, "n must be >= 0");

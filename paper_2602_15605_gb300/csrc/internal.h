@@ -107,4 +107,23 @@ cudaError_t launch_sqrt_tables(const double *g, const double *h, int np1, int nn
 cudaError_t launch_threej_m11(const float2 *sg, const float2 *sh, const float2 *sn, const int *j2, const int *j3,
                               int n, double *out, long long stride, cudaStream_t st);
 
+// Mode decoupling (decouple.cu): one CTA per n x n system of Eq. pseudo_cl.
+// kind 0: K = M[slot1], rhs = pcl[field1], out[field1] = x;
+// kind 1: K = M[slot1] + M[slot2], rhs = pcl[field1] + pcl[field2], x/2 added to out[field1] and out[field2];
+// kind 2: the same with "-", x/2 added to out[field1] and -x/2 to out[field2].
+struct DecoupleArgs {
+    const double *M;        // [n_windows][nspec][n][n]
+    const double *pcl;      // [n_windows][n_rhs][n_fields][n]
+    double *out;            // layout of pcl
+    int *info;              // [n_sys] or NULL
+    int n, ld, n_rhs, n_fields, nspec, sys_per_window;
+    long long n_sys;
+    int kind[5], slot1[5], slot2[5], field1[5], field2[5];
+    double *ws;             // global workspace (grid x ws_stride doubles), NULL: shared memory
+    size_t ws_stride;
+};
+int decouple_smem_limit();
+cudaError_t launch_decouple(const DecoupleArgs &a, int grid, size_t smem, cudaStream_t st);
+cudaError_t decouple_blocks_per_sm(size_t smem, int *n);
+
 }  // namespace cpl

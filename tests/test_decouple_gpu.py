@@ -1,0 +1,184 @@
+"""Parity of cpl_decouple (GPU) with the decoupling oracle.
+
+Bar, per system K x = b of Eq. pseudo_cl (the EE/BB one as its 2n x 2n
+block matrix):
+  forward error  max|x - x_oracle| / max|x_oracle| <= 8 n eps cond_inf(K)
+  backward error max|K x - b| / (|K|_inf max|x| + max|b|) <= 8 n eps
+(both are the textbook bounds of LU with partial pivoting, with a small
+growth factor; eps = 2^-53).  Cases: dense and binned coupling matrices from
+the oracle, shared-memory and global-workspace sizes on both sides of the
+switch, several right-hand sides, n = 1 and n = CPL_DECOUPLE_NMAX, singular
+systems, and the full-size binned workload (16 band-limited windows,
+l_max = 8000, Delta l = 50) checked through the backward error.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import decouple as dc
+from paper_2602_15605_gb300 import coupling, windows
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+ALL = coupling.ALL
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2602_15605_gb300 import build_ext
+    build_ext.build()
+    c = coupling.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype or torch.float64, device="cuda")
+
+
+def systems(M, pcl, x, spectra):
+    """(K, b, x) of every system of Eq. pseudo_cl, the EE/BB one as a block matrix."""
+    f = dc.fields(spectra)
+    slots = [b for b in (1, 2, 4, 8, 16) if spectra & b]
+    out = []
+    for w in range(M.shape[0]):
+        for bit, name in ((1, "TT"), (2, "TE"), (16, "EB")):
+            if spectra & bit:
+                K = M[w, slots.index(bit)]
+                out.append((K, pcl[w, :, f.index(name)].T, x[w, :, f.index(name)].T))
+        if spectra & 4:
+            A, B = M[w, slots.index(4)], M[w, slots.index(8)]
+            K = np.block([[A, B], [B, A]])
+            ie, ib = f.index("EE"), f.index("BB")
+            out.append((K, np.concatenate([pcl[w, :, ie], pcl[w, :, ib]], axis=1).T,
+                        np.concatenate([x[w, :, ie], x[w, :, ib]], axis=1).T))
+    return out
+
+
+def check(M, pcl, got, spectra, ref=None):
+    worst_f = worst_b = 0.0
+    for q, (K, b, x) in enumerate(systems(M, pcl, got, spectra)):
+        n = K.shape[0]
+        bw = np.max(np.abs(K @ x - b)) / (np.max(np.abs(K).sum(axis=1)) * np.max(np.abs(x)) + np.max(np.abs(b)))
+        assert bw <= 8 * n * EPS, (q, bw)
+        worst_b = max(worst_b, bw / (n * EPS))
+        if ref is not None:
+            xr = systems(M, pcl, ref, spectra)[q][2]
+            fe = np.max(np.abs(x - xr)) / np.max(np.abs(xr))
+            kappa = np.linalg.cond(K, np.inf)
+            assert fe <= 8 * n * EPS * kappa, (q, fe, kappa)
+            worst_f = max(worst_f, fe / (n * EPS * kappa))
+    return worst_f, worst_b
+
+
+def run(ctx, M, pcl, spectra):
+    import torch
+    info = torch.full((M.shape[0], coupling.decouple_systems(spectra)), -7, dtype=torch.int32, device="cuda")
+    out = ctx.decouple(dev(M), dev(pcl), spectra, info=info)
+    ctx.sync()
+    return out.cpu().numpy(), info.cpu().numpy()
+
+
+def test_dense_small_all_spectra(ctx):
+    lmax = 40
+    W = np.stack([windows.mask_like(lmax, seed=60 + q) for q in range(3)])
+    M = np.concatenate([oracle.coupling_dense(lmax, W[q], W[q], W[q], ALL)[0] for q in range(3)])
+    rng = np.random.default_rng(11)
+    pcl = rng.uniform(0.1, 1.0, size=(3, 4, 5, lmax - 1))
+    got, info = run(ctx, M, pcl, ALL)
+    assert np.all(info == 0)
+    print("dense 39:", check(M, pcl, got, ALL, dc.decouple(M, pcl, ALL)))
+
+
+@pytest.mark.parametrize("lmax,delta,n_rhs", [(300, 5, 1), (300, 1, 3), (161, 1, 1), (161, 1, 20)])
+def test_binned_and_dense_sizes(ctx, lmax, delta, n_rhs):
+    # n = 60 (shared memory), 299 (global), 160 with one right-hand side
+    # (shared memory, 206 KB) and with 20 (global)
+    W = windows.mask_like(lmax, seed=90)
+    sp = coupling.TT | coupling.EE | coupling.EEBB | coupling.EB
+    Md = oracle.coupling_dense(lmax, W, W, W, sp)[0]
+    edges = oracle.bin_edges(2, lmax, delta)
+    M = oracle.bin_matrix(Md, 2, edges) if delta > 1 else Md
+    n = M.shape[-1]
+    rng = np.random.default_rng(n + n_rhs)
+    pcl = rng.uniform(0.1, 1.0, size=(1, n_rhs, 4, n))
+    got, info = run(ctx, M, pcl, sp)
+    assert np.all(info == 0)
+    print("n=%d rhs=%d:" % (n, n_rhs), check(M, pcl, got, sp, dc.decouple(M, pcl, sp)))
+
+
+def test_piecewise_constant_recovery(ctx):
+    lmax, delta = 200, 10
+    W = windows.mask_like(lmax, seed=5)
+    M = oracle.coupling_dense(lmax, W, W, W, ALL)[0]
+    edges = oracle.bin_edges(2, lmax, delta)
+    nb = len(edges) - 1
+    rng = np.random.default_rng(3)
+    Cb = rng.uniform(0.2, 1.0, size=(1, 2, 5, nb))
+    pcb = dc.bin_vector(dc.forward(M, np.repeat(Cb, np.diff(edges), axis=-1), ALL), 2, edges)
+    got, info = run(ctx, oracle.bin_matrix(M, 2, edges), pcb, ALL)
+    assert np.all(info == 0)
+    assert np.max(np.abs(got - Cb) / Cb) < 1e-11
+
+
+@pytest.mark.parametrize("n", [1, 2, 1024])
+def test_generic_matrices_edge_sizes(ctx, n):
+    # G + 3 sqrt(n) I (condition number <= 5 for Gaussian G), rows permuted so
+    # that partial pivoting has to find every pivot away from the diagonal
+    rng = np.random.default_rng(n)
+    sp = coupling.TT | coupling.TE
+    M = rng.normal(size=(2, 2, n, n)) + np.eye(n) * (3.0 * n ** 0.5)
+    for w in range(2):
+        for s_ in range(2):
+            M[w, s_] = M[w, s_][rng.permutation(n)]
+    pcl = rng.normal(size=(2, 2, 2, n))
+    got, info = run(ctx, M, pcl, sp)
+    assert np.all(info == 0)
+    print("n=%d:" % n, check(M, pcl, got, sp, dc.decouple(M, pcl, sp)))
+
+
+def test_singular_systems_report_info(ctx):
+    n = 12
+    sp = coupling.TT | coupling.EE | coupling.EEBB
+    rng = np.random.default_rng(8)
+    M = rng.normal(size=(2, 3, n, n)) + 4 * np.eye(n)
+    M[0, 0] = 0.0                       # TT of window 0: first pivot is zero
+    M[1, 2] = M[1, 1]                   # window 1: EE - EEBB = 0 (EE + EEBB = 2 EE stays regular)
+    pcl = rng.normal(size=(2, 1, 3, n))
+    got, info = run(ctx, M, pcl, sp)
+    assert info[0, 0] == 1 and np.all(np.isnan(got[0, :, 0]))
+    assert info[0, 1] == 0 and info[0, 2] == 0
+    assert info[1, 0] == 0 and info[1, 2] == 1
+    assert np.all(np.isnan(got[1, :, 1:3]))      # EE and BB share the failed difference system
+    assert np.all(np.isfinite(got[0, :, 1:3])) and np.all(np.isfinite(got[1, :, 0]))
+
+
+def test_argument_errors(ctx):
+    import torch
+    M = torch.zeros((1, 1, 4, 4), dtype=torch.float64, device="cuda")
+    p = torch.zeros((1, 1, 2, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(coupling.CouplingError):
+        ctx.decouple(M, p, coupling.EE)                      # EE without EE->BB (rejected by the library)
+    big = torch.zeros((1, 1, 1025, 1025), dtype=torch.float64, device="cuda")
+    with pytest.raises(coupling.CouplingError):
+        ctx.decouple(big, torch.zeros((1, 1, 1, 1025), dtype=torch.float64, device="cuda"), coupling.TT)
+
+
+def test_full_size_binned_band_limited(ctx):
+    """The binned coupling matrices of 16 band-limited windows at l_max = 8000
+    (Delta l = 50, 160 bins, all spectra), decoupled for 8 right-hand sides:
+    backward error of every system at the full size."""
+    import torch
+    lmax = 8000
+    W, Lw = windows.band_limited(lmax)
+    edges = oracle.bin_edges(2, lmax, 50)
+    d = dev(W)
+    M = ctx.build(lmax, d, d, d, ALL, band_limit=Lw, bin_edges=edges, precision=coupling.MIXED_BF16)
+    rng = np.random.default_rng(12)
+    pcl = rng.uniform(0.1, 1.0, size=(16, 8, 5, len(edges) - 1))
+    info = torch.full((16, 5), -7, dtype=torch.int32, device="cuda")
+    out = ctx.decouple(M, dev(pcl), ALL, info=info)
+    ctx.sync()
+    assert np.all(info.cpu().numpy() == 0)
+    print("full size:", check(M.cpu().numpy(), pcl, out.cpu().numpy(), ALL))
