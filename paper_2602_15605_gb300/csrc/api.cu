@@ -703,19 +703,39 @@ cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, cons
     cudaStream_t st = (cudaStream_t)stream;
     int nsm = 0;
     CPL_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    const size_t sys_bytes = sizeof(double) * (size_t)n * a.ld;
-    size_t smem = 0;
-    int grid;
-    if (sys_bytes <= (size_t)decouple_smem_limit()) {
-        smem = sys_bytes;
-        int bps = 0;
-        CPL_CUDA_TRY(decouple_blocks_per_sm(smem, &bps));
-        grid = (int)std::min<long long>(a.n_sys, (long long)nsm * std::max(bps, 1));
-    } else {
-        grid = (int)std::min<long long>(a.n_sys, nsm);
-        a.ws_stride = (size_t)n * a.ld;
+    // FP64 solver: augmented matrix in shared memory when it fits.  Refined
+    // solver (FP32 factors + FP64 residuals) when it needs fewer FP64
+    // operations: its residuals cost about 3 n^2 n_rhs per system against
+    // n^3 / 3 + 1.5 n^2 n_rhs for the FP64 solve, i.e. n_rhs <= 2n/9.
+    const size_t limit = (size_t)decouple_smem_limit();
+    const size_t direct_bytes = sizeof(double) * (size_t)n * a.ld;
+    a.direct_in_ws = direct_bytes > limit;
+    a.refine = 9 * n_rhs <= 2 * n && n <= IR_NMAX;
+    size_t ir_bytes = 0;
+    if (a.refine) {
+        ir_bytes = ir_layout(n, n_rhs, true).total;
+        a.l_in_ws = ir_bytes > limit;
+        if (a.l_in_ws) ir_bytes = ir_layout(n, n_rhs, false).total;
+        if (ir_bytes > limit) {
+            a.refine = 0;
+            a.l_in_ws = 0;
+            ir_bytes = 0;
+        }
+    }
+    const size_t smem = std::max(ir_bytes, a.direct_in_ws ? (size_t)0 : direct_bytes);
+    int bps = 0;
+    CPL_CUDA_TRY(decouple_blocks_per_sm(smem, &bps));
+    const int grid = (int)std::min<long long>(a.n_sys, (long long)nsm * std::max(bps, 1));
+    if (a.direct_in_ws || a.refine) {
+        // one slice per CTA: the refined solver's FP64 K1 +- K2 (n^2 doubles,
+        // whole 16-byte units) and, when not in shared memory, its padded FP32
+        // factors; or the FP64 solver's augmented matrix -- the larger, even
+        const size_t kc = ((size_t)n * n + 1) & ~(size_t)1;
+        const size_t f32 = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;
+        const size_t fp64 = a.direct_in_ws ? (size_t)n * a.ld : 0;
+        a.ws_stride = (std::max(a.refine ? kc + f32 : 0, fp64) + 1) & ~(size_t)1;
         CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
-        if ((s = c->dec_ws.ensure(sys_bytes * grid, "decoupling workspace")) != CPL_OK) return s;
+        if ((s = c->dec_ws.ensure(sizeof(double) * a.ws_stride * grid, "decoupling workspace")) != CPL_OK) return s;
         a.ws = c->dec_ws.as<double>();
     }
     if (fEE >= 0)

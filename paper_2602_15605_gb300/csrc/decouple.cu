@@ -12,12 +12,27 @@
 // add s/2 and +-t/2 into zeroed outputs with atomics; two addends onto zero
 // give the same rounded sum in either order, so the result is deterministic.
 //
-// Each CTA holds the augmented matrix [K | pcl^T] (n rows, ld = n + n_rhs
-// padded to odd for conflict-free column reads) in shared memory when it
-// fits, else in a global workspace slice (L2-resident at these sizes), and
-// runs Gaussian elimination with partial pivoting (the largest |a_ik|, the
-// lowest row on ties) followed by back substitution, all in FP64.  A zero or
-// non-finite pivot marks the system singular: info = k + 1 and NaN outputs.
+// Two solvers, both Gaussian elimination with partial pivoting (the largest
+// |a_ik|, the lowest row on ties):
+//
+// * Refined (few right-hand sides): GB300's FP64 pipe issues 2 FMA/clk/SM
+//   against 128 for FP32, so the O(n^3) factorisation runs in FP32 on
+//   K 2^-e (a power-of-two scale, exact) and the answer is brought to FP64
+//   accuracy by iterative refinement: x += K^-1 r with the FP32 factors,
+//   r = b - K x in FP64 from the FP64 matrix, until
+//   max|r| <= max|x| |K|_inf eps sqrt(n) for every right-hand side (the
+//   stopping rule of LAPACK's mixed-precision dsgesv, at most 30 steps).
+//   Each right-hand side is scaled by a power of two before it is rounded to
+//   FP32.  A zero FP32 pivot, a non-finite value or no convergence sends
+//   the system to the FP64 solver.
+// * FP64: elimination on the augmented matrix [K | pcl^T] (ld = n + n_rhs,
+//   padded to odd for conflict-free column reads) and back substitution.
+//   A zero or non-finite pivot marks the system singular: info = k + 1 and
+//   NaN outputs.
+//
+// Matrices live in shared memory when they fit, else in a per-CTA slice of a
+// global workspace (L2-resident at these sizes).  Every reduction has a fixed
+// order, so results are deterministic.
 #include <cmath>
 
 #include "internal.h"
@@ -27,6 +42,35 @@ namespace {
 
 constexpr int DC_THREADS = 512;
 constexpr int DC_WARPS = DC_THREADS / 32;
+constexpr int IR_ITMAX = 30;
+constexpr double EPS64 = 1.1102230246251565e-16;   // 2^-53
+
+// One system: K = K1 (+ or -) K2 and b = P[f1] (+ or -) P[f2] by kind.
+struct SysView {
+    const double *K1, *K2, *P;
+    int kind, f1, f2, nf, n;
+    __device__ __forceinline__ double k(size_t idx) const {
+        double v = K1[idx];
+        if (kind == 1) v = v + K2[idx];
+        else if (kind == 2) v = v - K2[idx];
+        return v;
+    }
+    __device__ __forceinline__ double b(int r, int i) const {
+        double v = P[((size_t)r * nf + f1) * n + i];
+        if (kind == 1) v = v + P[((size_t)r * nf + f2) * n + i];
+        else if (kind == 2) v = v - P[((size_t)r * nf + f2) * n + i];
+        return v;
+    }
+};
+
+struct Scratch {           // static shared scalars of the block reductions
+    double red_v[DC_WARPS];
+    int red_i[DC_WARPS];
+    double pv;
+    int piv;
+    double wnorm[2][DC_WARPS];            // per-warp |K|_inf and max |K_ij| candidates
+    unsigned long long wkey[2][DC_WARPS]; // per-warp pivot keys of the refined solver (2 buffers)
+};
 
 __device__ __forceinline__ void argmax_combine(double &v, int &i, double v2, int i2) {
     if (v2 > v || (v2 == v && i2 < i)) {
@@ -35,139 +79,534 @@ __device__ __forceinline__ void argmax_combine(double &v, int &i, double v2, int
     }
 }
 
-__global__ void __launch_bounds__(DC_THREADS) k_decouple(DecoupleArgs a) {
-    extern __shared__ __align__(16) double dsm[];
-    __shared__ double red_v[DC_WARPS];
-    __shared__ int red_i[DC_WARPS];
-    __shared__ int piv_s, bad_s;
+__device__ __forceinline__ void warp_argmax(double &v, int &i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        argmax_combine(v, i, v2, i2);
+    }
+}
 
+// Block-wide argmax of per-thread (v, i); all threads find the winner in
+// sc.piv / sc.pv on return.
+__device__ __forceinline__ void block_argmax(double v, int i, int nfill, Scratch &sc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_argmax(v, i);
+    if (lane == 0) {
+        sc.red_v[warp] = v;
+        sc.red_i[warp] = i;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < DC_WARPS ? sc.red_v[lane] : -1.0;
+        i = lane < DC_WARPS ? sc.red_i[lane] : nfill;
+        warp_argmax(v, i);
+        if (lane == 0) {
+            sc.piv = i;
+            sc.pv = v;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool finite_pos(double v) { return v > 0.0 && v <= 1.7976931348623157e308; }
+
+
+__device__ __forceinline__ unsigned long long pivot_key(float v, int i) {
+    return ((unsigned long long)__float_as_uint(fabsf(v)) << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)i);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// The largest of the DC_WARPS per-warp keys (every thread reads them all).
+__device__ __forceinline__ unsigned long long max_of_warps(const unsigned long long *w) {
+    unsigned long long v = 0ull;
+#pragma unroll
+    for (int q = 0; q < DC_WARPS; ++q) v = w[q] > v ? w[q] : v;
+    return v;
+}
+
+// FP32 LU + FP64 iterative refinement for n <= 32 NC.  Returns true with the
+// solution in xs[r * n + i] when every right-hand side met the stopping
+// rule; false sends the system to the FP64 solver.
+//
+// GB300 runs FP64 arithmetic, comparisons and conversions at 1/64 of the
+// FP32 rate, so besides the residual's n^2 FMAs per right-hand side the
+// solver spends no FP64 instruction per matrix element: K is rounded to FP32
+// unscaled (an entry outside FP32's range becomes inf or 0 and the
+// factorisation falls back), |K|_inf comes from FP32 row sums, maxima are
+// taken on the bit patterns of non-negative doubles, and the residual runs
+// one thread per row so no FP64 reduction is needed.  For kind 1 and 2 the
+// FP64 matrix K1 +- K2 is formed once into Kc (global scratch).
+//
+// The factorisation is LAPACK's right-looking blocked LU with 32-column
+// panels, on the system padded to np = 32 NC with identity rows and columns
+// (the padding never pivots and leaves the n x n factors unchanged):
+//   panel: 32 elimination steps on its columns, each pivot found while the
+//          previous step updates that column -- the lane that owns it offers
+//          (|a|, ~row) as one 64-bit key; each warp leaves its largest key
+//          in shared memory and every thread takes the largest of those
+//          after the barrier (largest |a|, lowest row on ties, independent of
+//          timing) -- with the row swaps applied to full rows (two barriers a
+//          step);
+//   U12 = L11^-1 A12: one thread per column, the 32 unknowns in registers;
+//   A22 -= L21 U12: register tiles of 4 x 4, 32-deep, float4 shared loads.
+// perm[i] is the original row now at position i.
+template <int NC>
+__device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, unsigned char *base,
+                                           const IrLayout &lay, Scratch &sc) {
+    constexpr int NP = 32 * NC;
+    constexpr int LDF = NP + 4;
+    constexpr int G2 = NC <= 4 ? 4 : (NC <= 8 ? 2 : 1);   // rows per group in the fill
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kind = S.kind;
+    const double *K1 = S.K1, *K2 = S.K2;
+    const double *P1 = S.P + (size_t)S.f1 * n, *P2 = S.P + (size_t)S.f2 * n;
+    const size_t pstride = (size_t)S.nf * n;
+    const double *Kr = kind ? Kc : K1;   // the FP64 matrix of the residuals
+    int *perm = reinterpret_cast<int *>(base + lay.perm);
+    float *dinv = reinterpret_cast<float *>(base + lay.dinv);
+    double *xs = reinterpret_cast<double *>(base + lay.x);
+    double *rs = reinterpret_cast<double *>(base + lay.r);
+    unsigned long long *xn = reinterpret_cast<unsigned long long *>(base + lay.xn);   // [2][R] bits of max |x|
+    unsigned long long *rn = reinterpret_cast<unsigned long long *>(base + lay.rn);   // [2][warp][R] bits of max |r|
+
+    // L = fl32(K) padded with identity (Kc = K1 +- K2 on the way), FP32 row sums of |L|
+    float wrow = 0.f;
+    for (int i0 = warp; i0 < NP; i0 += G2 * DC_WARPS) {
+        double v[G2][NC];
+#pragma unroll
+        for (int g = 0; g < G2; ++g) {
+            const int i = i0 + g * DC_WARPS;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const int j = lane + 32 * m;
+                v[g][m] = (i < n && j < n) ? __ldg(K1 + (size_t)i * n + j) : (i == j ? 1.0 : 0.0);
+            }
+        }
+        if (kind) {
+#pragma unroll
+            for (int g = 0; g < G2; ++g) {
+                const int i = i0 + g * DC_WARPS;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const int j = lane + 32 * m;
+                    if (i < n && j < n) {
+                        const double w = __ldg(K2 + (size_t)i * n + j);
+                        v[g][m] = kind == 1 ? v[g][m] + w : v[g][m] - w;
+                        Kc[(size_t)i * n + j] = v[g][m];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G2; ++g) {
+            const int i = i0 + g * DC_WARPS;
+            float rsum = 0.f;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const int j = lane + 32 * m;
+                const float f = (float)v[g][m];
+                if (i < NP) L[(size_t)i * LDF + j] = f;
+                if (i < n) rsum += fabsf(f);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+            wrow = fmaxf(wrow, rsum);
+        }
+    }
+    if (lane == 0) sc.wnorm[0][warp] = (double)wrow;
+    for (int i = tid; i < NP; i += DC_THREADS) perm[i] = i;
+    for (int idx = tid; idx < R * n; idx += DC_THREADS) {
+        const int r = idx / n, i = idx - r * n;
+        const double u = P1[r * pstride + i], w = P2[r * pstride + i];
+        xs[idx] = 0.0;
+        rs[idx] = kind == 0 ? u : (kind == 1 ? u + w : u - w);
+    }
+    __syncthreads();
+    float amax = 0.f;
+#pragma unroll
+    for (int q = 0; q < DC_WARPS; ++q) amax = fmaxf(amax, (float)sc.wnorm[0][q]);
+    if (!(amax > 0.f && amax <= 3.4028234663852886e38f)) return false;
+    const double anrm = (double)amax;
+
+    // blocked FP32 factorisation: L U = rows perm[0..np-1] of the padded fl32(K)
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+        const int k0 = 32 * c;
+        {
+            unsigned long long best = 0ull;
+            for (int i = k0 + tid; i < NP; i += DC_THREADS) {
+                const unsigned long long q = pivot_key(L[(size_t)i * LDF + k0], i);
+                best = q > best ? q : best;
+            }
+            best = warp_max_u64(best);
+            if (lane == 0) sc.wkey[k0 & 1][warp] = best;
+        }
+        __syncthreads();
+        for (int t = 0; t < 32; ++t) {
+            const int k = k0 + t;
+            const unsigned long long kk = max_of_warps(sc.wkey[k & 1]);
+            const int p = (int)(0xFFFFFFFFu - (unsigned)(kk & 0xFFFFFFFFull));
+            const float pv = __uint_as_float((unsigned)(kk >> 32));
+            if (!(pv > 0.f && pv <= 3.4028234663852886e38f)) return false;
+            if (p != k) {
+                for (int j = tid; j < NP; j += DC_THREADS) {
+                    const float tmp = L[(size_t)k * LDF + j];
+                    L[(size_t)k * LDF + j] = L[(size_t)p * LDF + j];
+                    L[(size_t)p * LDF + j] = tmp;
+                }
+                if (tid == 0) {
+                    const int tmp = perm[k];
+                    perm[k] = perm[p];
+                    perm[p] = tmp;
+                }
+            }
+            __syncthreads();
+            const float rinv = 1.0f / L[(size_t)k * LDF + k];
+            if (tid == 0) dinv[k] = rinv;
+            const float pkv = L[(size_t)k * LDF + k0 + lane];
+            unsigned long long kbest = 0ull;   // lane t + 1: best key of column k + 1 over this warp's rows
+            for (int i0 = k + 1 + warp; i0 < NP; i0 += 4 * DC_WARPS) {
+                float a[4], l[4];
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int i = i0 + g * DC_WARPS;
+                    const int ii = i < NP ? i : k;
+                    l[g] = L[(size_t)ii * LDF + k] * rinv;
+                    a[g] = L[(size_t)ii * LDF + k0 + lane];
+                }
+                __syncwarp();
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int i = i0 + g * DC_WARPS;
+                    if (i < NP) {
+                        if (lane > t) {
+                            const float u = fmaf(-l[g], pkv, a[g]);
+                            L[(size_t)i * LDF + k0 + lane] = u;
+                            if (lane == t + 1) {
+                                const unsigned long long q = pivot_key(u, i);
+                                kbest = q > kbest ? q : kbest;
+                            }
+                        } else if (lane == t) {
+                            L[(size_t)i * LDF + k] = l[g];
+                        }
+                    }
+                }
+            }
+            if (lane == t + 1) sc.wkey[(k + 1) & 1][warp] = kbest;
+            __syncthreads();
+        }
+        if (c + 1 == NC) break;
+        // U12 = L11^-1 A12, one thread per column of A12
+        const int j1 = k0 + 32, ncol = NP - j1;
+        for (int q = tid; q < ncol; q += DC_THREADS) {
+            const int j = j1 + q;
+            float u[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                float v = L[(size_t)(k0 + t) * LDF + j];
+#pragma unroll
+                for (int s2 = 0; s2 < t; ++s2) v = fmaf(-L[(size_t)(k0 + t) * LDF + k0 + s2], u[s2], v);
+                u[t] = v;
+            }
+#pragma unroll
+            for (int t = 1; t < 32; ++t) L[(size_t)(k0 + t) * LDF + j] = u[t];
+        }
+        __syncthreads();
+        // A22 -= L21 U12 in 4 x 4 register tiles
+        const int nb = ncol / 4;
+        for (int q = tid; q < nb * nb; q += DC_THREADS) {
+            const int rb = q / nb, cb = q - rb * nb;
+            const int i0 = j1 + 4 * rb, c0 = j1 + 4 * cb;
+            float acc[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 8
+            for (int s2 = 0; s2 < 32; ++s2) {
+                const float4 u4 = *reinterpret_cast<const float4 *>(L + (size_t)(k0 + s2) * LDF + c0);
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float lv = L[(size_t)(i0 + x) * LDF + k0 + s2];
+                    acc[x][0] = fmaf(lv, u4.x, acc[x][0]);
+                    acc[x][1] = fmaf(lv, u4.y, acc[x][1]);
+                    acc[x][2] = fmaf(lv, u4.z, acc[x][2]);
+                    acc[x][3] = fmaf(lv, u4.w, acc[x][3]);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                float4 *d = reinterpret_cast<float4 *>(L + (size_t)(i0 + x) * LDF + c0);
+                float4 v = *d;
+                v.x -= acc[x][0];
+                v.y -= acc[x][1];
+                v.z -= acc[x][2];
+                v.w -= acc[x][3];
+                *d = v;
+            }
+        }
+        __syncthreads();
+    }
+
+    // refinement: it = 0 is the first solve from x = 0
+    const double cte = anrm * EPS64 * sqrt((double)n);
+    for (int it = 0; it <= IR_ITMAX; ++it) {
+        unsigned long long *xnb = xn + (it & 1) * R;
+        unsigned long long *rnb = rn + (size_t)(it & 1) * DC_WARPS * R;
+        // x += K^-1 r through the FP32 factors, one warp per right-hand side,
+        // y in registers (lane owns rows lane + 32 m), pivots broadcast by shuffles
+        for (int r = warp; r < R; r += DC_WARPS) {
+            const double *rr = rs + (size_t)r * n;
+            unsigned long long mb = 0ull;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const int i = lane + 32 * m;
+                if (i < n) {
+                    const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rr[i]));
+                    mb = q > mb ? q : mb;
+                }
+            }
+            mb = warp_max_u64(mb);
+            const double m0 = __longlong_as_double((long long)mb);
+            unsigned long long xb = 0ull;
+            int e = 0;
+            float y[NC];
+            const bool solve = m0 > 0.0 && m0 <= 1.7976931348623157e308;
+            if (solve) {
+                frexp(m0, &e);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const int i = lane + 32 * m;
+                    y[m] = i < n ? (float)ldexp(rr[perm[i]], -e) : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    for (int t = 0; t < 32; ++t) {
+                        const int k = 32 * c + t;
+                        if (k >= n) break;
+                        const float yk = __shfl_sync(0xffffffffu, y[c], t);
+#pragma unroll
+                        for (int m = c; m < NC; ++m) {
+                            const int i = lane + 32 * m;
+                            if (i > k && i < n) y[m] = fmaf(-L[(size_t)i * LDF + k], yk, y[m]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = NC - 1; c >= 0; --c) {
+                    for (int t = 31; t >= 0; --t) {
+                        const int k = 32 * c + t;
+                        if (k >= n) continue;
+                        const float yk = __shfl_sync(0xffffffffu, y[c], t) * dinv[k];
+                        if (lane == t) y[c] = yk;
+#pragma unroll
+                        for (int m = 0; m <= c; ++m) {
+                            const int i = lane + 32 * m;
+                            if (i < k) y[m] = fmaf(-L[(size_t)i * LDF + k], yk, y[m]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const int i = lane + 32 * m;
+                if (i < n) {
+                    double xv = xs[(size_t)r * n + i];
+                    if (solve) {
+                        xv += ldexp((double)y[m], e);
+                        xs[(size_t)r * n + i] = xv;
+                    }
+                    const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(xv));
+                    xb = q > xb ? q : xb;
+                }
+            }
+            xb = warp_max_u64(xb);
+            if (lane == 0) xnb[r] = (m0 != m0) ? 0x7ff8000000000000ull : xb;   // a NaN residual never converges
+        }
+        __syncthreads();
+        // r = b - K x in FP64, one thread per row (no cross-lane FP64 reduction)
+        for (int r = 0; r < R; ++r) {
+            unsigned long long best = 0ull;
+            const double *xr = xs + (size_t)r * n;
+            for (int i = tid; i < n; i += DC_THREADS) {
+                const double *kr = Kr + (size_t)i * n;
+                double acc = 0.0;
+                int j = 0;
+                for (; j + 4 <= n; j += 4) {
+                    const double k0 = __ldg(kr + j), k1 = __ldg(kr + j + 1), k2 = __ldg(kr + j + 2),
+                                 k3 = __ldg(kr + j + 3);
+                    acc = fma(k0, xr[j], acc);
+                    acc = fma(k1, xr[j + 1], acc);
+                    acc = fma(k2, xr[j + 2], acc);
+                    acc = fma(k3, xr[j + 3], acc);
+                }
+                for (; j < n; ++j) acc = fma(__ldg(kr + j), xr[j], acc);
+                const double u = P1[r * pstride + i], w = P2[r * pstride + i];
+                const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - acc;
+                rs[(size_t)r * n + i] = rv;
+                const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
+                best = q > best ? q : best;   // NaN patterns exceed every number's
+            }
+            best = warp_max_u64(best);
+            if (lane == 0) rnb[(size_t)warp * R + r] = best;
+        }
+        __syncthreads();
+        bool conv = true;
+        for (int r = 0; r < R && conv; ++r) {
+            unsigned long long mb = 0ull;
+#pragma unroll
+            for (int q = 0; q < DC_WARPS; ++q) mb = rnb[(size_t)q * R + r] > mb ? rnb[(size_t)q * R + r] : mb;
+            const double rmax = __longlong_as_double((long long)mb);
+            const double xmax = __longlong_as_double((long long)xnb[r]);
+            if (!(rmax <= xmax * cte)) conv = false;
+        }
+        if (conv) return true;
+    }
+    return false;
+}
+
+__device__ bool solve_refined_n(const SysView &S, int n, int R, float *L, double *Kc, unsigned char *base,
+                                const IrLayout &lay, Scratch &sc) {
+    switch ((n + 31) / 32) {
+        case 1: return solve_refined<1>(S, n, R, L, Kc, base, lay, sc);
+        case 2: return solve_refined<2>(S, n, R, L, Kc, base, lay, sc);
+        case 3: return solve_refined<3>(S, n, R, L, Kc, base, lay, sc);
+        case 4: return solve_refined<4>(S, n, R, L, Kc, base, lay, sc);
+        case 5: return solve_refined<5>(S, n, R, L, Kc, base, lay, sc);
+        case 6: return solve_refined<6>(S, n, R, L, Kc, base, lay, sc);
+        case 7: return solve_refined<7>(S, n, R, L, Kc, base, lay, sc);
+        case 8: return solve_refined<8>(S, n, R, L, Kc, base, lay, sc);
+        case 9: case 10: return solve_refined<10>(S, n, R, L, Kc, base, lay, sc);
+        case 11: case 12: return solve_refined<12>(S, n, R, L, Kc, base, lay, sc);
+        case 13: case 14: return solve_refined<14>(S, n, R, L, Kc, base, lay, sc);
+        case 15: case 16: return solve_refined<16>(S, n, R, L, Kc, base, lay, sc);
+        default: return false;
+    }
+}
+
+// FP64 elimination on [K | b] and back substitution.  Returns 0, or k + 1
+// when the k-th pivot was zero or not finite; x[r] of row i is then at
+// A[i * ld + n + r].
+__device__ int solve_fp64(const SysView &S, int n, int ld, int R, double *A, Scratch &sc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int idx = tid; idx < n * n; idx += DC_THREADS) {
+        const int i = idx / n, j = idx - i * n;
+        A[(size_t)i * ld + j] = S.k(idx);
+    }
+    for (int idx = tid; idx < R * n; idx += DC_THREADS) {
+        const int r = idx / n, i = idx - r * n;
+        A[(size_t)i * ld + n + r] = S.b(r, i);
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bi = n;
+        for (int i = k + tid; i < n; i += DC_THREADS) {
+            const double v = fabs(A[(size_t)i * ld + k]);
+            if (v > best) {   // NaN never wins; rows visited in increasing order
+                best = v;
+                bi = i;
+            }
+        }
+        block_argmax(best, bi, n, sc);
+        if (!finite_pos(sc.pv)) return k + 1;
+        const int p = sc.piv;
+        if (p != k) {
+            for (int j = k + tid; j < ld; j += DC_THREADS) {
+                const double t = A[(size_t)k * ld + j];
+                A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
+                A[(size_t)p * ld + j] = t;
+            }
+            __syncthreads();
+        }
+        const double rinv = 1.0 / A[(size_t)k * ld + k];
+        const double *rowk = A + (size_t)k * ld;
+        for (int i = k + 1 + warp; i < n; i += DC_WARPS) {
+            double *rowi = A + (size_t)i * ld;
+            const double l = rowi[k] * rinv;
+            for (int j = k + 1 + lane; j < ld; j += 32) rowi[j] = fma(-l, rowk[j], rowi[j]);
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        const double ukk = A[(size_t)k * ld + k];
+        for (int r = tid; r < R; r += DC_THREADS) A[(size_t)k * ld + n + r] /= ukk;
+        __syncthreads();
+        for (int idx = tid; idx < k * R; idx += DC_THREADS) {
+            const int i = idx / R, r = idx - i * R;
+            double *bi = A + (size_t)i * ld + n + r;
+            *bi = fma(-A[(size_t)i * ld + k], A[(size_t)k * ld + n + r], *bi);
+        }
+        __syncthreads();
+    }
+    return 0;
+}
+
+__global__ void __launch_bounds__(DC_THREADS, 1) k_decouple(DecoupleArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ Scratch sc;
+
+    const int tid = threadIdx.x;
     const int n = a.n, ld = a.ld, R = a.n_rhs, nf = a.n_fields;
-    double *A = a.ws ? a.ws + (size_t)blockIdx.x * a.ws_stride : dsm;
+    // workspace slice: the refined solver's FP64 K1 +- K2 (n^2, rounded up to
+    // 16 bytes), then its FP32 factors when they are not in shared memory;
+    // the FP64 solver's augmented matrix from the start when it is not
+    double *slice = a.ws ? a.ws + (size_t)blockIdx.x * a.ws_stride : nullptr;
+    const IrLayout lay = ir_layout(n, R, !a.l_in_ws);
+    double *Kc = slice;
+    float *L = a.l_in_ws ? reinterpret_cast<float *>(slice + (((size_t)n * n + 1) & ~(size_t)1))
+                         : reinterpret_cast<float *>(dsm + lay.L);
+    double *A = a.direct_in_ws ? slice : reinterpret_cast<double *>(dsm);
+    const double *xs = reinterpret_cast<const double *>(dsm + lay.x);
 
     for (long long sys = blockIdx.x; sys < a.n_sys; sys += gridDim.x) {
         const int w = (int)(sys / a.sys_per_window), q = (int)(sys % a.sys_per_window);
-        const int kind = a.kind[q];
-        const double *K1 = a.M + ((size_t)w * a.nspec + a.slot1[q]) * (size_t)n * n;
-        const double *K2 = a.M + ((size_t)w * a.nspec + a.slot2[q]) * (size_t)n * n;
-        const double *P = a.pcl + (size_t)w * R * nf * n;
-        const int f1 = a.field1[q], f2 = a.field2[q];
+        SysView S;
+        S.kind = a.kind[q];
+        S.K1 = a.M + ((size_t)w * a.nspec + a.slot1[q]) * (size_t)n * n;
+        S.K2 = a.M + ((size_t)w * a.nspec + a.slot2[q]) * (size_t)n * n;
+        S.P = a.pcl + (size_t)w * R * nf * n;
+        S.f1 = a.field1[q];
+        S.f2 = a.field2[q];
+        S.nf = nf;
+        S.n = n;
 
-        // ---- load [K | pcl^T]
-        for (int idx = tid; idx < n * n; idx += DC_THREADS) {
-            const int i = idx / n, j = idx - i * n;
-            double v = K1[idx];
-            if (kind == 1) v = v + K2[idx];
-            else if (kind == 2) v = v - K2[idx];
-            A[(size_t)i * ld + j] = v;
-        }
-        for (int idx = tid; idx < R * n; idx += DC_THREADS) {
-            const int r = idx / n, i = idx - r * n;
-            double b = P[((size_t)r * nf + f1) * n + i];
-            if (kind == 1) b = b + P[((size_t)r * nf + f2) * n + i];
-            else if (kind == 2) b = b - P[((size_t)r * nf + f2) * n + i];
-            A[(size_t)i * ld + n + r] = b;
-        }
-        __syncthreads();
+        const bool refined = a.refine && solve_refined_n(S, n, R, L, Kc, dsm, lay, sc);
+        __syncthreads();   // the FP64 solver reuses the refinement's shared memory
+        const int bad = refined ? 0 : solve_fp64(S, n, ld, R, A, sc);
 
-        // ---- elimination with partial pivoting
-        int bad = 0;
-        for (int k = 0; k < n; ++k) {
-            double best = -1.0;
-            int bi = n;
-            for (int i = k + tid; i < n; i += DC_THREADS) {
-                const double v = fabs(A[(size_t)i * ld + k]);
-                if (v > best) {   // NaN never wins; rows visited in increasing order
-                    best = v;
-                    bi = i;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                argmax_combine(best, bi, v2, i2);
-            }
-            if (lane == 0) {
-                red_v[warp] = best;
-                red_i[warp] = bi;
-            }
-            __syncthreads();
-            if (warp == 0) {
-                double v = lane < DC_WARPS ? red_v[lane] : -1.0;
-                int i = lane < DC_WARPS ? red_i[lane] : n;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-                    argmax_combine(v, i, v2, i2);
-                }
-                if (lane == 0) {
-                    piv_s = i;
-                    bad_s = (v > 0.0 && v <= 1.7976931348623157e308) ? 0 : k + 1;
-                }
-            }
-            __syncthreads();
-            if (bad_s) {
-                bad = bad_s;
-                break;
-            }
-            const int p = piv_s;
-            if (p != k) {
-                for (int j = k + tid; j < ld; j += DC_THREADS) {
-                    const double t = A[(size_t)k * ld + j];
-                    A[(size_t)k * ld + j] = A[(size_t)p * ld + j];
-                    A[(size_t)p * ld + j] = t;
-                }
-                __syncthreads();
-            }
-            const double rinv = 1.0 / A[(size_t)k * ld + k];
-            const double *rowk = A + (size_t)k * ld;
-            for (int i = k + 1 + warp; i < n; i += DC_WARPS) {
-                double *rowi = A + (size_t)i * ld;
-                const double l = rowi[k] * rinv;
-                for (int j = k + 1 + lane; j < ld; j += 32) rowi[j] = fma(-l, rowk[j], rowi[j]);
-            }
-            __syncthreads();
-        }
-
-        // ---- back substitution on the n_rhs columns
-        if (!bad) {
-            for (int k = n - 1; k >= 0; --k) {
-                const double ukk = A[(size_t)k * ld + k];
-                for (int r = tid; r < R; r += DC_THREADS) A[(size_t)k * ld + n + r] /= ukk;
-                __syncthreads();
-                for (int idx = tid; idx < k * R; idx += DC_THREADS) {
-                    const int i = idx / R, r = idx - i * R;
-                    double *bi = A + (size_t)i * ld + n + r;
-                    *bi = fma(-A[(size_t)i * ld + k], A[(size_t)k * ld + n + r], *bi);
-                }
-                __syncthreads();
-            }
-        }
-
-        // ---- outputs
         double *O = a.out + (size_t)w * R * nf * n;
         for (int idx = tid; idx < R * n; idx += DC_THREADS) {
             const int r = idx / n, i = idx - r * n;
-            const double x = bad ? __longlong_as_double(0x7ff8000000000000LL) : A[(size_t)i * ld + n + r];
-            double *o1 = O + ((size_t)r * nf + f1) * n + i;
-            if (kind == 0) {
+            const double x = bad ? __longlong_as_double(0x7ff8000000000000LL)
+                                 : (refined ? xs[(size_t)r * n + i] : A[(size_t)i * ld + n + r]);
+            double *o1 = O + ((size_t)r * nf + S.f1) * n + i;
+            if (S.kind == 0) {
                 *o1 = x;
             } else {
-                double *o2 = O + ((size_t)r * nf + f2) * n + i;
+                double *o2 = O + ((size_t)r * nf + S.f2) * n + i;
                 atomicAdd(o1, 0.5 * x);
-                atomicAdd(o2, (kind == 1 ? 0.5 : -0.5) * x);
+                atomicAdd(o2, (S.kind == 1 ? 0.5 : -0.5) * x);
             }
         }
         if (tid == 0 && a.info) a.info[sys] = bad;
-        __syncthreads();   // A is reused by the CTA's next system
+        __syncthreads();   // shared memory is reused by the CTA's next system
     }
 }
 
 }  // namespace
 
-int decouple_smem_limit() { return 226 * 1024; }   // dynamic part; the static reduction scratch fits in the rest
+int decouple_smem_limit() { return 226 * 1024; }   // dynamic part; the static Scratch fits in the rest
 
 cudaError_t launch_decouple(const DecoupleArgs &a, int grid, size_t smem, cudaStream_t st) {
     static bool attr = false;

@@ -119,9 +119,44 @@ struct DecoupleArgs {
     int n, ld, n_rhs, n_fields, nspec, sys_per_window;
     long long n_sys;
     int kind[5], slot1[5], slot2[5], field1[5], field2[5];
-    double *ws;             // global workspace (grid x ws_stride doubles), NULL: shared memory
+    int refine;             // FP32 LU + FP64 iterative refinement first (FP64 LU on failure)
+    int l_in_ws;            // refinement: FP32 factors in the workspace slice instead of shared memory
+    int direct_in_ws;       // FP64 LU: augmented matrix in the workspace slice instead of shared memory
+    double *ws;             // global workspace, ws_stride doubles per CTA (NULL when unused)
     size_t ws_stride;
 };
+
+#ifdef __CUDACC__
+#define CPL_HD __host__ __device__
+#else
+#define CPL_HD
+#endif
+// Shared-memory carve of the refinement path (byte offsets).  The FP32
+// factors hold the system padded to np = 32 ceil(n / 32) rows and columns
+// (identity in the padding) with row stride ir_ldf(n) floats; they come
+// first when they are in shared memory.
+CPL_HD inline int ir_np(int n) { return (n + 31) & ~31; }
+CPL_HD inline int ir_ldf(int n) { return ir_np(n) + 4; }
+struct IrLayout {
+    size_t L, perm, dinv, x, r, xn, rn, total;
+};
+CPL_HD inline size_t ir_align(size_t b) { return (b + 15) & ~(size_t)15; }
+CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
+    IrLayout s;
+    size_t o = 0;
+    const size_t np = (size_t)ir_np(n);
+    s.L = o;
+    if (l_in_smem) o += ir_align(sizeof(float) * np * (size_t)ir_ldf(n));
+    s.perm = o; o += ir_align(sizeof(int) * np);
+    s.dinv = o; o += ir_align(sizeof(float) * np);
+    s.x = o;    o += ir_align(sizeof(double) * (size_t)R * n);
+    s.r = o;    o += ir_align(sizeof(double) * (size_t)R * n);
+    s.xn = o;   o += ir_align(sizeof(double) * 2 * (size_t)R);
+    s.rn = o;   o += ir_align(sizeof(double) * 2 * 16 * (size_t)R);   // per-warp residual maxima, 2 buffers
+    s.total = o;
+    return s;
+}
+constexpr int IR_NMAX = 512;   // largest n of the refined solver (16 column chunks of 32)
 int decouple_smem_limit();
 cudaError_t launch_decouple(const DecoupleArgs &a, int grid, size_t smem, cudaStream_t st);
 cudaError_t decouple_blocks_per_sm(size_t smem, int *n);

@@ -138,6 +138,47 @@ def test_generic_matrices_edge_sizes(ctx, n):
     print("n=%d:" % n, check(M, pcl, got, sp, dc.decouple(M, pcl, sp)))
 
 
+def test_ill_conditioned_system_falls_back_to_fp64(ctx):
+    # Hilbert matrix, cond ~ 5e11: the FP32 factors carry no digit, so the
+    # refinement cannot converge and the FP64 solver answers (backward error bar)
+    n = 9
+    H = 1.0 / (np.arange(n)[:, None] + np.arange(n)[None, :] + 1.0)
+    rng = np.random.default_rng(4)
+    pcl = rng.normal(size=(1, 1, 1, n))
+    got, info = run(ctx, H[None, None], pcl, coupling.TT)
+    assert np.all(info == 0)
+    print("hilbert 9:", check(H[None, None], pcl, got, coupling.TT))
+
+
+@pytest.mark.parametrize("scale", [1e200, 1e-200])
+def test_matrices_outside_fp32_range(ctx, scale):
+    # entries beyond FP32's range: the refined solver's FP32 factors fail and
+    # the FP64 solver answers; the result scales exactly with 1 / scale
+    lmax = 60
+    W = windows.mask_like(lmax, seed=17)
+    M = oracle.coupling_dense(lmax, W, W, W, coupling.TT)[0]
+    rng = np.random.default_rng(5)
+    pcl = rng.uniform(0.1, 1.0, size=(1, 1, 1, lmax - 1))
+    got, info = run(ctx, M * scale, pcl, coupling.TT)
+    assert np.all(info == 0)
+    print("scale %g:" % scale, check(M * scale, pcl, got, coupling.TT, dc.decouple(M * scale, pcl, coupling.TT)))
+
+
+def test_refined_and_fp64_solvers_agree(ctx):
+    # n_rhs <= 2n/9 takes the refined solver, more right-hand sides the FP64
+    # one: the first right-hand side must agree to the forward-error bar
+    lmax = 161
+    W = windows.mask_like(lmax, seed=31)
+    sp = coupling.TT | coupling.EE | coupling.EEBB
+    M = oracle.coupling_dense(lmax, W, W, W, sp)[0]
+    rng = np.random.default_rng(7)
+    pcl = rng.uniform(0.1, 1.0, size=(1, 100, 3, 160))
+    many, _ = run(ctx, M, pcl, sp)
+    one, _ = run(ctx, M, np.ascontiguousarray(pcl[:, :1]), sp)
+    ref = dc.decouple(M, pcl[:, :1], sp)
+    print("refined:", check(M, pcl[:, :1], one, sp, ref), "fp64:", check(M, pcl[:, :1], many[:, :1], sp, ref))
+
+
 def test_singular_systems_report_info(ctx):
     n = 12
     sp = coupling.TT | coupling.EE | coupling.EEBB
