@@ -359,6 +359,48 @@ cpl_status cpl_decouple(cpl_ctx *ctx, int n, int n_windows, unsigned spectra, co
                         int n_rhs, double *out, int *info, void *stream);
 
 /*
+ * cpl_cov_gaussian -- approximate Gaussian covariance of pseudo-spectra from
+ * coupling-type kernels (Sec. 2 and Sec. 4.3, band-limited covariance
+ * matrices): when the spectra vary little across the masks' band limit the
+ * covariance reduces to kernels of the squared masks,
+ *
+ *   Cov_{l1 l2} = sum_t Xi_{X_t}(l1, l2; W~_t) (A^t_l1 B^t_l2 + A^t_l2 B^t_l1) / 2,
+ *   Xi_X(l1, l2; W~) = (1/4pi) sum_l3 (2 l3 + 1) W~_l3 S_X(l1, l2, l3)
+ *
+ * (S_X of App. A; Xi is the coupling matrix without its (2 l2 + 1)), with W~
+ * the power spectrum of the product of the squared masks and the l3 sum cut
+ * at the band limit.  One term per Wick pairing of the four fields, e.g. the
+ * TT auto-spectrum: one term X = CPL_TT, A = C^TT, B = 2 C^TT (full sky:
+ * 2 C_l^2 / (2l + 1) on the diagonal).
+ *
+ *   lmax, lmin   as in cpl_request (lmin >= 2 with a polarisation kernel).
+ *   terms[t]     spectrum: one CPL_* bit (the kernel X_t); W: device [w_len]
+ *                FP64; band_limit: last l3 kept, or -1 for none (then w_len
+ *                must reach 2 lmax + 1); A, B: device [lmax + 1] FP64
+ *                indexed by l.  Terms with the same W pointer and band limit
+ *                share one kernel build.
+ *   n_terms      >= 1.
+ *   w_len        entries of each W.
+ *   precision    cpl_precision of the kernel builds.
+ *   bin_edges    host [n_bins + 1] as in cpl_request, or NULL: binned output
+ *                Cov_bb' = (1/|b||b'|) sum_{l1 in b} sum_{l2 in b'} Cov_{l1 l2}.
+ *   out          device, caller-owned: [n][n] (n = lmax - lmin + 1) or
+ *                [n_bins][n_bins] FP64, exactly symmetric.
+ *   stream       cudaStream_t or NULL.
+ * Asynchronous on `stream`; deterministic.  Errors as cpl_build (output
+ * untouched on CPL_ERR_ARG / CPL_ERR_RANGE).
+ */
+typedef struct {
+    unsigned spectrum;
+    const double *W;
+    int band_limit;
+    const double *A;
+    const double *B;
+} cpl_cov_term;
+cpl_status cpl_cov_gaussian(cpl_ctx *ctx, int lmax, int lmin, const cpl_cov_term *terms, int n_terms, int w_len,
+                            int precision, const int *bin_edges, int n_bins, double *out, void *stream);
+
+/*
  * Lookup table of Eqs. gdef / g_rec, as the library builds it: out[p] =
  * g(p) = (2p)! / (2^{2p} (p!)^2) for p = 0 .. pmax, each value the
  * double-double recurrence g(p) = (p - 1/2)/p g(p-1), g(0) = 1, rounded once

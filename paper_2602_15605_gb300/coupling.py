@@ -46,7 +46,11 @@ class KernelStat(ctypes.Structure):
                 ("flop", ctypes.c_double), ("bytes", ctypes.c_double), ("issued_flop", ctypes.c_double)]
 
 
-# Every symbol include/coupling.h declares.
+class CovTerm(ctypes.Structure):
+    _fields_ = [("spectrum", ctypes.c_uint), ("W", ctypes.c_void_p), ("band_limit", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p)]
+
+
 def decouple_fields(spectra):
     """Pseudo-spectrum fields per right-hand side of cpl_decouple: TT, TE, EE, BB, EB."""
     return (bool(spectra & TT) + bool(spectra & TE) + 2 * bool(spectra & EE) + bool(spectra & EB))
@@ -57,10 +61,11 @@ def decouple_systems(spectra):
     return (bool(spectra & TT) + bool(spectra & TE) + 2 * bool(spectra & EE) + bool(spectra & EB))
 
 
+# Every symbol include/coupling.h declares.
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
            "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
-           "cpl_decouple", "cpl_g_table")
+           "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table")
 
 _lock = threading.Lock()
 _lib = None
@@ -98,6 +103,8 @@ def load():
         L.cpl_threej_m11.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, vp,
                                      ctypes.c_longlong, vp]
         L.cpl_decouple.argtypes = [vp, ip, ip, ctypes.c_uint, vp, vp, ip, vp, vp, vp]
+        L.cpl_cov_gaussian.argtypes = [vp, ip, ip, ctypes.POINTER(CovTerm), ip, ip, ip,
+                                       ctypes.POINTER(ctypes.c_int), ip, vp, vp]
         L.cpl_ctx_stats.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]
         for name in EXPORTS:
             if name not in ("cpl_version", "cpl_last_error"):
@@ -235,6 +242,44 @@ class Context:
         _check(load().cpl_decouple(self.handle, int(n), int(nw), int(spectra), ctypes.c_void_p(M.data_ptr()),
                                    ctypes.c_void_p(pcl.data_ptr()), int(pcl.shape[1]), ctypes.c_void_p(out.data_ptr()),
                                    ctypes.c_void_p(ip_), ctypes.c_void_p(st)))
+        return out
+
+    def cov_gaussian(self, lmax, terms, lmin=2, precision=FP64, bin_edges=None, out=None):
+        """cpl_cov_gaussian: sum over terms (spectrum, W~, band_limit or None, A, B)
+        of Xi_spectrum(l1, l2; W~) (A_l1 B_l2 + A_l2 B_l1) / 2; W~, A, B float64
+        CUDA tensors (A, B indexed by l, length >= lmax + 1).  Returns the dense
+        [n, n] or binned [n_bins, n_bins] covariance on torch's current stream."""
+        import torch
+        if not terms:
+            raise ValueError("at least one term")
+        keep = []
+        arr = (CovTerm * len(terms))()
+        w_len = None
+        for q, (sp, W, band, A, B) in enumerate(terms):
+            for t in (W, A, B):
+                if t.dtype != torch.float64 or not t.is_contiguous() or not t.is_cuda:
+                    raise ValueError("W, A and B must be contiguous float64 CUDA tensors")
+            if A.numel() < lmax + 1 or B.numel() < lmax + 1:
+                raise ValueError("A and B need lmax + 1 entries")
+            if w_len is not None and W.numel() != w_len:
+                raise ValueError("every W must have the same length")
+            w_len = W.numel()
+            arr[q] = CovTerm(int(sp), W.data_ptr(), -1 if band is None else int(band), A.data_ptr(), B.data_ptr())
+            keep += [W, A, B]
+        if bin_edges is not None:
+            e = np.ascontiguousarray(np.asarray(bin_edges, dtype=np.int32))
+            ep, nb = e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(e.size - 1)
+            shape = (nb, nb)
+        else:
+            e, ep, nb = None, None, 0
+            shape = (lmax - lmin + 1, lmax - lmin + 1)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda:%d" % self.device)
+        elif tuple(out.shape) != shape or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float64 tensor of shape %s" % (shape,))
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        _check(load().cpl_cov_gaussian(self.handle, int(lmax), int(lmin), arr, len(terms), int(w_len), int(precision),
+                                       ep, nb, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
         return out
 
     def inject_alloc_failure(self, n):

@@ -102,6 +102,7 @@ struct cpl_ctx {
     DevBuf sqrt_tab;             // cpl_threej_m11: sqrt g | sqrt h (pmax + 1 each) | sqrt n (sq_nn), FP32 pairs
     int sq_pmax = -1, sq_nn = 0;
     DevBuf dec_ws;               // cpl_decouple: augmented systems too large for shared memory
+    DevBuf cov_M, cov_dense, cov_edges;   // cpl_cov_gaussian: kernels of one build, dense covariance, bin edges
     cudaStream_t own_stream = nullptr;
     cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams
     // per-kernel accounting (cpl_ctx_stats)

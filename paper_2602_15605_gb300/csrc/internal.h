@@ -158,6 +158,27 @@ CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
 }
 constexpr int IR_NMAX = 512;   // largest n of the refined solver (16 column chunks of 32)
 int decouple_smem_limit();
+
+// Approximate covariance (cov.cu).  One combine launch adds the terms of one
+// kernel build (the same window and band limit) into the dense covariance.
+constexpr int COV_TERMS_PER_LAUNCH = 16;
+struct CovCombineArgs {
+    const double *M;        // [nspec][n][n] dense kernels of the group's build (M = (2 l2 + 1) Xi)
+    int n, lmin, n_terms;
+    int slot[COV_TERMS_PER_LAUNCH];            // spectrum slot of each term in M
+    const double *A[COV_TERMS_PER_LAUNCH];     // [lmax + 1], indexed by l
+    const double *B[COV_TERMS_PER_LAUNCH];
+    double *out;            // dense [n][n]
+    int accumulate;         // add to out (else overwrite)
+};
+struct CovBinArgs {
+    const double *cov;      // dense [n][n]
+    int n, lmin, nb;
+    const int *edges;       // device [nb + 1]
+    double *out;            // [nb][nb]
+};
+cudaError_t launch_cov_combine(const CovCombineArgs &a, cudaStream_t st);
+cudaError_t launch_cov_bin(const CovBinArgs &a, cudaStream_t st);
 cudaError_t launch_decouple(const DecoupleArgs &a, int grid, size_t smem, cudaStream_t st);
 cudaError_t decouple_blocks_per_sm(size_t smem, int *n);
 
