@@ -17,6 +17,8 @@ Printed JSON line (rank 0):
                against the FP64 pipe peak (2 FMA/clk/SM x 152 SMs x 2.07 GHz)
   cpu_baseline the CPU oracle (Schulten-Gordon recursion + direct sum) on a
                bounded random sample of pairs of the same workload
+  cov          cpl_cov_gaussian (TT + EE terms, l_max = 3000) with squared-mask
+               spectra band-limited at L_cut = 16, 64, 512, FP64 and mixed kernels
   decouple     cpl_decouple on the binned matrices of 16 band-limited windows
                (l_max = 8000, 160 bins): event time per call for 1 and 32
                right-hand sides
@@ -634,6 +636,61 @@ def run_ours(args, rank, world, local):
             del pcl, dout
         del Mb, db
 
+    # approximate covariance from squared-mask kernels (Sec. 4.3 band limits):
+    # TT + EE Wick terms at l_max = 3000, L_cut in {16, 64, 512}, dense output
+    cov = None
+    if not args.no_batch:
+        cov = {"workload": "Cov = Xi_TT(W~) C C' + Xi_EE(W~) E E' (2 Wick terms), l_max = 3000, dense "
+                           "2999 x 2999, W~ band-limited at L_cut"}
+        cv_l = 3000
+        cv_ell = np.arange(cv_l + 1, dtype=np.float64)
+        cv_ct = torch.as_tensor(1e3 / (cv_ell + 10.0) ** 2, device="cuda:%d" % local)
+        cv_ce = torch.as_tensor(20.0 / (cv_ell + 10.0) ** 2, device="cuda:%d" % local)
+        cv_out = torch.empty((cv_l - 1, cv_l - 1), dtype=torch.float64, device="cuda:%d" % local)
+        for cv_cut in (16, 64, 512):
+            cv_w = torch.as_tensor(windows.random_positive(cv_l, seed=90 + cv_cut, band=cv_cut),
+                                   device="cuda:%d" % local)
+            cv_terms = [(coupling.TT, cv_w, cv_cut, cv_ct, 2 * cv_ct), (coupling.EE, cv_w, cv_cut, cv_ce, 2 * cv_ce)]
+            cv_entry = {}
+            for cv_prec, cv_name in ((coupling.FP64, "fp64"), (coupling.MIXED_BF16, "mixed_bf16")):
+                for _ in range(2):
+                    ctx.cov_gaussian(cv_l, cv_terms, precision=cv_prec, out=cv_out)
+                torch.cuda.synchronize()
+                ctx.stats(reset=True)
+                cv_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+                for a, b in cv_ev:
+                    flush.fill_(1)
+                    a.record()
+                    ctx.cov_gaussian(cv_l, cv_terms, precision=cv_prec, out=cv_out)
+                    b.record()
+                torch.cuda.synchronize()
+                ctx.sync()
+                cv_ms = statistics.median(a.elapsed_time(b) for a, b in cv_ev)
+                # per-kernel event times from a separate profiled pass
+                ctx.stats(reset=True)
+                ctx.profile(True)
+                for _ in range(3):
+                    flush.fill_(1)
+                    ctx.cov_gaussian(cv_l, cv_terms, precision=cv_prec, out=cv_out)
+                ctx.sync()
+                ctx.profile(False)
+                cv_st = {k: v for k, v in ctx.stats(reset=True).items() if v["launches"]}
+                cv_cb = cv_st.get("cov_combine", {})
+                cv_entry[cv_name] = {"ms": cv_ms, "elements_per_s": (cv_l - 1) ** 2 / (cv_ms * 1e-3),
+                                     "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in cv_st.items()}}
+                if cv_cb.get("ms"):
+                    cv_tf = cv_cb["flop"] / (cv_cb["ms"] * 1e-3) / 1e12
+                    cv_entry[cv_name]["combine_roofline"] = {
+                        "bound": "alu", "achieved": cv_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": cv_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                        "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz",
+                        "achieved_counts": "2 FLOP x 3 FP64 operations per upper-triangle element and term / "
+                                           "event time of the combine launches (profiled pass); the kernel is "
+                                           "FP64-pipe bound, DRAM below a fifth of its peak"}
+            cov["L_cut_%d" % cv_cut] = cv_entry
+            del cv_w
+        del cv_out, cv_ct, cv_ce
+
     batch = None
     if not args.no_batch:
         batch = batch_arm(ctx, args, world, local, mixed_roofline)
@@ -679,6 +736,8 @@ def run_ours(args, rank, world, local):
             line["threej_m11"] = threej
         if decouple is not None:
             line["decouple"] = decouple
+        if cov is not None:
+            line["cov"] = cov
         try:
             line["tuner"] = [dict(lmax=e["key"][1], n_windows=e["key"][3], src=e["src"], order=e["order"],
                                   ms=e["ms"]) for e in map(json.loads, open(tune_file).read().splitlines())]
