@@ -69,10 +69,15 @@ enum {
 
 typedef enum {
     CPL_FP64 = 0,        /* plain FP64 arithmetic throughout (target <= 1e-11 relative) */
-    CPL_MIXED_BF16 = 1   /* l3 contraction on tcgen05 tensor cores with BF16 fixed-point
+    CPL_MIXED_BF16 = 1,  /* l3 contraction on tcgen05 tensor cores with BF16 fixed-point
                             limbs and exact FP32 partial sums; FP64 tables, scales and
                             final values (bound 1e-9 relative, see mixed_slices) */
+    CPL_DF32 = 2         /* the plain path's contractions in double-float (pairs of FP32,
+                            ~48-bit significands) on the FP32 pipe; weights scaled per tile,
+                            FP64 epilogue; lmax <= CPL_DF32_LMAX (target <= 1e-11 relative
+                            like CPL_FP64; measured <= 5e-12) */
 } cpl_precision;
+#define CPL_DF32_LMAX 10000
 
 typedef struct cpl_ctx cpl_ctx;
 

@@ -20,7 +20,7 @@ TT, TE, EE, EEBB, EB = 1, 2, 4, 8, 16
 SPEC_BITS = (TT, TE, EE, EEBB, EB)
 SPEC_NAMES = {TT: "TT", TE: "TE", EE: "EE", EEBB: "EEBB", EB: "EB"}
 ALL = TT | TE | EE | EEBB | EB
-FP64, MIXED_BF16 = 0, 1
+FP64, MIXED_BF16, DF32 = 0, 1, 2
 TUNE_OFF, TUNE_MEASURE = 0, 1
 
 STATUS = {0: "CPL_OK", 1: "CPL_ERR_ARG", 2: "CPL_ERR_RANGE", 3: "CPL_ERR_OOM", 4: "CPL_ERR_CUDA",

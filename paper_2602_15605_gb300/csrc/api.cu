@@ -154,8 +154,10 @@ cpl_status validate(const cpl_request *r, bool device_ptrs) {
         if (r->w_len < top + 1)
             return fail(CPL_ERR_ARG, "w_len too short: the l3 sum needs W up to min(2 lmax, band_limit)");
     }
-    if (r->precision != CPL_FP64 && r->precision != CPL_MIXED_BF16)
+    if (r->precision != CPL_FP64 && r->precision != CPL_MIXED_BF16 && r->precision != CPL_DF32)
         return fail(CPL_ERR_ARG, "unknown precision");
+    if (r->precision == CPL_DF32 && r->lmax > CPL_DF32_LMAX)
+        return fail(CPL_ERR_RANGE, "CPL_DF32 needs lmax <= CPL_DF32_LMAX (FP32 exponent range of the contractions)");
     if (r->precision == CPL_MIXED_BF16 && r->mixed_slices != 0 &&
         (r->mixed_slices < 4 || r->mixed_slices > 6))
         return fail(CPL_ERR_ARG, "mixed_slices must be 0 or in 4..6");
@@ -255,6 +257,19 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
     int lmax_all = 2;
     for (int q = 0; q < n; ++q) lmax_all = std::max(lmax_all, reqs[q].lmax);
     if ((s = ensure_tables(c, lmax_all)) != CPL_OK) return s;
+    const bool df = reqs[0].precision == CPL_DF32;
+    if (df && c->df_pmax != c->pmax) {
+        // g and h as FP32 pairs for the double-float kernels
+        const int np1 = c->pmax + 1;
+        c->df_pmax = -1;
+        CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
+        if ((s = c->df_tab.ensure(sizeof(float2) * 2 * (size_t)np1, "double-float tables")) != CPL_OK) return s;
+        float2 *t2 = c->df_tab.as<float2>();
+        LaunchScope ls(c, "df_tables", st);
+        CPL_CUDA_TRY(launch_df_tables(c->g.as<double>(), c->h.as<double>(), np1, t2, t2 + np1, st));
+        ls.done(0.0, 32.0 * np1);
+        c->df_pmax = c->pmax;
+    }
 
     struct JobInfo {
         TileSet *ts = nullptr;
@@ -426,8 +441,14 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         a.nge = keys[k] / 2;
         a.odd = keys[k] & 1;
         const bool odd = a.odd != 0;
-        const char *kname = a.nge == 1 ? "plain_fp64_tt" : a.nge == 3 ? "plain_fp64_te"
-                          : (a.nge == 6 && odd) ? "plain_fp64_pol" : a.nge == 6 ? "plain_fp64_even" : "plain_fp64_odd";
+        const char *kname = df ? (a.nge == 1 ? "plain_df_tt" : a.nge == 3 ? "plain_df_te"
+                                  : (a.nge == 6 && odd) ? "plain_df_pol" : a.nge == 6 ? "plain_df_even" : "plain_df_odd")
+                               : (a.nge == 1 ? "plain_fp64_tt" : a.nge == 3 ? "plain_fp64_te"
+                                  : (a.nge == 6 && odd) ? "plain_fp64_pol" : a.nge == 6 ? "plain_fp64_even" : "plain_fp64_odd");
+        if (df) {
+            a.gdf = c->df_tab.as<float2>();
+            a.hdf = a.gdf + (c->pmax + 1);
+        }
         double flop = 0.0, bytes = 0.0;
         if (c->profiling) {
             // 2 FLOP per FMA: nge FMAs per even-L term, 3 per odd-L term;
@@ -445,7 +466,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
             }
         }
         LaunchScope ls(c, kname, st);
-        CPL_CUDA_TRY(launch_plain(a, st));
+        CPL_CUDA_TRY(df ? launch_plain_df(a, st) : launch_plain(a, st));
         ls.done(flop, bytes);
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));

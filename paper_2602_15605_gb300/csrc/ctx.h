@@ -101,6 +101,8 @@ struct cpl_ctx {
     DevBuf threej_idx;           // cpl_threej_m11: (j2, j3) of the last call
     DevBuf sqrt_tab;             // cpl_threej_m11: sqrt g | sqrt h (pmax + 1 each) | sqrt n (sq_nn), FP32 pairs
     int sq_pmax = -1, sq_nn = 0;
+    DevBuf df_tab;               // CPL_DF32: g | h as FP32 pairs (pmax + 1 each)
+    int df_pmax = -1;
     DevBuf dec_ws;               // cpl_decouple: augmented systems too large for shared memory
     DevBuf cov_M, cov_dense, cov_edges;   // cpl_cov_gaussian: kernels of one build, dense covariance, bin edges
     cudaStream_t own_stream = nullptr;

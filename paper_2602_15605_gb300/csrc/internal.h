@@ -90,9 +90,13 @@ struct PlainArgs {
     int n_items;
     int nge;                // even-sweep contractions of the variant (0, 1, 3 or 6)
     int odd;                // whether the odd sweep runs
+    const float2 *gdf;      // [pmax + 1] g and h as FP32 pairs (double-float kernels only)
+    const float2 *hdf;
 };
 
 cudaError_t launch_plain(const PlainArgs &a, cudaStream_t st);   // variant from a.nge / a.odd
+cudaError_t launch_plain_df(const PlainArgs &a, cudaStream_t st);   // the same in double-float (plain_df.cu)
+cudaError_t launch_df_tables(const double *g, const double *h, int n, float2 *gdf, float2 *hdf, cudaStream_t st);
 // Which template variant launch_plain runs: even-sweep contractions (0, 1,
 // 3 or 6) and whether the odd sweep runs.
 void plain_variant(int mode, const int slot[5], int *nge, bool *odd);

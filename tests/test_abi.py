@@ -86,7 +86,9 @@ def test_output_size_and_validation(lib):
         assert coupling.output_size(10, 1, coupling.TT, precision=coupling.MIXED_BF16, slices=sl) == 81
     for sl in (3, 7, -1):
         assert _status(lambda: coupling.output_size(10, 1, coupling.TT, precision=coupling.MIXED_BF16, slices=sl)) == 1
-    assert _status(lambda: coupling.output_size(10, 1, coupling.TT, precision=2)) == 1
+    assert _status(lambda: coupling.output_size(10, 1, coupling.TT, precision=3)) == 1
+    assert coupling.output_size(10, 1, coupling.TT, precision=coupling.DF32) == 81
+    assert _status(lambda: coupling.output_size(10001, 1, coupling.TT, precision=coupling.DF32)) == 2
 
 
 def test_ctx_create_without_gpu_fails_cleanly(lib):
