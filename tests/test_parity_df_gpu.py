@@ -1,8 +1,8 @@
 """Double-float plain path (CPL_DF32) vs the CPU oracle and the FP64 path (GPU).
 
 Bar: per-element relative error against S_abs (reading 10) <= 1e-11 for
-every spectrum, the plain path's target; elements zero by parity or band exactly 0.0.  Cases: whole
-matrices against the oracle (TT at l_max = 512, the full spin set with
+every spectrum, the plain path's target; elements zero by parity or band
+exactly 0.0.  Cases: whole matrices against the oracle (TT at l_max = 512, the full spin set with
 separate windows, lmin = 0, a band limit, binning), the full-size l_max =
 3000 workload on sampled pairs against the oracle and on every element of
 the non-negative spectra (TT, EE, EE->BB, where S_abs equals the value)
