@@ -19,6 +19,8 @@ Printed JSON line (rank 0):
                bounded random sample of pairs of the same workload
   cov          cpl_cov_gaussian (TT + EE terms, l_max = 3000) with squared-mask
                spectra band-limited at L_cut = 16, 64, 512, FP64 and mixed kernels
+  df32         the same workload with the contractions in double-float (CPL_DF32)
+               and its error against the FP64 arm
   decouple     cpl_decouple on the binned matrices of 16 band-limited windows
                (l_max = 8000, 160 bins): event time per call for 1 and 32
                right-hand sides
@@ -524,11 +526,12 @@ def run_ours(args, rank, world, local):
                                    "at 6 limbs) / event-timed kernel duration; algorithmic_tflops counts 2 FLOP "
                                    "per window-term-contraction"}
 
-    def mixed_error():
-        """Relative error of the mixed arm against the plain FP64 arm on this workload."""
+    def mixed_error(prec=coupling.MIXED_BF16):
+        """Relative error of another arm (mixed or double-float) against the plain
+        FP64 arm on this workload."""
         ref = torch.empty_like(out)
         ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=ref)
-        ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=out, precision=coupling.MIXED_BF16)
+        ctx.build(LMAX, dWt, dWc, dWp, coupling.ALL, out=out, precision=prec)
         torch.cuda.synchronize()
         ctx.sync()
         err = {}
@@ -557,6 +560,27 @@ def run_ours(args, rank, world, local):
                  "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in o_stats.items()},
                  "clocks": o_clk, "spread": o_spread}
         other["max_rel_err_vs_fp64"] = mixed_error()
+    # the plain path's contractions in double-float (CPL_DF32), same workload
+    df32 = None
+    if not args.no_other and args.precision == "fp64":
+        d_steps = max(3, min(args.steps, 10))
+        d_ms, d_stats, d_clk, _, d_spread = timed_arm(coupling.DF32, d_steps, 2)
+        dk = max(((k, v) for k, v in d_stats.items() if k.startswith("plain_df") and v["launches"]),
+                 key=lambda kv: kv[1]["ms"], default=None)
+        df32 = {"value": job_value(world, 5 * n_el, d_ms * 1e-3), "unit": UNIT, "ms_per_step": d_ms,
+                "steps": d_steps, "precision": "df32 (FP32 pairs on the FP32 pipe)",
+                "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in d_stats.items()},
+                "clocks": d_clk, "spread": d_spread}
+        if dk is not None and dk[1]["ms"] > 0:
+            eq = dk[1]["flop"] / (dk[1]["ms"] * 1e-3) / 1e12
+            df32["roofline"] = {
+                "bound": "alu", "kernel": dk[0], "achieved": eq, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": eq / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz",
+                "achieved_counts": "FP64-equivalent FLOP of the contractions (2 per term and contraction, as the "
+                                   "FP64 kernel counts them) / event time: the fraction says how far the FP32-pair "
+                                   "kernel runs past the FP64 pipe's peak; ncu: FMA-heavy pipe ~80% busy"}
+        df32["max_rel_err_vs_fp64"] = mixed_error(coupling.DF32)
 
     # (j1 j2 j3; 0 -1 1) columns: 4096 pairs with j2, j3 in [1000, 3000]
     threej = None
@@ -730,6 +754,8 @@ def run_ours(args, rank, world, local):
                 "clocks": clk, "wall_s_timed": t_wall, "spread": spread}
         if other is not None:
             line["mixed" if args.precision == "fp64" else "fp64"] = other
+        if df32 is not None:
+            line["df32"] = df32
         if batch is not None:
             line["batch"] = batch
         if threej is not None:

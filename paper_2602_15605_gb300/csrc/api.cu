@@ -460,7 +460,20 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
                 int nslots = 0;
                 for (int q = 0; q < 5; ++q) nslots += sw.slot[q] >= 0;
                 double e, od, np;
-                tile_terms_split(J.ts->host[it.tile], r->lmax, r->lmin, J.caps[it.win], &e, &od, &np);
+                if (J.caps[it.win] >= 2 * r->lmax) {
+                    std::vector<double> &T = J.ts->terms;
+                    if (T.size() != 3 * J.ts->host.size()) {
+                        T.resize(3 * J.ts->host.size());
+                        for (size_t q = 0; q < J.ts->host.size(); ++q)
+                            tile_terms_split(J.ts->host[q], r->lmax, r->lmin, 2 * r->lmax, &T[3 * q], &T[3 * q + 1],
+                                             &T[3 * q + 2]);
+                    }
+                    e = T[3 * it.tile];
+                    od = T[3 * it.tile + 1];
+                    np = T[3 * it.tile + 2];
+                } else {
+                    tile_terms_split(J.ts->host[it.tile], r->lmax, r->lmin, J.caps[it.win], &e, &od, &np);
+                }
                 flop += 2.0 * (a.nge * e + (odd ? 3.0 : 0.0) * od);
                 bytes += (J.nb ? 0.0 : 16.0) * nslots * np;
             }

@@ -48,6 +48,9 @@ struct DevBuf {
 struct TileSet {
     std::vector<Tile> host;
     DevBuf dev;
+    // per-tile l3 term counts (even, odd, pairs) for windows without a band
+    // limit (cap >= 2 lmax), filled on first use by the launch accounting
+    std::vector<double> terms;
 };
 
 

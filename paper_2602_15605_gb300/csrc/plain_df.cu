@@ -12,9 +12,9 @@
 //   pairs stay inside FP32's exponent range; terms 2^126 below the tile's
 //   largest weight are lost, far below the error metric;
 // * products: p = a_h b_h exactly as (p, fma(a_h, b_h, -p)) plus the two
-//   cross terms; sums: a two-sum and a renormalisation per term into a
-//   chunk accumulator, and every chunk of 16 l3 values added to the running
-//   total with an accurate pair addition.  Two output columns share each
+//   cross terms; sums: compensated summation (a two-sum per term, the
+//   errors gathered in a low word) over chunks of 16 l3 values, each chunk
+//   then added to the running total with an accurate pair addition.  Two output columns share each
 //   instruction (packed f32x2 add, mul, fma);
 // * epilogue: hi + lo in FP64 times 2^E, then the FP64 combination of the
 //   contractions and the writes of plain_fp64.cu.
@@ -70,7 +70,10 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 // acc (hi2, lo2) += a * b for a scalar pair a and packed pairs b (bh2, bl2):
-// exact product error, two-sum, renormalisation.
+// the product's rounding error from fma, the sum's from a two-sum, both
+// collected in lo (compensated summation: lo is not renormalised into hi
+// until the chunk is added to the total, so a chunk of n terms is as
+// accurate as if summed in twice the working precision plus O(n^2 u^2)).
 __device__ __forceinline__ void df_fma2(float2 &hi, float2 &lo, float2 ah2, float2 al2, float2 bh, float2 bl) {
     const float2 p = __fmul2_rn(ah2, bh);
     float2 e = __ffma2_rn(ah2, bh, neg2(p));
@@ -79,9 +82,8 @@ __device__ __forceinline__ void df_fma2(float2 &hi, float2 &lo, float2 ah2, floa
     const float2 s = __fadd2_rn(hi, p);
     const float2 z = sub2(s, hi);
     const float2 t = __fadd2_rn(sub2(hi, sub2(s, z)), sub2(p, z));
-    const float2 l = __fadd2_rn(lo, __fadd2_rn(t, e));
-    hi = __fadd2_rn(s, l);
-    lo = sub2(l, sub2(hi, s));
+    lo = __fadd2_rn(lo, __fadd2_rn(t, e));
+    hi = s;
 }
 
 // (Th, Tl) += (Ch, Cl), packed, with an accurate pair addition.
