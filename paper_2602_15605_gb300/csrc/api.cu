@@ -227,15 +227,30 @@ namespace {
 // Work items (window, tile) of one request with their costs (l3 terms).  A
 // tile whose smallest |d| exceeds a window's last l3 contributes nothing for
 // that window and is dropped (the output is pre-zeroed in that case).
-void make_items(const std::vector<Tile> &tiles, const std::vector<int> &caps, int lmax, int lmin,
-                bool banded, std::vector<std::pair<double, WorkItem>> &items) {
+void make_items(TileSet &ts, const std::vector<int> &caps, int lmax, int lmin, bool banded,
+                std::vector<std::pair<double, WorkItem>> &items) {
+    const std::vector<Tile> &tiles = ts.host;
     items.clear();
     const int nw = (int)caps.size();
+    std::vector<const std::vector<double> *> cost_of(nw, nullptr);
+    if (banded) {
+        // term counts per (tile, cap), computed once per tile set and cap
+        if (ts.band_terms.size() > 64) ts.band_terms.clear();   // bound the cache
+        for (int w = 0; w < nw; ++w) {
+            std::vector<double> &v = ts.band_terms[caps[w]];
+            if (v.size() != tiles.size()) {
+                v.resize(tiles.size());
+                for (size_t ti = 0; ti < tiles.size(); ++ti)
+                    v[ti] = 2 * tiles[ti].i0 + tiles[ti].pi > caps[w] ? 0.0 : tile_terms(tiles[ti], lmax, lmin, caps[w]);
+            }
+            cost_of[w] = &v;
+        }
+    }
     for (int ti = 0; ti < (int)tiles.size(); ++ti) {
         const Tile &t = tiles[ti];
         for (int w = 0; w < nw; ++w) {
             if (banded && 2 * t.i0 + t.pi > caps[w]) continue;
-            const double cost = banded ? tile_terms(t, lmax, lmin, caps[w]) : (double)t.cost;
+            const double cost = banded ? (*cost_of[w])[ti] : (double)t.cost;
             items.emplace_back(cost, WorkItem{0, w, ti, 0});
         }
     }
@@ -314,7 +329,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
                 J.bin_inv[b] = 1.0 / (double)(r->bin_edges[b + 1] - r->bin_edges[b]);
             }
         }
-        make_items(J.ts->host, J.caps, r->lmax, r->lmin, J.banded, J.items);
+        make_items(*J.ts, J.caps, r->lmax, r->lmin, J.banded, J.items);
         // window roles sharing one pointer share one sweep
         std::vector<Group> groups;
         auto add = [&](const double *W, unsigned b) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <memory>
 #include <string>
 #include <utility>
@@ -51,6 +52,9 @@ struct TileSet {
     // per-tile l3 term counts (even, odd, pairs) for windows without a band
     // limit (cap >= 2 lmax), filled on first use by the launch accounting
     std::vector<double> terms;
+    // per-tile l3 term counts under a band limit (cap -> one count per tile),
+    // the scheduling costs of band-limited requests
+    std::map<int, std::vector<double>> band_terms;
 };
 
 
