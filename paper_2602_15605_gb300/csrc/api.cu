@@ -89,37 +89,6 @@ void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double f
     }
 }
 
-}  // namespace cpl
-
-namespace {
-
-// Brackets one kernel launch: counts it and, when profiling, times it with
-// events on the launching stream.
-struct LaunchScope {
-    cpl_ctx *c;
-    int idx;
-    cudaStream_t st;
-    cudaEvent_t a = nullptr;
-    LaunchScope(cpl_ctx *c_, const char *name, cudaStream_t st_) : c(c_), idx(stat_index(c_, name)), st(st_) {
-        if (c->profiling) {
-            a = take_event(c);
-            if (a) cudaEventRecord(a, st);
-        }
-    }
-    void done(double flop, double bytes) {
-        c->kstats[idx].launches++;
-        if (c->profiling && a) {
-            cudaEvent_t b = take_event(c);
-            if (b) {
-                cudaEventRecord(b, st);
-                c->pending.push_back({idx, a, b, flop, bytes, flop});
-                return;
-            }
-            c->ev_pool.push_back(a);
-        }
-    }
-};
-
 cpl_status select_device(cpl_ctx *c) {
     t_alloc_fault = &c->alloc_fault;   // allocations of this call count against the context's hook
     CPL_CUDA_TRY(cudaSetDevice(c->device));
@@ -172,6 +141,10 @@ cpl_status validate(const cpl_request *r, bool device_ptrs) {
     }
     return CPL_OK;
 }
+
+}  // namespace cpl
+
+namespace {
 
 size_t out_doubles(const cpl_request *r) {
     const size_t ns = (size_t)spec_count(r->spectra);
@@ -702,210 +675,6 @@ cpl_status cpl_threej_m11(cpl_ctx *c, const int *j2, const int *j3, int n, doubl
         LaunchScope ls(c, "threej_m11", st);
         CPL_CUDA_TRY(launch_threej_m11(sg, sh, sn, d, d + n, n, out, out_stride, st));
         ls.done(0.0, 8.0 * (double)n * (double)out_stride);
-    }
-    CPL_CUDA_TRY(cudaEventRecord(c->done, st));
-    return CPL_OK;
-}
-
-cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, const double *M, const double *pcl,
-                        int n_rhs, double *out, int *info, void *stream) {
-    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
-    if (!M || !pcl || !out) return fail(CPL_ERR_ARG, "M, pcl and out must be non-NULL");
-    if (n < 1 || n > CPL_DECOUPLE_NMAX) return fail(CPL_ERR_RANGE, "n must be in 1 .. CPL_DECOUPLE_NMAX");
-    if (n_windows < 1) return fail(CPL_ERR_ARG, "n_windows must be >= 1");
-    if (n_rhs < 1 || n_rhs > CPL_DECOUPLE_RHS_MAX) return fail(CPL_ERR_RANGE, "n_rhs must be in 1 .. CPL_DECOUPLE_RHS_MAX");
-    if (spectra == 0 || (spectra & ~31u)) return fail(CPL_ERR_ARG, "spectra must be a non-empty set of CPL_* bits");
-    if (!(spectra & kEE) != !(spectra & kEEBB))
-        return fail(CPL_ERR_ARG, "CPL_EE and CPL_EEBB must be decoupled together (the EE/BB system)");
-    DecoupleArgs a{};
-    a.M = M;
-    a.pcl = pcl;
-    a.out = out;
-    a.info = info;
-    a.n = n;
-    a.n_rhs = n_rhs;
-    a.ld = (n + n_rhs) | 1;
-    a.nspec = spec_count(spectra);
-    // fields TT, TE, EE, BB, EB of the requested set, systems TT, TE, EE+EEBB, EE-EEBB, EB
-    int nf = 0, fTT = -1, fTE = -1, fEE = -1, fBB = -1, fEB = -1;
-    if (spectra & kTT) fTT = nf++;
-    if (spectra & kTE) fTE = nf++;
-    if (spectra & kEE) { fEE = nf++; fBB = nf++; }
-    if (spectra & kEB) fEB = nf++;
-    a.n_fields = nf;
-    int q = 0;
-    auto add = [&](int kind, int s1, int s2, int f1, int f2) {
-        a.kind[q] = kind; a.slot1[q] = s1; a.slot2[q] = s2; a.field1[q] = f1; a.field2[q] = f2; ++q;
-    };
-    if (fTT >= 0) add(0, spec_slot(spectra, kTT), spec_slot(spectra, kTT), fTT, fTT);
-    if (fTE >= 0) add(0, spec_slot(spectra, kTE), spec_slot(spectra, kTE), fTE, fTE);
-    if (fEE >= 0) {
-        add(1, spec_slot(spectra, kEE), spec_slot(spectra, kEEBB), fEE, fBB);
-        add(2, spec_slot(spectra, kEE), spec_slot(spectra, kEEBB), fEE, fBB);
-    }
-    if (fEB >= 0) add(0, spec_slot(spectra, kEB), spec_slot(spectra, kEB), fEB, fEB);
-    a.sys_per_window = q;
-    a.n_sys = (long long)q * n_windows;
-
-    cpl_status s;
-    if ((s = select_device(c)) != CPL_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    int nsm = 0;
-    CPL_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    // FP64 solver: augmented matrix in shared memory when it fits.  Refined
-    // solver (FP32 factors + FP64 residuals) when it needs fewer FP64
-    // operations: its residuals cost about 3 n^2 n_rhs per system against
-    // n^3 / 3 + 1.5 n^2 n_rhs for the FP64 solve, i.e. n_rhs <= 2n/9.
-    const size_t limit = (size_t)decouple_smem_limit();
-    const size_t direct_bytes = sizeof(double) * (size_t)n * a.ld;
-    a.direct_in_ws = direct_bytes > limit;
-    a.refine = 9 * n_rhs <= 2 * n && n <= IR_NMAX;
-    size_t ir_bytes = 0;
-    if (a.refine) {
-        ir_bytes = ir_layout(n, n_rhs, true).total;
-        a.l_in_ws = ir_bytes > limit;
-        if (a.l_in_ws) ir_bytes = ir_layout(n, n_rhs, false).total;
-        if (ir_bytes > limit) {
-            a.refine = 0;
-            a.l_in_ws = 0;
-            ir_bytes = 0;
-        }
-    }
-    const size_t smem = std::max(ir_bytes, a.direct_in_ws ? (size_t)0 : direct_bytes);
-    int bps = 0;
-    CPL_CUDA_TRY(decouple_blocks_per_sm(smem, &bps));
-    const int grid = (int)std::min<long long>(a.n_sys, (long long)nsm * std::max(bps, 1));
-    if (a.direct_in_ws || a.refine) {
-        // one slice per CTA: the refined solver's FP64 K1 +- K2 (n^2 doubles,
-        // whole 16-byte units) and, when not in shared memory, its padded FP32
-        // factors; or the FP64 solver's augmented matrix -- the larger, even
-        const size_t kc = ((size_t)n * n + 1) & ~(size_t)1;
-        const size_t f32 = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;
-        const size_t fp64 = a.direct_in_ws ? (size_t)n * a.ld : 0;
-        a.ws_stride = (std::max(a.refine ? kc + f32 : 0, fp64) + 1) & ~(size_t)1;
-        CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
-        if ((s = c->dec_ws.ensure(sizeof(double) * a.ws_stride * grid, "decoupling workspace")) != CPL_OK) return s;
-        a.ws = c->dec_ws.as<double>();
-    }
-    if (fEE >= 0)
-        CPL_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)n_windows * n_rhs * nf * n, st));
-    {
-        LaunchScope ls(c, "decouple", st);
-        CPL_CUDA_TRY(launch_decouple(a, grid, smem, st));
-        const double nn = n, R = n_rhs;
-        const double flop = (double)a.n_sys * ((nn - 1) * nn * (2 * nn - 1) / 3.0 + 2.0 * R * nn * (nn - 1));
-        ls.done(flop, 8.0 * (double)a.n_sys * (nn * nn + 2.0 * R * nn));
-    }
-    if (a.ws) CPL_CUDA_TRY(cudaEventRecord(c->done, st));
-    return CPL_OK;
-}
-
-cpl_status cpl_cov_gaussian(cpl_ctx *c, int lmax, int lmin, const cpl_cov_term *terms, int n_terms, int w_len,
-                            int precision, const int *bin_edges, int n_bins, double *out, void *stream) {
-    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
-    if (!terms || n_terms < 1 || !out) return fail(CPL_ERR_ARG, "terms (n_terms >= 1) and out must be given");
-    if (lmax < 2 || lmin < 0 || lmin > lmax) return fail(CPL_ERR_RANGE, "need lmax >= 2 and 0 <= lmin <= lmax");
-    // group the terms by (window, band limit): one kernel build per group
-    struct Group {
-        const double *W;
-        int band;
-        unsigned spectra;
-        std::vector<int> idx;
-    };
-    std::vector<Group> groups;
-    for (int t = 0; t < n_terms; ++t) {
-        const cpl_cov_term &T = terms[t];
-        const unsigned b = T.spectrum;
-        if (b == 0 || (b & (b - 1)) || b > kEB) return fail(CPL_ERR_ARG, "each term needs exactly one CPL_* spectrum bit");
-        if (!T.W || !T.A || !T.B) return fail(CPL_ERR_ARG, "each term needs W, A and B");
-        if (T.band_limit < -1) return fail(CPL_ERR_ARG, "band_limit must be >= -1");
-        Group *g = nullptr;
-        for (auto &x : groups)
-            if (x.W == T.W && x.band == T.band_limit) g = &x;
-        if (!g) {
-            groups.push_back(Group{T.W, T.band_limit, 0u, {}});
-            g = &groups.back();
-        }
-        g->spectra |= b;
-        g->idx.push_back(t);
-    }
-    // validate every build (and the binning) before any device work
-    const int n = lmax - lmin + 1;
-    std::vector<cpl_request> reqs(groups.size());
-    for (size_t q = 0; q < groups.size(); ++q) {
-        cpl_request &r = reqs[q];
-        r = cpl_request{};
-        r.lmax = lmax;
-        r.lmin = lmin;
-        r.n_windows = 1;
-        r.W_tt = r.W_tp = r.W_pp = groups[q].W;
-        r.w_len = w_len;
-        r.band_limit = groups[q].band >= 0 ? &groups[q].band : nullptr;
-        r.spectra = groups[q].spectra;
-        r.precision = precision;
-        size_t nd = 0;
-        cpl_status s = cpl_output_size(&r, &nd);
-        if (s != CPL_OK) return s;
-    }
-    if (bin_edges || n_bins) {
-        cpl_request rb = reqs[0];
-        rb.bin_edges = bin_edges;
-        rb.n_bins = n_bins;
-        size_t nd = 0;
-        cpl_status s = cpl_output_size(&rb, &nd);
-        if (s != CPL_OK) return s;
-    }
-    cpl_status s;
-    if ((s = select_device(c)) != CPL_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    int max_spec = 1;
-    for (auto &g : groups) max_spec = std::max(max_spec, spec_count(g.spectra));
-    const size_t nn = (size_t)n * n;
-    CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
-    if ((s = c->cov_M.ensure(sizeof(double) * nn * max_spec, "covariance kernels")) != CPL_OK) return s;
-    const bool binned = bin_edges != nullptr;
-    if (binned) {
-        if ((s = c->cov_dense.ensure(sizeof(double) * nn, "dense covariance")) != CPL_OK) return s;
-        if ((s = c->cov_edges.ensure(sizeof(int) * (n_bins + 1), "covariance bin edges")) != CPL_OK) return s;
-        CPL_CUDA_TRY(cudaMemcpyAsync(c->cov_edges.ptr, bin_edges, sizeof(int) * (n_bins + 1), cudaMemcpyHostToDevice, st));
-    }
-    double *dense = binned ? c->cov_dense.as<double>() : out;
-    bool first = true;
-    for (size_t q = 0; q < groups.size(); ++q) {
-        if ((s = cpl_build(c, &reqs[q], c->cov_M.as<double>(), stream)) != CPL_OK) return s;
-        const auto &idx = groups[q].idx;
-        for (size_t t0 = 0; t0 < idx.size(); t0 += COV_TERMS_PER_LAUNCH) {
-            CovCombineArgs a{};
-            a.M = c->cov_M.as<double>();
-            a.n = n;
-            a.lmin = lmin;
-            a.n_terms = (int)std::min<size_t>(COV_TERMS_PER_LAUNCH, idx.size() - t0);
-            for (int k = 0; k < a.n_terms; ++k) {
-                const cpl_cov_term &T = terms[idx[t0 + k]];
-                a.slot[k] = spec_slot(groups[q].spectra, T.spectrum);
-                a.A[k] = T.A;
-                a.B[k] = T.B;
-            }
-            a.out = dense;
-            a.accumulate = first ? 0 : 1;
-            first = false;
-            LaunchScope ls(c, "cov_combine", st);
-            CPL_CUDA_TRY(launch_cov_combine(a, st));
-            ls.done(3.0 * 2.0 * a.n_terms * 0.5 * (double)nn,
-                    8.0 * (double)nn * (0.5 * a.n_terms + (a.accumulate ? 2.0 : 1.0)));
-        }
-    }
-    if (binned) {
-        CovBinArgs b{};
-        b.cov = dense;
-        b.n = n;
-        b.lmin = lmin;
-        b.nb = n_bins;
-        b.edges = c->cov_edges.as<int>();
-        b.out = out;
-        LaunchScope ls(c, "cov_bin", st);
-        CPL_CUDA_TRY(launch_cov_bin(b, st));
-        ls.done((double)nn, 8.0 * (double)nn);
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));
     return CPL_OK;

@@ -15,6 +15,10 @@
 // k_cov_bin: Cov_bb' = (1/|b||b'|) sum over the bin rectangle, one warp per
 //   bin pair b <= b' in a fixed summation order (lane-strided columns, rows
 //   in order, then a fixed shuffle tree), mirrored to (b', b).
+#include <algorithm>
+#include <vector>
+
+#include "ctx.h"
 #include "internal.h"
 
 namespace cpl {
@@ -124,3 +128,121 @@ cudaError_t launch_cov_bin(const CovBinArgs &a, cudaStream_t st) {
 }
 
 }  // namespace cpl
+
+// ---------------------------------------------------------------- entry point
+using namespace cpl;
+
+extern "C" {
+
+cpl_status cpl_cov_gaussian(cpl_ctx *c, int lmax, int lmin, const cpl_cov_term *terms, int n_terms, int w_len,
+                            int precision, const int *bin_edges, int n_bins, double *out, void *stream) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (!terms || n_terms < 1 || !out) return fail(CPL_ERR_ARG, "terms (n_terms >= 1) and out must be given");
+    if (lmax < 2 || lmin < 0 || lmin > lmax) return fail(CPL_ERR_RANGE, "need lmax >= 2 and 0 <= lmin <= lmax");
+    // group the terms by (window, band limit): one kernel build per group
+    struct Group {
+        const double *W;
+        int band;
+        unsigned spectra;
+        std::vector<int> idx;
+    };
+    std::vector<Group> groups;
+    for (int t = 0; t < n_terms; ++t) {
+        const cpl_cov_term &T = terms[t];
+        const unsigned b = T.spectrum;
+        if (b == 0 || (b & (b - 1)) || b > kEB) return fail(CPL_ERR_ARG, "each term needs exactly one CPL_* spectrum bit");
+        if (!T.W || !T.A || !T.B) return fail(CPL_ERR_ARG, "each term needs W, A and B");
+        if (T.band_limit < -1) return fail(CPL_ERR_ARG, "band_limit must be >= -1");
+        Group *g = nullptr;
+        for (auto &x : groups)
+            if (x.W == T.W && x.band == T.band_limit) g = &x;
+        if (!g) {
+            groups.push_back(Group{T.W, T.band_limit, 0u, {}});
+            g = &groups.back();
+        }
+        g->spectra |= b;
+        g->idx.push_back(t);
+    }
+    // validate every build (and the binning) before any device work
+    const int n = lmax - lmin + 1;
+    std::vector<cpl_request> reqs(groups.size());
+    for (size_t q = 0; q < groups.size(); ++q) {
+        cpl_request &r = reqs[q];
+        r = cpl_request{};
+        r.lmax = lmax;
+        r.lmin = lmin;
+        r.n_windows = 1;
+        r.W_tt = r.W_tp = r.W_pp = groups[q].W;
+        r.w_len = w_len;
+        r.band_limit = groups[q].band >= 0 ? &groups[q].band : nullptr;
+        r.spectra = groups[q].spectra;
+        r.precision = precision;
+        size_t nd = 0;
+        cpl_status s = cpl_output_size(&r, &nd);
+        if (s != CPL_OK) return s;
+    }
+    if (bin_edges || n_bins) {
+        cpl_request rb = reqs[0];
+        rb.bin_edges = bin_edges;
+        rb.n_bins = n_bins;
+        size_t nd = 0;
+        cpl_status s = cpl_output_size(&rb, &nd);
+        if (s != CPL_OK) return s;
+    }
+    cpl_status s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int max_spec = 1;
+    for (auto &g : groups) max_spec = std::max(max_spec, spec_count(g.spectra));
+    const size_t nn = (size_t)n * n;
+    CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
+    if ((s = c->cov_M.ensure(sizeof(double) * nn * max_spec, "covariance kernels")) != CPL_OK) return s;
+    const bool binned = bin_edges != nullptr;
+    if (binned) {
+        if ((s = c->cov_dense.ensure(sizeof(double) * nn, "dense covariance")) != CPL_OK) return s;
+        if ((s = c->cov_edges.ensure(sizeof(int) * (n_bins + 1), "covariance bin edges")) != CPL_OK) return s;
+        CPL_CUDA_TRY(cudaMemcpyAsync(c->cov_edges.ptr, bin_edges, sizeof(int) * (n_bins + 1), cudaMemcpyHostToDevice, st));
+    }
+    double *dense = binned ? c->cov_dense.as<double>() : out;
+    bool first = true;
+    for (size_t q = 0; q < groups.size(); ++q) {
+        if ((s = cpl_build(c, &reqs[q], c->cov_M.as<double>(), stream)) != CPL_OK) return s;
+        const auto &idx = groups[q].idx;
+        for (size_t t0 = 0; t0 < idx.size(); t0 += COV_TERMS_PER_LAUNCH) {
+            CovCombineArgs a{};
+            a.M = c->cov_M.as<double>();
+            a.n = n;
+            a.lmin = lmin;
+            a.n_terms = (int)std::min<size_t>(COV_TERMS_PER_LAUNCH, idx.size() - t0);
+            for (int k = 0; k < a.n_terms; ++k) {
+                const cpl_cov_term &T = terms[idx[t0 + k]];
+                a.slot[k] = spec_slot(groups[q].spectra, T.spectrum);
+                a.A[k] = T.A;
+                a.B[k] = T.B;
+            }
+            a.out = dense;
+            a.accumulate = first ? 0 : 1;
+            first = false;
+            LaunchScope ls(c, "cov_combine", st);
+            CPL_CUDA_TRY(launch_cov_combine(a, st));
+            ls.done(3.0 * 2.0 * a.n_terms * 0.5 * (double)nn,
+                    8.0 * (double)nn * (0.5 * a.n_terms + (a.accumulate ? 2.0 : 1.0)));
+        }
+    }
+    if (binned) {
+        CovBinArgs b{};
+        b.cov = dense;
+        b.n = n;
+        b.lmin = lmin;
+        b.nb = n_bins;
+        b.edges = c->cov_edges.as<int>();
+        b.out = out;
+        LaunchScope ls(c, "cov_bin", st);
+        CPL_CUDA_TRY(launch_cov_bin(b, st));
+        ls.done((double)nn, 8.0 * (double)nn);
+    }
+    CPL_CUDA_TRY(cudaEventRecord(c->done, st));
+    return CPL_OK;
+}
+
+}  // extern "C"

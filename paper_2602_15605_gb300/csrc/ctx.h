@@ -143,4 +143,35 @@ int stat_index(cpl_ctx *c, const char *name);
 void record_launch(cpl_ctx *c, int idx, cudaEvent_t a, cudaStream_t st, double flop, double bytes,
                    double issued = -1.0);
 cudaEvent_t begin_launch(cpl_ctx *c, cudaStream_t st);
+cudaEvent_t take_event(cpl_ctx *c);
+// Makes the context's device current and points the allocation-failure hook
+// at the context (every public entry point calls it before device work).
+cpl_status select_device(cpl_ctx *c);
+
+// Brackets one kernel launch: counts it and, when profiling, times it with
+// events on the launching stream.
+struct LaunchScope {
+    cpl_ctx *c;
+    int idx;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    LaunchScope(cpl_ctx *c_, const char *name, cudaStream_t st_) : c(c_), idx(stat_index(c_, name)), st(st_) {
+        if (c->profiling) {
+            a = take_event(c);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    void done(double flop, double bytes) {
+        c->kstats[idx].launches++;
+        if (c->profiling && a) {
+            cudaEvent_t b = take_event(c);
+            if (b) {
+                cudaEventRecord(b, st);
+                c->pending.push_back({idx, a, b, flop, bytes, flop});
+                return;
+            }
+            c->ev_pool.push_back(a);
+        }
+    }
+};
 }  // namespace cpl

@@ -35,6 +35,9 @@
 // order, so results are deterministic.
 #include <cmath>
 
+#include <algorithm>
+
+#include "ctx.h"
 #include "internal.h"
 
 namespace cpl {
@@ -625,3 +628,103 @@ cudaError_t decouple_blocks_per_sm(size_t smem, int *n) {
 }
 
 }  // namespace cpl
+
+// ---------------------------------------------------------------- entry point
+using namespace cpl;
+
+extern "C" {
+
+cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, const double *M, const double *pcl,
+                        int n_rhs, double *out, int *info, void *stream) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    if (!M || !pcl || !out) return fail(CPL_ERR_ARG, "M, pcl and out must be non-NULL");
+    if (n < 1 || n > CPL_DECOUPLE_NMAX) return fail(CPL_ERR_RANGE, "n must be in 1 .. CPL_DECOUPLE_NMAX");
+    if (n_windows < 1) return fail(CPL_ERR_ARG, "n_windows must be >= 1");
+    if (n_rhs < 1 || n_rhs > CPL_DECOUPLE_RHS_MAX) return fail(CPL_ERR_RANGE, "n_rhs must be in 1 .. CPL_DECOUPLE_RHS_MAX");
+    if (spectra == 0 || (spectra & ~31u)) return fail(CPL_ERR_ARG, "spectra must be a non-empty set of CPL_* bits");
+    if (!(spectra & kEE) != !(spectra & kEEBB))
+        return fail(CPL_ERR_ARG, "CPL_EE and CPL_EEBB must be decoupled together (the EE/BB system)");
+    DecoupleArgs a{};
+    a.M = M;
+    a.pcl = pcl;
+    a.out = out;
+    a.info = info;
+    a.n = n;
+    a.n_rhs = n_rhs;
+    a.ld = (n + n_rhs) | 1;
+    a.nspec = spec_count(spectra);
+    // fields TT, TE, EE, BB, EB of the requested set, systems TT, TE, EE+EEBB, EE-EEBB, EB
+    int nf = 0, fTT = -1, fTE = -1, fEE = -1, fBB = -1, fEB = -1;
+    if (spectra & kTT) fTT = nf++;
+    if (spectra & kTE) fTE = nf++;
+    if (spectra & kEE) { fEE = nf++; fBB = nf++; }
+    if (spectra & kEB) fEB = nf++;
+    a.n_fields = nf;
+    int q = 0;
+    auto add = [&](int kind, int s1, int s2, int f1, int f2) {
+        a.kind[q] = kind; a.slot1[q] = s1; a.slot2[q] = s2; a.field1[q] = f1; a.field2[q] = f2; ++q;
+    };
+    if (fTT >= 0) add(0, spec_slot(spectra, kTT), spec_slot(spectra, kTT), fTT, fTT);
+    if (fTE >= 0) add(0, spec_slot(spectra, kTE), spec_slot(spectra, kTE), fTE, fTE);
+    if (fEE >= 0) {
+        add(1, spec_slot(spectra, kEE), spec_slot(spectra, kEEBB), fEE, fBB);
+        add(2, spec_slot(spectra, kEE), spec_slot(spectra, kEEBB), fEE, fBB);
+    }
+    if (fEB >= 0) add(0, spec_slot(spectra, kEB), spec_slot(spectra, kEB), fEB, fEB);
+    a.sys_per_window = q;
+    a.n_sys = (long long)q * n_windows;
+
+    cpl_status s;
+    if ((s = select_device(c)) != CPL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int nsm = 0;
+    CPL_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    // FP64 solver: augmented matrix in shared memory when it fits.  Refined
+    // solver (FP32 factors + FP64 residuals) when it needs fewer FP64
+    // operations: its residuals cost about 3 n^2 n_rhs per system against
+    // n^3 / 3 + 1.5 n^2 n_rhs for the FP64 solve, i.e. n_rhs <= 2n/9.
+    const size_t limit = (size_t)decouple_smem_limit();
+    const size_t direct_bytes = sizeof(double) * (size_t)n * a.ld;
+    a.direct_in_ws = direct_bytes > limit;
+    a.refine = 9 * n_rhs <= 2 * n && n <= IR_NMAX;
+    size_t ir_bytes = 0;
+    if (a.refine) {
+        ir_bytes = ir_layout(n, n_rhs, true).total;
+        a.l_in_ws = ir_bytes > limit;
+        if (a.l_in_ws) ir_bytes = ir_layout(n, n_rhs, false).total;
+        if (ir_bytes > limit) {
+            a.refine = 0;
+            a.l_in_ws = 0;
+            ir_bytes = 0;
+        }
+    }
+    const size_t smem = std::max(ir_bytes, a.direct_in_ws ? (size_t)0 : direct_bytes);
+    int bps = 0;
+    CPL_CUDA_TRY(decouple_blocks_per_sm(smem, &bps));
+    const int grid = (int)std::min<long long>(a.n_sys, (long long)nsm * std::max(bps, 1));
+    if (a.direct_in_ws || a.refine) {
+        // one slice per CTA: the refined solver's FP64 K1 +- K2 (n^2 doubles,
+        // whole 16-byte units) and, when not in shared memory, its padded FP32
+        // factors; or the FP64 solver's augmented matrix -- the larger, even
+        const size_t kc = ((size_t)n * n + 1) & ~(size_t)1;
+        const size_t f32 = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;
+        const size_t fp64 = a.direct_in_ws ? (size_t)n * a.ld : 0;
+        a.ws_stride = (std::max(a.refine ? kc + f32 : 0, fp64) + 1) & ~(size_t)1;
+        CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
+        if ((s = c->dec_ws.ensure(sizeof(double) * a.ws_stride * grid, "decoupling workspace")) != CPL_OK) return s;
+        a.ws = c->dec_ws.as<double>();
+    }
+    if (fEE >= 0)
+        CPL_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double) * (size_t)n_windows * n_rhs * nf * n, st));
+    {
+        LaunchScope ls(c, "decouple", st);
+        CPL_CUDA_TRY(launch_decouple(a, grid, smem, st));
+        const double nn = n, R = n_rhs;
+        const double flop = (double)a.n_sys * ((nn - 1) * nn * (2 * nn - 1) / 3.0 + 2.0 * R * nn * (nn - 1));
+        ls.done(flop, 8.0 * (double)a.n_sys * (nn * nn + 2.0 * R * nn));
+    }
+    if (a.ws) CPL_CUDA_TRY(cudaEventRecord(c->done, st));
+    return CPL_OK;
+}
+
+}  // extern "C"
