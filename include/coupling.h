@@ -392,8 +392,9 @@ cpl_status cpl_decouple(cpl_ctx *ctx, int n, int n_windows, unsigned spectra, co
  *   out          device, caller-owned: [n][n] (n = lmax - lmin + 1) or
  *                [n_bins][n_bins] FP64, exactly symmetric.
  *   stream       cudaStream_t or NULL.
- * Asynchronous on `stream`; deterministic.  Errors as cpl_build (output
- * untouched on CPL_ERR_ARG / CPL_ERR_RANGE).
+ * Asynchronous on `stream`; deterministic.  The sum is formed in context
+ * scratch and `out` is written last, so on any error status `out` is
+ * untouched.
  */
 typedef struct {
     unsigned spectrum;

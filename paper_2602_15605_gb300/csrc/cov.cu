@@ -197,13 +197,15 @@ cpl_status cpl_cov_gaussian(cpl_ctx *c, int lmax, int lmin, const cpl_cov_term *
     const size_t nn = (size_t)n * n;
     CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
     if ((s = c->cov_M.ensure(sizeof(double) * nn * max_spec, "covariance kernels")) != CPL_OK) return s;
+    // the sum is formed in context scratch and written to `out` only at the
+    // end (binning or one copy), so a failure part-way leaves `out` untouched
     const bool binned = bin_edges != nullptr;
+    if ((s = c->cov_dense.ensure(sizeof(double) * nn, "dense covariance")) != CPL_OK) return s;
     if (binned) {
-        if ((s = c->cov_dense.ensure(sizeof(double) * nn, "dense covariance")) != CPL_OK) return s;
         if ((s = c->cov_edges.ensure(sizeof(int) * (n_bins + 1), "covariance bin edges")) != CPL_OK) return s;
         CPL_CUDA_TRY(cudaMemcpyAsync(c->cov_edges.ptr, bin_edges, sizeof(int) * (n_bins + 1), cudaMemcpyHostToDevice, st));
     }
-    double *dense = binned ? c->cov_dense.as<double>() : out;
+    double *dense = c->cov_dense.as<double>();
     bool first = true;
     for (size_t q = 0; q < groups.size(); ++q) {
         if ((s = cpl_build(c, &reqs[q], c->cov_M.as<double>(), stream)) != CPL_OK) return s;
@@ -240,6 +242,8 @@ cpl_status cpl_cov_gaussian(cpl_ctx *c, int lmax, int lmin, const cpl_cov_term *
         LaunchScope ls(c, "cov_bin", st);
         CPL_CUDA_TRY(launch_cov_bin(b, st));
         ls.done((double)nn, 8.0 * (double)nn);
+    } else {
+        CPL_CUDA_TRY(cudaMemcpyAsync(out, dense, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st));
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));
     return CPL_OK;

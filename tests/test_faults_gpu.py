@@ -69,6 +69,44 @@ def test_mixed_allocation_failures():
     assert n >= 6   # tables, double-float tables, B cache (3), arena, error word, ticket, plan metadata
 
 
+def test_df32_allocation_failures():
+    lmax = 90
+    Wt, Wc, Wp = (dev(windows.gaussian_taper(lmax, s)) for s in (6, 7, 8))
+    c = coupling.Context(0)
+    ref = c.build(lmax, Wt, Wc, Wp, coupling.ALL, precision=coupling.DF32).cpu().numpy()
+    c.close()
+    n = _sweep(lambda c, out: c.build(lmax, Wt, Wc, Wp, coupling.ALL, precision=coupling.DF32, out=out), ref, 12)
+    assert n >= 4   # tables, double-float tables, tile list, weights, metadata
+
+
+def test_decouple_allocation_failures():
+    # n = 300 with 3 right-hand sides: the refined solver's workspace is allocated
+    import torch
+    rng = np.random.default_rng(2)
+    n = 300
+    M = dev(rng.normal(size=(2, 3, n, n)) + 3 * n ** 0.5 * np.eye(n))
+    pcl = dev(rng.normal(size=(2, 3, 3, n)))
+    sp = coupling.TT | coupling.EE | coupling.EEBB
+    c = coupling.Context(0)
+    ref = c.decouple(M, pcl, sp).cpu().numpy()
+    c.close()
+    n_fail = _sweep(lambda c, out: c.decouple(M, pcl, sp, out=out), ref, 4)
+    assert n_fail >= 1
+
+
+def test_cov_allocation_failures():
+    lmax = 80
+    W1 = dev(windows.mask_like(lmax, seed=4))
+    W2 = dev(windows.random_positive(lmax, seed=5, band=10))
+    C = dev(1.0 / (np.arange(lmax + 1) + 5.0) ** 2)
+    terms = [(coupling.TT, W1, None, C, 2 * C), (coupling.EE, W2, 10, C, C)]
+    c = coupling.Context(0)
+    ref = c.cov_gaussian(lmax, terms).cpu().numpy()
+    c.close()
+    n = _sweep(lambda c, out: c.cov_gaussian(lmax, terms, out=out), ref, 16)
+    assert n >= 4   # scratch, tables, tiles, weights and metadata of two builds
+
+
 def test_injection_arguments():
     c = coupling.Context(0)
     with pytest.raises(coupling.CouplingError):
