@@ -28,7 +28,7 @@ def dev(a):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("precision", [coupling.FP64, coupling.MIXED_BF16])
+@pytest.mark.parametrize("precision", [coupling.FP64, coupling.MIXED_BF16, coupling.DF32])
 def test_every_element_written_and_mirrors_agree(ctx, case, precision):
     import torch
     cs = CASES[case]
