@@ -149,9 +149,10 @@ struct MxEpiArgs {
     MxLayout L;
 };
 
-struct MxBandArgs {   // FP64 evaluation of the pairs with l1 < MX_L1_FP64
-    const double *g, *h;
-    const double *A;               // [nsrc][a_stride] FP64 weights
+struct MxBandArgs {   // double-float evaluation of the pairs with l1 < MX_L1_FP64
+    const float *gh, *gl, *hh, *hl;   // g and h as FP32 pairs
+    const float *Ah, *Al;          // [nsrc][a_stride] weights A = (Ah + Al) 2^Ae
+    const int *Ae;
     int a_stride;
     const int *l3cap;
     const int *src_win, *src_role;

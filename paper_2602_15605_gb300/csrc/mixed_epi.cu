@@ -11,10 +11,11 @@
 // FP64 with integer operations (the binned variant then applies the
 // (2l+1) / |bin| weights in FP64).
 //
-// k_mixed_band: pairs with l1 < MX_L1_FP64 in plain FP64.  For them the
+// k_mixed_band: pairs with l1 < MX_L1_FP64 outside the GEMM.  For them the
 // polynomial expansion of the polarisation factor cancels by up to two
 // orders of magnitude, which the limb contraction's 1e-10-level error would
-// amplify; their l3 sums are short (2 l1 + 1 terms), so FP64 costs little.
+// amplify; their l3 sums are short (2 l1 + 1 terms) and run in double-float
+// (~1e-14 per contraction), the combination in FP64.
 #include <cuda_runtime.h>
 
 #include "dd.cuh"
@@ -337,7 +338,13 @@ __device__ __forceinline__ void put_out_d(const MxBandArgs &a, int w, int slot, 
 }
 
 // One thread per (pair with l1 < MX_L1_FP64, source): the separable sums of
-// plain_fp64.cu over the pair's few l3 terms, in FP64.
+// plain_fp64.cu over the pair's few l3 terms, in double-float relative to
+// 2^E0, E0 the largest weight exponent over the pair's l3 range (the weights
+// of such a short range differ by a few orders of magnitude at most, so the
+// scaled terms stay inside FP32's range), then to FP64 for the combination.
+// Only the contractions the source's spectra use are formed.
+__device__ __forceinline__ dfl pair_df(const float *h, const float *l, int q) { return {h[q], l[q]}; }
+
 __global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
     const int l2 = blockIdx.x * blockDim.x + threadIdx.x;
     const int l1 = a.lmin + blockIdx.y;
@@ -345,53 +352,82 @@ __global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
     if (l1 >= MX_L1_FP64 || l2 < l1 || l2 > a.lmax) return;
     const int d = l2 - l1, sm = l1 + l2, pi = d & 1;
     const int i = (d - pi) >> 1, j = (sm - pi) >> 1;
-    const double *A = a.A + (size_t)s * a.a_stride;
+    const float *Ah = a.Ah + (size_t)s * a.a_stride, *Al = a.Al + (size_t)s * a.a_stride;
+    const int *Ae = a.Ae + (size_t)s * a.a_stride;
     const int cap = a.l3cap[s];
     const int role = a.src_role[s], w = a.src_win[s];
-    double S[MX_NPROD];
+    const bool pol = (role & (kTE | kEE | kEEBB | kEB)) != 0;
+    const bool need_ee = (role & (kEE | kEB)) != 0, odd = (role & (kEEBB | kEB)) != 0;
+    int E0 = -2147483647;
+    for (int l3 = d; l3 <= min(sm, cap); ++l3)
+        if (Ah[l3] != 0.f) E0 = max(E0, Ae[l3]);
+    dfl S[MX_NPROD];
 #pragma unroll
-    for (int p = 0; p < MX_NPROD; ++p) S[p] = 0.0;
-    // even sweep: l3 = 2k + pi, i <= k <= j
-    for (int k = i; k <= j; ++k) {
-        const int l3 = 2 * k + pi;
-        if (l3 > cap) break;
-        const double a0 = A[l3] * a.g[i + k + pi] * a.g[k - i];
-        const double v = (double)(2 * k + 2 * i + 2 * pi + 1) * (double)(2 * k - 2 * i);
-        const double b0 = a.g[j - k] * a.h[j + k + pi];
-        const double u = (double)(2 * j + 2 * k + 2 * pi + 2) * (double)(2 * j - 2 * k + 1);
-        S[0] += a0 * b0;
-        S[1] += a0 * b0 * u;
-        S[2] += a0 * v * b0 * u;
-        S[3] += a0 * b0 * u * u;
-        S[4] += a0 * v * b0 * u * u;
-        S[5] += a0 * v * v * b0 * u * u;
+    for (int p = 0; p < MX_NPROD; ++p) S[p] = {0.f, 0.f};
+    if (E0 != -2147483647) {
+        // even sweep: l3 = 2k + pi, i <= k <= j
+        for (int k = i; k <= j; ++k) {
+            const int l3 = 2 * k + pi;
+            if (l3 > cap) break;
+            const int f = Ae[l3] - E0;
+            const dfl mA = {scale2(Ah[l3], f), scale2(Al[l3], f)};
+            const dfl a0 = df_mul(df_mul(mA, pair_df(a.gh, a.gl, i + k + pi)), pair_df(a.gh, a.gl, k - i));
+            const dfl b0 = df_mul(pair_df(a.gh, a.gl, j - k), pair_df(a.hh, a.hl, j + k + pi));
+            const dfl t = df_mul(a0, b0);
+            S[0] = df_add(S[0], t);
+            if (pol) {
+                const dfl u = df_from_ll((long long)(2 * j + 2 * k + 2 * pi + 2) * (2 * j - 2 * k + 1));
+                const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (2 * k - 2 * i));
+                const dfl tu = df_mul(t, u);
+                S[1] = df_add(S[1], tu);
+                S[2] = df_add(S[2], df_mul(tu, v));
+                if (need_ee) {
+                    const dfl tuu = df_mul(tu, u);
+                    const dfl tuuv = df_mul(tuu, v);
+                    S[3] = df_add(S[3], tuu);
+                    S[4] = df_add(S[4], tuuv);
+                    S[5] = df_add(S[5], df_mul(tuuv, v));
+                }
+            }
+        }
+        // odd sweep: l3 = 2k + 1 - pi, i + pi <= k <= j + pi - 1
+        if (odd) {
+            for (int k = i + pi; k <= j + pi - 1; ++k) {
+                const int l3 = 2 * k + 1 - pi;
+                if (l3 > cap) break;
+                const int f = Ae[l3] - E0;
+                const dfl mA = {scale2(Ah[l3], f), scale2(Al[l3], f)};
+                const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (2 * k + 1 - 2 * i - 2 * pi));
+                const dfl u1 = df_from_ll((long long)(2 * j + 2 * k + 3) * (2 * j - 2 * k + 2 * pi));
+                const dfl up = df_from_ll((long long)(2 * j + 2 * k + 4) * (2 * j - 2 * k + 2 * pi + 1));
+                const dfl a1v = df_mul(df_mul(df_mul(mA, pair_df(a.gh, a.gl, i + k + 1)),
+                                              pair_df(a.gh, a.gl, k - i - pi)), v1);
+                const dfl b1u = df_mul(df_mul(pair_df(a.gh, a.gl, j - k + pi), pair_df(a.hh, a.hl, j + k + 1)), u1);
+                const dfl t = df_mul(a1v, b1u);
+                const dfl tu = df_mul(t, up);
+                S[6] = df_add(S[6], t);
+                S[7] = df_add(S[7], tu);
+                S[8] = df_add(S[8], df_mul(tu, up));
+            }
+        }
     }
-    // odd sweep: l3 = 2k + 1 - pi, i + pi <= k <= j + pi - 1
-    for (int k = i + pi; k <= j + pi - 1; ++k) {
-        const int l3 = 2 * k + 1 - pi;
-        if (l3 > cap) break;
-        const double a1v = A[l3] * a.g[i + k + 1] * a.g[k - i - pi] *
-                           ((double)(2 * i + 2 * k + 2) * (double)(2 * k + 1 - 2 * i - 2 * pi));
-        const double b1u = a.g[j - k + pi] * a.h[j + k + 1] *
-                           ((double)(2 * j + 2 * k + 3) * (double)(2 * j - 2 * k + 2 * pi));
-        const double up = (double)(2 * j + 2 * k + 4) * (double)(2 * j - 2 * k + 2 * pi + 1);
-        S[6] += a1v * b1u;
-        S[7] += a1v * b1u * up;
-        S[8] += a1v * b1u * up * up;
-    }
-    if (role & kTT) put_out_d(a, w, a.slot[0], l1, l2, S[0]);
+    double D[MX_NPROD];
+#pragma unroll
+    for (int p = 0; p < MX_NPROD; ++p)
+        D[p] = E0 == -2147483647 ? 0.0 : ldexp((double)S[p].h + (double)S[p].l, E0);
+    if (role & kTT) put_out_d(a, w, a.slot[0], l1, l2, D[0]);
     if (role & (kTE | kEE | kEEBB | kEB)) {
         const double L1 = l1, L2 = l2;
         const double eta2 = (L1 - 1.0) * (L1 + 2.0) * (L2 - 1.0) * L2;
         const double c1 = 1.0 / (L1 * (L1 + 1.0) * (L2 + 1.0));
         const double r2 = L1 * (L1 + 1.0) * (L2 + 1.0) * (L2 + 2.0) / eta2;
         const double c0 = 1.0 + 2.0 / L1, c2 = c1 / (2.0 * (L2 + 2.0));
-        if (role & kTE) put_out_d(a, w, a.slot[1], l1, l2, sqrt(r2) * (c0 * S[0] - c1 * S[1] - c2 * S[2]));
-        const double ee = r2 * (c0 * c0 * S[0] - 2.0 * c0 * c1 * S[1] - 2.0 * c0 * c2 * S[2] + c1 * c1 * S[3] +
-                                2.0 * c1 * c2 * S[4] + c2 * c2 * S[5]);
+        if (role & kTE) put_out_d(a, w, a.slot[1], l1, l2, sqrt(r2) * (c0 * D[0] - c1 * D[1] - c2 * D[2]));
+        const double ee = r2 * (c0 * c0 * D[0] - 2.0 * c0 * c1 * D[1] - 2.0 * c0 * c2 * D[2] + c1 * c1 * D[3] +
+                                2.0 * c1 * c2 * D[4] + c2 * c2 * D[5]);
         if (role & kEE) put_out_d(a, w, a.slot[2], l1, l2, ee);
         const double e0 = L1 + 2.0, e1 = 1.0 / (2.0 * (L2 + 2.0));
-        const double bb = (L2 + 2.0) * c1 / eta2 * (e0 * e0 * S[6] - 2.0 * e0 * e1 * S[7] + e1 * e1 * S[8]);
+        const double bb = (L2 + 2.0) * c1 / eta2 * (e0 * e0 * D[6] - 2.0 * e0 * e1 * D[7] + e1 * e1 * D[8]);
         if (role & kEEBB) put_out_d(a, w, a.slot[3], l1, l2, bb);
         if (role & kEB) put_out_d(a, w, a.slot[4], l1, l2, ee - bb);
     }

@@ -569,9 +569,17 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             }
             MxBandArgs ba;
             std::memset(&ba, 0, sizeof(ba));
-            ba.g = c->g.as<double>();
-            ba.h = c->h.as<double>();
-            ba.A = reinterpret_cast<const double *>(base + J.o_A64);
+            {
+                const int np1 = c->pmax + 1;
+                const float *gd = M.gdd.as<float>();
+                ba.gh = gd;
+                ba.gl = gd + np1;
+                ba.hh = gd + 2 * np1;
+                ba.hl = gd + 3 * np1;
+                ba.Ah = reinterpret_cast<const float *>(base + J.o_Add);
+                ba.Al = ba.Ah + (size_t)J.nsrc * J.a_stride;
+                ba.Ae = reinterpret_cast<const int *>(ba.Al + (size_t)J.nsrc * J.a_stride);
+            }
             ba.a_stride = J.a_stride;
             ba.l3cap = reinterpret_cast<const int *>(meta + J.m_cap);
             ba.src_win = srcp;
@@ -586,7 +594,7 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             ba.bin_of = ea.bin_of;
             ba.bin_inv = ea.bin_inv;
             if (J.r.lmin < MX_L1_FP64) {
-                const int idx = stat_index(c, "mixed_band_fp64");
+                const int idx = stat_index(c, "mixed_band");
                 cudaEvent_t ev = begin_launch(c, st);
                 CPL_CUDA_TRY(mx_launch_band(ba, st));
                 record_launch(c, idx, ev, st, 0.0, 0.0);
