@@ -4,6 +4,7 @@ enough to profile (a few hundred MB on the device at most).
     python -m paper_2602_15605_gb300.kernel_cases decouple   # k_decouple: 80 systems of 160 x 160, 1 rhs
     python -m paper_2602_15605_gb300.kernel_cases cov        # k_cov_combine: TT + EE terms, l_max 3000, L_cut 64
     python -m paper_2602_15605_gb300.kernel_cases plain_df   # k_plain_df: full spin set, l_max 3000, CPL_DF32
+    python -m paper_2602_15605_gb300.kernel_cases mixed      # the mixed path's kernels: full spin set, l_max 3000
 
 Each case runs its call three times (the first includes one-off set-up) and
 prints the last call's event time.
@@ -74,7 +75,20 @@ def case_plain_df(ctx):
     return ms
 
 
-CASES = {"decouple": case_decouple, "cov": case_cov, "plain_df": case_plain_df}
+def case_mixed(ctx):
+    """The full spin set at l_max = 3000 from three separate windows (the
+    bench's workload) in CPL_MIXED_BF16."""
+    import torch
+    from . import coupling, windows
+    d = [torch.as_tensor(W, device="cuda") for W in windows.full_spin_3000()]
+    out = torch.empty((1, 5, 2999, 2999), dtype=torch.float64, device="cuda")
+    ms = 0.0
+    for _ in range(3):
+        ms = _event_ms(lambda: ctx.build(3000, *d, coupling.ALL, precision=coupling.MIXED_BF16, out=out))
+    return ms
+
+
+CASES = {"decouple": case_decouple, "cov": case_cov, "plain_df": case_plain_df, "mixed": case_mixed}
 
 
 def main(argv):
