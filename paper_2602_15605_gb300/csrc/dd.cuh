@@ -49,6 +49,15 @@ __device__ __forceinline__ dfl df_from_int(int v) {
     return {h, l};
 }
 
+// exact double-float of the product of two integers |a|, |b| < 2^24 (the
+// 32-bit conversions and the fma run on the FP32 pipe; 64-bit integer
+// conversions would occupy the FP64 pipe)
+__device__ __forceinline__ dfl df_int_prod(int a, int b) {
+    const float fa = __int2float_rn(a), fb = __int2float_rn(b);
+    const float p = __fmul_rn(fa, fb);
+    return {p, fmaf(fa, fb, -p)};
+}
+
 // double-float of a 64-bit integer product (exact below 2^48)
 __device__ __forceinline__ dfl df_from_ll(long long v) {
     const float h = __ll2float_rn(v);
@@ -109,6 +118,9 @@ __device__ __forceinline__ xdf xdf_make(dfl m, int e) {
 }
 
 __device__ __forceinline__ xdf xdf_from_ll(long long v) { return xdf_make(df_from_ll(v), 0); }
+__device__ __forceinline__ xdf xdf_from_int(int v) { return xdf_make(df_from_int(v), 0); }
+// a b for |a|, |b| < 2^31 (relative error about 2^-48), on the FP32 pipe
+__device__ __forceinline__ xdf xdf_int_mul(int a, int b) { return xdf_make(df_mul(df_from_int(a), df_from_int(b)), 0); }
 
 __device__ __forceinline__ xdf xdf_mul(xdf a, xdf b) {
     if (a.h == 0.0f || b.h == 0.0f) return {0.0f, 0.0f, 0};

@@ -32,16 +32,16 @@ __device__ __forceinline__ bool mx_alpha_used(int v, int np) {
 // Pair coefficients of the spectra (exact integer inputs), in the order
 // TE[0..2], EE[0..5], EE->BB[0..2] (see plain_fp64.cu for the formulas).
 __device__ __forceinline__ void pair_coeffs(int l1, int l2, xdf (&qTE)[3], xdf (&qEE)[6], xdf (&qB)[3]) {
-    const long long L1 = l1, L2 = l2;
-    const xdf eta2 = xdf_from_ll((L1 - 1) * (L1 + 2) * (L2 - 1) * L2);
-    const xdf lam2 = xdf_from_ll(L1 * (L1 + 1) * (L2 + 1) * (L2 + 2));
+    // integer factors below 2^31 combined in double-float (no 64-bit conversions)
+    const xdf eta2 = xdf_int_mul((l1 - 1) * (l1 + 2), (l2 - 1) * l2);
+    const xdf lam2 = xdf_int_mul(l1 * (l1 + 1), (l2 + 1) * (l2 + 2));
     const xdf r2 = xdf_mul(lam2, xdf_recip(eta2));
     const xdf r = xdf_sqrt(r2);
-    const xdf c1 = xdf_recip(xdf_from_ll(L1 * (L1 + 1) * (L2 + 1)));
-    const xdf c0 = xdf_mul(xdf_from_ll(L1 + 2), xdf_recip(xdf_from_ll(L1)));
-    const xdf inv2l2p2 = xdf_recip(xdf_from_ll(2 * (L2 + 2)));
+    const xdf c1 = xdf_recip(xdf_int_mul(l1 * (l1 + 1), l2 + 1));
+    const xdf c0 = xdf_mul(xdf_from_int(l1 + 2), xdf_recip(xdf_from_int(l1)));
+    const xdf inv2l2p2 = xdf_recip(xdf_from_int(2 * (l2 + 2)));
     const xdf c2 = xdf_mul(c1, inv2l2p2);
-    const xdf two = xdf_from_ll(2);
+    const xdf two = xdf_from_int(2);
     qTE[0] = xdf_mul(r, c0);
     qTE[1] = xdf_neg(xdf_mul(r, c1));
     qTE[2] = xdf_neg(xdf_mul(r, c2));
@@ -51,9 +51,9 @@ __device__ __forceinline__ void pair_coeffs(int l1, int l2, xdf (&qTE)[3], xdf (
     qEE[3] = xdf_mul(r2, xdf_mul(c1, c1));
     qEE[4] = xdf_mul(r2, xdf_mul(two, xdf_mul(c1, c2)));
     qEE[5] = xdf_mul(r2, xdf_mul(c2, c2));
-    const xdf e0 = xdf_from_ll(L1 + 2);
+    const xdf e0 = xdf_from_int(l1 + 2);
     const xdf e1 = inv2l2p2;
-    const xdf Cc = xdf_mul(xdf_mul(xdf_from_ll(L2 + 2), c1), xdf_recip(eta2));
+    const xdf Cc = xdf_mul(xdf_mul(xdf_from_int(l2 + 2), c1), xdf_recip(eta2));
     qB[0] = xdf_mul(Cc, xdf_mul(e0, e0));
     qB[1] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
     qB[2] = xdf_mul(Cc, xdf_mul(e1, e1));
@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
             const dfl t = df_mul(a0, b0);
             S[0] = df_add(S[0], t);
             if (pol) {
-                const dfl u = df_from_ll((long long)(2 * j + 2 * k + 2 * pi + 2) * (2 * j - 2 * k + 1));
-                const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (2 * k - 2 * i));
+                const dfl u = df_int_prod(2 * j + 2 * k + 2 * pi + 2, 2 * j - 2 * k + 1);
+                const dfl v = df_int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
                 const dfl tu = df_mul(t, u);
                 S[1] = df_add(S[1], tu);
                 S[2] = df_add(S[2], df_mul(tu, v));
@@ -397,9 +397,9 @@ __global__ void __launch_bounds__(128) k_mixed_band(const MxBandArgs a) {
                 if (l3 > cap) break;
                 const int f = Ae[l3] - E0;
                 const dfl mA = {scale2(Ah[l3], f), scale2(Al[l3], f)};
-                const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (2 * k + 1 - 2 * i - 2 * pi));
-                const dfl u1 = df_from_ll((long long)(2 * j + 2 * k + 3) * (2 * j - 2 * k + 2 * pi));
-                const dfl up = df_from_ll((long long)(2 * j + 2 * k + 4) * (2 * j - 2 * k + 2 * pi + 1));
+                const dfl v1 = df_int_prod(2 * i + 2 * k + 2, 2 * k + 1 - 2 * i - 2 * pi);
+                const dfl u1 = df_int_prod(2 * j + 2 * k + 3, 2 * j - 2 * k + 2 * pi);
+                const dfl up = df_int_prod(2 * j + 2 * k + 4, 2 * j - 2 * k + 2 * pi + 1);
                 const dfl a1v = df_mul(df_mul(df_mul(mA, pair_df(a.gh, a.gl, i + k + 1)),
                                               pair_df(a.gh, a.gl, k - i - pi)), v1);
                 const dfl b1u = df_mul(df_mul(pair_df(a.gh, a.gl, j - k + pi), pair_df(a.hh, a.hl, j + k + 1)), u1);

@@ -95,7 +95,7 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
         val[0] = a0;
         vex[0] = a0.h != 0.f ? value_exp(a0, e) : EXP_ZERO;
         if (k > i && (a.alpha_mask & 6)) {
-            const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (long long)(2 * k - 2 * i));
+            const dfl v = df_int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
             const dfl a0v = df_mul(a0, v);
             const dfl a0v2 = df_mul(a0v, v);
             val[1] = a0v;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
         const dfl A = {Ah[l3o], Al[l3o]};
         const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
         const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
-        const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (long long)(2 * k + 1 - 2 * i - 2 * pi));
+        const dfl v1 = df_int_prod(2 * i + 2 * k + 2, 2 * k + 1 - 2 * i - 2 * pi);
         const dfl x = df_mul(df_mul(df_mul(A, g1), g2), v1);
         if (x.h != 0.f) {
             val[3] = x;
@@ -131,7 +131,7 @@ __device__ __forceinline__ dfl a_value(const MxPrepAArgs &a, const float *Ah, co
         const dfl g2 = {a.gh[k - i], a.gl[k - i]};
         dfl x = df_mul(df_mul(A, g1), g2);
         if (q > 0) {
-            const dfl v = df_from_ll((long long)(2 * k + 2 * i + 2 * pi + 1) * (long long)(2 * k - 2 * i));
+            const dfl v = df_int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
             x = df_mul(x, v);
             if (q > 1) x = df_mul(x, v);
         }
@@ -143,7 +143,7 @@ __device__ __forceinline__ dfl a_value(const MxPrepAArgs &a, const float *Ah, co
     const dfl A = {Ah[l3o], Al[l3o]};
     const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
     const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
-    const dfl v1 = df_from_ll((long long)(2 * i + 2 * k + 2) * (long long)(2 * k + 1 - 2 * i - 2 * pi));
+    const dfl v1 = df_int_prod(2 * i + 2 * k + 2, 2 * k + 1 - 2 * i - 2 * pi);
     const dfl x = df_mul(df_mul(df_mul(A, g1), g2), v1);
     if (x.h != 0.f) *vex = value_exp(x, Ae[l3o]);
     return x;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) k_prep_b(const MxPrepBArgs a, int c_hi) {
             // even: b0 = g(j-k) h(j+k+pi), u = (2j+2k+2pi+2)(2j-2k+1)
             if (k <= j) {
                 const dfl b0 = df_mul(dfl{a.gh[j - k], a.gl[j - k]}, dfl{a.hh[j + k + pi], a.hl[j + k + pi]});
-                const dfl u = df_from_ll((long long)(2 * j + 2 * k + 2 * pi + 2) * (long long)(2 * j - 2 * k + 1));
+                const dfl u = df_int_prod(2 * j + 2 * k + 2 * pi + 2, 2 * j - 2 * k + 1);
                 val[0][m] = b0;
                 val[1][m] = df_mul(b0, u);
                 val[2][m] = df_mul(val[1][m], u);
@@ -301,8 +301,8 @@ __global__ void __launch_bounds__(256) k_prep_b(const MxPrepBArgs a, int c_hi) {
             // odd: b1 = g(j-k+pi) h(j+k+1), u1 = (2j+2k+3)(2j-2k+2pi), u' = (2j+2k+4)(2j-2k+2pi+1)
             if (k <= j + pi - 1) {
                 const dfl b1 = df_mul(dfl{a.gh[j - k + pi], a.gl[j - k + pi]}, dfl{a.hh[j + k + 1], a.hl[j + k + 1]});
-                const dfl u1 = df_from_ll((long long)(2 * j + 2 * k + 3) * (long long)(2 * j - 2 * k + 2 * pi));
-                const dfl up = df_from_ll((long long)(2 * j + 2 * k + 4) * (long long)(2 * j - 2 * k + 2 * pi + 1));
+                const dfl u1 = df_int_prod(2 * j + 2 * k + 3, 2 * j - 2 * k + 2 * pi);
+                const dfl up = df_int_prod(2 * j + 2 * k + 4, 2 * j - 2 * k + 2 * pi + 1);
                 val[3][m] = df_mul(b1, u1);
                 val[4][m] = df_mul(val[3][m], up);
                 val[5][m] = df_mul(val[4][m], up);
