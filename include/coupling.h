@@ -54,7 +54,7 @@ typedef enum {
     CPL_ERR_OOM = 3,         /* a device or host allocation failed */
     CPL_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
     CPL_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
-    CPL_ERR_UNSUPPORTED = 6  /* the request is valid but this build/device cannot run it */
+    CPL_ERR_UNSUPPORTED = 6  /* the request is valid but this library build or device cannot run it */
 } cpl_status;
 
 /* Spectrum bits; OR them into cpl_request.spectra.  Outputs are stored in
