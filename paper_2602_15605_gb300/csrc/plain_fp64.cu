@@ -60,6 +60,11 @@ struct Shape {
     static constexpr int NG = NGE + (ODD ? 3 : 0);
 };
 
+// Exact product of two integer factors as a double: one 64-bit integer
+// multiply and one conversion (the same value as converting both factors and
+// multiplying in FP64, with two fewer FP64-pipe instructions).
+__device__ __forceinline__ double int_prod(int a, int b) { return (double)((long long)a * (long long)b); }
+
 __device__ __forceinline__ void write_out(const PlainJob &p, int win, int slot, int l1, int l2,
                                           double xi) {
     if (slot < 0) return;
@@ -125,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
                 double a0 = 0.0, v = 0.0;
                 if (k >= i && k <= khi_e) {
                     a0 = A[2 * k + pi] * g[i + k + pi] * g[k - i];
-                    v = (double)(2 * k + 2 * i + 2 * pi + 1) * (double)(2 * k - 2 * i);
+                    v = int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
                 }
                 sa[0][kk][ii] = a0;
                 if (S::NAE > 1) sa[1][kk][ii] = a0 * v;
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
             if (ODD) {
                 double a1v = 0.0;
                 if (k >= i + pi && k <= khi_o) {
-                    const double v1 = (double)(2 * i + 2 * k + 2) * (double)(2 * k + 1 - 2 * i - 2 * pi);
+                    const double v1 = int_prod(2 * i + 2 * k + 2, 2 * k + 1 - 2 * i - 2 * pi);
                     a1v = A[2 * k + 1 - pi] * g[i + k + 1] * g[k - i - pi] * v1;
                 }
                 sa[S::NAE][kk][ii] = a1v;
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
                 double b0 = 0.0, u = 0.0;
                 if (k <= j && k <= khi_e) {
                     b0 = g[j - k] * h[j + k + pi];
-                    u = (double)(2 * j + 2 * k + 2 * pi + 2) * (double)(2 * j - 2 * k + 1);
+                    u = int_prod(2 * j + 2 * k + 2 * pi + 2, 2 * j - 2 * k + 1);
                 }
                 sb[0][kk][jj] = b0;
                 if (S::NBE > 1) sb[1][kk][jj] = b0 * u;
@@ -157,8 +162,8 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
             if (ODD) {
                 double b1u = 0.0, up = 0.0;
                 if (k <= j + pi - 1 && k <= khi_o) {
-                    const double u1 = (double)(2 * j + 2 * k + 3) * (double)(2 * j - 2 * k + 2 * pi);
-                    up = (double)(2 * j + 2 * k + 4) * (double)(2 * j - 2 * k + 2 * pi + 1);
+                    const double u1 = int_prod(2 * j + 2 * k + 3, 2 * j - 2 * k + 2 * pi);
+                    up = int_prod(2 * j + 2 * k + 4, 2 * j - 2 * k + 2 * pi + 1);
                     b1u = g[j - k + pi] * h[j + k + 1] * u1;
                 }
                 sb[S::NBE][kk][jj] = b1u;
