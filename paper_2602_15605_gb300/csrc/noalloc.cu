@@ -62,6 +62,10 @@ struct NaArgs {
 // Same contraction and epilogue as k_plain (plain_fp64.cu), dense output
 // only; the (parity, i-block) pair is blockIdx.y, the j-block blockIdx.x and
 // the window blockIdx.z.  Blocks without a valid pair return at once.
+// Exact product of two integer factors as a double (one 64-bit multiply and
+// one conversion instead of two conversions and an FP64 multiply).
+__device__ __forceinline__ double int_prod(int a, int b) { return (double)((long long)a * (long long)b); }
+
 template <int NGE, bool ODD>
 __global__ void __launch_bounds__(NT) k_plain_noalloc(const NaArgs p) {
     constexpr int NAE = NGE == 0 ? 0 : NGE == 1 ? 1 : NGE == 3 ? 2 : 3;
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(NT) k_plain_noalloc(const NaArgs p) {
                 double a0 = 0.0, v = 0.0;
                 if (k >= i && k <= khi_e) {
                     a0 = A[2 * k + pi] * g[i + k + pi] * g[k - i];
-                    v = (double)(2 * k + 2 * i + 2 * pi + 1) * (double)(2 * k - 2 * i);
+                    v = int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
                 }
                 sa[0][kk][ii] = a0;
                 if (NAE > 1) sa[1][kk][ii] = a0 * v;
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(NT) k_plain_noalloc(const NaArgs p) {
             if (ODD) {
                 double a1v = 0.0;
                 if (k >= i + pi && k <= khi_o) {
-                    const double v1 = (double)(2 * i + 2 * k + 2) * (double)(2 * k + 1 - 2 * i - 2 * pi);
+                    const double v1 = int_prod(2 * i + 2 * k + 2, 2 * k + 1 - 2 * i - 2 * pi);
                     a1v = A[2 * k + 1 - pi] * g[i + k + 1] * g[k - i - pi] * v1;
                 }
                 sa[NAE][kk][ii] = a1v;
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(NT) k_plain_noalloc(const NaArgs p) {
                 double b0 = 0.0, u = 0.0;
                 if (k <= j && k <= khi_e) {
                     b0 = g[j - k] * h[j + k + pi];
-                    u = (double)(2 * j + 2 * k + 2 * pi + 2) * (double)(2 * j - 2 * k + 1);
+                    u = int_prod(2 * j + 2 * k + 2 * pi + 2, 2 * j - 2 * k + 1);
                 }
                 sb[0][kk][jj] = b0;
                 if (NBE > 1) sb[1][kk][jj] = b0 * u;
@@ -141,8 +145,8 @@ __global__ void __launch_bounds__(NT) k_plain_noalloc(const NaArgs p) {
             if (ODD) {
                 double b1u = 0.0, up = 0.0;
                 if (k <= j + pi - 1 && k <= khi_o) {
-                    const double u1 = (double)(2 * j + 2 * k + 3) * (double)(2 * j - 2 * k + 2 * pi);
-                    up = (double)(2 * j + 2 * k + 4) * (double)(2 * j - 2 * k + 2 * pi + 1);
+                    const double u1 = int_prod(2 * j + 2 * k + 3, 2 * j - 2 * k + 2 * pi);
+                    up = int_prod(2 * j + 2 * k + 4, 2 * j - 2 * k + 2 * pi + 1);
                     b1u = g[j - k + pi] * h[j + k + 1] * u1;
                 }
                 sb[NBE][kk][jj] = b1u;
