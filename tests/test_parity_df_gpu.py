@@ -126,3 +126,27 @@ def test_band_limited_8000_binned(ctx):
             e = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
         print("df 8000 binned %s vs fp64: %.3g" % (nm, e))
         assert e <= TOL, (nm, e)
+
+
+def test_lmax_limit_10000_sampled(ctx):
+    """At CPL_DF32_LMAX (where the polarisation contractions come closest to
+    FP32's exponent range): sampled pairs against the oracle, every spectrum,
+    including the last rows and near-diagonal pairs."""
+    lmax = 10000
+    W = windows.ragged_jobs(lmaxes=(lmax,), n_win=1)[0][1]
+    d = dev(W)
+    M = ctx.build(lmax, d, d, d, coupling.ALL, precision=DF)
+    rng = np.random.default_rng(10000)
+    P = [rng.integers(2, lmax + 1, size=(1200, 2)),
+         np.stack([np.full(150, lmax), rng.integers(2, lmax + 1, size=150)], axis=1),
+         np.stack([d := rng.integers(2, lmax - 2, size=150), d + rng.integers(0, 3, size=150)], axis=1)]
+    P = np.concatenate(P).astype(np.int32)
+    l1, l2 = P[:, 0], P[:, 1]
+    import torch
+    got = M[:, :, torch.as_tensor(l1 - 2, device="cuda"), torch.as_tensor(l2 - 2, device="cuda")].cpu().numpy()
+    assert np.all(np.isfinite(got))
+    ref, sab = oracle.coupling_pairs(l1, l2, W, W, W, coupling.ALL)
+    errs = per_spectrum(got, ref, sab, ALLN)
+    print("df 10000 sampled vs oracle:", errs)
+    assert max(errs.values()) <= TOL
+
