@@ -113,6 +113,11 @@ typedef struct cpl_ctx cpl_ctx;
  *                l in [bin_edges[b], bin_edges[b+1]); the binned matrix is
  *                M_bb' = (1/|b|) sum_{l1 in b} sum_{l2 in b'} M_{l1 l2}.
  *   n_bins       number of bins (0 when bin_edges is NULL).
+ *   bin_weight   0: flat band powers as above.  1: band powers of
+ *                D_l = l(l+1) C_l / 2pi, i.e. P_bl = l(l+1) / (2pi |b|) and
+ *                Q_lb = 2pi / (l(l+1)):  M_bb' = (1/|b|) sum_{l1 in b}
+ *                sum_{l2 in b'} [l1(l1+1) / (l2(l2+1))] M_{l1 l2}; needs
+ *                bin_edges[0] >= 1.  Ignored (must be 0) without bin_edges.
  */
 typedef struct {
     int lmax;
@@ -128,6 +133,7 @@ typedef struct {
     int mixed_slices;
     const int *bin_edges;
     int n_bins;
+    int bin_weight;
 } cpl_request;
 
 /* Library version string (static storage). */
@@ -290,6 +296,17 @@ cpl_status cpl_ctx_tune(cpl_ctx *ctx, int mode, const char *cache_path);
  * by the next call.  CPL_ERR_ARG for n < 0.
  */
 cpl_status cpl_ctx_inject_alloc_failure(cpl_ctx *ctx, int n);
+
+/*
+ * cpl_ctx_validate -- optional input validation (off by default).  When
+ * enabled, cpl_build, cpl_build_batch and cpl_build_host (and the builds of
+ * cpl_cov_gaussian) first check every window entry the request reads
+ * (n_windows x w_len values of each distinct W pointer) on the device and
+ * return CPL_ERR_ARG, naming the window and l, if one is NaN or Inf; nothing
+ * is written.  The check waits for its result, so validated calls are
+ * synchronous on their stream.
+ */
+cpl_status cpl_ctx_validate(cpl_ctx *ctx, int enable);
 
 /*
  * cpl_threej_m11 -- the Wigner symbols (j1 j2 j3; 0 -1 1) for every j1 of

@@ -137,10 +137,15 @@ def bin_edges(lmin, lmax, delta):
     return np.asarray(edges, dtype=np.int32)
 
 
-def bin_matrix(M, lmin, edges):
+def bin_matrix(M, lmin, edges, weight=0):
     """M_bb' = (1/|b|) sum_{l1 in b} sum_{l2 in b'} M[l1][l2] over the last two
-    axes (rows and columns indexed from lmin)."""
+    axes (rows and columns indexed from lmin).  weight=1: band powers of
+    D_l = l(l+1) C_l / 2pi, each term times l1(l1+1) / (l2(l2+1))."""
     M = np.asarray(M, dtype=np.float64)
+    if weight:
+        l = np.arange(lmin, lmin + M.shape[-1], dtype=np.float64)
+        lw = l * (l + 1.0)
+        M = M * lw[:, None] / lw[None, :]
     nb = len(edges) - 1
     out = np.zeros(M.shape[:-2] + (nb, nb), dtype=np.float64)
     for b in range(nb):

@@ -110,9 +110,13 @@ def decouple(M, pcl, spectra):
     return out
 
 
-def bin_vector(v, lmin, edges):
-    """pcl_b = (1/|b|) sum_{l in b} pcl_l over the last axis (indexed from lmin)."""
+def bin_vector(v, lmin, edges, weight=0):
+    """pcl_b = (1/|b|) sum_{l in b} pcl_l over the last axis (indexed from lmin);
+    weight=1: each term times l(l+1)/2pi (band powers of D_l)."""
     v = np.asarray(v, dtype=np.float64)
+    if weight:
+        l = np.arange(lmin, lmin + v.shape[-1], dtype=np.float64)
+        v = v * (l * (l + 1.0) / (2.0 * np.pi))
     nb = len(edges) - 1
     out = np.zeros(v.shape[:-1] + (nb,), dtype=np.float64)
     for b in range(nb):

@@ -38,7 +38,8 @@ class Request(ctypes.Structure):
                 ("W_tt", ctypes.c_void_p), ("W_tp", ctypes.c_void_p), ("W_pp", ctypes.c_void_p),
                 ("w_len", ctypes.c_int), ("band_limit", ctypes.POINTER(ctypes.c_int)),
                 ("spectra", ctypes.c_uint), ("precision", ctypes.c_int), ("mixed_slices", ctypes.c_int),
-                ("bin_edges", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int)]
+                ("bin_edges", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int),
+                ("bin_weight", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -64,7 +65,8 @@ def decouple_systems(spectra):
 # Every symbol include/coupling.h declares.
 EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy", "cpl_ctx_sync",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
-           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
+           "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_validate",
+           "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
            "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table")
 
 _lock = threading.Lock()
@@ -98,6 +100,7 @@ def load():
         L.cpl_build_batch.argtypes = [vp, ctypes.POINTER(Request), ip, ctypes.POINTER(vp), vp]
         L.cpl_g_table.argtypes = [ip, dp]
         L.cpl_ctx_profile.argtypes = [vp, ip]
+        L.cpl_ctx_validate.argtypes = [vp, ip]
         L.cpl_ctx_tune.argtypes = [vp, ip, ctypes.c_char_p]
         L.cpl_ctx_inject_alloc_failure.argtypes = [vp, ip]
         L.cpl_threej_m11.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip, vp,
@@ -141,7 +144,7 @@ class _Keep:
 
 
 def _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges, precision, slices,
-                  ptr_of, n_windows, w_len, keep):
+                  ptr_of, n_windows, w_len, keep, bin_weight=0):
     r = Request()
     r.lmax, r.lmin, r.n_windows, r.w_len = int(lmax), int(lmin), int(n_windows), int(w_len)
     r.W_tt, r.W_tp, r.W_pp = ptr_of(W_tt), ptr_of(W_tp), ptr_of(W_pp)
@@ -155,6 +158,7 @@ def _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges, 
         keep.refs.append(be)
         r.bin_edges = be.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         r.n_bins = be.size - 1
+    r.bin_weight = int(bin_weight)
     return r
 
 
@@ -181,6 +185,10 @@ class Context:
 
     def sync(self):
         _check(load().cpl_ctx_sync(self.handle))
+
+    def validate(self, enable=True):
+        """Check the windows of every build for NaN / Inf first (cpl_ctx_validate)."""
+        _check(load().cpl_ctx_validate(self.handle, 1 if enable else 0))
 
     def profile(self, enable=True):
         """Turn per-launch event timing on or off (cpl_ctx_profile)."""
@@ -300,7 +308,7 @@ class Context:
 
     # ------------------------------------------------------------------ device
     def request(self, lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None,
-                bin_edges=None, precision=FP64, slices=0):
+                bin_edges=None, precision=FP64, slices=0, bin_weight=0):
         """(Request, keepalive, shape) for torch device windows [n_win, w_len]."""
         import torch
         ws = [W for W in (W_tt, W_tp, W_pp) if W is not None]
@@ -315,7 +323,7 @@ class Context:
                 raise ValueError("all windows must have the same shape")
         keep = _Keep()
         r = _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges, precision, slices,
-                          lambda W: None if W is None else W.data_ptr(), n_windows, w_len, keep)
+                          lambda W: None if W is None else W.data_ptr(), n_windows, w_len, keep, bin_weight)
         ns = nspec(spectra)
         if bin_edges is not None:
             nb = len(bin_edges) - 1
@@ -326,11 +334,11 @@ class Context:
         return r, keep, shape
 
     def build(self, lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None,
-              bin_edges=None, precision=FP64, slices=0, out=None, stream=None):
+              bin_edges=None, precision=FP64, slices=0, out=None, stream=None, bin_weight=0):
         """cpl_build on torch's current stream; returns out [n_win, nspec, n, n] (float64, device)."""
         import torch
         r, keep, shape = self.request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges,
-                                      precision, slices)
+                                      precision, slices, bin_weight)
         if out is None:
             out = torch.empty(shape, dtype=torch.float64, device="cuda:%d" % self.device)
         elif tuple(out.shape) != shape or out.dtype != torch.float64 or not out.is_contiguous():
@@ -361,7 +369,7 @@ class Context:
 
     # ------------------------------------------------------------------ host
     def build_host(self, lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, band_limit=None,
-                   bin_edges=None, precision=FP64, slices=0, out=None):
+                   bin_edges=None, precision=FP64, slices=0, out=None, bin_weight=0):
         """cpl_build_host: numpy windows in, numpy matrix out (copies inside the call)."""
         ws = [np.asarray(W) for W in (W_tt, W_tp, W_pp) if W is not None]
         ref = ws[0]
@@ -386,7 +394,7 @@ class Context:
             return cache[id(W)]
 
         r = _make_request(lmax, W_tt, W_tp, W_pp, spectra, lmin, band_limit, bin_edges, precision, slices,
-                          ptr_shared, n_windows, w_len, keep)
+                          ptr_shared, n_windows, w_len, keep, bin_weight)
         ns = nspec(spectra)
         if bin_edges is not None:
             nb = len(bin_edges) - 1
@@ -429,14 +437,14 @@ def build_noalloc(lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, ban
 
 
 def output_size(lmax, n_windows, spectra, lmin=2, w_len=None, band_limit=None, bin_edges=None,
-                precision=FP64, slices=0):
+                precision=FP64, slices=0, bin_weight=0):
     """cpl_output_size for a request (validates it; needs no GPU)."""
     keep = _Keep()
     w_len = 2 * lmax + 1 if w_len is None else w_len
     fake = 0x1000  # any non-NULL address: output_size never dereferences the windows
     r = _make_request(lmax, fake if spectra & TT else None, fake if spectra & TE else None,
                       fake if spectra & (EE | EEBB | EB) else None, spectra, lmin, band_limit, bin_edges,
-                      precision, slices, lambda W: W, n_windows, w_len, keep)
+                      precision, slices, lambda W: W, n_windows, w_len, keep, bin_weight)
     n = ctypes.c_size_t()
     _check(load().cpl_output_size(ctypes.byref(r), ctypes.byref(n)))
     return n.value

@@ -32,6 +32,15 @@ int spec_count(unsigned s) {
     return c;
 }
 
+void bin_weights_dl(int lmax, std::vector<double> &w) {
+    w.assign(2 * (size_t)(lmax + 1), 0.0);
+    for (int l = 1; l <= lmax; ++l) {
+        const double x = (double)l * (double)(l + 1);
+        w[l] = x;
+        w[lmax + 1 + l] = 1.0 / x;
+    }
+}
+
 int spec_slot(unsigned s, unsigned bit) {
     if (!(s & bit)) return -1;
     int c = 0;
@@ -139,6 +148,9 @@ cpl_status validate(const cpl_request *r, bool device_ptrs) {
     } else if (r->n_bins != 0) {
         return fail(CPL_ERR_ARG, "n_bins must be 0 without bin_edges");
     }
+    if (r->bin_weight != 0 && r->bin_weight != 1) return fail(CPL_ERR_ARG, "bin_weight must be 0 or 1");
+    if (r->bin_weight && (!r->bin_edges || r->bin_edges[0] < 1))
+        return fail(CPL_ERR_ARG, "bin_weight = 1 needs bin_edges starting at l >= 1");
     return CPL_OK;
 }
 
@@ -266,8 +278,9 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         int nb = 0;
         std::vector<int> bin_of;
         std::vector<double> bin_inv;
+        std::vector<double> bin_lw;   // D_l weighting: l(l+1) | 1 / (l(l+1)), or empty
         std::vector<std::pair<double, WorkItem>> items;
-        size_t o_cap = 0, o_binof = 0, o_bininv = 0;
+        size_t o_cap = 0, o_binof = 0, o_bininv = 0, o_binlw = 0;
     };
     struct Sweep {
         int job;
@@ -301,6 +314,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
                 for (int l = r->bin_edges[b]; l < r->bin_edges[b + 1]; ++l) J.bin_of[l] = b;
                 J.bin_inv[b] = 1.0 / (double)(r->bin_edges[b + 1] - r->bin_edges[b]);
             }
+            if (r->bin_weight) bin_weights_dl(r->lmax, J.bin_lw);
         }
         make_items(*J.ts, J.caps, r->lmax, r->lmin, J.banded, J.items);
         // window roles sharing one pointer share one sweep
@@ -363,6 +377,8 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         o = align256(o + sizeof(int) * J.bin_of.size());
         J.o_bininv = o;
         o = align256(o + sizeof(double) * J.bin_inv.size());
+        J.o_binlw = o;
+        o = align256(o + sizeof(double) * J.bin_lw.size());
     }
     std::vector<size_t> o_items(keys.size());
     for (size_t k = 0; k < keys.size(); ++k) {
@@ -392,6 +408,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         pj.n_bins = J.nb;
         pj.bin_of = J.nb ? reinterpret_cast<const int *>(dmeta + J.o_binof) : nullptr;
         pj.bin_inv = J.nb ? reinterpret_cast<const double *>(dmeta + J.o_bininv) : nullptr;
+        pj.bin_lw = J.bin_lw.empty() ? nullptr : reinterpret_cast<const double *>(dmeta + J.o_binlw);
         std::memcpy(host.data() + o_jobs + x * sizeof(PlainJob), &pj, sizeof(pj));
     }
     for (const JobInfo &J : jobs) {
@@ -399,6 +416,8 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         if (J.nb) {
             std::memcpy(host.data() + J.o_binof, J.bin_of.data(), sizeof(int) * J.bin_of.size());
             std::memcpy(host.data() + J.o_bininv, J.bin_inv.data(), sizeof(double) * J.bin_inv.size());
+            if (!J.bin_lw.empty())
+                std::memcpy(host.data() + J.o_binlw, J.bin_lw.data(), sizeof(double) * J.bin_lw.size());
         }
     }
     for (size_t k = 0; k < keys.size(); ++k)
@@ -477,6 +496,42 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
 cpl_status build_fp64(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
     double *outs[1] = {out};
     return build_fp64_batch(c, r, outs, 1, st);
+}
+
+// Lowest index of a non-finite value among n doubles (atomicMin; ~0 if none).
+__global__ void k_first_nonfinite(const double *__restrict__ W, long long n, unsigned long long *first) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(W[q]);
+        if (((b >> 52) & 0x7ff) == 0x7ff) atomicMin(first, (unsigned long long)q);
+    }
+}
+
+// cpl_ctx_validate: the windows a request reads must be finite.  Runs before
+// any output is written and waits for its answer on `st`.
+cpl_status check_windows(cpl_ctx *c, const cpl_request *r, cudaStream_t st) {
+    if (!c->validate_w) return CPL_OK;
+    cpl_status s;
+    if ((s = c->check.ensure(sizeof(unsigned long long), "window check")) != CPL_OK) return s;
+    const double *W[3] = {r->W_tt, r->W_tp, r->W_pp};
+    const char *names[3] = {"W_tt", "W_tp", "W_pp"};
+    const long long n = (long long)r->n_windows * r->w_len;
+    for (int q = 0; q < 3; ++q) {
+        if (!W[q]) continue;
+        bool seen = false;
+        for (int p = 0; p < q; ++p) seen |= W[p] == W[q];
+        if (seen) continue;
+        unsigned long long first = ~0ull;
+        CPL_CUDA_TRY(cudaMemcpyAsync(c->check.ptr, &first, sizeof(first), cudaMemcpyHostToDevice, st));
+        const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+        k_first_nonfinite<<<blocks, 256, 0, st>>>(W[q], n, c->check.as<unsigned long long>());
+        CPL_CUDA_TRY(cudaGetLastError());
+        CPL_CUDA_TRY(cudaMemcpyAsync(&first, c->check.ptr, sizeof(first), cudaMemcpyDeviceToHost, st));
+        CPL_CUDA_TRY(cudaStreamSynchronize(st));
+        if (first != ~0ull)
+            return fail(CPL_ERR_ARG, std::string(names[q]) + " of window " + std::to_string(first / r->w_len) +
+                                         " is NaN or Inf at l = " + std::to_string(first % r->w_len));
+    }
+    return CPL_OK;
 }
 
 cpl_status build_one(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t st) {
@@ -582,6 +637,7 @@ cpl_status cpl_build(cpl_ctx *c, const cpl_request *r, double *out, void *stream
     cpl_status s = validate(r, true);
     if (s != CPL_OK) return s;
     if ((s = select_device(c)) != CPL_OK) return s;
+    if ((s = check_windows(c, r, (cudaStream_t)stream)) != CPL_OK) return s;
     return build_one(c, r, out, (cudaStream_t)stream);
 }
 
@@ -614,6 +670,7 @@ cpl_status cpl_build_host(cpl_ctx *c, const cpl_request *r, double *out_host) {
     rd.W_tt = dsts[0];
     rd.W_tp = dsts[1];
     rd.W_pp = dsts[2];
+    if ((s = check_windows(c, &rd, st)) != CPL_OK) return s;
     if ((s = build_one(c, &rd, c->stage_out.as<double>(), st)) != CPL_OK) return s;
     CPL_CUDA_TRY(cudaMemcpyAsync(out_host, c->stage_out.ptr, ob, cudaMemcpyDeviceToHost, st));
     cudaError_t e = cudaStreamSynchronize(st);
@@ -632,6 +689,8 @@ cpl_status cpl_build_batch(cpl_ctx *c, const cpl_request *jobs, int n_jobs, doub
         if (jobs[q].precision != jobs[0].precision) return fail(CPL_ERR_ARG, "all jobs must use one precision");
     }
     if ((s = select_device(c)) != CPL_OK) return s;
+    for (int q = 0; q < n_jobs; ++q)
+        if ((s = check_windows(c, jobs + q, (cudaStream_t)stream)) != CPL_OK) return s;
     if (jobs[0].precision == CPL_MIXED_BF16)
         return cpl::build_mixed_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream, true);
     return build_fp64_batch(c, jobs, outs, n_jobs, (cudaStream_t)stream);
@@ -691,6 +750,12 @@ cpl_status cpl_ctx_tune(cpl_ctx *c, int mode, const char *cache_path) {
     if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
     if (mode != CPL_TUNE_OFF && mode != CPL_TUNE_MEASURE) return fail(CPL_ERR_ARG, "unknown tuning mode");
     return cpl::set_tuning(c, mode, cache_path);
+}
+
+cpl_status cpl_ctx_validate(cpl_ctx *c, int enable) {
+    if (!c) return fail(CPL_ERR_ARG, "ctx is NULL");
+    c->validate_w = enable != 0;
+    return CPL_OK;
 }
 
 cpl_status cpl_ctx_profile(cpl_ctx *c, int enable) {

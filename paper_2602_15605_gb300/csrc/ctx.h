@@ -127,6 +127,8 @@ struct cpl_ctx {
     };
     int alloc_fault = 0;         // cpl_ctx_inject_alloc_failure countdown (0 = off)
     bool profiling = false;
+    bool validate_w = false;     // cpl_ctx_validate: check windows for NaN / Inf before building
+    DevBuf check;                // its device result word
     std::vector<KStat> kstats;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> ev_pool;

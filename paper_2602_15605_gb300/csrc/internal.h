@@ -27,6 +27,8 @@ cpl_status fail(cpl_status s, const std::string &msg);
 constexpr unsigned kTT = 1u, kTE = 2u, kEE = 4u, kEEBB = 8u, kEB = 16u;
 int spec_slot(unsigned spectra, unsigned bit);   // index of bit in the requested set, -1 if absent
 int spec_count(unsigned spectra);
+// D_l band-power weights: w[l] = l(l+1), w[lmax + 1 + l] = 1 / (l(l+1)) (0 at l = 0).
+void bin_weights_dl(int lmax, std::vector<double> &w);
 
 // ---------------------------------------------------------------- tables
 // g(p) of Eq. gdef and h(p) = 1 / ((2p + 1) g(p)) (the 1/g and 1/(J+1) tables of
@@ -80,6 +82,7 @@ struct PlainJob {
     int n_bins;
     const int *bin_of;      // [lmax + 1] bin index or -1
     const double *bin_inv;  // [n_bins] 1 / |b|
+    const double *bin_lw;   // [2][lmax + 1] l(l+1) and its inverse (D_l band powers), NULL: flat
 };
 
 struct PlainArgs {

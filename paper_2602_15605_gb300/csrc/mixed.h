@@ -146,6 +146,7 @@ struct MxEpiArgs {
     int n_bins;
     const int *bin_of;
     const double *bin_inv;
+    const double *bin_lw;          // [2][lmax + 1] l(l+1) and its inverse (D_l band powers), NULL: flat
     MxLayout L;
 };
 
@@ -164,6 +165,7 @@ struct MxBandArgs {   // double-float evaluation of the pairs with l1 < MX_L1_FP
     int n_bins;
     const int *bin_of;
     const double *bin_inv;
+    const double *bin_lw;          // [2][lmax + 1] l(l+1) and its inverse (D_l band powers), NULL: flat
 };
 
 cudaError_t mx_launch_tables_dd(const double *g, const double *h, int n, float *gh, float *gl, float *hh,

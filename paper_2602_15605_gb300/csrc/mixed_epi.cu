@@ -80,8 +80,13 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const long long ncols = (long long)L.NC_B * MX_BJ;
     const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
-    const double f12 = (2.0 * l2 + 1.0) * a.bin_inv[b1];
-    const double f21 = (2.0 * l1 + 1.0) * a.bin_inv[b2];
+    double f12 = (2.0 * l2 + 1.0) * a.bin_inv[b1];
+    double f21 = (2.0 * l1 + 1.0) * a.bin_inv[b2];
+    if (a.bin_lw) {   // D_l band powers: l1(l1+1) / (l2(l2+1)) and its mirror
+        const double *iw = a.bin_lw + a.lmax + 1;
+        f12 *= a.bin_lw[l1] * iw[l2];
+        f21 *= a.bin_lw[l2] * iw[l1];
+    }
     for (int s = 0; s < a.nsrc; ++s) {
         const int role = a.src_role[s];
         if (role == 0 || l2 - l1 > a.l3cap[s]) continue;
@@ -332,8 +337,14 @@ __device__ __forceinline__ void put_out_d(const MxBandArgs &a, int w, int slot, 
         const int b1 = a.bin_of[l1], b2 = a.bin_of[l2];
         if (b1 < 0 || b2 < 0) return;
         double *base = a.out + ((size_t)w * a.nspec + slot) * (size_t)a.n_bins * (size_t)a.n_bins;
-        if (m12 != 0.0) atomicAdd(base + (size_t)b1 * a.n_bins + b2, m12 * a.bin_inv[b1]);
-        if (l1 != l2 && m21 != 0.0) atomicAdd(base + (size_t)b2 * a.n_bins + b1, m21 * a.bin_inv[b2]);
+        double w12 = a.bin_inv[b1], w21 = a.bin_inv[b2];
+        if (a.bin_lw) {
+            const double *iw = a.bin_lw + a.lmax + 1;
+            w12 *= a.bin_lw[l1] * iw[l2];
+            w21 *= a.bin_lw[l2] * iw[l1];
+        }
+        if (m12 != 0.0) atomicAdd(base + (size_t)b1 * a.n_bins + b2, m12 * w12);
+        if (l1 != l2 && m21 != 0.0) atomicAdd(base + (size_t)b2 * a.n_bins + b1, m21 * w21);
     }
 }
 

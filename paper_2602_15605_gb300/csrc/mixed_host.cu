@@ -105,12 +105,13 @@ struct MxJobPlan {
     int nb = 0;
     std::vector<int> bin_of;
     std::vector<double> bin_inv;
+    std::vector<double> bin_lw;        // D_l weighting: l(l+1) | 1 / (l(l+1)), or empty
     double gemm_flop = -1.0, gemm_issued = 0.0;   // profiling (flop computed on first use)
     // scratch: offsets relative to the job's base in the arena
     size_t o_A64 = 0, o_Add = 0, o_Aimg = 0, o_eA = 0, o_emaxA = 0, o_inter = 0, scratch_bytes = 0;
     size_t base = 0;                   // the job's base in the arena
     // metadata: offsets into the plan's meta buffer
-    size_t m_cap = 0, m_src = 0, m_tile_of = 0, m_bin_of = 0, m_bin_inv = 0;
+    size_t m_cap = 0, m_src = 0, m_tile_of = 0, m_bin_of = 0, m_bin_inv = 0, m_bin_lw = 0;
 };
 
 struct MxChunk {
@@ -284,6 +285,7 @@ void plan_job(const cpl_request *r, double *out, int S, MxParams prm, MxJobPlan 
             for (int l = r->bin_edges[bq]; l < r->bin_edges[bq + 1]; ++l) J.bin_of[l] = bq;
             J.bin_inv[bq] = 1.0 / (double)(r->bin_edges[bq + 1] - r->bin_edges[bq]);
         }
+        if (r->bin_weight) bin_weights_dl(lmax, J.bin_lw);
     }
     J.r.band_limit = nullptr;          // host arrays are consumed here
     J.r.bin_edges = nullptr;
@@ -347,6 +349,7 @@ void push_sig(std::vector<long long> &sig, const cpl_request *r, const double *o
     const int nb = r->bin_edges ? r->n_bins : 0;
     sig.push_back(nb);
     for (int q = 0; nb && q <= nb; ++q) sig.push_back(r->bin_edges[q]);
+    sig.push_back(r->bin_weight);
 }
 
 // Scratch budget for one chunk: CPL_MIXED_SCRATCH_GB if set, else 70% of
@@ -412,6 +415,7 @@ cpl_status materialize(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
         J.m_tile_of = put(J.tile_of.data(), sizeof(int32_t) * J.tile_of.size());
         J.m_bin_of = put(J.bin_of.data(), sizeof(int) * J.bin_of.size());
         J.m_bin_inv = put(J.bin_inv.data(), sizeof(double) * J.bin_inv.size());
+        J.m_bin_lw = put(J.bin_lw.data(), sizeof(double) * J.bin_lw.size());
     }
     uint8_t *arena = M.arena.as<uint8_t>();
     for (MxChunk &C : P.chunks) {
@@ -560,6 +564,7 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             ea.n_bins = J.nb;
             ea.bin_of = J.nb ? reinterpret_cast<const int *>(meta + J.m_bin_of) : nullptr;
             ea.bin_inv = J.nb ? reinterpret_cast<const double *>(meta + J.m_bin_inv) : nullptr;
+            ea.bin_lw = J.bin_lw.empty() ? nullptr : reinterpret_cast<const double *>(meta + J.m_bin_lw);
             ea.L = J.L;
             {
                 const int idx = stat_index(c, "mixed_epilogue");
@@ -593,6 +598,7 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             ba.n_bins = J.nb;
             ba.bin_of = ea.bin_of;
             ba.bin_inv = ea.bin_inv;
+            ba.bin_lw = ea.bin_lw;
             if (J.r.lmin < MX_L1_FP64) {
                 const int idx = stat_index(c, "mixed_band");
                 cudaEvent_t ev = begin_launch(c, st);

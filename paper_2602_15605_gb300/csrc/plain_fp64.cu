@@ -80,8 +80,14 @@ __device__ __forceinline__ void write_out(const PlainJob &p, int win, int slot, 
         if (b1 < 0 || b2 < 0) return;
         const int nb = p.n_bins;
         double *base = p.out + ((size_t)win * p.nspec + slot) * (size_t)nb * (size_t)nb;
-        atomicAdd(base + (size_t)b1 * nb + b2, m12 * p.bin_inv[b1]);
-        if (l1 != l2) atomicAdd(base + (size_t)b2 * nb + b1, m21 * p.bin_inv[b2]);
+        double w12 = p.bin_inv[b1], w21 = p.bin_inv[b2];
+        if (p.bin_lw) {   // D_l band powers: l1(l1+1) / (l2(l2+1)) and its mirror
+            const double *iw = p.bin_lw + p.lmax + 1;
+            w12 *= p.bin_lw[l1] * iw[l2];
+            w21 *= p.bin_lw[l2] * iw[l1];
+        }
+        atomicAdd(base + (size_t)b1 * nb + b2, m12 * w12);
+        if (l1 != l2) atomicAdd(base + (size_t)b2 * nb + b1, m21 * w21);
     }
 }
 

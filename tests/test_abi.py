@@ -87,6 +87,10 @@ def test_output_size_and_validation(lib):
     for sl in (3, 7, -1):
         assert _status(lambda: coupling.output_size(10, 1, coupling.TT, precision=coupling.MIXED_BF16, slices=sl)) == 1
     assert _status(lambda: coupling.output_size(10, 1, coupling.TT, precision=3)) == 1
+    assert coupling.output_size(20, 1, coupling.TT, bin_edges=[2, 7, 21], bin_weight=1) == 4
+    assert _status(lambda: coupling.output_size(20, 1, coupling.TT, bin_weight=1)) == 1
+    assert _status(lambda: coupling.output_size(20, 1, coupling.TT, lmin=0, bin_edges=[0, 7, 21], bin_weight=1)) == 1
+    assert _status(lambda: coupling.output_size(20, 1, coupling.TT, bin_edges=[2, 7, 21], bin_weight=2)) == 1
     assert coupling.output_size(10, 1, coupling.TT, precision=coupling.DF32) == 81
     assert _status(lambda: coupling.output_size(10001, 1, coupling.TT, precision=coupling.DF32)) == 2
 

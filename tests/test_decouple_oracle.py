@@ -115,3 +115,26 @@ def test_sum_difference_split_equals_block_solve():
     t = np.linalg.solve(A - B, (pcl[0, :, 0] - pcl[0, :, 1]).T).T
     assert np.max(np.abs(0.5 * (s + t) - ref[0, :, 0]) / np.abs(ref[0, :, 0])) < 1e-11
     assert np.max(np.abs(0.5 * (s - t) - ref[0, :, 1]) / np.abs(ref[0, :, 1])) < 1e-11
+
+
+def test_dl_binning_single_l_bins_and_piecewise_constant_recovery():
+    # weight=1 with one multipole per bin is M l1(l1+1) / (l2(l2+1)); with
+    # wider bins, spectra whose D_l = l(l+1) C_l / 2pi is constant in each bin
+    # are recovered exactly as D_b from the D_l-weighted binned system
+    lmax, delta = 62, 6
+    W = windows.mask_like(lmax, seed=78)
+    M = _dense(lmax, W, ALL)
+    l = np.arange(2, lmax + 1, dtype=np.float64)
+    one = oracle.bin_matrix(M, 2, oracle.bin_edges(2, lmax, 1), weight=1)
+    assert np.max(np.abs(one - M * (l * (l + 1))[:, None] / (l * (l + 1))[None, :])) < 1e-15 * np.max(np.abs(M))
+    edges = oracle.bin_edges(2, lmax, delta)
+    rng = np.random.default_rng(19)
+    Db = rng.uniform(0.2, 1.0, size=(1, 1, 5, len(edges) - 1))
+    C = np.repeat(Db, np.diff(edges), axis=-1) * (2 * np.pi / (l * (l + 1)))
+    pcb = dc.bin_vector(dc.forward(M, C, ALL), 2, edges, weight=1)
+    got = dc.decouple(oracle.bin_matrix(M, 2, edges, weight=1), pcb, ALL)
+    assert np.max(np.abs(got - Db) / Db) < 1e-11
+    # the flat binning does not recover D_b from the same input
+    bad = dc.decouple(oracle.bin_matrix(M, 2, edges), dc.bin_vector(dc.forward(M, C, ALL), 2, edges), ALL)
+    assert np.max(np.abs(bad - Db) / Db) > 1e-3
+
