@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -185,6 +186,14 @@ cpl_status ensure_tables(cpl_ctx *c, int lmax) {
     return CPL_OK;
 }
 
+cpl_status ensure_err_word(cpl_ctx *c, cudaStream_t st) {
+    if (c->mx.err.ptr) return CPL_OK;
+    cpl_status s;
+    if ((s = c->mx.err.ensure(sizeof(int), "device error word")) != CPL_OK) return s;
+    CPL_CUDA_TRY(cudaMemsetAsync(c->mx.err.ptr, 0, sizeof(int), st));
+    return CPL_OK;
+}
+
 cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out) {
     const long long key = (long long)lmax * 65536LL + lmin;
     for (auto &kv : c->tile_index)
@@ -209,33 +218,20 @@ cpl_status get_tiles(cpl_ctx *c, int lmax, int lmin, TileSet **out) {
 
 namespace {
 
-// Work items (window, tile) of one request with their costs (l3 terms).  A
-// tile whose smallest |d| exceeds a window's last l3 contributes nothing for
-// that window and is dropped (the output is pre-zeroed in that case).
-void make_items(TileSet &ts, const std::vector<int> &caps, int lmax, int lmin, bool banded,
+// Work items (window, tile) of one request with their run-time costs
+// (tile_time; a band-limited window shortens a tile's k range).  A tile whose
+// smallest |d| exceeds a window's last l3 contributes nothing for that window
+// and is dropped (the output is pre-zeroed in that case).
+void make_items(const TileSet &ts, const std::vector<int> &caps, bool banded,
                 std::vector<std::pair<double, WorkItem>> &items) {
     const std::vector<Tile> &tiles = ts.host;
     items.clear();
     const int nw = (int)caps.size();
-    std::vector<const std::vector<double> *> cost_of(nw, nullptr);
-    if (banded) {
-        // term counts per (tile, cap), computed once per tile set and cap
-        if (ts.band_terms.size() > 64) ts.band_terms.clear();   // bound the cache
-        for (int w = 0; w < nw; ++w) {
-            std::vector<double> &v = ts.band_terms[caps[w]];
-            if (v.size() != tiles.size()) {
-                v.resize(tiles.size());
-                for (size_t ti = 0; ti < tiles.size(); ++ti)
-                    v[ti] = 2 * tiles[ti].i0 + tiles[ti].pi > caps[w] ? 0.0 : tile_terms(tiles[ti], lmax, lmin, caps[w]);
-            }
-            cost_of[w] = &v;
-        }
-    }
     for (int ti = 0; ti < (int)tiles.size(); ++ti) {
         const Tile &t = tiles[ti];
         for (int w = 0; w < nw; ++w) {
             if (banded && 2 * t.i0 + t.pi > caps[w]) continue;
-            const double cost = banded ? (*cost_of[w])[ti] : (double)t.cost;
+            const double cost = banded ? tile_time(t, caps[w]) : (double)t.cost;
             items.emplace_back(cost, WorkItem{0, w, ti, 0});
         }
     }
@@ -289,6 +285,11 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         int nge;
         bool odd;
         size_t a_off;   // doubles into the weights buffer
+        // tabled kernel: A-block offsets [n_win][2][nib] + 1 and the sweep's place in the A table
+        int nib = 0, nae = 0, max_count = 0;
+        std::vector<long long> aoff;
+        size_t atab_off = 0;   // doubles into the A table
+        size_t o_aoff = 0;     // bytes into the metadata buffer
     };
     std::vector<JobInfo> jobs(n);
     std::vector<Sweep> sweeps;
@@ -316,7 +317,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
             }
             if (r->bin_weight) bin_weights_dl(r->lmax, J.bin_lw);
         }
-        make_items(*J.ts, J.caps, r->lmax, r->lmin, J.banded, J.items);
+        make_items(*J.ts, J.caps, J.banded, J.items);
         // window roles sharing one pointer share one sweep
         std::vector<Group> groups;
         auto add = [&](const double *W, unsigned b) {
@@ -342,6 +343,53 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
             sw.a_off = a_total;
             a_total += (size_t)a_stride * nw;
             sweeps.push_back(sw);
+        }
+    }
+
+    // ---- operand tables of the tabled FP64 kernel (sizes; built after the weights)
+    bool tab = !df;
+    if (const char *e = std::getenv("CPL_PLAIN_TABLES")) tab = tab && std::strcmp(e, "0") != 0;
+    int njb_need = 0;
+    size_t atab_total = 0;   // doubles
+    if (tab) {
+        for (Sweep &sw : sweeps) {
+            const cpl_request *r = reqs + sw.job;
+            const JobInfo &J = jobs[sw.job];
+            const int nw = r->n_windows;
+            sw.nae = sw.nge == 0 ? 0 : sw.nge == 1 ? 1 : sw.nge == 3 ? 2 : 3;
+            const int na = sw.nae + (sw.odd ? 1 : 0);
+            sw.nib = (r->lmax - r->lmin) / 2 / TILE_I + 1;
+            sw.aoff.assign((size_t)nw * 2 * sw.nib + 1, 0);
+            long long blocks = 0;
+            for (int w = 0; w < nw; ++w)
+                for (int pi = 0; pi < 2; ++pi) {
+                    const int imax = (r->lmax - r->lmin - pi) / 2;   // rows of this parity's tiles
+                    for (int ib = 0; ib < sw.nib; ++ib) {
+                        // chunks 2 ib .. of the row block: k <= j0 + 31 <= lmax - pi - i0 + 31 and k <= cap / 2
+                        int count = 0;
+                        if (r->lmax - r->lmin - pi >= 0 && TILE_I * ib <= imax) {
+                            const int cend = std::min((r->lmax - pi - TILE_I * ib + TILE_J - 1) / PT_KC,
+                                                      (J.caps[w] / 2) / PT_KC) + 1;
+                            count = std::max(0, cend - 2 * ib);
+                        }
+                        sw.aoff[((size_t)w * 2 + pi) * sw.nib + ib] = blocks;
+                        blocks += count;
+                        sw.max_count = std::max(sw.max_count, count);
+                    }
+                }
+            sw.aoff.back() = blocks;
+            sw.atab_off = atab_total;
+            atab_total += (size_t)blocks * na * PT_BLK;
+            njb_need = std::max(njb_need, r->lmax / TILE_J + 1);
+        }
+        // budget: the tables may take at most half of the free device memory
+        size_t need = 0;
+        if (njb_need > c->ptab_njb) need += sizeof(double) * (size_t)btab_block(njb_need, 0, 0) * PT_BROWS * PT_BLK;
+        if (sizeof(double) * atab_total > c->ptab_a.cap) need += sizeof(double) * atab_total;
+        size_t free_b = 0, total_b = 0;
+        if (need > 0 && (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || need > free_b / 2)) {
+            cudaGetLastError();
+            tab = false;
         }
     }
 
@@ -385,8 +433,24 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         o_items[k] = o;
         o = align256(o + sizeof(WorkItem) * vitems[k].size());
     }
+    if (tab)
+        for (Sweep &sw : sweeps) {
+            sw.o_aoff = o;
+            o = align256(o + sizeof(long long) * sw.aoff.size());
+        }
     if ((s = c->items.ensure(std::max<size_t>(o, 256), "work items")) != CPL_OK) return s;
     if ((s = c->weights.ensure(sizeof(double) * std::max<size_t>(a_total, 1), "weights")) != CPL_OK) return s;
+    if (tab) {
+        if (njb_need > c->ptab_njb) {
+            c->ptab_njb = 0;   // invalid until rebuilt
+            if ((s = c->ptab_b.ensure(sizeof(double) * (size_t)btab_block(njb_need, 0, 0) * PT_BROWS * PT_BLK,
+                                      "operand B table")) != CPL_OK)
+                return s;
+        }
+        if ((s = c->ptab_a.ensure(sizeof(double) * std::max<size_t>(atab_total, 1), "operand A table")) != CPL_OK)
+            return s;
+        if ((s = ensure_err_word(c, st)) != CPL_OK) return s;
+    }
     uint8_t *dmeta = c->items.as<uint8_t>();
     double *dA = c->weights.as<double>();
     std::vector<uint8_t> host(o, 0);
@@ -409,6 +473,11 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         pj.bin_of = J.nb ? reinterpret_cast<const int *>(dmeta + J.o_binof) : nullptr;
         pj.bin_inv = J.nb ? reinterpret_cast<const double *>(dmeta + J.o_bininv) : nullptr;
         pj.bin_lw = J.bin_lw.empty() ? nullptr : reinterpret_cast<const double *>(dmeta + J.o_binlw);
+        if (tab) {
+            pj.atab = c->ptab_a.as<double>() + sw.atab_off;
+            pj.aoff = reinterpret_cast<const long long *>(dmeta + sw.o_aoff);
+            pj.nib = sw.nib;
+        }
         std::memcpy(host.data() + o_jobs + x * sizeof(PlainJob), &pj, sizeof(pj));
     }
     for (const JobInfo &J : jobs) {
@@ -423,6 +492,9 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
     for (size_t k = 0; k < keys.size(); ++k)
         if (!vitems[k].empty())
             std::memcpy(host.data() + o_items[k], vitems[k].data(), sizeof(WorkItem) * vitems[k].size());
+    if (tab)
+        for (const Sweep &sw : sweeps)
+            std::memcpy(host.data() + sw.o_aoff, sw.aoff.data(), sizeof(long long) * sw.aoff.size());
 
     CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
     CPL_CUDA_TRY(cudaMemcpyAsync(dmeta, host.data(), o, cudaMemcpyHostToDevice, st));
@@ -436,6 +508,23 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
                                     reinterpret_cast<const int *>(dmeta + jobs[sw.job].o_cap), dA + sw.a_off, a_stride,
                                     st));
         ls.done(0.0, 16.0 * (double)a_stride * r->n_windows);
+    }
+    if (tab) {
+        if (njb_need > c->ptab_njb) {
+            LaunchScope ls(c, "plain_tables_b", st);
+            CPL_CUDA_TRY(launch_btab(c->g.as<double>(), c->h.as<double>(), njb_need, c->ptab_b.as<double>(), st));
+            ls.done(0.0, 8.0 * (double)btab_block(njb_need, 0, 0) * PT_BROWS * PT_BLK);
+            c->ptab_njb = njb_need;
+        }
+        for (const Sweep &sw : sweeps) {
+            const cpl_request *r = reqs + sw.job;
+            LaunchScope ls(c, "plain_tables_a", st);
+            CPL_CUDA_TRY(launch_atab(dA + sw.a_off, 2 * r->lmax + 2, reinterpret_cast<const int *>(dmeta + jobs[sw.job].o_cap),
+                                     c->g.as<double>(), reinterpret_cast<const long long *>(dmeta + sw.o_aoff),
+                                     r->n_windows, sw.nib, sw.max_count, sw.nae, sw.odd ? 1 : 0,
+                                     c->ptab_a.as<double>() + sw.atab_off, st));
+            ls.done(0.0, 8.0 * (double)sw.aoff.back() * (sw.nae + (sw.odd ? 1 : 0)) * PT_BLK);
+        }
     }
     for (size_t k = 0; k < keys.size(); ++k) {
         PlainArgs a;
@@ -455,6 +544,11 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         if (df) {
             a.gdf = c->df_tab.as<float2>();
             a.hdf = a.gdf + (c->pmax + 1);
+        }
+        if (tab) {
+            a.btab = c->ptab_b.as<double>();
+            a.btab_njb = c->ptab_njb;
+            a.err = c->mx.err.as<int>();
         }
         double flop = 0.0, bytes = 0.0;
         if (c->profiling) {
@@ -585,6 +679,8 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     for (auto &t : c->tile_sets) t->dev.release();
     c->weights.release();
     c->items.release();
+    c->ptab_a.release();
+    c->ptab_b.release();
     c->stage_w.release();
     c->stage_out.release();
     c->threej_idx.release();
@@ -616,8 +712,12 @@ cpl_status cpl_ctx_sync(cpl_ctx *c) {
         if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
         if (code != 0) {
             cudaMemset(c->mx.err.ptr, 0, sizeof(int));
-            return fail(CPL_ERR_TIMEOUT, "a bounded device wait of the tensor-core kernel ran out (code " +
-                                             std::to_string(code) + ")");
+            const bool plain = code == PT_ERR_RANGE || code == PT_ERR_WAIT;
+            return fail(CPL_ERR_TIMEOUT, std::string(plain ? code == PT_ERR_RANGE
+                                                                 ? "the tabled FP64 kernel found a tile outside its operand tables"
+                                                                 : "a bounded wait of the tabled FP64 kernel ran out"
+                                                           : "a bounded device wait of the tensor-core kernel ran out") +
+                                             " (code " + std::to_string(code) + ")");
         }
     }
     return CPL_OK;

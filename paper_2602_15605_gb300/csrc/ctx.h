@@ -52,9 +52,6 @@ struct TileSet {
     // per-tile l3 term counts (even, odd, pairs) for windows without a band
     // limit (cap >= 2 lmax), filled on first use by the launch accounting
     std::vector<double> terms;
-    // per-tile l3 term counts under a band limit (cap -> one count per tile),
-    // the scheduling costs of band-limited requests
-    std::map<int, std::vector<double>> band_terms;
 };
 
 
@@ -110,6 +107,9 @@ struct cpl_ctx {
     int sq_pmax = -1, sq_nn = 0;
     DevBuf df_tab;               // CPL_DF32: g | h as FP32 pairs (pmax + 1 each)
     int df_pmax = -1;
+    DevBuf ptab_b;               // tabled FP64 kernel: B operand blocks (window independent)
+    int ptab_njb = 0;            // column blocks ptab_b covers (0: none)
+    DevBuf ptab_a;               // tabled FP64 kernel: A operand blocks of the last build
     DevBuf dec_ws;               // cpl_decouple: augmented systems too large for shared memory
     DevBuf cov_M, cov_dense, cov_edges;   // cpl_cov_gaussian: kernels of one build, dense covariance, bin edges
     cudaStream_t own_stream = nullptr;
@@ -149,6 +149,9 @@ cudaEvent_t take_event(cpl_ctx *c);
 // Makes the context's device current and points the allocation-failure hook
 // at the context (every public entry point calls it before device work).
 cpl_status select_device(cpl_ctx *c);
+// The device error word of the bounded waits (mx.err), allocated and zeroed
+// on first use.
+cpl_status ensure_err_word(cpl_ctx *c, cudaStream_t st);
 
 // Brackets one kernel launch: counts it and, when profiling, times it with
 // events on the launching stream.

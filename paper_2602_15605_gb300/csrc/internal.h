@@ -42,7 +42,7 @@ struct Tile {
     int16_t pi;      // parity class of d (and s)
     int16_t pad;
     int32_t i0, j0;  // first row / column of the block
-    int32_t cost;    // l3 terms (both sweeps) summed over the block's valid pairs, /1024
+    int32_t cost;    // run-time model of the block (tile_time with the full l3 range)
 };
 static_assert(sizeof(Tile) == 16, "Tile must be 16 bytes");
 
@@ -60,7 +60,9 @@ constexpr int TILE_J = 32;
 // All tiles of the valid region lmin <= l1 <= l2 <= lmax, ordered by cost
 // (largest first).
 void make_tiles(int lmax, int lmin, std::vector<Tile> &tiles);
-double tile_terms(const Tile &t, int lmax, int lmin, int band);  // exact l3 term count (both parities) of a tile
+// Run time of a tile in the plain kernels when l3 <= cap, in k steps of the
+// block (its k range, the staging chunks and the epilogue).
+double tile_time(const Tile &t, int cap);
 
 // ---------------------------------------------------------------- plain FP64 kernels
 // Kernel families by which GEMM products they run (see plain_fp64.cu).
@@ -83,6 +85,10 @@ struct PlainJob {
     const int *bin_of;      // [lmax + 1] bin index or -1
     const double *bin_inv;  // [n_bins] 1 / |b|
     const double *bin_lw;   // [2][lmax + 1] l(l+1) and its inverse (D_l band powers), NULL: flat
+    // operand blocks of the tabled kernel (NULL: the kernel stages its own)
+    const double *atab;     // this sweep's A blocks, NA x PT_BLK doubles each
+    const long long *aoff;  // [n_win][2][nib] + 1: first A block of (window, parity, row block); counts by difference
+    int nib;                // row blocks per parity
 };
 
 struct PlainArgs {
@@ -95,6 +101,9 @@ struct PlainArgs {
     int odd;                // whether the odd sweep runs
     const float2 *gdf;      // [pmax + 1] g and h as FP32 pairs (double-float kernels only)
     const float2 *hdf;
+    const double *btab;     // B blocks (btab_block order), NULL: the kernel stages its own operands
+    int btab_njb;           // column blocks the B table covers
+    int *err;               // device error word of the tabled kernel's bounded waits
 };
 
 cudaError_t launch_plain(const PlainArgs &a, cudaStream_t st);   // variant from a.nge / a.odd
@@ -107,6 +116,12 @@ void plain_variant(int mode, const int slot[5], int *nge, bool *odd);
 void tile_terms_split(const Tile &t, int lmax, int lmin, int cap, double *even, double *odd, double *pairs);
 cudaError_t launch_weights(const double *W, int w_len, int n_win, const int *l3cap,
                            double *A, int a_stride, cudaStream_t st);
+// Operand blocks of the tabled plain FP64 kernel: the window-independent B
+// blocks of column blocks [0, njb), and one sweep's A blocks (nae even rows,
+// odd: the odd row) for n_win windows from their weights A.
+cudaError_t launch_btab(const double *g, const double *h, int njb, double *B, cudaStream_t st);
+cudaError_t launch_atab(const double *A, int a_stride, const int *l3cap, const double *g, const long long *aoff,
+                        int n_win, int nib, int max_count, int nae, int odd, double *At, cudaStream_t st);
 // (j1 j2 j3; 0 -1 1) rows for device arrays j2, j3 from sqrt g, sqrt h, sqrt n
 // held as double-float (threej.cu)
 cudaError_t launch_sqrt_tables(const double *g, const double *h, int np1, int nn, float2 *sg, float2 *sh, float2 *sn,
@@ -143,6 +158,20 @@ struct DecoupleArgs {
 // (identity in the padding) with row stride ir_ldf(n) floats; they come
 // first when they are in shared memory.
 CPL_HD inline int ir_np(int n) { return (n + 31) & ~31; }
+
+// Operand blocks of the tabled plain FP64 kernel: PT_BLK = 16 k x 32 (i or
+// j) doubles per operand row.  B blocks hold the six j-side rows of column
+// block jb, parity pi and k chunk c <= 2 jb + 1, ordered by (jb, pi, c), so
+// the table for a smaller l_max is a prefix of a larger one.
+constexpr int PT_KC = 16;    // k per chunk
+constexpr int PT_BLK = 512;
+constexpr int PT_BROWS = 6;
+CPL_HD inline long long btab_block(int jb, int pi, int c) {
+    return 2LL * jb * (jb + 1) + (long long)pi * (2 * jb + 2) + c;
+}
+// Error codes of the tabled kernel (device error word)
+constexpr int PT_ERR_RANGE = 0x1001;   // a tile's chunks are not covered by its tables
+constexpr int PT_ERR_WAIT = 0x1002;    // a bulk copy did not complete within the bounded wait
 CPL_HD inline int ir_ldf(int n) { return ir_np(n) + 4; }
 struct IrLayout {
     size_t L, perm, dinv, x, r, xn, rn, total;

@@ -681,10 +681,7 @@ static cpl_status ensure_common(cpl_ctx *c, int S, int nc_max, size_t scratch, c
         record_launch(c, idx, ev, st, 0.0, (double)2 * MX_NBV * L.b_var_bytes);
     }
     if ((s = M.arena.ensure(std::max<size_t>(scratch, 256), "mixed scratch arena")) != CPL_OK) return s;
-    if (!M.err.ptr) {
-        if ((s = M.err.ensure(sizeof(int), "mixed error word")) != CPL_OK) return s;
-        CPL_CUDA_TRY(cudaMemsetAsync(M.err.ptr, 0, sizeof(int), st));
-    }
+    if ((s = ensure_err_word(c, st)) != CPL_OK) return s;
     if ((s = M.ticket.ensure(sizeof(int), "mixed ticket")) != CPL_OK) return s;
     CPL_CUDA_TRY(mx_gemm_prepare(S));
     return CPL_OK;

@@ -42,6 +42,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "mbar.cuh"
 
 namespace cpl {
 namespace {
@@ -92,6 +93,97 @@ __device__ __forceinline__ void write_out(const PlainJob &p, int win, int slot, 
 }
 
 template <int NGE, bool ODD>
+using Acc = double[Shape<NGE, ODD>::NG > 0 ? Shape<NGE, ODD>::NG : 1][2][2];
+
+// One staged l3 chunk of the register-tiled contractions: kn k steps of
+// operand rows sa [NA][KC][TILE_I] and sb [NB][KC][TILE_J] (shared memory)
+// into this thread's 2 x 2 outputs.
+template <int NGE, bool ODD>
+__device__ __forceinline__ void fma_chunk(const double *sa, const double *sb, int kn, int tx, int ty,
+                                          Acc<NGE, ODD> &acc) {
+    using S = Shape<NGE, ODD>;
+#pragma unroll 2
+    for (int kk = 0; kk < kn; ++kk) {
+        double a[S::NA > 0 ? S::NA : 1][2], b[S::NB > 0 ? S::NB : 1][2];
+#pragma unroll
+        for (int q = 0; q < S::NA; ++q) {
+            a[q][0] = sa[(q * KC + kk) * TILE_I + ty];
+            a[q][1] = sa[(q * KC + kk) * TILE_I + ty + 16];
+        }
+#pragma unroll
+        for (int q = 0; q < S::NB; ++q) {
+            b[q][0] = sb[(q * KC + kk) * TILE_J + tx];
+            b[q][1] = sb[(q * KC + kk) * TILE_J + tx + 16];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (NGE >= 1) acc[0][r][c] = fma(a[0][r], b[0][c], acc[0][r][c]);
+                if (NGE >= 3) {
+                    acc[1][r][c] = fma(a[0][r], b[1][c], acc[1][r][c]);
+                    acc[2][r][c] = fma(a[1][r], b[1][c], acc[2][r][c]);
+                }
+                if (NGE >= 6) {
+                    acc[3][r][c] = fma(a[0][r], b[2][c], acc[3][r][c]);
+                    acc[4][r][c] = fma(a[1][r], b[2][c], acc[4][r][c]);
+                    acc[5][r][c] = fma(a[2][r], b[2][c], acc[5][r][c]);
+                }
+                if (ODD) {
+                    acc[NGE + 0][r][c] = fma(a[S::NAE][r], b[S::NBE][c], acc[NGE + 0][r][c]);
+                    acc[NGE + 1][r][c] = fma(a[S::NAE][r], b[S::NBE + 1][c], acc[NGE + 1][r][c]);
+                    acc[NGE + 2][r][c] = fma(a[S::NAE][r], b[S::NBE + 2][c], acc[NGE + 2][r][c]);
+                }
+            }
+    }
+}
+
+// Per-pair combination of the contractions (the App. A kernels through the
+// separable forms above) and the writes of both mirror entries.
+template <int NGE, bool ODD>
+__device__ __forceinline__ void epilogue(const PlainJob &p, int win, int pi, int i0, int j0, int tx, int ty,
+                                         const Acc<NGE, ODD> &acc) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+            const int l1 = j - i, l2 = i + j + pi;
+            if (l1 < p.lmin || l2 > p.lmax || l1 > l2) continue;
+            if (NGE >= 1) write_out(p, win, p.slot[0], l1, l2, acc[0][r][c]);
+            double ee = 0.0, eebb = 0.0;
+            if (NGE >= 3 || ODD) {
+                const double L1 = l1, L2 = l2;
+                const double eta2 = (L1 - 1.0) * (L1 + 2.0) * (L2 - 1.0) * L2;
+                const double c1 = 1.0 / (L1 * (L1 + 1.0) * (L2 + 1.0));
+                if (NGE >= 3) {
+                    const double r2 = L1 * (L1 + 1.0) * (L2 + 1.0) * (L2 + 2.0) / eta2;  // (lambda/eta)^2
+                    const double c0 = 1.0 + 2.0 / L1;
+                    const double c2 = c1 / (2.0 * (L2 + 2.0));
+                    const double s00 = acc[0][r][c], s01 = acc[1][r][c], s11 = acc[2][r][c];
+                    const double xp = c0 * s00 - c1 * s01 - c2 * s11;
+                    write_out(p, win, p.slot[1], l1, l2, sqrt(r2) * xp);
+                    if (NGE >= 6) {
+                        const double s02 = acc[3][r][c], s12 = acc[4][r][c], s22 = acc[5][r][c];
+                        const double xp2 = c0 * c0 * s00 - 2.0 * c0 * c1 * s01 - 2.0 * c0 * c2 * s11 +
+                                           c1 * c1 * s02 + 2.0 * c1 * c2 * s12 + c2 * c2 * s22;
+                        ee = r2 * xp2;
+                        write_out(p, win, p.slot[2], l1, l2, ee);
+                    }
+                }
+                if (ODD) {
+                    const double e0 = L1 + 2.0, e1 = 1.0 / (2.0 * (L2 + 2.0));
+                    const double Cc = (L2 + 2.0) * c1 / eta2;   // (l2+2) / (eta^2 l1 (l1+1) (l2+1))
+                    const double t0 = acc[NGE][r][c], t1 = acc[NGE + 1][r][c], t2 = acc[NGE + 2][r][c];
+                    eebb = Cc * (e0 * e0 * t0 - 2.0 * e0 * e1 * t1 + e1 * e1 * t2);
+                    write_out(p, win, p.slot[3], l1, l2, eebb);
+                    if (NGE >= 6) write_out(p, win, p.slot[4], l1, l2, ee - eebb);
+                }
+            }
+        }
+}
+
+template <int NGE, bool ODD>
 __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
     using S = Shape<NGE, ODD>;
     __shared__ double sa[S::NA > 0 ? S::NA : 1][KC][TILE_I];
@@ -118,7 +210,7 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
     if (NGE > 0) k_hi = khi_e;
     if (ODD) k_hi = max(k_hi, khi_o);
 
-    double acc[S::NG > 0 ? S::NG : 1][2][2];
+    Acc<NGE, ODD> acc;
 #pragma unroll
     for (int q = 0; q < S::NG; ++q)
 #pragma unroll
@@ -178,82 +270,176 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
             }
         }
         __syncthreads();
-        const int kn = min(KC, k_hi - kb + 1);
-#pragma unroll 2
-        for (int kk = 0; kk < kn; ++kk) {
-            double a[S::NA > 0 ? S::NA : 1][2], b[S::NB > 0 ? S::NB : 1][2];
-#pragma unroll
-            for (int q = 0; q < S::NA; ++q) {
-                a[q][0] = sa[q][kk][ty];
-                a[q][1] = sa[q][kk][ty + 16];
-            }
-#pragma unroll
-            for (int q = 0; q < S::NB; ++q) {
-                b[q][0] = sb[q][kk][tx];
-                b[q][1] = sb[q][kk][tx + 16];
-            }
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (NGE >= 1) acc[0][r][c] = fma(a[0][r], b[0][c], acc[0][r][c]);
-                    if (NGE >= 3) {
-                        acc[1][r][c] = fma(a[0][r], b[1][c], acc[1][r][c]);
-                        acc[2][r][c] = fma(a[1][r], b[1][c], acc[2][r][c]);
-                    }
-                    if (NGE >= 6) {
-                        acc[3][r][c] = fma(a[0][r], b[2][c], acc[3][r][c]);
-                        acc[4][r][c] = fma(a[1][r], b[2][c], acc[4][r][c]);
-                        acc[5][r][c] = fma(a[2][r], b[2][c], acc[5][r][c]);
-                    }
-                    if (ODD) {
-                        acc[NGE + 0][r][c] = fma(a[S::NAE][r], b[S::NBE][c], acc[NGE + 0][r][c]);
-                        acc[NGE + 1][r][c] = fma(a[S::NAE][r], b[S::NBE + 1][c], acc[NGE + 1][r][c]);
-                        acc[NGE + 2][r][c] = fma(a[S::NAE][r], b[S::NBE + 2][c], acc[NGE + 2][r][c]);
-                    }
-                }
-        }
+        fma_chunk<NGE, ODD>(&sa[0][0][0], &sb[0][0][0], min(KC, k_hi - kb + 1), tx, ty, acc);
     }
 
-    // ---- epilogue: combine the contractions per pair and write both mirror entries
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
-            const int l1 = j - i, l2 = i + j + pi;
-            if (l1 < p.lmin || l2 > p.lmax || l1 > l2) continue;
-            if (NGE >= 1) write_out(p, win, p.slot[0], l1, l2, acc[0][r][c]);
-            double ee = 0.0, eebb = 0.0;
-            if (NGE >= 3 || ODD) {
-                const double L1 = l1, L2 = l2;
-                const double eta2 = (L1 - 1.0) * (L1 + 2.0) * (L2 - 1.0) * L2;
-                const double c1 = 1.0 / (L1 * (L1 + 1.0) * (L2 + 1.0));
-                if (NGE >= 3) {
-                    const double r2 = L1 * (L1 + 1.0) * (L2 + 1.0) * (L2 + 2.0) / eta2;  // (lambda/eta)^2
-                    const double c0 = 1.0 + 2.0 / L1;
-                    const double c2 = c1 / (2.0 * (L2 + 2.0));
-                    const double s00 = acc[0][r][c], s01 = acc[1][r][c], s11 = acc[2][r][c];
-                    const double xp = c0 * s00 - c1 * s01 - c2 * s11;
-                    write_out(p, win, p.slot[1], l1, l2, sqrt(r2) * xp);
-                    if (NGE >= 6) {
-                        const double s02 = acc[3][r][c], s12 = acc[4][r][c], s22 = acc[5][r][c];
-                        const double xp2 = c0 * c0 * s00 - 2.0 * c0 * c1 * s01 - 2.0 * c0 * c2 * s11 +
-                                           c1 * c1 * s02 + 2.0 * c1 * c2 * s12 + c2 * c2 * s22;
-                        ee = r2 * xp2;
-                        write_out(p, win, p.slot[2], l1, l2, ee);
-                    }
-                }
-                if (ODD) {
-                    const double e0 = L1 + 2.0, e1 = 1.0 / (2.0 * (L2 + 2.0));
-                    const double Cc = (L2 + 2.0) * c1 / eta2;   // (l2+2) / (eta^2 l1 (l1+1) (l2+1))
-                    const double t0 = acc[NGE][r][c], t1 = acc[NGE + 1][r][c], t2 = acc[NGE + 2][r][c];
-                    eebb = Cc * (e0 * e0 * t0 - 2.0 * e0 * e1 * t1 + e1 * e1 * t2);
-                    write_out(p, win, p.slot[3], l1, l2, eebb);
-                    if (NGE >= 6) write_out(p, win, p.slot[4], l1, l2, ee - eebb);
-                }
-            }
+    epilogue<NGE, ODD>(p, win, pi, i0, j0, tx, ty, acc);
+}
+
+// ---------------------------------------------------------------- tabled kernel
+// k_plain recomputes the operand rows of each l3 chunk in every tile that
+// covers it: a row block's i-side rows are rebuilt by each of its column
+// tiles and a column block's j-side rows by each row tile, about 20 FP64-pipe
+// instructions (products and integer conversions) per staged element.  The
+// tabled form computes each block once -- B blocks (j side, window
+// independent, cached per context) and A blocks (i side, per sweep and
+// window) -- and a tile streams its chunks into shared memory with two bulk
+// copies per chunk, double-buffered.  Values, zero pattern and the order of
+// every operation are those of k_plain, so the two kernels agree bit for bit.
+static_assert(TILE_I == 32 && TILE_J == 32 && KC == PT_KC && KC * TILE_I == PT_BLK, "operand block geometry");
+
+// B blocks: column block jb, parity pi, chunk c <= 2 jb + 1 (k <= j0 + 31):
+// rows b0, b0 u, b0 u^2 (even sweep) and b1 u, b1 u u', b1 u u'^2 (odd sweep)
+// as [6][KC][TILE_J], zero where k lies outside the pair's range.  (A band
+// limit needs no zeros here: the A side is zero past it.)
+__global__ void k_btab(const double *__restrict__ g, const double *__restrict__ h, int njb, double *__restrict__ B) {
+    const int c = blockIdx.x, jb = blockIdx.y, pi = blockIdx.z;
+    if (jb >= njb || c > 2 * jb + 1) return;
+    double *blk = B + (size_t)btab_block(jb, pi, c) * PT_BROWS * PT_BLK;
+    for (int e = threadIdx.x; e < PT_BLK; e += blockDim.x) {
+        const int kk = e / TILE_J, jj = e % TILE_J;
+        const int j = jb * TILE_J + jj, k = c * KC + kk;
+        double b0 = 0.0, u = 0.0;
+        if (k <= j) {
+            b0 = g[j - k] * h[j + k + pi];
+            u = int_prod(2 * j + 2 * k + 2 * pi + 2, 2 * j - 2 * k + 1);
         }
+        blk[e] = b0;
+        blk[PT_BLK + e] = b0 * u;
+        blk[2 * PT_BLK + e] = b0 * u * u;
+        double b1u = 0.0, up = 0.0;
+        if (k <= j + pi - 1) {
+            const double u1 = int_prod(2 * j + 2 * k + 3, 2 * j - 2 * k + 2 * pi);
+            up = int_prod(2 * j + 2 * k + 4, 2 * j - 2 * k + 2 * pi + 1);
+            b1u = g[j - k + pi] * h[j + k + 1] * u1;
+        }
+        blk[3 * PT_BLK + e] = b1u;
+        blk[4 * PT_BLK + e] = b1u * up;
+        blk[5 * PT_BLK + e] = b1u * up * up;
+    }
+}
+
+// A blocks of one sweep: window w, parity pi, row block ib, chunk
+// c = 2 ib + m: the even rows a0, a0 v, a0 v^2 (the first nae) and, if odd,
+// a1 v, as [nae + odd][KC][TILE_I]; zero outside the pair range and past the
+// window's band (l3 > cap).
+__global__ void k_atab(const double *__restrict__ A, int a_stride, const int *__restrict__ l3cap,
+                       const double *__restrict__ g, const long long *__restrict__ aoff, int nib, int nae, int odd,
+                       double *__restrict__ At) {
+    const int m = blockIdx.x, ib = blockIdx.y, w = blockIdx.z >> 1, pi = blockIdx.z & 1;
+    const size_t idx = ((size_t)w * 2 + pi) * nib + ib;
+    const long long first = aoff[idx];
+    if (m >= aoff[idx + 1] - first) return;
+    const int na = nae + odd;
+    double *blk = At + (size_t)(first + m) * na * PT_BLK;
+    const double *__restrict__ Aw = A + (size_t)w * a_stride;
+    const int cap = l3cap[w];
+    const int c = 2 * ib + m;
+    for (int e = threadIdx.x; e < PT_BLK; e += blockDim.x) {
+        const int kk = e / TILE_I, ii = e % TILE_I;
+        const int i = ib * TILE_I + ii, k = c * KC + kk;
+        if (nae > 0) {
+            double a0 = 0.0, v = 0.0;
+            if (k >= i && 2 * k + pi <= cap) {
+                a0 = Aw[2 * k + pi] * g[i + k + pi] * g[k - i];
+                v = int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
+            }
+            blk[e] = a0;
+            if (nae > 1) blk[PT_BLK + e] = a0 * v;
+            if (nae > 2) blk[2 * PT_BLK + e] = a0 * v * v;
+        }
+        if (odd) {
+            double a1v = 0.0;
+            if (k >= i + pi && 2 * k + 1 - pi <= cap) {
+                const double v1 = int_prod(2 * i + 2 * k + 2, 2 * k + 1 - 2 * i - 2 * pi);
+                a1v = Aw[2 * k + 1 - pi] * g[i + k + 1] * g[k - i - pi] * v1;
+            }
+            blk[nae * PT_BLK + e] = a1v;
+        }
+    }
+}
+
+template <int NGE, bool ODD>
+__global__ void __launch_bounds__(NT, 2) k_plain_tab(const PlainArgs pa) {
+    using S = Shape<NGE, ODD>;
+    constexpr int NA = S::NA, NB = S::NB;
+    constexpr int BQ0 = NGE > 0 ? 0 : 3;             // first B row the variant reads
+    constexpr int STAGE = (NA + NB) * PT_BLK;        // doubles per pipeline stage
+    static_assert(NGE == 0 || !ODD || S::NBE == 3, "B rows of the variant must be contiguous");
+    extern __shared__ __align__(128) double stage[];   // [2][NA + NB][KC][32]
+    __shared__ __align__(8) uint64_t full[2];
+
+    const WorkItem it = pa.items[blockIdx.x];
+    const PlainJob &p = pa.jobs[it.job];
+    const int win = it.win;
+    const Tile t = p.tiles[it.tile];
+    const int pi = t.pi, i0 = t.i0, j0 = t.j0;
+    const int cap = p.l3cap[win];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+
+    // the k range k_plain runs (same bounds)
+    const int kcap_e = (cap - pi) >> 1, kcap_o = (cap - 1 + pi) >> 1;
+    const int k_lo = i0;
+    int k_hi = -1;
+    if (NGE > 0) k_hi = min(j0 + TILE_J - 1, kcap_e);
+    if (ODD) k_hi = max(k_hi, min(j0 + TILE_J - 2 + pi, kcap_o));
+    const int nch = k_hi >= k_lo ? (k_hi - k_lo) / KC + 1 : 0;
+    const int ib = i0 / TILE_I, jb = j0 / TILE_J;
+    const size_t aidx = ((size_t)win * 2 + pi) * p.nib + ib;
+    const long long afirst = p.aoff[aidx];
+    if (nch > p.aoff[aidx + 1] - afirst || (nch > 0 && (jb >= pa.btab_njb || k_lo / KC + nch - 1 > 2 * jb + 1))) {
+        if (tid == 0) atomicCAS(pa.err, 0, PT_ERR_RANGE);
+        return;
+    }
+    const double *asrc = p.atab + (size_t)afirst * NA * PT_BLK;
+    const double *bsrc = pa.btab + ((size_t)btab_block(jb, pi, k_lo / KC) * PT_BROWS + BQ0) * PT_BLK;
+
+    const uint32_t bar0 = mbar::smem_u32(&full[0]), bar1 = mbar::smem_u32(&full[1]);
+    if (tid == 0) {
+        mbar::init(bar0, 1);
+        mbar::init(bar1, 1);
+        mbar::fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int m) {   // chunk m into stage m & 1 (one thread)
+        const uint32_t bar = (m & 1) ? bar1 : bar0;
+        const uint32_t dst = mbar::smem_u32(stage + (m & 1) * STAGE);
+        mbar::expect_tx(bar, STAGE * 8);
+        mbar::copy_g2s(dst, asrc + (size_t)m * NA * PT_BLK, NA * PT_BLK * 8, bar);
+        mbar::copy_g2s(dst + NA * PT_BLK * 8, bsrc + (size_t)m * PT_BROWS * PT_BLK, NB * PT_BLK * 8, bar);
+    };
+    if (tid == 0) {
+        if (nch > 0) issue(0);
+        if (nch > 1) issue(1);
+    }
+
+    Acc<NGE, ODD> acc;
+#pragma unroll
+    for (int q = 0; q < S::NG; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) acc[q][r][c] = 0.0;
+
+    for (int m = 0; m < nch; ++m) {
+        const bool got = mbar::wait((m & 1) ? bar1 : bar0, (m >> 1) & 1);
+        if (!__syncthreads_and(got)) {
+            // record, let the copies this CTA issued finish (bounded), leave
+            if (tid == 0) {
+                atomicCAS(pa.err, 0, PT_ERR_WAIT);
+                if (m + 1 < nch) mbar::wait(((m + 1) & 1) ? bar1 : bar0, ((m + 1) >> 1) & 1);
+                mbar::wait((m & 1) ? bar1 : bar0, (m >> 1) & 1);
+            }
+            return;
+        }
+        const double *st = stage + (m & 1) * STAGE;
+        fma_chunk<NGE, ODD>(st, st + NA * PT_BLK, min(KC, k_hi - (k_lo + m * KC) + 1), tx, ty, acc);
+        __syncthreads();   // stage m & 1 is free again
+        if (tid == 0 && m + 2 < nch) issue(m + 2);
+    }
+
+    epilogue<NGE, ODD>(p, win, pi, i0, j0, tx, ty, acc);
 }
 
 __global__ void k_weights(const double *__restrict__ W, int w_len, const int *__restrict__ l3cap,
@@ -291,13 +477,49 @@ void plain_variant(int mode, const int slot[5], int *nge, bool *odd) {
     }
 }
 
+cudaError_t launch_btab(const double *g, const double *h, int njb, double *B, cudaStream_t st) {
+    if (njb <= 0) return cudaSuccess;
+    k_btab<<<dim3(2 * njb, njb, 2), 256, 0, st>>>(g, h, njb, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_atab(const double *A, int a_stride, const int *l3cap, const double *g, const long long *aoff,
+                        int n_win, int nib, int max_count, int nae, int odd, double *At, cudaStream_t st) {
+    if (max_count <= 0 || nib <= 0 || n_win <= 0) return cudaSuccess;
+    k_atab<<<dim3(max_count, nib, 2 * n_win), 256, 0, st>>>(A, a_stride, l3cap, g, aoff, nib, nae, odd, At);
+    return cudaGetLastError();
+}
+
+template <int NGE, bool ODD>
+static cudaError_t launch_tab(const PlainArgs &a, cudaStream_t st) {
+    using S = Shape<NGE, ODD>;
+    const int smem = 2 * (S::NA + S::NB) * PT_BLK * (int)sizeof(double);
+    static bool attr = false;   // per variant; the attribute is per function and device-independent here
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_plain_tab<NGE, ODD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_plain_tab<NGE, ODD><<<a.n_items, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 // One CTA per work item; the variant (even contractions, odd sweep) is the
-// same for every sweep of the launch (plain_variant of each sweep).
+// same for every sweep of the launch (plain_variant of each sweep).  With
+// operand tables (a.btab) the tabled kernel runs.
 cudaError_t launch_plain(const PlainArgs &a, cudaStream_t st) {
     if (a.n_items == 0) return cudaSuccess;
     dim3 grid(a.n_items);
     const int nge = a.nge;
     const bool odd = a.odd != 0;
+    if (a.btab) {
+        if (nge == 1 && !odd) return launch_tab<1, false>(a, st);
+        if (nge == 3 && !odd) return launch_tab<3, false>(a, st);
+        if (nge == 6 && odd) return launch_tab<6, true>(a, st);
+        if (nge == 6) return launch_tab<6, false>(a, st);
+        if (nge == 0 && odd) return launch_tab<0, true>(a, st);
+        return cudaErrorInvalidValue;
+    }
     if (nge == 1) k_plain<1, false><<<grid, NT, 0, st>>>(a);
     else if (nge == 3) k_plain<3, false><<<grid, NT, 0, st>>>(a);
     else if (nge == 6 && odd) k_plain<6, true><<<grid, NT, 0, st>>>(a);

@@ -3,41 +3,29 @@
 // The valid pairs lmin <= l1 <= l2 <= lmax become, per parity class pi,
 // the region  i >= 0,  j - i >= lmin,  i + j + pi <= lmax  of the (i, j)
 // plane (d = 2i + pi, s = 2j + pi).  It is covered by TILE_I x TILE_J
-// blocks; a block's work is the number of l3 terms of its valid pairs,
-// 2 l1 + 1 per pair over both parities of L (Sec. 3: the l3 sum of a pair
-// runs over |l1 - l2| .. l1 + l2), so blocks far from the diagonal cost
-// more.  The list is sorted by decreasing cost (longest-processing-time
-// order) so that the heaviest blocks start first.
+// blocks.  The plain kernels run every pair of a block over the block's
+// whole k range (l3 = 2k + pi or 2k + 1 - pi, from the first row's
+// smallest k to the last column's largest; a pair's own range, |l1 - l2|
+// .. l1 + l2 (Sec. 3), is selected by zero operands), so a block's run time
+// is set by that range, not by its count of valid terms: edge blocks with
+// few valid pairs cost as much as full ones.  The list is sorted by this
+// run-time model, largest first (longest-processing-time order), so that
+// the longest blocks start first and the launch ends with short ones.
 #include <algorithm>
 
 #include "internal.h"
 
 namespace cpl {
 
-static inline long long pair_terms(int l1, int band) {
-    // l3 terms of a pair with l1 <= l2 over both parities, l3 <= band
-    (void)band;
-    return 2LL * l1 + 1;
-}
-
-double tile_terms(const Tile &t, int lmax, int lmin, int band) {
-    double sum = 0.0;
-    for (int di = 0; di < TILE_I; ++di) {
-        const int i = t.i0 + di;
-        const int d = 2 * i + t.pi;
-        for (int dj = 0; dj < TILE_J; ++dj) {
-            const int j = t.j0 + dj;
-            const int l1 = j - i, l2 = i + j + t.pi;
-            if (l1 < lmin || l2 > lmax || l1 > l2) continue;
-            if (band < 0) {
-                sum += (double)pair_terms(l1, band);
-            } else {
-                const int hi = std::min(l1 + l2, band);
-                if (hi >= d) sum += (double)(hi - d + 1);
-            }
-        }
-    }
-    return sum;
+double tile_time(const Tile &t, int cap) {
+    // k range of the block as the kernels run it (even and odd sweeps),
+    // staged in chunks of 16 k, plus the epilogue (about a dozen k steps of
+    // FP64 work per pair); in units of one k step of the block
+    const int pi = t.pi;
+    const int kce = (cap - pi) >> 1, kco = (cap - 1 + pi) >> 1;
+    const int khi = std::max(std::min(t.j0 + TILE_J - 1, kce), std::min(t.j0 + TILE_J - 2 + pi, kco));
+    const int span = std::max(khi - t.i0 + 1, 0);
+    return (double)span + (double)((span + 15) / 16) + 12.0;
 }
 
 void tile_terms_split(const Tile &t, int lmax, int lmin, int cap, double *even, double *odd,
@@ -65,6 +53,16 @@ void tile_terms_split(const Tile &t, int lmax, int lmin, int cap, double *even, 
     *pairs = np;
 }
 
+static bool tile_has_pairs(const Tile &t, int lmax, int lmin) {
+    for (int di = 0; di < TILE_I; ++di)
+        for (int dj = 0; dj < TILE_J; ++dj) {
+            const int i = t.i0 + di, j = t.j0 + dj;
+            const int l1 = j - i, l2 = i + j + t.pi;
+            if (l1 >= lmin && l2 <= lmax && l1 <= l2) return true;
+        }
+    return false;
+}
+
 void make_tiles(int lmax, int lmin, std::vector<Tile> &tiles) {
     tiles.clear();
     for (int pi = 0; pi < 2; ++pi) {
@@ -80,9 +78,8 @@ void make_tiles(int lmax, int lmin, std::vector<Tile> &tiles) {
                 t.pad = 0;
                 t.i0 = i0;
                 t.j0 = j0;
-                const double c = tile_terms(t, lmax, lmin, -1);
-                if (c <= 0.0) continue;
-                t.cost = (int32_t)std::min(c / 1024.0 + 1.0, 2.0e9);
+                if (!tile_has_pairs(t, lmax, lmin)) continue;
+                t.cost = (int32_t)tile_time(t, 2 * lmax);
                 tiles.push_back(t);
             }
         }
