@@ -247,8 +247,12 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // The plain FP64 build of a batch of requests on `st` (device pointers).
 // Every request's window-role groups become sweeps (PlainJob); the work
 // items of all sweeps that run the same kernel variant are merged into one
-// list, heaviest first, and run by one launch.
-cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *outs, int n, cudaStream_t st) {
+// list, heaviest first, and run by one launch; the launches run longest
+// first.  With host_outs, the output blocks a launch completes are copied
+// to host_outs on c->copy_stream while the later launches run (the caller
+// synchronises that stream).
+cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *outs, int n, cudaStream_t st,
+                            double *const *host_outs = nullptr) {
     cpl_status s;
     int lmax_all = 2;
     for (int q = 0; q < n; ++q) lmax_all = std::max(lmax_all, reqs[q].lmax);
@@ -413,6 +417,19 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         vitems[k].reserve(tmp.size());
         for (auto &p : tmp) vitems[k].push_back(p.second);
     }
+    // launch order: the longest variant first (its output blocks can then be
+    // copied out while the shorter ones run)
+    std::vector<size_t> korder(keys.size());
+    {
+        std::vector<double> kcost(keys.size(), 0.0);
+        for (size_t x = 0; x < sweeps.size(); ++x) {
+            const size_t k = std::find(keys.begin(), keys.end(), vkey(sweeps[x].nge, sweeps[x].odd)) - keys.begin();
+            const double per = (double)(sweeps[x].nge + (sweeps[x].odd ? 3 : 0));
+            for (const auto &it : jobs[sweeps[x].job].items) kcost[k] += per * it.first;
+        }
+        for (size_t k = 0; k < keys.size(); ++k) korder[k] = k;
+        std::stable_sort(korder.begin(), korder.end(), [&](size_t a, size_t b) { return kcost[a] > kcost[b]; });
+    }
 
     // ---- one metadata buffer: sweep table, caps, bins, items
     size_t o = 0;
@@ -526,7 +543,16 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
             ls.done(0.0, 8.0 * (double)sw.aoff.back() * (sw.nae + (sw.odd ? 1 : 0)) * PT_BLK);
         }
     }
-    for (size_t k = 0; k < keys.size(); ++k) {
+    if (host_outs) {
+        if (!c->copy_stream) CPL_CUDA_TRY(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        while (c->copy_ev.size() < keys.size()) {
+            cudaEvent_t e;
+            CPL_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            c->copy_ev.push_back(e);
+        }
+    }
+    for (size_t ko = 0; ko < korder.size(); ++ko) {
+        const size_t k = korder[ko];
         PlainArgs a;
         std::memset(&a, 0, sizeof(a));
         a.g = c->g.as<double>();
@@ -573,7 +599,22 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
                     od = T[3 * it.tile + 1];
                     np = T[3 * it.tile + 2];
                 } else {
-                    tile_terms_split(J.ts->host[it.tile], r->lmax, r->lmin, J.caps[it.win], &e, &od, &np);
+                    if (J.ts->band_terms.size() > 64 && !J.ts->band_terms.count(J.caps[it.win])) J.ts->band_terms.clear();
+                    std::vector<double> &T = J.ts->band_terms[J.caps[it.win]];
+                    if (T.size() != 3 * J.ts->host.size()) {
+                        T.resize(3 * J.ts->host.size());
+                        for (size_t q = 0; q < J.ts->host.size(); ++q) {
+                            const Tile &tq = J.ts->host[q];
+                            if (2 * tq.i0 + tq.pi > J.caps[it.win]) {   // dropped for this cap: no work
+                                T[3 * q] = T[3 * q + 1] = T[3 * q + 2] = 0.0;
+                                continue;
+                            }
+                            tile_terms_split(tq, r->lmax, r->lmin, J.caps[it.win], &T[3 * q], &T[3 * q + 1], &T[3 * q + 2]);
+                        }
+                    }
+                    e = T[3 * it.tile];
+                    od = T[3 * it.tile + 1];
+                    np = T[3 * it.tile + 2];
                 }
                 flop += 2.0 * (a.nge * e + (odd ? 3.0 : 0.0) * od);
                 bytes += (J.nb ? 0.0 : 16.0) * nslots * np;
@@ -582,6 +623,24 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         LaunchScope ls(c, kname, st);
         CPL_CUDA_TRY(df ? launch_plain_df(a, st) : launch_plain(a, st));
         ls.done(flop, bytes);
+        if (host_outs) {
+            // the blocks (window, slot) this launch wrote, to the host behind it
+            CPL_CUDA_TRY(cudaEventRecord(c->copy_ev[ko], st));
+            CPL_CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->copy_ev[ko], 0));
+            for (const Sweep &sw : sweeps) {
+                if (vkey(sw.nge, sw.odd) != keys[k]) continue;
+                const cpl_request *r = reqs + sw.job;
+                const int nspec = spec_count(r->spectra);
+                const size_t blk = out_doubles(r) / ((size_t)r->n_windows * nspec);
+                for (int w = 0; w < r->n_windows; ++w)
+                    for (int q = 0; q < 5; ++q) {
+                        if (sw.slot[q] < 0) continue;
+                        const size_t off = ((size_t)w * nspec + sw.slot[q]) * blk;
+                        CPL_CUDA_TRY(cudaMemcpyAsync(host_outs[sw.job] + off, outs[sw.job] + off, sizeof(double) * blk,
+                                                     cudaMemcpyDeviceToHost, c->copy_stream));
+                    }
+            }
+        }
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));
     return CPL_OK;
@@ -696,6 +755,8 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->done) cudaEventDestroy(c->done);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (auto e : c->copy_ev) cudaEventDestroy(e);
     delete c;
     return CPL_OK;
 }
@@ -771,9 +832,27 @@ cpl_status cpl_build_host(cpl_ctx *c, const cpl_request *r, double *out_host) {
     rd.W_tp = dsts[1];
     rd.W_pp = dsts[2];
     if ((s = check_windows(c, &rd, st)) != CPL_OK) return s;
-    if ((s = build_one(c, &rd, c->stage_out.as<double>(), st)) != CPL_OK) return s;
-    CPL_CUDA_TRY(cudaMemcpyAsync(out_host, c->stage_out.ptr, ob, cudaMemcpyDeviceToHost, st));
-    cudaError_t e = cudaStreamSynchronize(st);
+    cudaError_t e;
+    // overlapped copies need page-locked memory (a copy to pageable memory
+    // would hold the host until it ends, delaying the later launches)
+    cudaPointerAttributes pa;
+    bool pinned = cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    if (rd.precision == CPL_MIXED_BF16 || !pinned) {
+        if ((s = build_one(c, &rd, c->stage_out.as<double>(), st)) != CPL_OK) return s;
+        CPL_CUDA_TRY(cudaMemcpyAsync(out_host, c->stage_out.ptr, ob, cudaMemcpyDeviceToHost, st));
+    } else {
+        // each launch's output blocks travel while the later launches run
+        double *douts[1] = {c->stage_out.as<double>()};
+        double *houts[1] = {out_host};
+        s = build_fp64_batch(c, &rd, douts, 1, st, houts);
+        if (c->copy_stream) {
+            e = cudaStreamSynchronize(c->copy_stream);
+            if (e != cudaSuccess && s == CPL_OK) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+        }
+        if (s != CPL_OK) return s;
+    }
+    e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
     return CPL_OK;
 }

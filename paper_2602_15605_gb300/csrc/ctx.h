@@ -52,6 +52,8 @@ struct TileSet {
     // per-tile l3 term counts (even, odd, pairs) for windows without a band
     // limit (cap >= 2 lmax), filled on first use by the launch accounting
     std::vector<double> terms;
+    // the same under band limits (cap -> counts), bounded in number of caps
+    std::map<int, std::vector<double>> band_terms;
 };
 
 
@@ -113,6 +115,8 @@ struct cpl_ctx {
     DevBuf dec_ws;               // cpl_decouple: augmented systems too large for shared memory
     DevBuf cov_M, cov_dense, cov_edges;   // cpl_cov_gaussian: kernels of one build, dense covariance, bin edges
     cudaStream_t own_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;      // cpl_build_host: device-to-host copies overlapped with later kernels
+    std::vector<cudaEvent_t> copy_ev;        // its ordering events (one per kernel variant)
     cudaEvent_t done = nullptr;  // orders scratch reuse across caller streams
     // per-kernel accounting (cpl_ctx_stats)
     struct KStat {

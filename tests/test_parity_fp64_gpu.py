@@ -155,6 +155,25 @@ def test_build_host_matches_device(ctx):
     assert np.array_equal(Md, Mh)
 
 
+@pytest.mark.parametrize("binned", [False, True])
+def test_build_host_pinned_overlapped_copies(ctx, binned):
+    # page-locked output: each launch's blocks are copied out while the later
+    # launches run (three launches: separate windows; two windows per role)
+    import torch
+    lmax = 130
+    Wt, Wc, Wp = (np.stack([windows.mask_like(lmax, seed=s + q) for q in range(2)]) for s in (60, 70, 80))
+    edges = list(range(2, lmax + 2, 16)) + ([lmax + 1] if (lmax - 1) % 16 else []) if binned else None
+    Md = ctx.build(lmax, dev(Wt), dev(Wc), dev(Wp), coupling.ALL, bin_edges=edges).cpu().numpy()
+    pinned = torch.full(Md.shape, -1.0, dtype=torch.float64, pin_memory=True).numpy()
+    Mh = ctx.build_host(lmax, Wt, Wc, Wp, coupling.ALL, bin_edges=edges, out=pinned)
+    if binned:   # FP64 atomics: order not fixed
+        assert np.max(np.abs(Mh - Md)) <= 1e-14 * np.max(np.abs(Md))
+    else:
+        assert np.array_equal(Md, Mh)
+    pageable = ctx.build_host(lmax, Wt, Wc, Wp, coupling.ALL, bin_edges=edges)
+    assert np.max(np.abs(pageable - Mh)) <= 1e-14 * np.max(np.abs(Md))
+
+
 def test_batch_matches_single(ctx):
     jobs = []
     for lm, s in ((40, 1), (77, 2), (130, 3)):
