@@ -95,25 +95,26 @@ __device__ __forceinline__ void write_out(const PlainJob &p, int win, int slot, 
 template <int NGE, bool ODD>
 using Acc = double[Shape<NGE, ODD>::NG > 0 ? Shape<NGE, ODD>::NG : 1][2][2];
 
-// One staged l3 chunk of the register-tiled contractions: kn k steps of
-// operand rows sa [NA][KC][TILE_I] and sb [NB][KC][TILE_J] (shared memory)
-// into this thread's 2 x 2 outputs.
-template <int NGE, bool ODD>
-__device__ __forceinline__ void fma_chunk(const double *sa, const double *sb, int kn, int tx, int ty,
+// k steps kk0 <= kk < kk1 of one staged l3 chunk of the register-tiled
+// contractions: operand rows sa [NA][KC][TILE_I] and sb [NB][KC][TILE_J]
+// (shared memory) into this thread's 2 x 2 outputs, rows ar and ar + RS of
+// the tile, columns bc and bc + CS.
+template <int NGE, bool ODD, int RS, int CS>
+__device__ __forceinline__ void fma_chunk(const double *sa, const double *sb, int kk0, int kk1, int ar, int bc,
                                           Acc<NGE, ODD> &acc) {
     using S = Shape<NGE, ODD>;
 #pragma unroll 2
-    for (int kk = 0; kk < kn; ++kk) {
+    for (int kk = kk0; kk < kk1; ++kk) {
         double a[S::NA > 0 ? S::NA : 1][2], b[S::NB > 0 ? S::NB : 1][2];
 #pragma unroll
         for (int q = 0; q < S::NA; ++q) {
-            a[q][0] = sa[(q * KC + kk) * TILE_I + ty];
-            a[q][1] = sa[(q * KC + kk) * TILE_I + ty + 16];
+            a[q][0] = sa[(q * KC + kk) * TILE_I + ar];
+            a[q][1] = sa[(q * KC + kk) * TILE_I + ar + RS];
         }
 #pragma unroll
         for (int q = 0; q < S::NB; ++q) {
-            b[q][0] = sb[(q * KC + kk) * TILE_J + tx];
-            b[q][1] = sb[(q * KC + kk) * TILE_J + tx + 16];
+            b[q][0] = sb[(q * KC + kk) * TILE_J + bc];
+            b[q][1] = sb[(q * KC + kk) * TILE_J + bc + CS];
         }
 #pragma unroll
         for (int r = 0; r < 2; ++r)
@@ -139,15 +140,16 @@ __device__ __forceinline__ void fma_chunk(const double *sa, const double *sb, in
 }
 
 // Per-pair combination of the contractions (the App. A kernels through the
-// separable forms above) and the writes of both mirror entries.
-template <int NGE, bool ODD>
-__device__ __forceinline__ void epilogue(const PlainJob &p, int win, int pi, int i0, int j0, int tx, int ty,
+// separable forms above) and the writes of both mirror entries; this
+// thread's pairs are rows i0 + ar + RS r and columns j0 + bc + CS c.
+template <int NGE, bool ODD, int RS, int CS>
+__device__ __forceinline__ void epilogue(const PlainJob &p, int win, int pi, int i0, int j0, int ar, int bc,
                                          const Acc<NGE, ODD> &acc) {
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+            const int i = i0 + ar + RS * r, j = j0 + bc + CS * c;
             const int l1 = j - i, l2 = i + j + pi;
             if (l1 < p.lmin || l2 > p.lmax || l1 > l2) continue;
             if (NGE >= 1) write_out(p, win, p.slot[0], l1, l2, acc[0][r][c]);
@@ -270,10 +272,10 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
             }
         }
         __syncthreads();
-        fma_chunk<NGE, ODD>(&sa[0][0][0], &sb[0][0][0], min(KC, k_hi - kb + 1), tx, ty, acc);
+        fma_chunk<NGE, ODD, 16, 16>(&sa[0][0][0], &sb[0][0][0], 0, min(KC, k_hi - kb + 1), ty, tx, acc);
     }
 
-    epilogue<NGE, ODD>(p, win, pi, i0, j0, tx, ty, acc);
+    epilogue<NGE, ODD, 16, 16>(p, win, pi, i0, j0, ty, tx, acc);
 }
 
 // ---------------------------------------------------------------- tabled kernel
@@ -376,7 +378,16 @@ __global__ void __launch_bounds__(NT, 2) k_plain_tab(const PlainArgs pa) {
     const int pi = t.pi, i0 = t.i0, j0 = t.j0;
     const int cap = p.l3cap[win];
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    // Each warp owns a 16 x 8 block of the tile (rows 16 h .., columns 8 q ..),
+    // each thread rows ar, ar + 8 and columns bc, bc + 4 of it.  A warp skips
+    // the k steps before its first row's range and after its last column's
+    // (its products there are exact zeros) and all of them when its block has
+    // no valid pair.  The two warps of each SM sub-partition (w and w + 4) take
+    // opposite halves and column quarters q, 3 - q, so that every
+    // sub-partition skips equally.
+    const int warp = tid >> 5, lane = tid & 31;
+    const int wh = warp >> 2, wq = wh ? 3 - (warp & 3) : (warp & 3);
+    const int ar = 16 * wh + (lane >> 2), bc = 8 * wq + (lane & 3);
 
     // the k range k_plain runs (same bounds)
     const int kcap_e = (cap - pi) >> 1, kcap_o = (cap - 1 + pi) >> 1;
@@ -385,6 +396,14 @@ __global__ void __launch_bounds__(NT, 2) k_plain_tab(const PlainArgs pa) {
     if (NGE > 0) k_hi = min(j0 + TILE_J - 1, kcap_e);
     if (ODD) k_hi = max(k_hi, min(j0 + TILE_J - 2 + pi, kcap_o));
     const int nch = k_hi >= k_lo ? (k_hi - k_lo) / KC + 1 : 0;
+    // this warp's k range (same bounds as the tile's, for its rows and columns)
+    const int wi0 = i0 + 16 * wh, wj1 = j0 + 8 * wq + 7;
+    const int wk_lo = wi0;
+    int wk_hi = -1;
+    if (NGE > 0) wk_hi = min(wj1, kcap_e);
+    if (ODD) wk_hi = max(wk_hi, min(wj1 - 1 + pi, kcap_o));
+    // a valid pair (j - i >= lmin, i + j <= lmax - pi) in the block exists iff one does on its first row
+    if (max(j0 + 8 * wq, wi0 + p.lmin) > min(wj1, p.lmax - pi - wi0)) wk_hi = -1;
     const int ib = i0 / TILE_I, jb = j0 / TILE_J;
     const size_t aidx = ((size_t)win * 2 + pi) * p.nib + ib;
     const long long afirst = p.aoff[aidx];
@@ -434,12 +453,14 @@ __global__ void __launch_bounds__(NT, 2) k_plain_tab(const PlainArgs pa) {
             return;
         }
         const double *st = stage + (m & 1) * STAGE;
-        fma_chunk<NGE, ODD>(st, st + NA * PT_BLK, min(KC, k_hi - (k_lo + m * KC) + 1), tx, ty, acc);
+        const int kb = k_lo + m * KC;
+        const int kk0 = max(0, wk_lo - kb), kk1 = min(KC, wk_hi - kb + 1);
+        if (kk0 < kk1) fma_chunk<NGE, ODD, 8, 4>(st, st + NA * PT_BLK, kk0, kk1, ar, bc, acc);
         __syncthreads();   // stage m & 1 is free again
         if (tid == 0 && m + 2 < nch) issue(m + 2);
     }
 
-    epilogue<NGE, ODD>(p, win, pi, i0, j0, tx, ty, acc);
+    epilogue<NGE, ODD, 8, 4>(p, win, pi, i0, j0, ar, bc, acc);
 }
 
 __global__ void k_weights(const double *__restrict__ W, int w_len, const int *__restrict__ l3cap,
