@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include "dd.cuh"
+#include "mbar.cuh"
 #include "mixed.h"
 
 namespace cpl {
@@ -45,44 +46,6 @@ namespace {
 
 constexpr int NTH = 576;                   // 2 control warps + 16 drain warps (96 registers each)
 constexpr int LPAD = MX_ROWS + 1;          // padded stride of the [col][row] planes
-constexpr uint64_t WAIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t gtime() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const uint64_t t0 = gtime();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (gtime() - t0 > WAIT_NS) return false;
-    }
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -160,36 +123,36 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
     float2 *Ls = reinterpret_cast<float2 *>(dsm + NST * STAGE);   // [64 column pairs][LPAD]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t s_full0 = smem_u32(&sh.full[0]), s_empty0 = smem_u32(&sh.empty[0]);
-    const uint32_t s_accf = smem_u32(&sh.acc_full), s_acce = smem_u32(&sh.acc_empty), s_done = smem_u32(&sh.done);
+    const uint32_t s_full0 = mbar::smem_u32(&sh.full[0]), s_empty0 = mbar::smem_u32(&sh.empty[0]);
+    const uint32_t s_accf = mbar::smem_u32(&sh.acc_full), s_acce = mbar::smem_u32(&sh.acc_empty), s_done = mbar::smem_u32(&sh.done);
 
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(mbar::smem_u32(&sh.tmem)),
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         for (int q = 0; q < NST; ++q) {
-            mbar_init(s_full0 + 8 * q, 1);
-            mbar_init(s_empty0 + 8 * q, 1);
+            mbar::init(s_full0 + 8 * q, 1);
+            mbar::init(s_empty0 + 8 * q, 1);
         }
-        mbar_init(s_accf, 1);
-        mbar_init(s_acce, 16);
-        mbar_init(s_done, 1);
+        mbar::init(s_accf, 1);
+        mbar::init(s_acce, 16);
+        mbar::init(s_done, 1);
         for (int q = 0; q < TQ; ++q) {
-            mbar_init(smem_u32(&sh.tfull[q]), 1);
-            mbar_init(smem_u32(&sh.tempty[q]), 2);   // MMA lane + drain
+            mbar::init(mbar::smem_u32(&sh.tfull[q]), 1);
+            mbar::init(mbar::smem_u32(&sh.tempty[q]), 2);   // MMA lane + drain
         }
         sh.abort = 0;
         sh.dabort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;");
+        mbar::fence_init();
         asm volatile("fence.proxy.async.shared::cta;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = sh.tmem;
-    const uint32_t stage_base = smem_u32(dsm);
+    const uint32_t stage_base = mbar::smem_u32(dsm);
 
     // Every role takes the items in ticket order and keeps its pipeline
     // counters running across items, so the mbarrier phases stay in step.
@@ -200,7 +163,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             for (int nt = 0; !*(volatile int *)&sh.abort; ++nt) {
                 // draw a ticket and publish it
                 const int ts = nt % TQ;
-                if (nt >= TQ && !mbar_wait(smem_u32(&sh.tempty[ts]), ((nt / TQ) - 1) & 1)) {
+                if (nt >= TQ && !mbar::wait(mbar::smem_u32(&sh.tempty[ts]), ((nt / TQ) - 1) & 1)) {
                     atomicExch(a.err, 17);
                     sh.abort = 1;
                     break;
@@ -208,7 +171,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                 int w = atomicAdd(a.ticket, 1);
                 if (w >= a.n_items) w = -1;
                 sh.tick[ts] = w;
-                mbar_arrive(smem_u32(&sh.tfull[ts]));
+                mbar::arrive(mbar::smem_u32(&sh.tfull[ts]));
                 if (w < 0) break;
                 const MxItem it = a.items[w];
                 const MxJob &J = a.jobs[it.job];
@@ -218,24 +181,24 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                 for (int kb = it.kb_lo; kb <= it.kb_hi; ++kb, ++n) {
                     if (*(volatile int *)&sh.abort) break;
                     const int s = n % NST, u = n / NST;
-                    if (u > 0 && !mbar_wait(s_empty0 + 8 * s, (u - 1) & 1)) {
+                    if (u > 0 && !mbar::wait(s_empty0 + 8 * s, (u - 1) & 1)) {
                         atomicExch(a.err, 11);
                         sh.abort = 1;
                         break;
                     }
                     const uint32_t fb = s_full0 + 8 * s;
-                    mbar_expect_tx(fb, STAGE);
+                    mbar::expect_tx(fb, STAGE);
                     const uint8_t *asrc = Ab + (long long)(kb - L.fA * it.b) * S * IMG;
                     const uint8_t *bsrc = a.Bimg + mx_b_off(L, it.pi, beta, it.c, kb, 0);
                     const uint32_t dst = stage_base + s * STAGE;
-                    bulk_g2s(dst, asrc, S * IMG, fb);
-                    bulk_g2s(dst + S * IMG, bsrc, S * IMG, fb);
+                    mbar::copy_g2s(dst, asrc, S * IMG, fb);
+                    mbar::copy_g2s(dst + S * IMG, bsrc, S * IMG, fb);
                 }
             }
             // wait (bounded) for the copies still in flight before the CTA may exit
             for (int q = n - NST; q < n; ++q) {
                 if (q < 0) continue;
-                if (!mbar_wait(s_full0 + 8 * (q % NST), (q / NST) & 1)) atomicExch(a.err, 12);
+                if (!mbar::wait(s_full0 + 8 * (q % NST), (q / NST) & 1)) atomicExch(a.err, 12);
             }
         }
     } else if (warp == 1) {
@@ -247,13 +210,13 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             bool started[4] = {false, false, false, false};
             for (int nt = 0; !*(volatile int *)&sh.abort; ++nt) {
                 const int ts = nt % TQ;
-                if (!mbar_wait(smem_u32(&sh.tfull[ts]), (nt / TQ) & 1)) {
+                if (!mbar::wait(mbar::smem_u32(&sh.tfull[ts]), (nt / TQ) & 1)) {
                     atomicExch(a.err, 18);
                     sh.abort = 1;
                     break;
                 }
                 const int w = *(volatile int *)&sh.tick[ts];
-                mbar_arrive(smem_u32(&sh.tempty[ts]));
+                mbar::arrive(mbar::smem_u32(&sh.tempty[ts]));
                 if (w < 0) break;
                 const MxItem it = a.items[w];
                 for (int kb = it.kb_lo; kb <= it.kb_hi; ++kb, ++n) {
@@ -261,7 +224,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                     const bool sfirst = (kb == it.kb_lo) || (kb % KPS == 0);
                     const bool slast = (kb == it.kb_hi) || (kb % KPS == KPS - 1);
                     if (sfirst) {
-                        if (m > 0 && !mbar_wait(s_acce, (m - 1) & 1)) {
+                        if (m > 0 && !mbar::wait(s_acce, (m - 1) & 1)) {
                             atomicExch(a.err, 13);
                             sh.abort = 1;
                             break;
@@ -269,7 +232,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                         started[0] = started[1] = started[2] = started[3] = false;
                     }
                     const int s = n % NST;
-                    if (!mbar_wait(s_full0 + 8 * s, (n / NST) & 1)) {
+                    if (!mbar::wait(s_full0 + 8 * s, (n / NST) & 1)) {
                         atomicExch(a.err, 14);
                         sh.abort = 1;
                         break;
@@ -300,7 +263,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             }
             // all issued MMAs complete before TMEM is released
             umma_commit(s_done);
-            if (!mbar_wait(s_done, 0)) atomicExch(a.err, 15);
+            if (!mbar::wait(s_done, 0)) atomicExch(a.err, 15);
         }
     } else {
         // ------------------------------------------------------------ drain
@@ -314,7 +277,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
         int m = 0;
         for (int nt = 0;; ++nt) {
             const int ts = nt % TQ;
-            const bool tok = !*(volatile int *)&sh.abort && mbar_wait(smem_u32(&sh.tfull[ts]), (nt / TQ) & 1);
+            const bool tok = !*(volatile int *)&sh.abort && mbar::wait(mbar::smem_u32(&sh.tfull[ts]), (nt / TQ) & 1);
             if (!tok) sh.dabort = 1;
             const int w = *(volatile int *)&sh.tick[ts];
             // (T): every drain thread has read the ticket; the abort decision is uniform
@@ -327,7 +290,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                 break;
             }
             if (w < 0) break;
-            if (dtid == 0) mbar_arrive(smem_u32(&sh.tempty[ts]));
+            if (dtid == 0) mbar::arrive(mbar::smem_u32(&sh.tempty[ts]));
             bool stop = false;
             const MxItem it = a.items[w];
             const MxJob &J = a.jobs[it.job];
@@ -359,7 +322,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                 }
                 const float fa = pow2_or_zero((int)eArow[sb] - emA);
                 const float2 fa2 = make_float2(fa, fa);
-                const bool ok = !*(volatile int *)&sh.abort && mbar_wait(s_accf, m & 1);
+                const bool ok = !*(volatile int *)&sh.abort && mbar::wait(s_accf, m & 1);
                 if (!ok) sh.dabort = 1;
                 // (A): column exponents visible; the abort decision is the same for all drain threads
                 asm volatile("bar.sync 1, 512;" ::: "memory");
@@ -401,7 +364,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(s_acce);
+                if (lane == 0) mbar::arrive(s_acce);
                 // (B): every drain thread is done with the column exponents
                 asm volatile("bar.sync 1, 512;" ::: "memory");
                 ++m;

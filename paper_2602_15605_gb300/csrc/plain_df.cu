@@ -151,7 +151,12 @@ __global__ void __launch_bounds__(NT, 1) k_plain_df(const PlainArgs pa) {
     const float2 *__restrict__ hdf = pa.hdf;
     const int cap = p.l3cap[win];
     const int tid = threadIdx.x, lane = tid & 31;
-    const int tx = tid & 15, ty = tid >> 4;
+    // warp blocks of 16 x 8 pairs (rows ar, ar + 8, columns bc, bc + 4 per
+    // thread) with their own k ranges, as in the tabled FP64 kernel: the two
+    // warps of a sub-partition take opposite row halves and column quarters
+    const int warp = tid >> 5;
+    const int wh = warp >> 2, wq = wh ? 3 - (warp & 3) : (warp & 3);
+    const int ar = 16 * wh + (lane >> 2), bc = 8 * wq + (lane & 3);
 
     const int kcap_e = (cap - pi) >> 1;
     const int kcap_o = (cap - 1 + pi) >> 1;
@@ -160,6 +165,13 @@ __global__ void __launch_bounds__(NT, 1) k_plain_df(const PlainArgs pa) {
     int k_lo = i0, k_hi = -1;
     if (NGE > 0) k_hi = khi_e;
     if (ODD) k_hi = max(k_hi, khi_o);
+    // this warp's k range; none when its block holds no valid pair (the
+    // steps outside it multiply exact zeros)
+    const int wi0 = i0 + 16 * wh, wj1 = j0 + 8 * wq + 7;
+    int wk_hi = -1;
+    if (NGE > 0) wk_hi = min(wj1, kcap_e);
+    if (ODD) wk_hi = max(wk_hi, min(wj1 - 1 + pi, kcap_o));
+    if (max(j0 + 8 * wq, wi0 + p.lmin) > min(wj1, p.lmax - pi - wi0)) wk_hi = -1;
 
     // tile scale 2^-E: E from the largest |A| over the tile's l3 range
     {
@@ -256,26 +268,26 @@ __global__ void __launch_bounds__(NT, 1) k_plain_df(const PlainArgs pa) {
             }
         }
         __syncthreads();
-        const int kn = min(KC, k_hi - kb + 1);
+        const int kk0 = max(0, wi0 - kb), kk1 = min(min(KC, k_hi - kb + 1), wk_hi - kb + 1);
         float2 ch[NG][2], cl[NG][2];
 #pragma unroll
         for (int q = 0; q < NG; ++q)
 #pragma unroll
             for (int r = 0; r < 2; ++r) ch[q][r] = cl[q][r] = make_float2(0.f, 0.f);
-        for (int kk = 0; kk < kn; ++kk) {
+        for (int kk = kk0; kk < kk1; ++kk) {
             float2 ah[S::NA > 0 ? S::NA : 1][2], al[S::NA > 0 ? S::NA : 1][2];
             float2 bh[S::NB > 0 ? S::NB : 1], bl[S::NB > 0 ? S::NB : 1];
 #pragma unroll
             for (int q = 0; q < S::NA; ++q)
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    const float2 x = sa[q][kk][ty + 16 * r];
+                    const float2 x = sa[q][kk][ar + 8 * r];
                     ah[q][r] = make_float2(x.x, x.x);
                     al[q][r] = make_float2(x.y, x.y);
                 }
 #pragma unroll
             for (int q = 0; q < S::NB; ++q) {
-                const float2 x0 = sb[q][kk][tx], x1 = sb[q][kk][tx + 16];
+                const float2 x0 = sb[q][kk][bc], x1 = sb[q][kk][bc + 4];
                 bh[q] = make_float2(x0.x, x1.x);
                 bl[q] = make_float2(x0.y, x1.y);
             }
@@ -312,7 +324,7 @@ __global__ void __launch_bounds__(NT, 1) k_plain_df(const PlainArgs pa) {
     for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+            const int i = i0 + ar + 8 * r, j = j0 + bc + 4 * c;
             const int l1 = j - i, l2 = i + j + pi;
             if (l1 < p.lmin || l2 > p.lmax || l1 > l2) continue;
             double acc[NG];
