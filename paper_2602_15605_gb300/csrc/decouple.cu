@@ -612,13 +612,9 @@ __global__ void __launch_bounds__(DC_THREADS, 1) k_decouple(DecoupleArgs a) {
 int decouple_smem_limit() { return 226 * 1024; }   // dynamic part; the static Scratch fits in the rest
 
 cudaError_t launch_decouple(const DecoupleArgs &a, int grid, size_t smem, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_decouple, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             decouple_smem_limit());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = opt_in_smem(k_decouple, decouple_smem_limit(), attr);
+    if (e != cudaSuccess) return e;
     k_decouple<<<grid, DC_THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -1,6 +1,7 @@
 // internal.h -- shared declarations of the coupling library (not installed).
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -147,6 +148,21 @@ struct DecoupleArgs {
     double *ws;             // global workspace, ws_stride doubles per CTA (NULL when unused)
     size_t ws_stride;
 };
+
+// Opts kernel fn into `bytes` of dynamic shared memory on the current
+// device.  The attribute belongs to the function on one device, so it is set
+// once per device (bit d of `done`; devices beyond 63 set it on every call).
+template <class F>
+cudaError_t opt_in_smem(F *fn, int bytes, std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_relaxed);
+    return e;
+}
 
 #ifdef __CUDACC__
 #define CPL_HD __host__ __device__

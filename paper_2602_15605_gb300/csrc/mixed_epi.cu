@@ -454,13 +454,9 @@ cudaError_t mx_launch_epilogue(const MxEpiArgs &a, cudaStream_t st) {
         return cudaGetLastError();
     }
     dim3 grid((a.lmax + 1 + EB_J - 1) / EB_J, NI / EB_I);
-    static bool attr = false;   // the attribute is per function; set once per process
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_mixed_epilogue_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)sizeof(EpiSmem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = opt_in_smem(k_mixed_epilogue_dense, (int)sizeof(EpiSmem), attr);
+    if (e != cudaSuccess) return e;
     k_mixed_epilogue_dense<<<grid, EB_T, sizeof(EpiSmem), st>>>(a);
     return cudaGetLastError();
 }

@@ -515,12 +515,9 @@ template <int NGE, bool ODD>
 static cudaError_t launch_tab(const PlainArgs &a, cudaStream_t st) {
     using S = Shape<NGE, ODD>;
     const int smem = 2 * (S::NA + S::NB) * PT_BLK * (int)sizeof(double);
-    static bool attr = false;   // per variant; the attribute is per function and device-independent here
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_plain_tab<NGE, ODD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};   // per variant
+    const cudaError_t e = opt_in_smem(k_plain_tab<NGE, ODD>, smem, attr);
+    if (e != cudaSuccess) return e;
     k_plain_tab<NGE, ODD><<<a.n_items, NT, smem, st>>>(a);
     return cudaGetLastError();
 }
