@@ -2,8 +2,8 @@
 
 Bar: per-element relative error (against S_abs) <= 1e-11 for every
 spectrum; elements that are zero by parity or band exactly 0.0.  Sizes span
-several 32 x 32 tiles with ragged tails; the full-size l_max = 3000 case is
-checked on sampled pairs, and identities that hold at any size (full sky,
+several 32 x 32 tiles with ragged tails; the full-size l_max = 3000 case and
+an l_max = 10000 build are checked on sampled pairs, and identities that hold at any size (full sky,
 constant window) are checked on whole matrices.
 """
 import math
@@ -223,3 +223,28 @@ def test_batch_mixed_variants_band_and_bins(ctx):
     e = oracle.bin_edges(2, 150, 20)
     errs = per_spectrum(outs[2].cpu().numpy(), oracle.bin_matrix(ref, 2, e), oracle.bin_matrix(sab, 2, e), ["TE", "EEBB"])
     assert max(errs.values()) <= 1e-11, errs
+
+
+def test_lmax_10000_separate_windows_sampled(ctx):
+    """The tabled kernel at l_max = 10000 (operand tables of ~7 GB, 64-bit
+    block offsets) with three separate windows, so that all three kernel
+    variants run: sampled pairs against the oracle, every spectrum, including
+    the last row and near-diagonal pairs."""
+    import torch
+    lmax = 10000
+    W = windows.ragged_jobs(lmaxes=(lmax,), n_win=3, seed0=900)[0][1]
+    M = ctx.build(lmax, dev(W[0]), dev(W[1]), dev(W[2]), coupling.ALL)
+    rng = np.random.default_rng(11000)
+    d = rng.integers(2, lmax - 2, size=120)
+    P = np.concatenate([rng.integers(2, lmax + 1, size=(900, 2)),
+                        np.stack([np.full(120, lmax), rng.integers(2, lmax + 1, size=120)], axis=1),
+                        np.stack([d, d + rng.integers(0, 3, size=120)], axis=1)]).astype(np.int32)
+    l1, l2 = P[:, 0], P[:, 1]
+    got = M[:, :, torch.as_tensor(l1 - 2, device="cuda"), torch.as_tensor(l2 - 2, device="cuda")].cpu().numpy()
+    del M
+    torch.cuda.empty_cache()
+    assert np.all(np.isfinite(got))
+    ref, sab = oracle.coupling_pairs(l1, l2, W[0], W[1], W[2], coupling.ALL)
+    errs = per_spectrum(got, ref, sab, ALLN)
+    print("fp64 10000 sampled vs oracle:", errs)
+    assert max(errs.values()) <= TOL
