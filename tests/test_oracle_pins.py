@@ -167,13 +167,28 @@ def _mp000(j1, j2, j3):
     return (-1) ** ((J // 2) % 2) * mp.sqrt(mp.mpf(sq.numerator) / mp.mpf(sq.denominator))
 
 
-def _paper_022(j1, j2, j3):
+def _mp000_lg(j1, j2, j3):
+    """The same as _mp000 from log-gamma values of Eq. 000_sq_main's
+    factorials (fast at large j; 40 digits)."""
+    J = j1 + j2 + j3
+    if J % 2 or j3 < abs(j1 - j2) or j3 > j1 + j2:
+        return mp.mpf(0)
+    g = J // 2
+    lf = lambda n: mp.loggamma(n + 1)
+    sq = mp.exp(lf(J - 2 * j1) + lf(J - 2 * j2) + lf(J - 2 * j3) - lf(J + 1)
+                + 2 * (lf(g) - lf(g - j1) - lf(g - j2) - lf(g - j3)))
+    return (-1) ** (g % 2) * mp.sqrt(sq)
+
+
+def _paper_022(j1, j2, j3, f000=None):
     """(j1 j2 j3; 0 -2 2) from the paper's Appendix B at 40 digits.
 
     Even J: Eq. 022_linear_closedform with alpha, beta of App. B.3.
     Odd J: Eq. 022_rearranged with the (0,-1,1) symbols of Eq. joneodd
     (at j3) and Eq. joneevenshifted (at j3 + 1); the (0 0 0) term vanishes.
+    f000 evaluates (0 0 0) symbols (default: the exact closed form).
     """
+    _mp000 = f000 or globals()["_mp000"]
     J = j1 + j2 + j3
     Jm, Jp, Jq = -j1 + j2 + j3, j1 - j2 + j3, j1 + j2 - j3
     lam = mp.sqrt(mp.mpf(j2 * (j2 + 1) * (j3 + 1) * (j3 + 2)))
@@ -211,6 +226,39 @@ def test_oracle_pol_large_l_vs_paper_appendix_b():
             scale = float(mp.sqrt(1 / mp.mpf(2 * max(l1, l2) + 1)))
             worst = max(worst, abs(col[l3 - jmin] - float(ref)) / scale)
     assert worst < 1e-12
+
+
+def test_oracle_pol_diagonal_small_odd_j_large_l():
+    # On the diagonal (j2 = j3) the recursion's lower end is j = 0, where the
+    # odd-j symbols are smallest; relative accuracy there, against App. B at
+    # 40 digits and the closed forms of (0 l l; 0 m -m) and (1 l l; 0 m -m)
+    mp.mp.dps = 40
+    for l in (5000, 12000, 20000, 30000):
+        jmin, col = oracle.threej_column(l, l, 0, -2, 2)
+        assert jmin == 0
+        sgn = -1.0 if l % 2 else 1.0                      # (-1)^(l - m), m = -2
+        assert abs(col[0] / (sgn / math.sqrt(2 * l + 1)) - 1.0) < 1e-12
+        assert abs(col[1] / (sgn * -2.0 / math.sqrt(l * (l + 1.0) * (2 * l + 1))) - 1.0) < 1e-12
+        for j in (3, 5):
+            ref = float(_paper_022(j, l, l))
+            assert abs(col[j] / ref - 1.0) < 1e-12, (l, j, col[j], ref)
+
+
+def test_oracle_eebb_diagonal_element_vs_40_digits():
+    # A whole l3 sum where the odd-j symbols carry the weight: M^EEBB(l, l)
+    # with a mask-like window (weight concentrated at small l3), against the
+    # App. A sum evaluated with App. B's symbols at 40 digits
+    mp.mp.dps = 40
+    lmax, l = 10000, 9000
+    W = windows.mask_like(lmax, seed=lmax)
+    ref, _ = oracle.coupling_pairs(np.array([l], np.int32), np.array([l], np.int32), W, W, W, oracle.EEBB)
+    tot = mp.mpf(0)
+    for l3 in range(1, 2 * l + 1, 2):   # odd L = 2 l + l3
+        if W[l3] == 0.0:
+            continue
+        tot += (2 * l3 + 1) * mp.mpf(W[l3]) * _paper_022(l3, l, l, f000=_mp000_lg) ** 2
+    want = (2 * l + 1) * tot / (4 * mp.pi)
+    assert abs(float(ref[0, 0, 0] / want) - 1.0) < 1e-12
 
 
 def _paper_011(j1, j2, j3):
