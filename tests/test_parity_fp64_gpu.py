@@ -248,3 +248,37 @@ def test_lmax_10000_separate_windows_sampled(ctx):
     errs = per_spectrum(got, ref, sab, ALLN)
     print("fp64 10000 sampled vs oracle:", errs)
     assert max(errs.values()) <= TOL
+
+
+def _sampled_large(ctx, lmax, spectra, seed, n_random=400, n_edge=60):
+    import torch
+    W = windows.mask_like(lmax, seed=seed)
+    M = ctx.build(lmax, dev(W), dev(W), dev(W), spectra)
+    rng = np.random.default_rng(seed)
+    d = rng.integers(2, lmax - 2, size=n_edge)
+    P = np.concatenate([rng.integers(2, lmax + 1, size=(n_random, 2)),
+                        np.stack([np.full(n_edge, lmax), rng.integers(2, lmax + 1, size=n_edge)], axis=1),
+                        np.stack([d, d], axis=1),
+                        np.stack([d, d + rng.integers(1, 3, size=n_edge)], axis=1)]).astype(np.int32)
+    l1, l2 = P[:, 0], P[:, 1]
+    got = M[:, :, torch.as_tensor(l1 - 2, device="cuda"), torch.as_tensor(l2 - 2, device="cuda")].cpu().numpy()
+    del M
+    torch.cuda.empty_cache()
+    assert np.all(np.isfinite(got))
+    ref, sab = oracle.coupling_pairs(l1, l2, W, W, W, spectra)
+    return per_spectrum(got, ref, sab, names(spectra))
+
+
+def test_lmax_20000_polarisation_sampled(ctx):
+    # EE and EE->BB (the spectrum whose odd sweep cancels the most) at
+    # l_max = 20000: sampled pairs incl. the diagonal and the last row
+    errs = _sampled_large(ctx, 20000, coupling.EE | coupling.EEBB, seed=20000)
+    print("fp64 20000 sampled vs oracle:", errs)
+    assert max(errs.values()) <= TOL
+
+
+def test_lmax_32000_tt_sampled(ctx):
+    # the largest l_max the library accepts (operand tables ~50 GB)
+    errs = _sampled_large(ctx, 32000, coupling.TT, seed=32000)
+    print("fp64 32000 sampled vs oracle:", errs)
+    assert max(errs.values()) <= TOL
