@@ -154,7 +154,8 @@ cpl_status cpl_ctx_create(cpl_ctx **ctx, int device);
 cpl_status cpl_ctx_destroy(cpl_ctx *ctx);
 
 /* Wait for all work the context queued and report any device-side error
- * (CPL_ERR_TIMEOUT for an exceeded bounded wait, CPL_ERR_CUDA otherwise). */
+ * (CPL_ERR_TIMEOUT for an exceeded bounded wait, CPL_ERR_CUDA otherwise,
+ * including an internal inconsistency a kernel detected). */
 cpl_status cpl_ctx_sync(cpl_ctx *ctx);
 
 /*
@@ -173,6 +174,16 @@ cpl_status cpl_output_size(const cpl_request *r, size_t *n_doubles);
  * order of r->spectra.  Binned layout: out[w][spec][b][b'].  Elements that
  * the parity selection or the band limit make exactly zero are written as
  * exactly 0.0.  The W_* pointers are device pointers.
+ *
+ * Memory: CPL_FP64 builds read precomputed operand blocks of the separable
+ * l3 contractions (Sec. 3.1 tables times the integer polarisation factors):
+ * a window-independent part cached in the context (about 48 lmax^2 bytes,
+ * kept for the largest lmax seen: 0.43 GB at lmax 3000, 4.7 GB at 10000)
+ * and a per-call part (about 28 lmax^2 bytes per window with all spectra,
+ * less with a band limit).  When both together would exceed half of the
+ * device's free memory, or the environment variable CPL_PLAIN_TABLES is
+ * "0", the kernels build the operands themselves instead (same results,
+ * bit for bit; about 10% slower).
  */
 cpl_status cpl_build(cpl_ctx *ctx, const cpl_request *r, double *out, void *stream);
 

@@ -773,11 +773,11 @@ cpl_status cpl_ctx_sync(cpl_ctx *c) {
         if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
         if (code != 0) {
             cudaMemset(c->mx.err.ptr, 0, sizeof(int));
-            const bool plain = code == PT_ERR_RANGE || code == PT_ERR_WAIT;
-            return fail(CPL_ERR_TIMEOUT, std::string(plain ? code == PT_ERR_RANGE
-                                                                 ? "the tabled FP64 kernel found a tile outside its operand tables"
-                                                                 : "a bounded wait of the tabled FP64 kernel ran out"
-                                                           : "a bounded device wait of the tensor-core kernel ran out") +
+            if (code == PT_ERR_RANGE)
+                return fail(CPL_ERR_CUDA, "internal error: the tabled FP64 kernel found a tile outside its operand "
+                                          "tables (code " + std::to_string(code) + ")");
+            return fail(CPL_ERR_TIMEOUT, std::string(code == PT_ERR_WAIT ? "a bounded wait of the tabled FP64 kernel ran out"
+                                                                         : "a bounded device wait of the tensor-core kernel ran out") +
                                              " (code " + std::to_string(code) + ")");
         }
     }
