@@ -119,49 +119,22 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
     }
 }
 
-// Variant q alone (same definitions as a_values).
-__device__ __forceinline__ dfl a_value(const MxPrepAArgs &a, const float *Ah, const float *Al, const int *Ae,
-                                       int cap, int i, int k, int pi, int q, int *vex) {
-    *vex = EXP_ZERO;
-    if (q < 3) {
-        const int l3e = 2 * k + pi;
-        if (!(k >= i && l3e <= cap && Ah[l3e] != 0.f) || (q > 0 && k == i)) return {0.f, 0.f};
-        const dfl A = {Ah[l3e], Al[l3e]};
-        const dfl g1 = {a.gh[i + k + pi], a.gl[i + k + pi]};
-        const dfl g2 = {a.gh[k - i], a.gl[k - i]};
-        dfl x = df_mul(df_mul(A, g1), g2);
-        if (q > 0) {
-            const dfl v = df_int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
-            x = df_mul(x, v);
-            if (q > 1) x = df_mul(x, v);
-        }
-        if (x.h != 0.f) *vex = value_exp(x, Ae[l3e]);
-        return x;
-    }
-    const int l3o = 2 * k + 1 - pi;
-    if (!(k >= i + pi && l3o <= cap && Ah[l3o] != 0.f)) return {0.f, 0.f};
-    const dfl A = {Ah[l3o], Al[l3o]};
-    const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
-    const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
-    const dfl v1 = df_int_prod(2 * i + 2 * k + 2, 2 * k + 1 - 2 * i - 2 * pi);
-    const dfl x = df_mul(df_mul(df_mul(A, g1), g2), v1);
-    if (x.h != 0.f) *vex = value_exp(x, Ae[l3o]);
-    return x;
-}
-
 // One block per (parity, row group, row block, octet of 8 tile rows): the 8
 // rows belong to one source (BI >= 8) and are 8 consecutive values of i.
 // Thread (warp w, lane) owns tile row 8 o + (lane & 7) and the 8 consecutive
 // k = sb MX_SB + 32 w + 8 (lane >> 3) + 0..7 of each scale block sb, so that
 // for every limb it writes one 16-byte core-matrix row and each warp writes
-// whole 128-byte core matrices.  Pass 1 finds the row maxima of the
-// exponents (shuffles over the 4 lanes of a row, then shared memory over the
-// 8 warps), pass 2 recomputes the values and writes the limbs.
+// whole 128-byte core matrices.  Pass 1 computes the values, keeps them in
+// shared memory (each thread its own 8 x 4 slots) and finds the row maxima
+// of the exponents (shuffles over the 4 lanes of a row, then shared memory
+// over the 8 warps); pass 2 writes the limbs of the kept values.
 template <int S>
 __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     constexpr int NW = 256 / 32;
     static_assert(MX_SB == 32 * NW, "one scale block per pass of the block");
     __shared__ int wmax[2][NW][8][MX_NA];
+    extern __shared__ float2 kept[];                        // [8 m][MX_NA][256]: values of pass 1
+    int *kept_ex = reinterpret_cast<int *>(kept + 8 * MX_NA * 256);   // [8 m][MX_NA][256]: their exponents
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int q8 = lane & 7, kg = lane >> 3;
     const MxLayout &L = a.L;
@@ -201,7 +174,11 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
             int vex[MX_NA];
             a_values(a, Ah, Al, Ae, cap, i, k0 + m, pi, val, vex);
 #pragma unroll
-            for (int q = 0; q < MX_NA; ++q) bmax[q] = max(bmax[q], vex[q]);
+            for (int q = 0; q < MX_NA; ++q) {
+                bmax[q] = max(bmax[q], vex[q]);
+                kept[(m * MX_NA + q) * 256 + tid] = make_float2(val[q].h, val[q].l);
+                kept_ex[(m * MX_NA + q) * 256 + tid] = vex[q];
+            }
         }
         const int buf = sb & 1;
 #pragma unroll
@@ -230,8 +207,9 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
             uint32_t pk[S][4];
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                int vex;
-                const dfl val = a_value(a, Ah, Al, Ae, cap, i, k0 + m, pi, q, &vex);
+                const float2 kv = kept[(m * MX_NA + q) * 256 + tid];
+                const dfl val = {kv.x, kv.y};
+                const int vex = kept_ex[(m * MX_NA + q) * 256 + tid];
                 dfl y = {0.f, 0.f};
                 if (vex != EXP_ZERO && E[q] != EXP_ZERO) {
                     // y = x 2^(7 - E) with x = val 2^(weight exponent): shift = vex - ilogb - 1 + 7 - E
@@ -358,10 +336,22 @@ cudaError_t mx_launch_prep_a(const MxPrepAArgs &a, cudaStream_t st) {
     if (octets == 0) return cudaSuccess;
     if (a.L.BI < 8 || a.L.KB % 8 != 0) return cudaErrorInvalidValue;
     const int blocks = (int)octets;
+    const int smem = 8 * MX_NA * 256 * (int)(sizeof(float2) + sizeof(int));   // the kept values
+    static std::atomic<unsigned long long> attr[3];
+    cudaError_t e;
     switch (a.L.S) {
-        case 4: k_prep_a<4><<<blocks, 256, 0, st>>>(a); break;
-        case 5: k_prep_a<5><<<blocks, 256, 0, st>>>(a); break;
-        case 6: k_prep_a<6><<<blocks, 256, 0, st>>>(a); break;
+        case 4:
+            if ((e = opt_in_smem(k_prep_a<4>, smem, attr[0])) != cudaSuccess) return e;
+            k_prep_a<4><<<blocks, 256, smem, st>>>(a);
+            break;
+        case 5:
+            if ((e = opt_in_smem(k_prep_a<5>, smem, attr[1])) != cudaSuccess) return e;
+            k_prep_a<5><<<blocks, 256, smem, st>>>(a);
+            break;
+        case 6:
+            if ((e = opt_in_smem(k_prep_a<6>, smem, attr[2])) != cudaSuccess) return e;
+            k_prep_a<6><<<blocks, 256, smem, st>>>(a);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
