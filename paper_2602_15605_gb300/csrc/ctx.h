@@ -80,6 +80,8 @@ struct MixedState {
     DevBuf arena;                // per-job scratch of the running chunk (A images, weights, GEMM output)
     DevBuf ticket;               // work-item ticket of the persistent GEMM
     DevBuf err;                  // device error word of the bounded waits
+    DevBuf coef;                 // per-l factors of the pair coefficients (MX_COEF_N per l, extended double-float)
+    int coef_n = 0;              // l < coef_n covered
     std::vector<std::unique_ptr<MxPlan, MxPlanDeleter>> plans;   // cached plans (LRU)
     unsigned long long clock = 0;
     int nsm = 0;

@@ -110,6 +110,7 @@ struct xdf {
     float h, l;
     int e;
 };
+static_assert(sizeof(xdf) == 12, "xdf tables are written by the host as three 32-bit words");
 
 __device__ __forceinline__ xdf xdf_make(dfl m, int e) {
     if (m.h == 0.0f) return {0.0f, 0.0f, 0};

@@ -147,8 +147,17 @@ struct MxEpiArgs {
     const int *bin_of;
     const double *bin_inv;
     const double *bin_lw;          // [2][lmax + 1] l(l+1) and its inverse (D_l band powers), NULL: flat
+    const void *coef;              // [l][MX_COEF_N] per-l factors of the pair coefficients: {float h, l; int e}
     MxLayout L;
 };
+
+// Per-l factors of the pair coefficients (lambda/eta, c0, c1, c2, C, e0, e1 of
+// plain_fp64.cu are products of a function of l1 and a function of l2):
+// MX_COEF_A factors of l1, then MX_COEF_B factors of l2.
+constexpr int MX_COEF_A = 9, MX_COEF_B = 12, MX_COEF_N = MX_COEF_A + MX_COEF_B;
+// Host build of the factors for l < n into out[n * MX_COEF_N * 3] (h, l as
+// float bits, e), from FP64 (53 bits; the extended double-float holds 48).
+void mx_coef_host(int n, std::vector<uint32_t> &out);
 
 struct MxBandArgs {   // double-float evaluation of the pairs with l1 < MX_L1_FP64
     const float *gh, *gl, *hh, *hl;   // g and h as FP32 pairs

@@ -7,9 +7,9 @@
 // the GEMM's double-float outputs with their power-of-two frames; the pair
 // coefficients (lambda/eta, c0, c1, c2, e0, e1, C of plain_fp64.cu) are
 // formed once per pair in extended double-float (FP32 pairs with an integer
-// exponent), and the spectra are combined in that form and converted to
-// FP64 with integer operations (the binned variant then applies the
-// (2l+1) / |bin| weights in FP64).
+// exponent) as products of per-l factors, and the spectra are combined in
+// that form and converted to FP64 with integer operations (the binned
+// variant then applies the (2l+1) / |bin| weights in FP64).
 //
 // k_mixed_band: pairs with l1 < MX_L1_FP64 outside the GEMM.  For them the
 // polynomial expansion of the polarisation factor cancels by up to two
@@ -29,34 +29,25 @@ __device__ __forceinline__ bool mx_alpha_used(int v, int np) {
     return v == 0 || (v == 1 && np > 2) || (v == 2 && np > 4) || (v == 3 && np > 6);
 }
 
-// Pair coefficients of the spectra (exact integer inputs), in the order
-// TE[0..2], EE[0..5], EE->BB[0..2] (see plain_fp64.cu for the formulas).
-__device__ __forceinline__ void pair_coeffs(int l1, int l2, xdf (&qTE)[3], xdf (&qEE)[6], xdf (&qB)[3]) {
-    // integer factors below 2^31 combined in double-float (no 64-bit conversions)
-    const xdf eta2 = xdf_int_mul((l1 - 1) * (l1 + 2), (l2 - 1) * l2);
-    const xdf lam2 = xdf_int_mul(l1 * (l1 + 1), (l2 + 1) * (l2 + 2));
-    const xdf r2 = xdf_mul(lam2, xdf_recip(eta2));
-    const xdf r = xdf_sqrt(r2);
-    const xdf c1 = xdf_recip(xdf_int_mul(l1 * (l1 + 1), l2 + 1));
-    const xdf c0 = xdf_mul(xdf_from_int(l1 + 2), xdf_recip(xdf_from_int(l1)));
-    const xdf inv2l2p2 = xdf_recip(xdf_from_int(2 * (l2 + 2)));
-    const xdf c2 = xdf_mul(c1, inv2l2p2);
-    const xdf two = xdf_from_int(2);
-    qTE[0] = xdf_mul(r, c0);
-    qTE[1] = xdf_neg(xdf_mul(r, c1));
-    qTE[2] = xdf_neg(xdf_mul(r, c2));
-    qEE[0] = xdf_mul(r2, xdf_mul(c0, c0));
-    qEE[1] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c1))));
-    qEE[2] = xdf_neg(xdf_mul(r2, xdf_mul(two, xdf_mul(c0, c2))));
-    qEE[3] = xdf_mul(r2, xdf_mul(c1, c1));
-    qEE[4] = xdf_mul(r2, xdf_mul(two, xdf_mul(c1, c2)));
-    qEE[5] = xdf_mul(r2, xdf_mul(c2, c2));
-    const xdf e0 = xdf_from_int(l1 + 2);
-    const xdf e1 = inv2l2p2;
-    const xdf Cc = xdf_mul(xdf_mul(xdf_from_int(l2 + 2), c1), xdf_recip(eta2));
-    qB[0] = xdf_mul(Cc, xdf_mul(e0, e0));
-    qB[1] = xdf_neg(xdf_mul(Cc, xdf_mul(two, xdf_mul(e0, e1))));
-    qB[2] = xdf_mul(Cc, xdf_mul(e1, e1));
+// Pair coefficients of the spectra in the order TE[0..2], EE[0..5],
+// EE->BB[0..2] (the formulas of plain_fp64.cu): each is the product of a
+// factor of l1 and a factor of l2 from the per-l table (mx_coef_host).
+__device__ __forceinline__ void pair_coeffs(const void *coef, int l1, int l2, xdf (&qTE)[3], xdf (&qEE)[6],
+                                            xdf (&qB)[3]) {
+    const xdf *T1 = reinterpret_cast<const xdf *>(coef) + (size_t)l1 * MX_COEF_N;
+    const xdf *T2 = reinterpret_cast<const xdf *>(coef) + (size_t)l2 * MX_COEF_N + MX_COEF_A;
+    qTE[0] = xdf_mul(T1[0], T2[0]);                 //  r c0
+    qTE[1] = xdf_neg(xdf_mul(T1[1], T2[1]));        // -r c1
+    qTE[2] = xdf_neg(xdf_mul(T1[1], T2[2]));        // -r c2
+    qEE[0] = xdf_mul(T1[2], T2[3]);                 //  r^2 c0^2
+    qEE[1] = xdf_neg(xdf_mul(T1[3], T2[4]));        // -2 r^2 c0 c1
+    qEE[2] = xdf_neg(xdf_mul(T1[3], T2[5]));        // -2 r^2 c0 c2
+    qEE[3] = xdf_mul(T1[4], T2[6]);                 //  r^2 c1^2
+    qEE[4] = xdf_mul(T1[5], T2[7]);                 //  2 r^2 c1 c2
+    qEE[5] = xdf_mul(T1[4], T2[8]);                 //  r^2 c2^2
+    qB[0] = xdf_mul(T1[6], T2[9]);                  //  C e0^2
+    qB[1] = xdf_neg(xdf_mul(T1[7], T2[10]));        // -2 C e0 e1
+    qB[2] = xdf_mul(T1[8], T2[11]);                 //  C e1^2
 }
 
 // Binned-output epilogue.  One thread per pair (parity, i, j), i fastest
@@ -75,7 +66,7 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
     if (b1 < 0 || b2 < 0) return;
 
     xdf qTE[3], qEE[6], qB[3];
-    pair_coeffs(l1, l2, qTE, qEE, qB);
+    pair_coeffs(a.coef, l1, l2, qTE, qEE, qB);
     const int b = i / L.BI, ii = i % L.BI, c = j / MX_BJ, cc = j % MX_BJ;
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const long long ncols = (long long)L.NC_B * MX_BJ;
@@ -211,7 +202,7 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
     // ---- coefficients of this thread's pair (TE[0..2], EE[3..8], EE->BB[9..11])
     if (valid) {
         xdf qTE[3], qEE[6], qB[3];
-        pair_coeffs(l1, l2, qTE, qEE, qB);
+        pair_coeffs(a.coef, l1, l2, qTE, qEE, qB);
         const xdf *c[12] = {&qTE[0], &qTE[1], &qTE[2], &qEE[0], &qEE[1], &qEE[2],
                             &qEE[3], &qEE[4], &qEE[5], &qB[0], &qB[1], &qB[2]};
 #pragma unroll

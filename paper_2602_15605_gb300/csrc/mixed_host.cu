@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -390,7 +391,8 @@ void make_chunks(MxPlan &P, size_t budget) {
 // Device pointers that the plan's kernel arguments and job tables contain.
 std::vector<const void *> baked_ptrs(cpl_ctx *c) {
     const MixedState &M = c->mx;
-    return {c->g.ptr, c->h.ptr, M.gdd.ptr, M.Bimg.ptr, M.eB.ptr, M.emaxB.ptr, M.arena.ptr, M.err.ptr, M.ticket.ptr};
+    return {c->g.ptr, c->h.ptr, M.gdd.ptr, M.Bimg.ptr, M.eB.ptr, M.emaxB.ptr, M.arena.ptr, M.err.ptr, M.ticket.ptr,
+            M.coef.ptr};
 }
 
 // Write the plan's metadata (per-job tables, item lists, job descriptors
@@ -565,6 +567,7 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             ea.bin_of = J.nb ? reinterpret_cast<const int *>(meta + J.m_bin_of) : nullptr;
             ea.bin_inv = J.nb ? reinterpret_cast<const double *>(meta + J.m_bin_inv) : nullptr;
             ea.bin_lw = J.bin_lw.empty() ? nullptr : reinterpret_cast<const double *>(meta + J.m_bin_lw);
+            ea.coef = M.coef.ptr;
             ea.L = J.L;
             {
                 const int idx = stat_index(c, "mixed_epilogue");
@@ -614,6 +617,39 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
 
 void MxPlanDeleter::operator()(MxPlan *p) const { delete p; }
 
+void mx_coef_host(int n, std::vector<uint32_t> &out) {
+    out.assign((size_t)n * MX_COEF_N * 3, 0u);
+    auto put = [&](size_t at, double x) {   // x = m 2^e with 1 <= |m| < 2, m as an FP32 pair
+        if (x == 0.0) return;
+        int k;
+        const double f = std::frexp(x, &k);   // x = f 2^k, 0.5 <= |f| < 1
+        const double m = 2.0 * f;
+        const float h = (float)m, l = (float)(m - (double)h);
+        std::memcpy(&out[3 * at], &h, 4);
+        std::memcpy(&out[3 * at + 1], &l, 4);
+        const int e = k - 1;
+        std::memcpy(&out[3 * at + 2], &e, 4);
+    };
+    for (int l = 2; l < n; ++l) {
+        const double L = l;
+        // l1 factors: rho = sqrt(l(l+1) / ((l-1)(l+2))) (lambda/eta = rho(l1) sigma(l2)),
+        // c0 = (l+2)/l, alpha = 1/(l(l+1)) (c1 = alpha beta), kappa = alpha / ((l-1)(l+2))
+        const double rho2 = L * (L + 1.0) / ((L - 1.0) * (L + 2.0)), rho = std::sqrt(rho2);
+        const double c0 = (L + 2.0) / L, al = 1.0 / (L * (L + 1.0)), ka = al / ((L - 1.0) * (L + 2.0));
+        const double A[MX_COEF_A] = {rho * c0, rho * al, rho2 * c0 * c0, 2.0 * rho2 * c0 * al, rho2 * al * al,
+                                     2.0 * rho2 * al * al, ka * (L + 2.0) * (L + 2.0), ka * (L + 2.0), ka};
+        // l2 factors: sigma = sqrt((l+1)(l+2) / ((l-1) l)), beta = 1/(l+1),
+        // beta' = 1/(2(l+1)(l+2)) (c2 = alpha beta'), mu = (l+2)/((l+1)(l-1) l) (C = kappa mu)
+        const double s2 = (L + 1.0) * (L + 2.0) / ((L - 1.0) * L), s = std::sqrt(s2);
+        const double be = 1.0 / (L + 1.0), bp = 1.0 / (2.0 * (L + 1.0) * (L + 2.0));
+        const double mu = (L + 2.0) / ((L + 1.0) * (L - 1.0) * L);
+        const double B[MX_COEF_B] = {s, s * be, s * bp, s2, s2 * be, s2 * bp, s2 * be * be, s2 * be * bp, s2 * bp * bp,
+                                     mu, mu / (L + 2.0), mu / (4.0 * (L + 2.0) * (L + 2.0))};
+        for (int q = 0; q < MX_COEF_A; ++q) put((size_t)l * MX_COEF_N + q, A[q]);
+        for (int q = 0; q < MX_COEF_B; ++q) put((size_t)l * MX_COEF_N + MX_COEF_A + q, B[q]);
+    }
+}
+
 // Shared state every plan relies on: lookup tables, their double-float
 // copies, the B-side image cache, the arena, the ticket and the error word.
 static cpl_status ensure_common(cpl_ctx *c, int S, int nc_max, size_t scratch, cudaStream_t st) {
@@ -642,6 +678,17 @@ static cpl_status ensure_common(cpl_ctx *c, int S, int nc_max, size_t scratch, c
         record_launch(c, idx, ev, st, 0.0, 48.0 * np1);
         M.pmax_dd = c->pmax;
         M.Bimg.release();   // the B cache is rebuilt with the new tables
+    }
+    // pair-coefficient factors for every l the B cache can reach
+    if (M.coef_n < M.NC_B * MX_BJ + 2) {
+        const int n = M.NC_B * MX_BJ + 2;
+        M.coef_n = 0;
+        if ((s = M.coef.ensure(sizeof(uint32_t) * 3 * (size_t)n * MX_COEF_N, "pair coefficient factors")) != CPL_OK)
+            return s;
+        std::vector<uint32_t> host;
+        mx_coef_host(n, host);
+        CPL_CUDA_TRY(cudaMemcpyAsync(M.coef.ptr, host.data(), sizeof(uint32_t) * host.size(), cudaMemcpyHostToDevice, st));
+        M.coef_n = n;
     }
     if (!M.Bimg.ptr) {
         MxLayout L;
