@@ -75,7 +75,7 @@ typedef enum {
     CPL_DF32 = 2         /* the plain path's contractions in double-float (pairs of FP32,
                             ~48-bit significands) on the FP32 pipe; weights scaled per tile,
                             FP64 epilogue; lmax <= CPL_DF32_LMAX (target <= 1e-11 relative
-                            like CPL_FP64; measured <= 5e-12) */
+                            like CPL_FP64; measured <= 4e-13) */
 } cpl_precision;
 #define CPL_DF32_LMAX 10000
 
