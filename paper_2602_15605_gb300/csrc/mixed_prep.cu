@@ -127,14 +127,14 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
 // whole 128-byte core matrices.  Pass 1 computes the values, keeps them in
 // shared memory (each thread its own 8 x 4 slots) and finds the row maxima
 // of the exponents (shuffles over the 4 lanes of a row, then shared memory
-// over the 8 warps); pass 2 writes the limbs of the kept values.
+// over the 8 warps); pass 2 writes the limbs of the kept values (a value's
+// shift against the row maximum needs only its weight's exponent).
 template <int S>
 __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     constexpr int NW = 256 / 32;
     static_assert(MX_SB == 32 * NW, "one scale block per pass of the block");
     __shared__ int wmax[2][NW][8][MX_NA];
     extern __shared__ float2 kept[];                        // [8 m][MX_NA][256]: values of pass 1
-    int *kept_ex = reinterpret_cast<int *>(kept + 8 * MX_NA * 256);   // [8 m][MX_NA][256]: their exponents
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int q8 = lane & 7, kg = lane >> 3;
     const MxLayout &L = a.L;
@@ -177,7 +177,6 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
             for (int q = 0; q < MX_NA; ++q) {
                 bmax[q] = max(bmax[q], vex[q]);
                 kept[(m * MX_NA + q) * 256 + tid] = make_float2(val[q].h, val[q].l);
-                kept_ex[(m * MX_NA + q) * 256 + tid] = vex[q];
             }
         }
         const int buf = sb & 1;
@@ -208,14 +207,13 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const float2 kv = kept[(m * MX_NA + q) * 256 + tid];
-                const dfl val = {kv.x, kv.y};
-                const int vex = kept_ex[(m * MX_NA + q) * 256 + tid];
                 dfl y = {0.f, 0.f};
-                if (vex != EXP_ZERO && E[q] != EXP_ZERO) {
-                    // y = x 2^(7 - E) with x = val 2^(weight exponent): shift = vex - ilogb - 1 + 7 - E
-                    const int sh = vex - (ilogbf_fast(fabsf(val.h)) + 1) + 7 - E[q];
-                    y.h = scale2(val.h, sh);
-                    y.l = scale2(val.l, sh);
+                if (kv.x != 0.f && E[q] != EXP_ZERO) {
+                    // y = x 2^(7 - E), x = val 2^(vex - ilogb(val) - 1) = val 2^(weight exponent)
+                    const int l3 = q < 3 ? 2 * (k0 + m) + pi : 2 * (k0 + m) + 1 - pi;
+                    const int sh = Ae[l3] + 7 - E[q];
+                    y.h = scale2(kv.x, sh);
+                    y.l = scale2(kv.y, sh);
                 }
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
@@ -336,7 +334,7 @@ cudaError_t mx_launch_prep_a(const MxPrepAArgs &a, cudaStream_t st) {
     if (octets == 0) return cudaSuccess;
     if (a.L.BI < 8 || a.L.KB % 8 != 0) return cudaErrorInvalidValue;
     const int blocks = (int)octets;
-    const int smem = 8 * MX_NA * 256 * (int)(sizeof(float2) + sizeof(int));   // the kept values
+    const int smem = 8 * MX_NA * 256 * (int)sizeof(float2);   // the kept values
     static std::atomic<unsigned long long> attr[3];
     cudaError_t e;
     switch (a.L.S) {
