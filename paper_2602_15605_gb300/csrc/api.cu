@@ -468,6 +468,17 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
             return s;
         if ((s = ensure_err_word(c, st)) != CPL_OK) return s;
     }
+    if (!df && c->pl_coef_n < lmax_all + 1) {
+        // per-l factors of the epilogue's pair coefficients (the same values for every call)
+        c->pl_coef_n = 0;
+        if ((s = c->pl_coef.ensure(sizeof(double) * PL_COEF_N * (size_t)(lmax_all + 1), "pair coefficient factors")) !=
+            CPL_OK)
+            return s;
+        std::vector<double> hc;
+        plain_coef_host(lmax_all + 1, hc);
+        CPL_CUDA_TRY(cudaMemcpyAsync(c->pl_coef.ptr, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice, st));
+        c->pl_coef_n = lmax_all + 1;
+    }
     uint8_t *dmeta = c->items.as<uint8_t>();
     double *dA = c->weights.as<double>();
     std::vector<uint8_t> host(o, 0);
@@ -571,6 +582,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
             a.gdf = c->df_tab.as<float2>();
             a.hdf = a.gdf + (c->pmax + 1);
         }
+        if (!df) a.lcoef = c->pl_coef.as<double>();
         if (tab) {
             a.btab = c->ptab_b.as<double>();
             a.btab_njb = c->ptab_njb;
@@ -740,6 +752,7 @@ cpl_status cpl_ctx_destroy(cpl_ctx *c) {
     c->items.release();
     c->ptab_a.release();
     c->ptab_b.release();
+    c->pl_coef.release();
     c->stage_w.release();
     c->stage_out.release();
     c->threej_idx.release();

@@ -114,6 +114,8 @@ struct cpl_ctx {
     DevBuf ptab_b;               // tabled FP64 kernel: B operand blocks (window independent)
     int ptab_njb = 0;            // column blocks ptab_b covers (0: none)
     DevBuf ptab_a;               // tabled FP64 kernel: A operand blocks of the last build
+    DevBuf pl_coef;              // FP64 epilogue: per-l factors of the pair coefficients
+    int pl_coef_n = 0;           // l < pl_coef_n covered
     DevBuf dec_ws;               // cpl_decouple: augmented systems too large for shared memory
     DevBuf cov_M, cov_dense, cov_edges;   // cpl_cov_gaussian: kernels of one build, dense covariance, bin edges
     cudaStream_t own_stream = nullptr;

@@ -102,6 +102,7 @@ struct PlainArgs {
     int odd;                // whether the odd sweep runs
     const float2 *gdf;      // [pmax + 1] g and h as FP32 pairs (double-float kernels only)
     const float2 *hdf;
+    const double *lcoef;    // [l][PL_COEF_N] per-l factors of the pair coefficients (plain_coef_host)
     const double *btab;     // B blocks (btab_block order), NULL: the kernel stages its own operands
     int btab_njb;           // column blocks the B table covers
     int *err;               // device error word of the tabled kernel's bounded waits
@@ -121,6 +122,12 @@ cudaError_t launch_weights(const double *W, int w_len, int n_win, const int *l3c
 // blocks of column blocks [0, njb), and one sweep's A blocks (nae even rows,
 // odd: the odd row) for n_win windows from their weights A.
 cudaError_t launch_btab(const double *g, const double *h, int njb, double *B, cudaStream_t st);
+// Per-l factors of the FP64 epilogue's pair coefficients for l < n (zero for
+// l < 2): lambda/eta = rho(l1) sigma(l2), c0(l1), c1 = alpha(l1) beta(l2),
+// c2 = alpha(l1) beta'(l2), e1(l2), C = kappa(l1) mu(l2).  Layout per l:
+// rho, rho^2, c0, alpha, kappa, sigma, sigma^2, beta, beta', e1, mu.
+constexpr int PL_COEF_N = 11;
+void plain_coef_host(int n, std::vector<double> &out);
 cudaError_t launch_atab(const double *A, int a_stride, const int *l3cap, const double *g, const long long *aoff,
                         int n_win, int nib, int max_count, int nae, int odd, double *At, cudaStream_t st);
 // (j1 j2 j3; 0 -1 1) rows for device arrays j2, j3 from sqrt g, sqrt h, sqrt n

@@ -59,9 +59,12 @@ struct NaArgs {
     int slot[5];
 };
 
-// Same contraction and epilogue as k_plain (plain_fp64.cu), dense output
-// only; the (parity, i-block) pair is blockIdx.y, the j-block blockIdx.x and
-// the window blockIdx.z.  Blocks without a valid pair return at once.
+// The same contraction as k_plain (plain_fp64.cu), dense output only; the
+// epilogue forms the pair coefficients directly (the context path reads
+// per-l factor tables, for which the fixed scratch array has no room), so the
+// two agree to rounding.  The (parity, i-block) pair is blockIdx.y, the
+// j-block blockIdx.x and the window blockIdx.z.  Blocks without a valid pair
+// return at once.
 // Exact product of two integer factors as a double (one 64-bit multiply and
 // one conversion instead of two conversions and an FP64 multiply).
 __device__ __forceinline__ double int_prod(int a, int b) { return (double)((long long)a * (long long)b); }

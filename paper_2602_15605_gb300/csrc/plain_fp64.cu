@@ -41,6 +41,8 @@
 // TT+TE+EE, 3 per odd term for EE->BB.  The FP64 pipe bounds this path.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "internal.h"
 #include "mbar.cuh"
 
@@ -141,10 +143,13 @@ __device__ __forceinline__ void fma_chunk(const double *sa, const double *sb, in
 
 // Per-pair combination of the contractions (the App. A kernels through the
 // separable forms above) and the writes of both mirror entries; this
-// thread's pairs are rows i0 + ar + RS r and columns j0 + bc + CS c.
+// thread's pairs are rows i0 + ar + RS r and columns j0 + bc + CS c.  The
+// pair coefficients are products of per-l factors (lcoef, plain_coef_host):
+// lambda/eta = rho(l1) sigma(l2), c1 = alpha(l1) beta(l2), c2 = alpha(l1)
+// beta'(l2), C = kappa(l1) mu(l2), so no division or square root runs here.
 template <int NGE, bool ODD, int RS, int CS>
-__device__ __forceinline__ void epilogue(const PlainJob &p, int win, int pi, int i0, int j0, int ar, int bc,
-                                         const Acc<NGE, ODD> &acc) {
+__device__ __forceinline__ void epilogue(const double *__restrict__ lcoef, const PlainJob &p, int win, int pi,
+                                         int i0, int j0, int ar, int bc, const Acc<NGE, ODD> &acc) {
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -155,17 +160,15 @@ __device__ __forceinline__ void epilogue(const PlainJob &p, int win, int pi, int
             if (NGE >= 1) write_out(p, win, p.slot[0], l1, l2, acc[0][r][c]);
             double ee = 0.0, eebb = 0.0;
             if (NGE >= 3 || ODD) {
-                const double L1 = l1, L2 = l2;
-                const double eta2 = (L1 - 1.0) * (L1 + 2.0) * (L2 - 1.0) * L2;
-                const double c1 = 1.0 / (L1 * (L1 + 1.0) * (L2 + 1.0));
+                const double *F1 = lcoef + (size_t)l1 * PL_COEF_N;   // rho, rho^2, c0, alpha, kappa
+                const double *F2 = lcoef + (size_t)l2 * PL_COEF_N;   // sigma, sigma^2, beta, beta', e1, mu at 5..10
                 if (NGE >= 3) {
-                    const double r2 = L1 * (L1 + 1.0) * (L2 + 1.0) * (L2 + 2.0) / eta2;  // (lambda/eta)^2
-                    const double c0 = 1.0 + 2.0 / L1;
-                    const double c2 = c1 / (2.0 * (L2 + 2.0));
+                    const double c0 = F1[2], c1 = F1[3] * F2[7], c2 = F1[3] * F2[8];
                     const double s00 = acc[0][r][c], s01 = acc[1][r][c], s11 = acc[2][r][c];
                     const double xp = c0 * s00 - c1 * s01 - c2 * s11;
-                    write_out(p, win, p.slot[1], l1, l2, sqrt(r2) * xp);
+                    write_out(p, win, p.slot[1], l1, l2, (F1[0] * F2[5]) * xp);
                     if (NGE >= 6) {
+                        const double r2 = F1[1] * F2[6];   // (lambda/eta)^2
                         const double s02 = acc[3][r][c], s12 = acc[4][r][c], s22 = acc[5][r][c];
                         const double xp2 = c0 * c0 * s00 - 2.0 * c0 * c1 * s01 - 2.0 * c0 * c2 * s11 +
                                            c1 * c1 * s02 + 2.0 * c1 * c2 * s12 + c2 * c2 * s22;
@@ -174,8 +177,8 @@ __device__ __forceinline__ void epilogue(const PlainJob &p, int win, int pi, int
                     }
                 }
                 if (ODD) {
-                    const double e0 = L1 + 2.0, e1 = 1.0 / (2.0 * (L2 + 2.0));
-                    const double Cc = (L2 + 2.0) * c1 / eta2;   // (l2+2) / (eta^2 l1 (l1+1) (l2+1))
+                    const double e0 = (double)(l1 + 2), e1 = F2[9];
+                    const double Cc = F1[4] * F2[10];   // (l2+2) / (eta^2 l1 (l1+1) (l2+1))
                     const double t0 = acc[NGE][r][c], t1 = acc[NGE + 1][r][c], t2 = acc[NGE + 2][r][c];
                     eebb = Cc * (e0 * e0 * t0 - 2.0 * e0 * e1 * t1 + e1 * e1 * t2);
                     write_out(p, win, p.slot[3], l1, l2, eebb);
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(NT) k_plain(const PlainArgs pa) {
         fma_chunk<NGE, ODD, 16, 16>(&sa[0][0][0], &sb[0][0][0], 0, min(KC, k_hi - kb + 1), ty, tx, acc);
     }
 
-    epilogue<NGE, ODD, 16, 16>(p, win, pi, i0, j0, ty, tx, acc);
+    epilogue<NGE, ODD, 16, 16>(pa.lcoef, p, win, pi, i0, j0, ty, tx, acc);
 }
 
 // ---------------------------------------------------------------- tabled kernel
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(NT, 2) k_plain_tab(const PlainArgs pa) {
         if (tid == 0 && m + 2 < nch) issue(m + 2);
     }
 
-    epilogue<NGE, ODD, 8, 4>(p, win, pi, i0, j0, ar, bc, acc);
+    epilogue<NGE, ODD, 8, 4>(pa.lcoef, p, win, pi, i0, j0, ar, bc, acc);
 }
 
 __global__ void k_weights(const double *__restrict__ W, int w_len, const int *__restrict__ l3cap,
@@ -495,6 +498,28 @@ void plain_variant(int mode, const int slot[5], int *nge, bool *odd) {
     } else {
         const bool even = slot[0] >= 0 || slot[1] >= 0 || slot[2] >= 0 || slot[4] >= 0;
         *nge = even ? 6 : 0;
+    }
+}
+
+void plain_coef_host(int n, std::vector<double> &out) {
+    out.assign((size_t)n * PL_COEF_N, 0.0);
+    for (int l = 2; l < n; ++l) {
+        const double L = l;
+        double *f = out.data() + (size_t)l * PL_COEF_N;
+        const double rho2 = L * (L + 1.0) / ((L - 1.0) * (L + 2.0));
+        const double al = 1.0 / (L * (L + 1.0));
+        const double s2 = (L + 1.0) * (L + 2.0) / ((L - 1.0) * L);
+        f[0] = std::sqrt(rho2);                             // rho
+        f[1] = rho2;
+        f[2] = 1.0 + 2.0 / L;                               // c0
+        f[3] = al;                                          // alpha
+        f[4] = al / ((L - 1.0) * (L + 2.0));                // kappa
+        f[5] = std::sqrt(s2);                               // sigma
+        f[6] = s2;
+        f[7] = 1.0 / (L + 1.0);                             // beta
+        f[8] = 1.0 / (2.0 * (L + 1.0) * (L + 2.0));         // beta'
+        f[9] = 1.0 / (2.0 * (L + 2.0));                     // e1
+        f[10] = (L + 2.0) / ((L + 1.0) * (L - 1.0) * L);    // mu
     }
 }
 

@@ -3,8 +3,11 @@
 The entry point keeps its scratch in a fixed device array inside the library
 instead of buffers a context allocates.  These tests call it through the C ABI
 twice in a row and compare each result with cpl_build's on the same inputs,
-at the plain path's tolerance (1e-11 relative); they also check that sizes
-beyond the array's limits are refused.  This file is collected last on
+at the plain path's tolerance (1e-11): element by element for TT, EE and
+EE->BB, whose l3 terms are all non-negative, and normwise for the signed TE
+and EB, whose elements can cancel to near zero (the two paths form the pair
+coefficients differently, so they agree to rounding, not bit for bit); they
+also check that sizes beyond the array's limits are refused.  This file is collected last on
 purpose, so a failure here comes after every other test has run.
 """
 import numpy as np
@@ -21,6 +24,9 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
+SIGNED = (1, 4)   # TE and EB slots of the full spectrum set
+
+
 def close(a, b):
     a = a.cpu().numpy()
     b = b.cpu().numpy()
@@ -31,7 +37,10 @@ def close(a, b):
     for w in range(b.shape[0]):
         for s in range(b.shape[1]):
             scale = np.max(np.abs(b[w, s])) or 1.0
-            rel = np.max(np.abs(a[w, s] - b[w, s]) / np.maximum(np.abs(b[w, s]), 1e-300 * scale))
+            if s in SIGNED:
+                rel = np.max(np.abs(a[w, s] - b[w, s])) / scale
+            else:
+                rel = np.max(np.abs(a[w, s] - b[w, s]) / np.maximum(np.abs(b[w, s]), 1e-300 * scale))
             assert rel <= TOL, (w, s, rel)
 
 
