@@ -188,6 +188,37 @@ cpl_status cpl_output_size(const cpl_request *r, size_t *n_doubles);
 cpl_status cpl_build(cpl_ctx *ctx, const cpl_request *r, double *out, void *stream);
 
 /*
+ * Host-only dry run of a plain-path build (CPL_FP64 or CPL_DF32) of `r`: no
+ * context, no device work; the W_* pointers are not read.  Validation as
+ * cpl_output_size; CPL_ERR_UNSUPPORTED for CPL_MIXED_BF16.
+ *   n_tiles        32 x 32 blocks of (i, j) = ((d - pi)/2, (s - pi)/2),
+ *                  d = l2 - l1, s = l1 + l2, pi = d mod 2, covering the
+ *                  pairs lmin <= l1 <= l2 <= lmax
+ *   n_items        (window, tile) work items over all contraction launches;
+ *                  a tile whose smallest l3 exceeds a window's band limit is
+ *                  dropped for that window
+ *   n_launches     contraction launches (one per kernel variant; window roles
+ *                  that share a pointer share one sweep)
+ *   terms_even     l3 terms of the sums of App. A over the pairs l1 <= l2 with
+ *   terms_odd      l1 + l2 + l3 even / odd, within each window's band, summed
+ *                  over windows
+ *   flop           algorithmic FLOP of the contractions: 2 per term and
+ *                  separable contraction (1, 3 or 6 per even term by the
+ *                  spectra a sweep serves, 3 per odd term) -- the count behind
+ *                  the plain path's roofline
+ *   table_bytes_b  CPL_FP64 operand blocks shared by all windows (a context
+ *                  keeps them for the largest lmax it has built); 0 for DF32
+ *   table_bytes_a  CPL_FP64 per-call operand blocks; 0 for CPL_DF32
+ */
+typedef struct {
+    long long n_tiles, n_items;
+    int n_launches;
+    double terms_even, terms_odd, flop;
+    unsigned long long table_bytes_b, table_bytes_a;
+} cpl_plan_info;
+cpl_status cpl_plan_info_fp64(const cpl_request *r, cpl_plan_info *info);
+
+/*
  * The same request with HOST buffers: W_* are host pointers and `out_host`
  * is a host buffer of cpl_output_size doubles.  The library copies the
  * windows to the device, builds, copies the result back and returns when

@@ -42,6 +42,12 @@ class Request(ctypes.Structure):
                 ("bin_weight", ctypes.c_int)]
 
 
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_tiles", ctypes.c_longlong), ("n_items", ctypes.c_longlong), ("n_launches", ctypes.c_int),
+                ("terms_even", ctypes.c_double), ("terms_odd", ctypes.c_double), ("flop", ctypes.c_double),
+                ("table_bytes_b", ctypes.c_ulonglong), ("table_bytes_a", ctypes.c_ulonglong)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
                 ("flop", ctypes.c_double), ("bytes", ctypes.c_double), ("issued_flop", ctypes.c_double)]
@@ -67,7 +73,7 @@ EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
            "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_validate",
            "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
-           "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table")
+           "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table", "cpl_plan_info_fp64")
 
 _lock = threading.Lock()
 _lib = None
@@ -95,6 +101,7 @@ def load():
         L.cpl_ctx_destroy.argtypes = [vp]
         L.cpl_ctx_sync.argtypes = [vp]
         L.cpl_output_size.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_size_t)]
+        L.cpl_plan_info_fp64.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(PlanInfo)]
         L.cpl_build.argtypes = [vp, ctypes.POINTER(Request), vp, vp]
         L.cpl_build_host.argtypes = [vp, ctypes.POINTER(Request), vp]
         L.cpl_build_batch.argtypes = [vp, ctypes.POINTER(Request), ip, ctypes.POINTER(vp), vp]
@@ -434,6 +441,22 @@ def build_noalloc(lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2, ban
     _check(L.cpl_build_noalloc(ctypes.byref(r), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
     del keep
     return out
+
+
+def plan_info(lmax, n_windows, spectra, lmin=2, w_len=None, band_limit=None, precision=FP64, shared=False):
+    """cpl_plan_info_fp64: host-only dry run of a plain-path build (needs no
+    GPU).  shared=True: one window pointer serves every role (one sweep);
+    False: separate W^TT, W^TP, W^PP.  Returns a dict of the PlanInfo fields."""
+    keep = _Keep()
+    w_len = 2 * lmax + 1 if w_len is None else w_len
+    # distinct non-NULL addresses per role (never dereferenced)
+    fakes = (0x1000, 0x1000, 0x1000) if shared else (0x1000, 0x2000, 0x3000)
+    r = _make_request(lmax, fakes[0] if spectra & TT else None, fakes[1] if spectra & TE else None,
+                      fakes[2] if spectra & (EE | EEBB | EB) else None, spectra, lmin, band_limit, None,
+                      precision, 0, lambda W: W, n_windows, w_len, keep, 0)
+    info = PlanInfo()
+    _check(load().cpl_plan_info_fp64(ctypes.byref(r), ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in PlanInfo._fields_}
 
 
 def output_size(lmax, n_windows, spectra, lmin=2, w_len=None, band_limit=None, bin_edges=None,

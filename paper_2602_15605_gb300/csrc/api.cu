@@ -242,6 +242,50 @@ struct Group {
     unsigned spectra;   // spectra this window pointer serves
 };
 
+// The window-role groups of a request: roles that share a pointer share one
+// sweep (PlainJob) and one kernel variant.
+std::vector<Group> window_groups(const cpl_request *r) {
+    std::vector<Group> groups;
+    auto add = [&](const double *W, unsigned b) {
+        if (!(r->spectra & b)) return;
+        for (auto &g : groups)
+            if (g.W == W) {
+                g.spectra |= (r->spectra & b);
+                return;
+            }
+        groups.push_back({W, r->spectra & b});
+    };
+    add(r->W_tt, kTT);
+    add(r->W_tp, kTE);
+    add(r->W_pp, kEE | kEEBB | kEB);
+    return groups;
+}
+
+// A blocks of the tabled kernel for row block ib and parity pi of a window
+// whose l3 ends at cap: the chunks 2 ib .. of the block's k range, which
+// ends at min(lmax - pi - i0 + 31, cap / 2) (the last column of the block's
+// last tile, or the band).
+int a_block_count(int lmax, int lmin, int pi, int ib, int cap) {
+    const int imax = (lmax - lmin - pi) / 2;   // rows of this parity's tiles
+    if (lmax - lmin - pi < 0 || TILE_I * ib > imax) return 0;
+    const int cend = std::min((lmax - pi - TILE_I * ib + TILE_J - 1) / PT_KC, (cap / 2) / PT_KC) + 1;
+    return std::max(0, cend - 2 * ib);
+}
+
+// l3 cap of each window of a request (its band limit, else 2 lmax or the
+// end of W), and whether any window is band-limited.
+bool window_caps(const cpl_request *r, std::vector<int> &caps) {
+    bool banded = false;
+    caps.resize(r->n_windows);
+    for (int w = 0; w < r->n_windows; ++w) {
+        int cap = std::min(2 * r->lmax, r->w_len - 1);
+        if (r->band_limit) cap = std::min(cap, r->band_limit[w]);
+        if (cap < 2 * r->lmax) banded = true;
+        caps[w] = cap;
+    }
+    return banded;
+}
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // The plain FP64 build of a batch of requests on `st` (device pointers).
@@ -304,13 +348,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         JobInfo &J = jobs[q];
         if ((s = get_tiles(c, r->lmax, r->lmin, &J.ts)) != CPL_OK) return s;
         const int nw = r->n_windows;
-        J.caps.resize(nw);
-        for (int w = 0; w < nw; ++w) {
-            int cap = std::min(2 * r->lmax, r->w_len - 1);
-            if (r->band_limit) cap = std::min(cap, r->band_limit[w]);
-            if (cap < 2 * r->lmax) J.banded = true;
-            J.caps[w] = cap;
-        }
+        J.banded = window_caps(r, J.caps);
         J.nb = r->bin_edges ? r->n_bins : 0;
         if (J.nb) {
             J.bin_of.assign(r->lmax + 1, -1);
@@ -323,19 +361,7 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
         }
         make_items(*J.ts, J.caps, J.banded, J.items);
         // window roles sharing one pointer share one sweep
-        std::vector<Group> groups;
-        auto add = [&](const double *W, unsigned b) {
-            if (!(r->spectra & b)) return;
-            for (auto &g : groups)
-                if (g.W == W) {
-                    g.spectra |= (r->spectra & b);
-                    return;
-                }
-            groups.push_back({W, r->spectra & b});
-        };
-        add(r->W_tt, kTT);
-        add(r->W_tp, kTE);
-        add(r->W_pp, kEE | kEEBB | kEB);
+        const std::vector<Group> groups = window_groups(r);
         const int a_stride = 2 * r->lmax + 2;
         for (const Group &G : groups) {
             Sweep sw;
@@ -367,15 +393,8 @@ cpl_status build_fp64_batch(cpl_ctx *c, const cpl_request *reqs, double *const *
             long long blocks = 0;
             for (int w = 0; w < nw; ++w)
                 for (int pi = 0; pi < 2; ++pi) {
-                    const int imax = (r->lmax - r->lmin - pi) / 2;   // rows of this parity's tiles
                     for (int ib = 0; ib < sw.nib; ++ib) {
-                        // chunks 2 ib .. of the row block: k <= j0 + 31 <= lmax - pi - i0 + 31 and k <= cap / 2
-                        int count = 0;
-                        if (r->lmax - r->lmin - pi >= 0 && TILE_I * ib <= imax) {
-                            const int cend = std::min((r->lmax - pi - TILE_I * ib + TILE_J - 1) / PT_KC,
-                                                      (J.caps[w] / 2) / PT_KC) + 1;
-                            count = std::max(0, cend - 2 * ib);
-                        }
+                        const int count = a_block_count(r->lmax, r->lmin, pi, ib, J.caps[w]);
                         sw.aoff[((size_t)w * 2 + pi) * sw.nib + ib] = blocks;
                         blocks += count;
                         sw.max_count = std::max(sw.max_count, count);
@@ -802,6 +821,67 @@ cpl_status cpl_output_size(const cpl_request *r, size_t *n_doubles) {
     cpl_status s = validate(r, true);
     if (s != CPL_OK) return s;
     *n_doubles = out_doubles(r);
+    return CPL_OK;
+}
+
+cpl_status cpl_plan_info_fp64(const cpl_request *r, cpl_plan_info *info) {
+    if (!info) return fail(CPL_ERR_ARG, "info is NULL");
+    cpl_status s = validate(r, true);
+    if (s != CPL_OK) return s;
+    if (r->precision == CPL_MIXED_BF16)
+        return fail(CPL_ERR_UNSUPPORTED, "cpl_plan_info_fp64 plans the plain path (CPL_FP64, CPL_DF32)");
+    cpl_plan_info pi_;
+    std::memset(&pi_, 0, sizeof(pi_));
+    std::vector<Tile> tiles;
+    make_tiles(r->lmax, r->lmin, tiles);
+    pi_.n_tiles = (long long)tiles.size();
+    std::vector<int> caps;
+    const bool banded = window_caps(r, caps);
+    // per window: kept tiles and their even / odd l3 terms (the launch accounting's counts)
+    const int nw = r->n_windows;
+    std::vector<double> E(nw, 0.0), O(nw, 0.0);
+    std::vector<long long> kept(nw, 0);
+    for (int w = 0; w < nw; ++w)
+        for (const Tile &t : tiles) {
+            if (banded && 2 * t.i0 + t.pi > caps[w]) continue;
+            double e, od, np;
+            tile_terms_split(t, r->lmax, r->lmin, caps[w], &e, &od, &np);
+            E[w] += e;
+            O[w] += od;
+            ++kept[w];
+        }
+    for (int w = 0; w < nw; ++w) {
+        pi_.terms_even += E[w];
+        pi_.terms_odd += O[w];
+    }
+    const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
+    std::vector<int> variants;
+    const int nib = (r->lmax - r->lmin) / 2 / TILE_I + 1;
+    for (const Group &G : window_groups(r)) {
+        int slot[5];
+        for (int x = 0; x < 5; ++x) slot[x] = (G.spectra & bits[x]) ? spec_slot(r->spectra, bits[x]) : -1;
+        const int mode = (G.spectra & (kEE | kEEBB | kEB)) ? MODE_POL : (G.spectra & kTE) ? MODE_TE : MODE_TT;
+        int nge;
+        bool odd;
+        plain_variant(mode, slot, &nge, &odd);
+        const int key = nge * 2 + (odd ? 1 : 0);
+        if (std::find(variants.begin(), variants.end(), key) == variants.end()) variants.push_back(key);
+        const int na = (nge == 0 ? 0 : nge == 1 ? 1 : nge == 3 ? 2 : 3) + (odd ? 1 : 0);
+        for (int w = 0; w < nw; ++w) {
+            pi_.n_items += kept[w];
+            pi_.flop += 2.0 * (nge * E[w] + (odd ? 3.0 : 0.0) * O[w]);
+            if (r->precision == CPL_FP64)
+                for (int p = 0; p < 2; ++p)
+                    for (int ib = 0; ib < nib; ++ib)
+                        pi_.table_bytes_a += (unsigned long long)a_block_count(r->lmax, r->lmin, p, ib, caps[w]) * na *
+                                             PT_BLK * sizeof(double);
+        }
+    }
+    pi_.n_launches = (int)variants.size();
+    if (r->precision == CPL_FP64)
+        pi_.table_bytes_b =
+            (unsigned long long)btab_block(r->lmax / TILE_J + 1, 0, 0) * PT_BROWS * PT_BLK * sizeof(double);
+    *info = pi_;
     return CPL_OK;
 }
 

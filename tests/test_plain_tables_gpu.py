@@ -132,3 +132,24 @@ def test_batch_two_lmax_and_growing_b_table(ctx):
     for tab, ref in outs:
         assert equal_bits(tab, ref)
     assert equal_bits(outs[0][0], outs[2][0])
+
+
+def test_launch_accounting_equals_host_plan(ctx):
+    # the FLOP the profiled launches report (the roofline's numerator) equal
+    # the host dry run's count, which the CPU tests pin to brute force
+    lmax = 333
+    W = [dev(windows.mask_like(lmax, seed=70 + q)) for q in range(3)]
+    band = [40, 2 * lmax]
+    Wb = [dev(np.stack([windows.mask_like(lmax, seed=80 + q), windows.mask_like(lmax, seed=90 + q)])) for q in range(3)]
+    for args, kw, plan_kw in [((lmax, *W, coupling.ALL), {}, dict(n_windows=1)),
+                              ((lmax, Wb[0], Wb[0], Wb[0], coupling.ALL), dict(band_limit=band),
+                               dict(n_windows=2, band_limit=band, shared=True))]:
+        ctx.stats(reset=True)
+        ctx.build(*args, **kw)
+        ctx.sync()
+        st = ctx.stats(reset=True)
+        flop = sum(v["flop"] for k, v in st.items() if k.startswith("plain_fp64_"))
+        plan = coupling.plan_info(lmax, spectra=coupling.ALL, **plan_kw)
+        assert flop == plan["flop"], (flop, plan["flop"])
+        launches = sum(v["launches"] for k, v in st.items() if k.startswith("plain_fp64_"))
+        assert launches == plan["n_launches"]
