@@ -244,6 +244,21 @@ def test_oracle_pol_diagonal_small_odd_j_large_l():
             assert abs(col[j] / ref - 1.0) < 1e-12, (l, j, col[j], ref)
 
 
+def test_oracle_m11_diagonal_small_odd_j_large_l():
+    # the same lower end for (j l l; 0 -1 1): closed forms at j = 0, 1 and
+    # App. B's Eq. joneodd at 40 digits for odd j
+    mp.mp.dps = 40
+    for l in (8000, 25000):
+        jmin, col = oracle.threej_column(l, l, 0, -1, 1)
+        assert jmin == 0
+        sgn = 1.0 if (l + 1) % 2 == 0 else -1.0           # (-1)^(l - m), m = -1
+        assert abs(col[0] / (sgn / math.sqrt(2 * l + 1)) - 1.0) < 1e-12
+        assert abs(col[1] / (sgn * -1.0 / math.sqrt(l * (l + 1.0) * (2 * l + 1))) - 1.0) < 1e-12
+        for j in (3, 7):
+            ref = float(_paper_011(j, l, l))
+            assert abs(col[j] / ref - 1.0) < 1e-12, (l, j, col[j], ref)
+
+
 def test_oracle_eebb_diagonal_element_vs_40_digits():
     # A whole l3 sum where the odd-j symbols carry the weight: M^EEBB(l, l)
     # with a mask-like window (weight concentrated at small l3), against the
