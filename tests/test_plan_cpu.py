@@ -145,3 +145,18 @@ def test_table_bytes():
     assert df["table_bytes_a"] == 0 and df["table_bytes_b"] == 0 and df["flop"] > 0
     with pytest.raises(coupling.CouplingError):
         coupling.plan_info(300, 1, coupling.ALL, precision=coupling.MIXED_BF16)
+
+
+def test_documented_table_sizes():
+    # the header's figures for the FP64 operand tables: about 48 lmax^2 bytes
+    # shared (0.43 GB at l_max 3000, 4.7 GB at 10000) and about 28 lmax^2
+    # bytes per window with all spectra and separate windows
+    for lmax, b_doc in ((3000, 0.43e9), (10000, 4.7e9)):
+        info = coupling.plan_info(lmax, 1, coupling.ALL)
+        assert abs(info["table_bytes_b"] / (48.0 * lmax ** 2) - 1.0) < 0.05
+        assert abs(info["table_bytes_b"] / b_doc - 1.0) < 0.05
+        assert abs(info["table_bytes_a"] / (28.0 * lmax ** 2) - 1.0) < 0.1
+    # a band limit shrinks the per-window blocks
+    full = coupling.plan_info(8000, 1, coupling.ALL)["table_bytes_a"]
+    band = coupling.plan_info(8000, 1, coupling.ALL, band_limit=[512])["table_bytes_a"]
+    assert band < full / 20
