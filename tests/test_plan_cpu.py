@@ -160,3 +160,14 @@ def test_documented_table_sizes():
     full = coupling.plan_info(8000, 1, coupling.ALL)["table_bytes_a"]
     band = coupling.plan_info(8000, 1, coupling.ALL, band_limit=[512])["table_bytes_a"]
     assert band < full / 20
+
+
+def test_errors():
+    def status(fn):
+        with pytest.raises(coupling.CouplingError) as e:
+            fn()
+        return e.value.status
+    assert status(lambda: coupling.plan_info(1, 1, coupling.TT)) == 1                       # CPL_ERR_ARG
+    assert status(lambda: coupling.plan_info(10, 1, coupling.EE, lmin=1)) == 1
+    assert status(lambda: coupling.plan_info(40000, 1, coupling.TT)) == 2                   # CPL_ERR_RANGE
+    assert status(lambda: coupling.plan_info(10, 1, coupling.TT, precision=coupling.MIXED_BF16)) == 6
