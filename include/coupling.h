@@ -258,7 +258,8 @@ cpl_status cpl_build_batch(cpl_ctx *ctx, const cpl_request *jobs, int n_jobs,
  * are not allowed).
  *
  * It computes the same matrices as cpl_build with CPL_FP64 and dense output
- * into `out` (device, caller-owned, cpl_output_size doubles) on the CURRENT
+ * (equal to rounding: it forms the pair coefficients directly rather than
+ * from the context's per-l factor table) into `out` (device, caller-owned, cpl_output_size doubles) on the CURRENT
  * CUDA device, asynchronously on `stream`.  W_* are device pointers.  It needs
  * no context: its scratch (lookup tables, window weights, l3 caps) is one
  * fixed 1 MiB device array inside the library, which every GPU that loads
