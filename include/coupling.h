@@ -474,6 +474,18 @@ cpl_status cpl_cov_gaussian(cpl_ctx *ctx, int lmax, int lmin, const cpl_cov_term
  */
 cpl_status cpl_g_table(int pmax, double *out_host);
 
+/*
+ * The second lookup table, as the library builds it: out[p] = h(p) =
+ * 1 / ((2p + 1) g(p)) for p = 0 .. pmax.  It fuses the (J + 1)^{-1} and 1/g
+ * factors of Eq. 000_sq_main (with J = 2p, the J-dependent part
+ * 1 / ((J + 1) g(J/2)) is one load).  Formed from the same double-double
+ * recurrence as g, then a double-double reciprocal, rounded once to FP64.
+ * Host-only (no device work); out_host holds pmax + 1 doubles.  Errors:
+ * CPL_ERR_ARG for pmax < 0 or a NULL out_host, CPL_ERR_RANGE for
+ * pmax > 2^24.
+ */
+cpl_status cpl_h_table(int pmax, double *out_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,7 +73,7 @@ EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
            "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_validate",
            "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
-           "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table", "cpl_plan_info_fp64")
+           "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table", "cpl_h_table", "cpl_plan_info_fp64")
 
 _lock = threading.Lock()
 _lib = None
@@ -106,6 +106,7 @@ def load():
         L.cpl_build_host.argtypes = [vp, ctypes.POINTER(Request), vp]
         L.cpl_build_batch.argtypes = [vp, ctypes.POINTER(Request), ip, ctypes.POINTER(vp), vp]
         L.cpl_g_table.argtypes = [ip, dp]
+        L.cpl_h_table.argtypes = [ip, dp]
         L.cpl_ctx_profile.argtypes = [vp, ip]
         L.cpl_ctx_validate.argtypes = [vp, ip]
         L.cpl_ctx_tune.argtypes = [vp, ip, ctypes.c_char_p]
@@ -136,6 +137,13 @@ def g_table(pmax):
     """The library's g(p) table (Eq. gdef), host-side, p = 0..pmax."""
     out = np.zeros(pmax + 1, dtype=np.float64)
     _check(load().cpl_g_table(int(pmax), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def h_table(pmax):
+    """The library's h(p) = 1 / ((2p + 1) g(p)) table, host-side, p = 0..pmax."""
+    out = np.zeros(pmax + 1, dtype=np.float64)
+    _check(load().cpl_h_table(int(pmax), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
 
 

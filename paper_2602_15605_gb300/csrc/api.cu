@@ -1079,4 +1079,13 @@ cpl_status cpl_g_table(int pmax, double *out_host) {
     return CPL_OK;
 }
 
+cpl_status cpl_h_table(int pmax, double *out_host) {
+    if (pmax < 0 || !out_host) return fail(CPL_ERR_ARG, "pmax must be >= 0 and out_host non-NULL");
+    if (pmax > 1 << 24) return fail(CPL_ERR_RANGE, "pmax too large");
+    std::vector<double> g, h;
+    build_tables_host(pmax, g, h);
+    std::memcpy(out_host, h.data(), sizeof(double) * (size_t)(pmax + 1));
+    return CPL_OK;
+}
+
 }  // extern "C"

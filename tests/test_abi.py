@@ -51,6 +51,74 @@ def test_g_table_matches_exact_rationals(lib):
         assert g[p] == float(Fraction(comb(2 * p, p), 4 ** p)), p
 
 
+def _round_ratio(n, d):
+    """The correctly rounded double (nearest, ties to even) of n / d for
+    positive integers whose ratio lies in the normal range: an integer
+    quotient of 66-67 bits with a sticky bit for the remainder, converted
+    (Python rounds int -> float correctly) and scaled by a power of two."""
+    k = 66 - (n.bit_length() - d.bit_length())
+    q, r = divmod(n << k, d) if k >= 0 else divmod(n, d << -k)
+    return math.ldexp(float((q << 1) | (1 if r else 0)), -k - 1)
+
+
+def _exact_g_h(p, c):
+    """g(p) = C(2p, p) / 4^p (Eq. gdef) and h(p) = 1 / ((2p + 1) g(p)),
+    correctly rounded, from the exact c = C(2p, p)."""
+    return _round_ratio(c, 1 << (2 * p)), _round_ratio(1 << (2 * p), (2 * p + 1) * c)
+
+
+# The plain and mixed paths read g and h up to p = 2 l_max + 144 (l_max <=
+# 32000: p <= 64144); cpl_threej_m11 builds them to 2 (j2 + j3 + 1) + 144
+# (j2 + j3 <= 200000: p <= 400146).
+P_BUILD_MAX = 64144
+P_THREEJ_MAX = 400146
+
+
+def test_g_h_tables_exact_over_the_build_range(lib):
+    # every entry up to 2^16 (beyond the 64144 that l_max = 32000 reads),
+    # from C(2p+2, p+1) = C(2p, p) * 2(2p+1) / (p+1) in exact integers
+    pmax = 1 << 16
+    assert pmax >= P_BUILD_MAX
+    g, h = coupling.g_table(pmax), coupling.h_table(pmax)
+    c = 1
+    bad_g, bad_h = [], []
+    for p in range(pmax + 1):
+        if p:
+            c = c * (2 * (2 * p - 1)) // p
+        eg, eh = _exact_g_h(p, c)
+        if g[p] != eg:
+            bad_g.append(p)
+        if h[p] != eh:
+            bad_h.append(p)
+    assert not bad_g, bad_g[:10]
+    assert not bad_h, bad_h[:10]
+    assert h[0] == 1.0 and h[1] == float(Fraction(2, 3)) and h[2] == float(Fraction(8, 15))
+
+
+def test_g_h_tables_exact_at_the_threej_range(lib):
+    # sampled entries up to the largest table the symbol generator builds
+    ps = [100003, 131072, 200000, P_THREEJ_MAX]
+    g, h = coupling.g_table(P_THREEJ_MAX), coupling.h_table(P_THREEJ_MAX)
+    for p in ps:
+        eg, eh = _exact_g_h(p, comb(2 * p, p))
+        assert g[p] == eg, p
+        assert h[p] == eh, p
+
+
+def test_round_ratio_is_correct_rounding():
+    # the rounding helper itself: halfway cases go to even, a remainder
+    # beyond the half rounds up, exact values stay exact
+    one = 1 << 52
+    assert _round_ratio(2 * one + 1, 2) == float(one)              # 2^52 + 1/2 -> even 2^52
+    assert _round_ratio(2 * one + 3, 2) == float(one + 2)          # 2^52 + 3/2 -> even 2^52 + 2
+    assert _round_ratio(4 * one + 3, 4) == float(one + 1)          # 2^52 + 3/4 -> up
+    assert _round_ratio(1, 3) == 1.0 / 3.0
+    assert _round_ratio(2, 3) == 2.0 / 3.0
+    assert _round_ratio(10, 4) == 2.5
+    for n, d in ((1, 7), (22, 7), (355, 113), (10 ** 30 + 7, 3 ** 60)):
+        assert _round_ratio(n, d) == float(Fraction(n, d))
+
+
 def test_g_table_asymptote(lib):
     g = coupling.g_table(10000)
     p = np.arange(1000, 10001)
