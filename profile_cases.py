@@ -1,10 +1,10 @@
 """One representative launch of a library kernel on synthetic inputs, small
 enough to profile (a few hundred MB on the device at most).
 
-    python -m paper_2602_15605_gb300.kernel_cases decouple   # k_decouple: 80 systems of 160 x 160, 1 rhs
-    python -m paper_2602_15605_gb300.kernel_cases cov        # k_cov_combine: TT + EE terms, l_max 3000, L_cut 64
-    python -m paper_2602_15605_gb300.kernel_cases plain_df   # k_plain_df: full spin set, l_max 3000, CPL_DF32
-    python -m paper_2602_15605_gb300.kernel_cases mixed      # the mixed path's kernels: full spin set, l_max 3000
+    python profile_cases.py decouple   # k_decouple: 80 systems of 160 x 160, 1 rhs
+    python profile_cases.py cov        # k_cov_combine: TT + EE terms, l_max 3000, L_cut 64
+    python profile_cases.py plain_df   # k_plain_df: full spin set, l_max 3000, CPL_DF32
+    python profile_cases.py mixed      # the mixed path's kernels: full spin set, l_max 3000
 
 Each case runs its call three times (the first includes one-off set-up) and
 prints the last call's event time.
@@ -29,7 +29,7 @@ def case_decouple(ctx):
     EE-EEBB, EB) of 160 x 160 coupling-like matrices (diagonally dominant
     with Gaussian off-diagonal entries), one right-hand side."""
     import torch
-    from . import coupling
+    from paper_2602_15605_gb300 import coupling
     rng = np.random.default_rng(1)
     n = 160
     M = rng.normal(scale=0.02, size=(16, 5, n, n)) + np.eye(n)
@@ -48,7 +48,7 @@ def case_cov(ctx):
     """Covariance from two Wick terms (TT and EE kernels) at l_max = 3000 with
     a squared-mask spectrum band-limited at L_cut = 64, dense output."""
     import torch
-    from . import coupling, windows
+    from paper_2602_15605_gb300 import coupling, windows
     lmax, lcut = 3000, 64
     l = np.arange(lmax + 1, dtype=np.float64)
     Ct = torch.as_tensor(1e3 / (l + 10.0) ** 2, device="cuda")
@@ -66,7 +66,7 @@ def case_plain_df(ctx):
     """The full spin set at l_max = 3000 from three separate windows (the
     bench's workload) in CPL_DF32: one launch per kernel variant."""
     import torch
-    from . import coupling, windows
+    from paper_2602_15605_gb300 import coupling, windows
     d = [torch.as_tensor(W, device="cuda") for W in windows.full_spin_3000()]
     out = torch.empty((1, 5, 2999, 2999), dtype=torch.float64, device="cuda")
     ms = 0.0
@@ -79,7 +79,7 @@ def case_mixed(ctx):
     """The full spin set at l_max = 3000 from three separate windows (the
     bench's workload) in CPL_MIXED_BF16."""
     import torch
-    from . import coupling, windows
+    from paper_2602_15605_gb300 import coupling, windows
     d = [torch.as_tensor(W, device="cuda") for W in windows.full_spin_3000()]
     out = torch.empty((1, 5, 2999, 2999), dtype=torch.float64, device="cuda")
     ms = 0.0
@@ -93,9 +93,9 @@ CASES = {"decouple": case_decouple, "cov": case_cov, "plain_df": case_plain_df, 
 
 def main(argv):
     if len(argv) != 1 or argv[0] not in CASES:
-        print("usage: python -m paper_2602_15605_gb300.kernel_cases {%s}" % "|".join(CASES))
+        print("usage: python profile_cases.py {%s}" % "|".join(CASES))
         return 2
-    from . import build_ext, coupling
+    from paper_2602_15605_gb300 import build_ext, coupling
     build_ext.build()
     ctx = coupling.Context(0)
     try:
