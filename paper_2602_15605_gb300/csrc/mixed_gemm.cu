@@ -26,6 +26,12 @@
 //               into a double-float running sum per element (high part in
 //               registers, low part in shared memory, renormalised once at
 //               the end).
+// The four accumulators fill TMEM, so they cannot be double-buffered; instead
+// they are released in two steps.  The drain loads the order >= 3
+// accumulator first and releases it at once; the MMA lane then issues the
+// order >= 3 products (15 of the 21 for S = 6) of the next block's first
+// stages while the drain still reads and combines orders 0-2, and issues
+// their order 0-2 products once those three accumulators are released too.
 // The accumulators of orders 0, 1 and 2 are integers below 2^24 in their
 // units over a 256-k block (|limb| <= 128, at most 3 products per k), so the
 // tensor core holds them exactly whatever its internal rounding; only the
@@ -101,8 +107,13 @@ __device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) { return make_flo
 // block is below 2^-126 of the element's largest block)
 __device__ __forceinline__ float pow2_or_zero(int e) { return e < -126 ? 0.0f : pow2f(min(e, 0)); }
 
+// Stages at the start of a scale block whose order >= 3 products are issued
+// before the accumulators of orders 0-2 are free again (see the MMA issuer).
+template <int S>
+__host__ __device__ constexpr int mx_npre() { return S >= 6 ? 2 : 1; }
+
 struct Shared {
-    uint64_t full[3], empty[3], acc_full, acc_empty, done;
+    uint64_t full[3], empty[3], acc_full, acc_empty3, acc_empty012, done;
     uint64_t tfull[TQ], tempty[TQ];
     int tick[TQ];
     uint32_t tmem;
@@ -124,7 +135,8 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s_full0 = mbar::smem_u32(&sh.full[0]), s_empty0 = mbar::smem_u32(&sh.empty[0]);
-    const uint32_t s_accf = mbar::smem_u32(&sh.acc_full), s_acce = mbar::smem_u32(&sh.acc_empty), s_done = mbar::smem_u32(&sh.done);
+    const uint32_t s_accf = mbar::smem_u32(&sh.acc_full), s_done = mbar::smem_u32(&sh.done);
+    const uint32_t s_acce3 = mbar::smem_u32(&sh.acc_empty3), s_acce012 = mbar::smem_u32(&sh.acc_empty012);
 
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(mbar::smem_u32(&sh.tmem)),
@@ -137,7 +149,8 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
             mbar::init(s_empty0 + 8 * q, 1);
         }
         mbar::init(s_accf, 1);
-        mbar::init(s_acce, 16);
+        mbar::init(s_acce3, 16);
+        mbar::init(s_acce012, 16);
         mbar::init(s_done, 1);
         for (int q = 0; q < TQ; ++q) {
             mbar::init(mbar::smem_u32(&sh.tfull[q]), 1);
@@ -206,9 +219,35 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MX_BJ >> 3) << 17) |
                                    ((uint32_t)(MX_ROWS >> 4) << 24);
+            // Issues the limb products of one stage whose order t + u lies in
+            // [olo, ohi] (orders >= 3 share accumulator 3); a product is the
+            // first of its accumulator in the scale block when flagged so.
+            auto issue = [&](int s, int olo, int ohi, bool first3, bool first012) {
+                const uint32_t abase = stage_base + s * STAGE;
+                const uint32_t bbase = abase + S * IMG;
+#pragma unroll
+                for (int k16 = 0; k16 < KB / 16; ++k16) {
+#pragma unroll
+                    for (int t = 0; t < S; ++t) {
+#pragma unroll
+                        for (int u = 0; u + t < S; ++u) {
+                            if (t + u < olo || t + u > ohi) continue;
+                            const int acc = (t + u) < 3 ? (t + u) : 3;
+                            // the first product of each accumulator (lowest t for that order,
+                            // k16 = 0) overwrites it; the rest accumulate
+                            const bool first = k16 == 0 && (acc == 3 ? (first3 && t == 0 && u == 3)
+                                                                     : (first012 && t == 0));
+                            const uint64_t ad = umma_desc<KB>(abase + t * IMG + k16 * 256);
+                            const uint64_t bd = umma_desc<KB>(bbase + u * IMG + k16 * 256);
+                            umma(tmem + acc * MX_BJ, ad, bd, idesc, first ? 0u : 1u);
+                        }
+                    }
+                }
+            };
+            constexpr int NPRE = mx_npre<S>();
             int n = 0, m = 0;
-            bool started[4] = {false, false, false, false};
-            for (int nt = 0; !*(volatile int *)&sh.abort; ++nt) {
+            bool bad = false;
+            for (int nt = 0; !bad && !*(volatile int *)&sh.abort; ++nt) {
                 const int ts = nt % TQ;
                 if (!mbar::wait(mbar::smem_u32(&sh.tfull[ts]), (nt / TQ) & 1)) {
                     atomicExch(a.err, 18);
@@ -219,48 +258,63 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                 mbar::arrive(mbar::smem_u32(&sh.tempty[ts]));
                 if (w < 0) break;
                 const MxItem it = a.items[w];
-                for (int kb = it.kb_lo; kb <= it.kb_hi; ++kb, ++n) {
-                    if (*(volatile int *)&sh.abort) break;
-                    const bool sfirst = (kb == it.kb_lo) || (kb % KPS == 0);
-                    const bool slast = (kb == it.kb_hi) || (kb % KPS == KPS - 1);
-                    if (sfirst) {
-                        if (m > 0 && !mbar::wait(s_acce, (m - 1) & 1)) {
-                            atomicExch(a.err, 13);
-                            sh.abort = 1;
+                // one scale block (the item's k blocks inside one 256-k block) per pass
+                for (int kb = it.kb_lo; kb <= it.kb_hi;) {
+                    if (*(volatile int *)&sh.abort) { bad = true; break; }
+                    const int kend = min((int)it.kb_hi, (kb / KPS) * KPS + KPS - 1);
+                    const int nkb = kend - kb + 1;
+                    const int pre = min(NPRE, nkb);
+                    // (1) accumulator 3 is free once the drain has loaded it: the
+                    // order >= 3 products of the block's first `pre` stages run
+                    // while the drain still combines orders 0-2 of the last block
+                    if (m > 0 && !mbar::wait(s_acce3, (m - 1) & 1)) {
+                        atomicExch(a.err, 13);
+                        bad = true;
+                        break;
+                    }
+                    for (int q = 0; q < pre && !bad; ++q) {
+                        const int s = (n + q) % NST;
+                        if (!mbar::wait(s_full0 + 8 * s, ((n + q) / NST) & 1)) {
+                            atomicExch(a.err, 14);
+                            bad = true;
                             break;
                         }
-                        started[0] = started[1] = started[2] = started[3] = false;
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        issue(s, 3, S - 1, q == 0, false);
                     }
-                    const int s = n % NST;
-                    if (!mbar::wait(s_full0 + 8 * s, (n / NST) & 1)) {
-                        atomicExch(a.err, 14);
-                        sh.abort = 1;
+                    if (bad) break;
+                    // (2) then orders 0-2 of those stages, once their accumulators are free
+                    if (m > 0 && !mbar::wait(s_acce012, (m - 1) & 1)) {
+                        atomicExch(a.err, 13);
+                        bad = true;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;");
-                    const uint32_t abase = stage_base + s * STAGE;
-                    const uint32_t bbase = abase + S * IMG;
-#pragma unroll
-                    for (int k16 = 0; k16 < KB / 16; ++k16) {
-#pragma unroll
-                        for (int t = 0; t < S; ++t) {
-#pragma unroll
-                            for (int u = 0; u + t < S; ++u) {
-                                const int acc = (t + u) < 3 ? (t + u) : 3;
-                                const uint64_t ad = umma_desc<KB>(abase + t * IMG + k16 * 256);
-                                const uint64_t bd = umma_desc<KB>(bbase + u * IMG + k16 * 256);
-                                umma(tmem + acc * MX_BJ, ad, bd, idesc, started[acc] ? 1u : 0u);
-                                started[acc] = true;
-                            }
+                    for (int q = 0; q < pre; ++q) {
+                        const int s = (n + q) % NST;
+                        issue(s, 0, 2, false, q == 0);
+                        umma_commit(s_empty0 + 8 * s);
+                    }
+                    // (3) the block's remaining stages, all orders
+                    for (int q = pre; q < nkb; ++q) {
+                        const int s = (n + q) % NST;
+                        if (!mbar::wait(s_full0 + 8 * s, ((n + q) / NST) & 1)) {
+                            atomicExch(a.err, 14);
+                            bad = true;
+                            break;
                         }
+                        asm volatile("tcgen05.fence::after_thread_sync;");
+                        issue(s, 0, S - 1, false, false);
+                        umma_commit(s_empty0 + 8 * s);
                     }
-                    umma_commit(s_empty0 + 8 * s);
-                    if (slast) {
-                        umma_commit(s_accf);
-                        ++m;
-                    }
+                    if (bad) break;
+                    umma_commit(s_accf);
+                    ++m;
+                    n += nkb;
+                    kb = kend + 1;
                 }
             }
+            if (bad) sh.abort = 1;
             // all issued MMAs complete before TMEM is released
             umma_commit(s_done);
             if (!mbar::wait(s_done, 0)) atomicExch(a.err, 15);
@@ -335,36 +389,56 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                // order >= 3 first: once it is in registers its accumulator is
+                // released, and the MMAs of the next block start on it
+                {
+                    uint32_t r3[32];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) TMEM_LD8(lane_addr + 3 * MX_BJ + (uint32_t)(c0 + 8 * g), (r3 + 8 * g));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) mbar::arrive(s_acce3);
+#pragma unroll
+                    for (int x = 0; x < 32; x += 2) {
+                        const int cp = (c0 + x) / 2;
+                        // scale of this block relative to the element's frame (0 if negligible)
+                        const float2 F = __fmul2_rn(fa2, sh.fcol[cp]);
+                        float2 &ls = Ls[cp * LPAD + row];
+                        ls = __fadd2_rn(ls, __fmul2_rn(u2f2(r3[x], r3[x + 1]), F));
+                    }
+                }
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
-                    uint32_t r0[8], r1[8], r2[8], r3[8];
+                    uint32_t r0[8], r1[8], r2[8];
                     const uint32_t col = (uint32_t)(c0 + 8 * g);
                     TMEM_LD8(lane_addr + col, r0);
                     TMEM_LD8(lane_addr + MX_BJ + col, r1);
                     TMEM_LD8(lane_addr + 2 * MX_BJ + col, r2);
-                    TMEM_LD8(lane_addr + 3 * MX_BJ + col, r3);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (g == 3) {
+                        // orders 0-2 are in registers: release their accumulators
+                        asm volatile("tcgen05.fence::before_thread_sync;");
+                        __syncwarp();
+                        if (lane == 0) mbar::arrive(s_acce012);
+                    }
 #pragma unroll
                     for (int x = 0; x < 8; x += 2) {
                         const int cp = (c0 + 8 * g + x) / 2;   // column pair
-                        // scale of this block relative to the element's frame (0 if negligible)
                         const float2 F = __fmul2_rn(fa2, sh.fcol[cp]);
                         // block value: orders 0, 1 and 2 summed exactly (two two-sums:
                         // with decaying operands order 2 can reach 2^-8 of order 0, so
                         // it must not be folded into the residue of the first sum);
-                        // the residues and order >= 3 are then added in FP32
+                        // the residues are then added in FP32
                         const dfl2 v01 = two_sum2(u2f2(r0[x], r0[x + 1]), u2f2(r1[x], r1[x + 1]));
                         const dfl2 v = two_sum2(v01.h, u2f2(r2[x], r2[x + 1]));
-                        const float2 vlo = __fadd2_rn(__fadd2_rn(v01.l, v.l), u2f2(r3[x], r3[x + 1]));
+                        const float2 vlo = __fadd2_rn(v01.l, v.l);
                         const dfl2 z = two_sum2(H[4 * g + x / 2], __fmul2_rn(v.h, F));
                         H[4 * g + x / 2] = z.h;
                         float2 &ls = Ls[cp * LPAD + row];
                         ls = __fadd2_rn(ls, __fadd2_rn(z.l, __fmul2_rn(vlo, F)));
                     }
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncwarp();
-                if (lane == 0) mbar::arrive(s_acce);
                 // (B): every drain thread is done with the column exponents
                 asm volatile("bar.sync 1, 512;" ::: "memory");
                 ++m;
