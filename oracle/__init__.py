@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "coupling_oracle.c")
+SOURCE = _SRC
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborcl.so")
 _lock = threading.Lock()
@@ -27,22 +28,36 @@ _lib = None
 TT, TE, EE, EEBB, EB = 1, 2, 4, 8, 16
 SPEC_BITS = (TT, TE, EE, EEBB, EB)
 
-FAULTS = {"none": 0, "drop_2l3p1": 1, "b_weight": 2, "prefactor_l1": 3,
-          "swap_parity": 4, "no_normalise": 5}
-
-
 def build(force=False):
     """Compile the C oracle into oracle/_build/liborcl.so (gcc, -O2, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
         return _SO
-    tmp = _SO + ".tmp%d" % os.getpid()
+    return compile_source(_SRC, _SO)
+
+
+def compile_source(src, so):
+    """gcc -O2 + OpenMP of one C source into a shared library."""
+    tmp = so + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC",
-           "-shared", _SRC, "-o", tmp, "-lm"]
+           "-shared", src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def load_library(path):
+    """ctypes handle of a compiled oracle with its argument types set."""
+    L = ctypes.CDLL(path)
+    ip = ctypes.POINTER(ctypes.c_int)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.orc_threej_j1.argtypes = [ctypes.c_int] * 5 + [dp, ctypes.c_int]
+    L.orc_threej_j1.restype = ctypes.c_int
+    L.orc_coupling_pairs.argtypes = [ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, dp,
+                                     ctypes.c_int, ip, ctypes.c_uint, dp, dp, ctypes.c_int]
+    L.orc_coupling_pairs.restype = ctypes.c_int
+    return L
 
 
 def lib():
@@ -50,16 +65,7 @@ def lib():
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_SO)
-            ip = ctypes.POINTER(ctypes.c_int)
-            dp = ctypes.POINTER(ctypes.c_double)
-            L.orc_threej_j1.argtypes = [ctypes.c_int] * 5 + [dp, ctypes.c_int]
-            L.orc_threej_j1.restype = ctypes.c_int
-            L.orc_coupling_pairs.argtypes = [ctypes.c_int, ip, ip, ctypes.c_int, dp, dp, dp,
-                                             ctypes.c_int, ip, ctypes.c_uint, dp, dp,
-                                             ctypes.c_int, ctypes.c_int]
-            L.orc_coupling_pairs.restype = ctypes.c_int
-            _lib = L
+            _lib = load_library(_SO)
     return _lib
 
 
@@ -94,11 +100,13 @@ def _win(W, n_win, w_len):
 
 
 def coupling_pairs(l1s, l2s, W_tt=None, W_tp=None, W_pp=None, spectra=TT,
-                   band_limit=None, threads=0, fault="none"):
+                   band_limit=None, threads=0, library=None):
     """M and S_abs for the listed (l1, l2) pairs.
 
     W_* are [n_win, w_len] (or 1-D for one window).  Returns two arrays of
-    shape [n_win, nspec, npairs]."""
+    shape [n_win, nspec, npairs].  `library` (default: this oracle) is a
+    handle from load_library with the same entry points -- the pin tests pass
+    copies of the oracle with a planted mistake."""
     ref = next(W for W in (W_tt, W_tp, W_pp) if W is not None)
     ref = np.asarray(ref)
     if ref.ndim == 1:
@@ -111,21 +119,21 @@ def coupling_pairs(l1s, l2s, W_tt=None, W_tp=None, W_pp=None, spectra=TT,
     ns = nspec(spectra)
     out = np.zeros((n_win, ns, l1s.size), dtype=np.float64)
     sab = np.zeros_like(out)
-    rc = lib().orc_coupling_pairs(int(l1s.size), _ip(l1s), _ip(l2s), n_win, _dp(Wt), _dp(Wc),
+    rc = (library or lib()).orc_coupling_pairs(int(l1s.size), _ip(l1s), _ip(l2s), n_win, _dp(Wt), _dp(Wc),
                                   _dp(Wp), w_len, _ip(bl), spectra, _dp(out), _dp(sab),
-                                  int(threads), FAULTS[fault])
+                                  int(threads))
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return out, sab
 
 
 def coupling_dense(lmax, W_tt=None, W_tp=None, W_pp=None, spectra=TT, lmin=2,
-                   band_limit=None, threads=0, fault="none"):
+                   band_limit=None, threads=0, library=None):
     """Dense M[w][spec][l1-lmin][l2-lmin] and S_abs over lmin..lmax."""
     ls = np.arange(lmin, lmax + 1, dtype=np.int32)
     L1, L2 = np.meshgrid(ls, ls, indexing="ij")
     out, sab = coupling_pairs(L1.ravel(), L2.ravel(), W_tt, W_tp, W_pp, spectra,
-                              band_limit, threads, fault)
+                              band_limit, threads, library)
     n = ls.size
     return out.reshape(out.shape[0], out.shape[1], n, n), sab.reshape(out.shape[0], out.shape[1], n, n)
 

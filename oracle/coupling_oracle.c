@@ -50,17 +50,6 @@
 #define ORC_EEBB 8u
 #define ORC_EB   16u
 
-/* Planted-mistake switches, used only by the tests that show the pins are
- * sensitive: 0 = none. */
-#define FAULT_NONE            0
-#define FAULT_DROP_2L3P1      1   /* drop the (2 l3 + 1) weight            */
-#define FAULT_B_WEIGHT        2   /* 2j instead of 2j+1 in B(j)            */
-#define FAULT_PREFACTOR_L1    3   /* (2 l1 + 1) instead of (2 l2 + 1)      */
-#define FAULT_SWAP_PARITY     4   /* EE takes odd L, EEBB takes even L     */
-#define FAULT_NO_NORMALISE    5   /* skip the orthogonality normalisation  */
-
-static int g_fault = FAULT_NONE;
-
 /* A(j) of the Schulten-Gordon recursion for f(j) = (j j2 j3; m1 m2 m3). */
 static double sg_A(double j, double j2, double j3, double m1)
 {
@@ -74,7 +63,7 @@ static double sg_A(double j, double j2, double j3, double m1)
 /* B(j) of the Schulten-Gordon recursion. */
 static double sg_B(double j, double j2, double j3, double m1, double m2, double m3)
 {
-    double w = (g_fault == FAULT_B_WEIGHT) ? 2.0 * j : 2.0 * j + 1.0;
+    double w = 2.0 * j + 1.0;
     return -w * (j2 * (j2 + 1.0) * m1 - j3 * (j3 + 1.0) * m1 - j * (j + 1.0) * (m3 - m2));
 }
 
@@ -177,7 +166,7 @@ int orc_threej_j1(int j2, int j3, int m1, int m2, int m3, double *out, int out_l
         double j = jmin + k;
         norm += (2.0 * j + 1.0) * out[k] * out[k];
     }
-    double c = (g_fault == FAULT_NO_NORMALISE) ? 1e-3 : 1.0 / sqrt(norm);
+    double c = 1.0 / sqrt(norm);
     int sgn_exp = j2 - j3 - m1;
     double want = (sgn_exp % 2 == 0) ? 1.0 : -1.0;
     if ((out[n - 1] < 0.0) != (want < 0.0)) c = -c;
@@ -204,13 +193,12 @@ static int popcount5(unsigned s)
  *   out, sabs   [n_win][nspec][npairs]       nspec = bits set in spectra,
  *                                            ordered by bit value
  *   nthreads    OpenMP threads (<= 0: library default)
- *   fault       planted-mistake switch for the pin tests (0 in normal use)
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
 int orc_coupling_pairs(int npairs, const int *l1s, const int *l2s, int n_win,
                        const double *W_tt, const double *W_tp, const double *W_pp,
                        int w_len, const int *band_limit, unsigned spectra,
-                       double *out, double *sabs, int nthreads, int fault)
+                       double *out, double *sabs, int nthreads)
 {
     if (npairs < 0 || n_win < 1 || w_len < 1 || (spectra & ~31u) || !spectra) return -1;
     if ((spectra & ORC_TT) && !W_tt) return -1;
@@ -222,7 +210,6 @@ int orc_coupling_pairs(int npairs, const int *l1s, const int *l2s, int n_win,
         if (l1s[q] > lmax_seen) lmax_seen = l1s[q];
         if (l2s[q] > lmax_seen) lmax_seen = l2s[q];
     }
-    g_fault = fault;
     const int nspec = popcount5(spectra);
     const int want_pol = (spectra & (ORC_TE | ORC_EE | ORC_EEBB | ORC_EB)) != 0;
     const int buf_len = 2 * lmax_seen + 2;
@@ -253,7 +240,7 @@ int orc_coupling_pairs(int npairs, const int *l1s, const int *l2s, int n_win,
             int n22 = 0;
             if (want_pol && l1 >= 2 && l2 >= 2)
                 n22 = orc_threej_j1(l1, l2, 0, -2, 2, f22, buf_len);
-            const double pref = (g_fault == FAULT_PREFACTOR_L1) ? (2.0 * l1 + 1.0) : (2.0 * l2 + 1.0);
+            const double pref = 2.0 * l2 + 1.0;
             for (int w = 0; w < n_win; w++) {
                 int top = hi;
                 if (top > w_len - 1) top = w_len - 1;
@@ -267,19 +254,17 @@ int orc_coupling_pairs(int npairs, const int *l1s, const int *l2s, int n_win,
                     for (int l3 = lo; l3 <= top; l3++) {
                         const int k = l3 - lo;
                         const int even = ((l1 + l2 + l3) % 2) == 0;
-                        int sel_even = even, sel_odd = !even;
-                        if (g_fault == FAULT_SWAP_PARITY) { sel_even = !even; sel_odd = even; }
                         double s = 0.0;
                         if (bit == ORC_TT) {
                             s = (n00 > 0) ? f00[k] * f00[k] : 0.0;
                         } else if (n22 > 0) {
                             const double p = f22[k];
                             if (bit == ORC_TE)        s = even ? f00[k] * p : 0.0;
-                            else if (bit == ORC_EE)   s = sel_even ? p * p : 0.0;
-                            else if (bit == ORC_EEBB) s = sel_odd ? p * p : 0.0;
-                            else                      s = sel_even ? p * p : -p * p;
+                            else if (bit == ORC_EE)   s = even ? p * p : 0.0;
+                            else if (bit == ORC_EEBB) s = !even ? p * p : 0.0;
+                            else                      s = even ? p * p : -p * p;
                         }
-                        const double wt = (g_fault == FAULT_DROP_2L3P1) ? 1.0 : (2.0 * l3 + 1.0);
+                        const double wt = 2.0 * l3 + 1.0;
                         const double term = wt * W[l3] * s;
                         acc += term;
                         aabs += fabs(term);
@@ -294,6 +279,5 @@ int orc_coupling_pairs(int npairs, const int *l1s, const int *l2s, int n_win,
         free(f00);
         free(f22);
     }
-    g_fault = FAULT_NONE;
     return status;
 }

@@ -397,20 +397,55 @@ def test_binning_definition():
 
 
 # ---------------------------------------------------------------- planted mistakes
-def _pins_pass(fault):
+# Each mistake is planted in a copy of the oracle's source (one expression
+# replaced), compiled on its own; the oracle itself carries no switches.
+MISTAKES = {
+    # drop the (2 l3 + 1) weight of the l3 sum
+    "drop_2l3p1": [("const double wt = 2.0 * l3 + 1.0;", "const double wt = 1.0;")],
+    # 2j instead of 2j + 1 in B(j) of the recursion
+    "b_weight": [("double w = 2.0 * j + 1.0;", "double w = 2.0 * j;")],
+    # (2 l1 + 1) instead of (2 l2 + 1) as the prefactor
+    "prefactor_l1": [("const double pref = 2.0 * l2 + 1.0;", "const double pref = 2.0 * l1 + 1.0;")],
+    # the parity projectors swapped: EE takes odd L, EE->BB even L
+    "swap_parity": [("(bit == ORC_EE)   s = even ? p * p : 0.0;", "(bit == ORC_EE)   s = !even ? p * p : 0.0;"),
+                    ("(bit == ORC_EEBB) s = !even ? p * p : 0.0;", "(bit == ORC_EEBB) s = even ? p * p : 0.0;"),
+                    ("s = even ? p * p : -p * p;", "s = !even ? p * p : -p * p;")],
+    # the orthogonality normalisation skipped
+    "no_normalise": [("double c = 1.0 / sqrt(norm);", "double c = 1e-3;")],
+}
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return str(tmp_path_factory.mktemp("oracle_mutants"))
+
+
+def _mutant(name, where):
+    src = open(oracle.SOURCE).read()
+    for old, new in MISTAKES[name]:
+        assert src.count(old) == 1, (name, old)    # the planted site exists exactly once
+        src = src.replace(old, new)
+    path = os.path.join(where, name + ".c")
+    with open(path, "w") as f:
+        f.write(src)
+    return oracle.load_library(oracle.compile_source(path, os.path.join(where, "lib" + name + ".so")))
+
+
+def _pins_pass(library=None):
     lmax = 32
     sp = oracle.TT | oracle.TE | oracle.EE | oracle.EEBB | oracle.EB
     ok = True
-    M, _ = _dense(lmax, windows.full_sky(lmax), sp, fault=fault)
+    M, _ = oracle.coupling_dense(lmax, *([windows.full_sky(lmax)] * 3), spectra=sp, library=library)
     I = np.eye(lmax - 1)
     ok &= all(np.max(np.abs(M[0, s] - w)) < 1e-12 for s, w in zip(range(5), (I, I, I, 0 * I, I)))
-    M, _ = _dense(lmax, windows.constant(lmax), oracle.TT | oracle.EE | oracle.EEBB, fault=fault)
+    M, _ = oracle.coupling_dense(lmax, *([windows.constant(lmax)] * 3), spectra=oracle.TT | oracle.EE | oracle.EEBB,
+                                 library=library)
     l2 = np.arange(2, lmax + 1)
     ok &= np.max(np.abs(M[0, 0] / (2 * l2 + 1) - 1)) < 1e-12
     ok &= np.max(np.abs((M[0, 1] + M[0, 2]) / (2 * l2 + 1) - 1)) < 1e-12
     # a few direct symbol checks against Racah through the matrix: TE, EE at one pair
     W = windows.random_positive(lmax, seed=3)
-    M, _ = oracle.coupling_pairs([5], [9], W, W, W, oracle.TE | oracle.EE, fault=fault)
+    M, _ = oracle.coupling_pairs([5], [9], W, W, W, oracle.TE | oracle.EE, library=library)
     ref_te = sum((2 * l3 + 1) * W[l3] * racah.threej_float(5, 9, l3, 0, 0, 0) *
                  racah.threej_float(5, 9, l3, -2, 2, 0) for l3 in range(4, 15) if (14 + l3) % 2 == 0)
     ref_ee = sum((2 * l3 + 1) * W[l3] * racah.threej_float(5, 9, l3, -2, 2, 0) ** 2
@@ -420,10 +455,10 @@ def _pins_pass(fault):
     return bool(ok)
 
 
-def test_pins_pass_without_fault():
-    assert _pins_pass("none")
+def test_pins_pass_on_the_oracle():
+    assert _pins_pass()
 
 
-@pytest.mark.parametrize("fault", ["drop_2l3p1", "b_weight", "prefactor_l1", "swap_parity", "no_normalise"])
-def test_planted_mistake_is_caught(fault):
-    assert not _pins_pass(fault)
+@pytest.mark.parametrize("name", sorted(MISTAKES))
+def test_planted_mistake_is_caught(name, mutant_dir):
+    assert not _pins_pass(_mutant(name, mutant_dir))
