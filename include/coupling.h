@@ -259,19 +259,27 @@ cpl_status cpl_build_batch(cpl_ctx *ctx, const cpl_request *jobs, int n_jobs,
  *
  * It computes the same matrices as cpl_build with CPL_FP64 and dense output
  * (equal to rounding: it forms the pair coefficients directly rather than
- * from the context's per-l factor table) into `out` (device, caller-owned, cpl_output_size doubles) on the CURRENT
- * CUDA device, asynchronously on `stream`.  W_* are device pointers.  It needs
- * no context: its scratch (lookup tables, window weights, l3 caps) is one
- * fixed 1 MiB device array inside the library, which every GPU that loads
- * the library holds until the process exits.  Limits of that array:
+ * from the context's per-l factor table) into `out` (device, caller-owned,
+ * cpl_output_size doubles) on the CURRENT CUDA device, asynchronously on
+ * `stream`.  W_* and `out` must be device memory of the current device (or
+ * managed memory): anything else -- a host pointer, another GPU's memory --
+ * fails with CPL_ERR_ARG before any work is queued.  It needs no context:
+ * its scratch (the g / h lookup tables and the window weights) is one fixed
+ * 1 MiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.  Limits of that array:
  * lmax <= 4096 and n_windows <= 4; larger requests fail with CPL_ERR_RANGE,
  * binned output and CPL_MIXED_BF16 with CPL_ERR_UNSUPPORTED.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
- *   - All calls share the array and it keeps the last call's contents (each
- *     call rewrites what it reads).  Calls whose GPU work overlaps -- different
- *     streams without ordering between them, or different host threads --
- *     race on it and must be serialised by the caller.
+ *   - The first call on a device sets the array up: it looks up the array's
+ *     device address (cudaGetSymbolAddress) and writes the lookup tables
+ *     into it with a synchronous host-to-device copy.  Make that first call
+ *     before any stream capture.  Later calls only launch kernels (the
+ *     per-window l3 caps travel in the kernel arguments) and read no host
+ *     memory.
+ *   - All calls share the array and it keeps the last call's contents: the
+ *     tables never change after the set-up, and each call rewrites the
+ *     weights it reads.  Calls whose GPU work overlaps -- different streams
+ *     without ordering between them, or different host threads -- race on
+ *     the weights and must be serialised by the caller.
  */
 cpl_status cpl_build_noalloc(const cpl_request *r, double *out, void *stream);
 

@@ -6,20 +6,24 @@
 // cudaFree can cause, or code running where allocation calls are not
 // allowed.  For them this entry point runs the same separable FP64
 // contraction as cpl_build (a variant of its kernel that takes its tile from
-// the launch grid instead of a work list), but keeps every piece of scratch
-// -- the g / h lookup tables, the per-window l3 weights and the per-window
-// l3 caps -- in one file-scope device array of fixed size, so nothing is
-// allocated on the device at any call.  The caller passes the windows and
-// the output, both on the current device.
+// the launch grid instead of a work list), but keeps its scratch -- the g / h
+// lookup tables and the per-window l3 weights -- in one file-scope device
+// array of fixed size, so nothing is allocated on the device at any call.
+// The caller passes the windows and the output, both on the current device;
+// the per-window l3 caps travel by value in the kernel arguments.
 //
 // The array lives in every GPU that loads this library until the process
 // exits; host code cannot use its name as a device address, so its address
-// is looked up once per device with cudaGetSymbolAddress on the first call
-// made on that device (make that first call before any stream capture).
-// All calls share the array and it keeps the last call's contents: every
-// region a call reads is rewritten by that call before use, and two calls
-// whose work overlaps on the GPU (different streams without ordering, or
-// different host threads) race on it.
+// is looked up once per device with cudaGetSymbolAddress, by the first call
+// made on that device, which also writes the g / h tables into the array
+// once, for the largest supported l_max (a table prefix does not depend on
+// its length), with a synchronous host-to-device copy.  Make that first call
+// before any stream capture.  Later calls only launch kernels: they read no
+// host memory.  All calls share the array and it keeps the last call's
+// contents: the tables never change after the set-up, and every call
+// rewrites the weights it reads before using them; two calls whose work
+// overlaps on the GPU (different streams without ordering, or different host
+// threads) race on the weights.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,10 +53,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[cpl::NA_SCRATCH
 namespace cpl {
 namespace {
 
+struct NaCaps {
+    int v[NA_MAX_WINDOWS];   // last l3 with a nonzero weight, per window
+};
+
 struct NaArgs {
     const double *g, *h, *A;
     int a_stride;
-    const int *l3cap;
+    NaCaps l3cap;
     int lmax, lmin;
     double *out;
     int nspec;
@@ -89,7 +97,7 @@ __global__ void __launch_bounds__(NT) k_plain_noalloc(const NaArgs p) {
     const double *__restrict__ A = p.A + (size_t)win * p.a_stride;
     const double *__restrict__ g = p.g;
     const double *__restrict__ h = p.h;
-    const int cap = p.l3cap[win];
+    const int cap = p.l3cap.v[win];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int kcap_e = (cap - pi) >> 1;
@@ -240,10 +248,35 @@ __global__ void __launch_bounds__(NT) k_plain_noalloc(const NaArgs p) {
         }
 }
 
+// Weights A(l3) = (2 l3 + 1) W(l3) / (4 pi), zero above the window's cap and
+// up to a_stride: the formula and rounding of the context path's weight
+// kernel, with the caps taken by value.
+__global__ void k_weights_noalloc(const double *__restrict__ W, int w_len, const NaCaps caps,
+                                  double *__restrict__ A, int a_stride) {
+    const int win = blockIdx.y;
+    const int cap = caps.v[win];
+    const double inv4pi = 0.07957747154594767;   // 1 / (4 pi)
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < a_stride; l += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        if (l <= cap && l < w_len) v = (2.0 * l + 1.0) * W[(size_t)win * w_len + l] * inv4pi;
+        A[(size_t)win * a_stride + l] = v;
+    }
+}
+
+// Scratch layout: g | h (both for p <= NA_PMAX, written once per device) |
+// A[role][window][a_stride] (rewritten by every call).
+constexpr int NA_PMAX = 2 * NA_MAX_LMAX + 2 * (TILE_I + TILE_J) + 16;
+constexpr size_t NA_OFF_G = 0;
+constexpr size_t NA_OFF_H = (NA_OFF_G + sizeof(double) * (NA_PMAX + 1) + 255) & ~size_t(255);
+constexpr size_t NA_OFF_A = (NA_OFF_H + sizeof(double) * (NA_PMAX + 1) + 255) & ~size_t(255);
+static_assert(NA_OFF_A + sizeof(double) * (2 * NA_MAX_LMAX + 2) * NA_MAX_WINDOWS * 3 <= NA_SCRATCH_BYTES,
+              "the largest request must fit the no-allocation scratch");
+
 std::mutex g_na_mutex;
 unsigned char *g_na_ptr[NA_MAX_DEVICES] = {};
 
-// Device address of g_noalloc_scratch on `dev` (current device), looked up once.
+// Set-up on `dev` (the current device), once: the device address of
+// g_noalloc_scratch, and the g / h tables written into it.
 cpl_status na_scratch(int dev, unsigned char **ptr) {
     if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(CPL_ERR_RANGE, "device index too large");
     std::lock_guard<std::mutex> lock(g_na_mutex);
@@ -253,13 +286,37 @@ cpl_status na_scratch(int dev, unsigned char **ptr) {
         if (e != cudaSuccess || !p)
             return fail(CPL_ERR_CUDA, std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") +
                                           cudaGetErrorString(e));
-        g_na_ptr[dev] = static_cast<unsigned char *>(p);
+        unsigned char *base = static_cast<unsigned char *>(p);
+        std::vector<double> g, h;
+        build_tables_host(NA_PMAX, g, h);
+        e = cudaMemcpy(base + NA_OFF_G, g.data(), sizeof(double) * (NA_PMAX + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(base + NA_OFF_H, h.data(), sizeof(double) * (NA_PMAX + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess)
+            return fail(CPL_ERR_CUDA, std::string("writing the lookup tables into the no-allocation scratch failed: ") +
+                                          cudaGetErrorString(e));
+        g_na_ptr[dev] = base;
     }
     *ptr = g_na_ptr[dev];
     return CPL_OK;
 }
 
-size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+// A pointer the kernels may dereference on `dev`: device memory of that
+// device, or managed memory.
+cpl_status na_check_ptr(const void *p, int dev, const char *what) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(CPL_ERR_ARG, std::string(what) + " is not a CUDA pointer: " + cudaGetErrorString(e));
+    }
+    if (at.type == cudaMemoryTypeManaged) return CPL_OK;
+    if (at.type != cudaMemoryTypeDevice)
+        return fail(CPL_ERR_ARG, std::string(what) + " must be device memory (got a host pointer)");
+    if (at.device != dev)
+        return fail(CPL_ERR_ARG, std::string(what) + " lies on another device than the current one");
+    return CPL_OK;
+}
 
 cpl_status na_launch(int nge, bool odd, const NaArgs &a, dim3 grid, cudaStream_t st) {
     if (nge == 1) k_plain_noalloc<1, false><<<grid, NT, 0, st>>>(a);
@@ -300,7 +357,8 @@ extern "C" cpl_status cpl_build_noalloc(const cpl_request *r, double *out, void 
     if ((r->spectra & (kEE | kEEBB | kEB)) && !r->W_pp)
         return fail(CPL_ERR_ARG, "W_pp is NULL but a polarisation spectrum is requested");
     if (r->w_len < 1) return fail(CPL_ERR_ARG, "w_len must be >= 1");
-    int caps[NA_MAX_WINDOWS];
+    NaCaps caps;
+    for (int w = 0; w < NA_MAX_WINDOWS; ++w) caps.v[w] = -1;
     for (int w = 0; w < r->n_windows; ++w) {
         int top = 2 * r->lmax;
         if (r->band_limit) {
@@ -309,15 +367,12 @@ extern "C" cpl_status cpl_build_noalloc(const cpl_request *r, double *out, void 
         }
         if (r->w_len < top + 1)
             return fail(CPL_ERR_ARG, "w_len too short: the l3 sum needs W up to min(2 lmax, band_limit)");
-        caps[w] = top;
+        caps.v[w] = top;
     }
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("cudaGetDevice failed: ") + cudaGetErrorString(e));
-    unsigned char *base = nullptr;
-    cpl_status s = na_scratch(dev, &base);
-    if (s != CPL_OK) return s;
 
     // window roles that share a pointer share one sweep (as in cpl_build)
     struct Role {
@@ -338,41 +393,39 @@ extern "C" cpl_status cpl_build_noalloc(const cpl_request *r, double *out, void 
     add(r->W_tp, kTE);
     add(r->W_pp, kEE | kEEBB | kEB);
 
-    // scratch layout: g | h | l3 caps | A[role][window][a_stride]
-    const int pmax = 2 * r->lmax + 2 * (TILE_I + TILE_J) + 16;
+    // the kernels dereference these: device memory of the current device
+    cpl_status s;
+    const char *role_name[3] = {"W_tt", "W_tp", "W_pp"};
+    for (int q = 0; q < nroles; ++q) {
+        const char *nm = roles[q].W == r->W_tt ? role_name[0] : roles[q].W == r->W_tp ? role_name[1] : role_name[2];
+        if ((s = na_check_ptr(roles[q].W, dev, nm)) != CPL_OK) return s;
+    }
+    if ((s = na_check_ptr(out, dev, "out")) != CPL_OK) return s;
+
+    unsigned char *base = nullptr;
+    if ((s = na_scratch(dev, &base)) != CPL_OK) return s;
+
     const int a_stride = 2 * r->lmax + 2;
-    const size_t off_g = 0;
-    const size_t off_h = round256(off_g + sizeof(double) * (pmax + 1));
-    const size_t off_cap = round256(off_h + sizeof(double) * (pmax + 1));
-    const size_t off_A = round256(off_cap + sizeof(int) * NA_MAX_WINDOWS);
-    const size_t end = off_A + sizeof(double) * (size_t)a_stride * r->n_windows * nroles;
+    const size_t end = NA_OFF_A + sizeof(double) * (size_t)a_stride * r->n_windows * nroles;
     if (end > NA_SCRATCH_BYTES) return fail(CPL_ERR_RANGE, "request does not fit the 1 MiB no-allocation scratch");
 
-    std::vector<double> g, h;
-    build_tables_host(pmax, g, h);
     cudaStream_t st = (cudaStream_t)stream;
-    e = cudaMemcpyAsync(base + off_g, g.data(), sizeof(double) * (pmax + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + off_h, h.data(), sizeof(double) * (pmax + 1), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + off_cap, caps, sizeof(int) * r->n_windows, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("scratch upload failed: ") + cudaGetErrorString(e));
-
-    const int *d_caps = reinterpret_cast<const int *>(base + off_cap);
     const int nib = (r->lmax - r->lmin) / 2 / TILE_I + 1;
     const int njb = r->lmax / TILE_J + 1;
     const dim3 grid(njb, 2 * nib, r->n_windows);
     for (int q = 0; q < nroles; ++q) {
-        double *A = reinterpret_cast<double *>(base + off_A) + (size_t)q * a_stride * r->n_windows;
-        e = launch_weights(roles[q].W, r->w_len, r->n_windows, d_caps, A, a_stride, st);
+        double *A = reinterpret_cast<double *>(base + NA_OFF_A) + (size_t)q * a_stride * r->n_windows;
+        k_weights_noalloc<<<dim3((a_stride + 255) / 256, r->n_windows), 256, 0, st>>>(roles[q].W, r->w_len, caps, A,
+                                                                                      a_stride);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("kernel launch failed: ") + cudaGetErrorString(e));
         NaArgs a;
         std::memset(&a, 0, sizeof(a));
-        a.g = reinterpret_cast<const double *>(base + off_g);
-        a.h = reinterpret_cast<const double *>(base + off_h);
+        a.g = reinterpret_cast<const double *>(base + NA_OFF_G);
+        a.h = reinterpret_cast<const double *>(base + NA_OFF_H);
         a.A = A;
         a.a_stride = a_stride;
-        a.l3cap = d_caps;
+        a.l3cap = caps;
         a.lmax = r->lmax;
         a.lmin = r->lmin;
         a.out = out;
