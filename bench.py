@@ -48,7 +48,10 @@ METRIC = "M_l1l2 elements/s and 3j terms/s, lmax 3000-10000, batched vs plain FP
 UNIT = "elements/s"
 LMAX = 3000
 SPEC_NAMES = ("TT", "TE", "EE", "EEBB", "EB")
-FP64_PEAK_TFLOPS = 2.0 * 2 * 152 * 2.070e9 / 1e12   # 2 FLOP x 2 DFMA/clk/SM x 152 SMs x max clock
+# nominal FP64 pipe rate: 2 FLOP x 2 DFMA/clk/SM x 152 SMs x max clock (context only; the rooflines
+# use the rate the library's FMA probe measures in the same run, FP64_PEAK below)
+FP64_NOMINAL_TFLOPS = 2.0 * 2 * 152 * 2.070e9 / 1e12
+FP64_PEAK = {"tflops": FP64_NOMINAL_TFLOPS, "source": "nominal (probe not run)"}
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 
@@ -70,6 +73,41 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback 6.8 TB/s"
+
+
+def measure_fp64_peak(local, n_blocks=152 * 4, iters=3000, steps=5):
+    """The FP64 pipe's FMA rate on this GPU, measured with the library's probe
+    (cpl_probe_fp64: independent FMA chains, no memory traffic): median of
+    `steps` event-timed launches after three warm-ups, with the SM clock
+    sampled during them.  Sets FP64_PEAK and returns the record."""
+    import torch
+    from paper_2602_15605_gb300 import coupling
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda:%d" % local)
+    for _ in range(3):
+        coupling.probe_fp64(n_blocks, iters, sink)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    flop = 0.0
+    for a, b in evs:
+        a.record()
+        flop = coupling.probe_fp64(n_blocks, iters, sink)
+        b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+    tf = flop / (ms * 1e-3) / 1e12
+    rec = {"tflops": tf, "ms_per_launch": ms, "flop_per_launch": flop, "clocks": clk,
+           "nominal_tflops": FP64_NOMINAL_TFLOPS, "frac_of_nominal": tf / FP64_NOMINAL_TFLOPS,
+           "kernel": "k_fp64_probe: %d blocks x 256 threads, 8 chains x 8 x %d FMAs per thread" % (n_blocks, iters)}
+    if clk and clk.get("sm_mhz"):
+        rec["tflops_per_ghz"] = tf / (clk["sm_mhz"] / 1e3)
+    FP64_PEAK["tflops"] = tf
+    FP64_PEAK["source"] = ("measured in this run: FMA probe (cpl_probe_fp64) %.4f TFLOP/s at a median %s MHz; "
+                           "nominal %.4f" % (tf, clk.get("sm_mhz") if clk else "?", FP64_NOMINAL_TFLOPS))
+    return rec
 
 
 def parse():
@@ -423,6 +461,59 @@ def batch_arm(ctx, args, world, local, mixed_roofline):
             "l2": "flushed between steps (256 MiB write, outside the timed events)"}
 
 
+def large_lmax_arm(ctx, local, flush, lmax=20000):
+    """TT at a large l_max in plain FP64: the operand-table memory, which
+    kernel ran (the tabled one builds its A blocks on every call, so a
+    plain_tables_a launch marks it), the FP64 rate against the probe's peak,
+    for the default choice and for the self-staging fallback."""
+    import torch
+    from paper_2602_15605_gb300 import coupling, windows
+    W = torch.as_tensor(windows.mask_like(lmax, seed=41), dtype=torch.float64, device="cuda:%d" % local)
+    out = torch.empty((1, 1, lmax - 1, lmax - 1), dtype=torch.float64, device="cuda:%d" % local)
+    info = coupling.plan_info(lmax, 1, coupling.TT)
+    res = {"workload": "TT, l_max = %d, one mask-like window, dense %d^2 FP64 output" % (lmax, lmax - 1),
+           "table_bytes_b": info["table_bytes_b"], "table_bytes_a": info["table_bytes_a"],
+           "algorithmic_flop": info["flop"]}
+    prev = os.environ.get("CPL_PLAIN_TABLES")
+    try:
+        for name, env in (("tabled", None), ("self_staging", "0")):
+            if env is None:
+                os.environ.pop("CPL_PLAIN_TABLES", None)
+            else:
+                os.environ["CPL_PLAIN_TABLES"] = env
+            t0 = time.perf_counter()
+            ctx.build(lmax, W, None, None, coupling.TT, out=out)   # first call: tables for this size
+            torch.cuda.synchronize()
+            first_s = time.perf_counter() - t0
+            free_b, total_b = torch.cuda.mem_get_info(local)
+            flush.fill_(3)
+            ctx.profile(True)
+            ctx.stats(reset=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.build(lmax, W, None, None, coupling.TT, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            st = ctx.stats(reset=True)
+            ctx.profile(False)
+            ctx.sync()
+            ms = a.elapsed_time(b)
+            k = st.get("plain_fp64_tt", {"ms": 0.0, "flop": 0.0, "launches": 0})
+            tf = k["flop"] / (k["ms"] * 1e-3) / 1e12 if k["ms"] else 0.0
+            res[name] = {"ms": ms, "first_call_s": first_s, "elements_per_s": (lmax - 1) ** 2 / (ms * 1e-3),
+                         "kernel": "k_plain_tab (operand tables)" if st.get("plain_tables_a", {}).get("launches")
+                                   else "k_plain (self-staging)",
+                         "kernel_ms": k["ms"], "fp64_tflops": tf, "frac_of_measured_fp64_peak": tf / FP64_PEAK["tflops"],
+                         "device_free_gb_after": free_b / 1e9, "device_total_gb": total_b / 1e9}
+    finally:
+        if prev is None:
+            os.environ.pop("CPL_PLAIN_TABLES", None)
+        else:
+            os.environ["CPL_PLAIN_TABLES"] = prev
+    del out, W
+    return res
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local):
     import numpy as np
@@ -444,6 +535,8 @@ def run_ours(args, rank, world, local):
     import tempfile
     tune_file = os.path.join(tempfile.mkdtemp(prefix="cpl_tune_"), "tune.jsonl")
     ctx.tune(True, tune_file)
+    # the FP64 pipe's measured rate: the denominator of every FP64-bound roofline below
+    fp64_peak = measure_fp64_peak(local)
     Wt, Wc, Wp = windows_for_rank(rank)
     dev = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:%d" % local)
     dWt, dWc, dWp = dev(Wt), dev(Wc), dev(Wp)
@@ -504,12 +597,13 @@ def run_ours(args, rank, world, local):
         achieved = dom["flop"] / (dom["ms"] * 1e-3) / 1e12 if dom["ms"] > 0 else 0.0
         traffic = recorded_traffic("ncu_%s_full_spin_3000.txt" % dom_name, "plain_fp64.cu",
                                    "dram_bytes_per_launch_full_size") if LMAX == 3000 else None
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom_name,
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK["tflops"], "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK["tflops"], "traffic": traffic, "kernel": dom_name,
                 "kernel_ms_per_launch": dom["ms"] / max(dom["launches"], 1),
-                "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.26 TFLOP/s)"}
+                "peak_source": FP64_PEAK["source"]}
         if clk and clk.get("sm_mhz"):
-            roof["frac_at_sampled_clock"] = achieved / (2.0 * 2 * 152 * clk["sm_mhz"] * 1e6 / 1e12)
+            roof["frac_of_nominal_at_sampled_clock"] = achieved / (2.0 * 2 * 152 * clk["sm_mhz"] * 1e6 / 1e12)
+        roof["frac_of_nominal"] = achieved / FP64_NOMINAL_TFLOPS
         return roof
 
     def mixed_roofline(stats, traffic_summary=None):
@@ -574,9 +668,9 @@ def run_ours(args, rank, world, local):
         if dk is not None and dk[1]["ms"] > 0:
             eq = dk[1]["flop"] / (dk[1]["ms"] * 1e-3) / 1e12
             df32["roofline"] = {
-                "bound": "alu", "kernel": dk[0], "achieved": eq, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": eq / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz",
+                "bound": "alu", "kernel": dk[0], "achieved": eq, "peak": FP64_PEAK["tflops"], "unit": "TFLOP/s",
+                "frac": eq / FP64_PEAK["tflops"], "traffic": None,
+                "peak_source": FP64_PEAK["source"],
                 "achieved_counts": "FP64-equivalent FLOP of the contractions (2 per term and contraction, as the "
                                    "FP64 kernel counts them) / event time: the fraction says how far the FP32-pair "
                                    "kernel runs past the FP64 pipe's peak; ncu: FMA-heavy pipe ~80% busy"}
@@ -649,9 +743,9 @@ def run_ours(args, rank, world, local):
             decouple["n_rhs_%d" % n_rhs] = {
                 "ms": dms, "systems_per_s": nsys / (dms * 1e-3),
                 "solver": "fp32 blocked LU + fp64 iterative refinement" if 9 * n_rhs <= 2 * nb else "fp64 LU",
-                "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
-                             "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz",
+                "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK["tflops"], "unit": "TFLOP/s",
+                             "frac": tf / FP64_PEAK["tflops"], "traffic": None,
+                             "peak_source": FP64_PEAK["source"],
                              "achieved_counts": "FP64-equivalent flops of the direct solve (2n^3/3 + 2 n^2 n_rhs "
                                                 "per system) / median event time; the refined solver runs the "
                                                 "factorisation in FP32 and only the residuals in FP64; one CTA "
@@ -705,9 +799,9 @@ def run_ours(args, rank, world, local):
                 if cv_cb.get("ms"):
                     cv_tf = cv_cb["flop"] / (cv_cb["ms"] * 1e-3) / 1e12
                     cv_entry[cv_name]["combine_roofline"] = {
-                        "bound": "alu", "achieved": cv_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                        "frac": cv_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                        "peak_source": "derived: FP64 pipe 2 FMA/clk/SM x 152 SMs x 2070 MHz",
+                        "bound": "alu", "achieved": cv_tf, "peak": FP64_PEAK["tflops"], "unit": "TFLOP/s",
+                        "frac": cv_tf / FP64_PEAK["tflops"], "traffic": None,
+                        "peak_source": FP64_PEAK["source"],
                         "achieved_counts": "2 FLOP x 3 FP64 operations per upper-triangle element and term / "
                                            "event time of the combine launches (profiled pass); the kernel is "
                                            "FP64-pipe bound, DRAM below a fifth of its peak"}
@@ -718,6 +812,13 @@ def run_ours(args, rank, world, local):
     batch = None
     if not args.no_batch:
         batch = batch_arm(ctx, args, world, local, mixed_roofline)
+
+    # the plain path at a large l_max: TT at l_max = 20000 (one window), with the
+    # operand tables (the default while they fit half of the free memory) and
+    # with the self-staging kernel (CPL_PLAIN_TABLES=0, the fallback beyond that)
+    large = None
+    if not args.no_batch:
+        large = large_lmax_arm(ctx, local, flush)
 
     # end to end through the public host-buffer call
     e2e = None
@@ -740,6 +841,20 @@ def run_ours(args, rank, world, local):
         e2e = {"value": job_value(world, 5 * n_el, dt), "unit": UNIT, "h2d_bytes_per_step": int(3 * Wt.nbytes),
                "d2h_bytes_per_step": int(host_out.nbytes), "ms_per_step": dt * 1e3,
                "host_buffers": "pinned (page-locked) windows in and matrices out"}
+        # the other precision arm end to end through the same call
+        if other is not None:
+            o_prec = coupling.FP64 if args.precision == "mixed" else coupling.MIXED_BF16
+            ctx.build_host(LMAX, *hW, coupling.ALL, out=host_out, precision=o_prec)
+            k_o = max(3, min(args.steps, 10))
+            t0 = time.perf_counter()
+            for _ in range(k_o):
+                ctx.build_host(LMAX, *hW, coupling.ALL, out=host_out, precision=o_prec)
+            dt_o = max_over_ranks((time.perf_counter() - t0) / k_o, world, "cuda:%d" % local)
+            other["e2e"] = {"value": job_value(world, 5 * n_el, dt_o), "unit": UNIT,
+                            "h2d_bytes_per_step": int(3 * Wt.nbytes), "d2h_bytes_per_step": int(host_out.nbytes),
+                            "ms_per_step": dt_o * 1e3, "device_ms_per_step": other["ms_per_step"],
+                            "exposed_transfer_ms": dt_o * 1e3 - other["ms_per_step"],
+                            "host_buffers": "pinned (page-locked) windows in and matrices out"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -760,13 +875,15 @@ def run_ours(args, rank, world, local):
                 "terms_per_s_by_spectrum": {k: world * v / step_s for k, v in terms.items()},
                 "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches),
                 "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in stats.items()},
-                "clocks": clk, "wall_s_timed": t_wall, "spread": spread}
+                "clocks": clk, "wall_s_timed": t_wall, "spread": spread, "fp64_peak": fp64_peak}
         if other is not None:
             line["mixed" if args.precision == "fp64" else "fp64"] = other
         if df32 is not None:
             line["df32"] = df32
         if batch is not None:
             line["batch"] = batch
+        if large is not None:
+            line["large_lmax"] = large
         if threej is not None:
             line["threej_m11"] = threej
         if decouple is not None:

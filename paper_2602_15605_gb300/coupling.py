@@ -73,7 +73,8 @@ EXPORTS = ("cpl_version", "cpl_last_error", "cpl_ctx_create", "cpl_ctx_destroy",
            "cpl_output_size", "cpl_build", "cpl_build_host", "cpl_build_batch", "cpl_build_noalloc",
            "cpl_ctx_profile", "cpl_ctx_stats", "cpl_ctx_tune", "cpl_ctx_validate",
            "cpl_ctx_inject_alloc_failure", "cpl_threej_m11",
-           "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table", "cpl_h_table", "cpl_plan_info_fp64")
+           "cpl_decouple", "cpl_cov_gaussian", "cpl_g_table", "cpl_h_table", "cpl_plan_info_fp64",
+           "cpl_probe_fp64")
 
 _lock = threading.Lock()
 _lib = None
@@ -107,6 +108,7 @@ def load():
         L.cpl_build_batch.argtypes = [vp, ctypes.POINTER(Request), ip, ctypes.POINTER(vp), vp]
         L.cpl_g_table.argtypes = [ip, dp]
         L.cpl_h_table.argtypes = [ip, dp]
+        L.cpl_probe_fp64.argtypes = [ip, ip, vp, dp, vp]
         L.cpl_ctx_profile.argtypes = [vp, ip]
         L.cpl_ctx_validate.argtypes = [vp, ip]
         L.cpl_ctx_tune.argtypes = [vp, ip, ctypes.c_char_p]
@@ -138,6 +140,18 @@ def g_table(pmax):
     out = np.zeros(pmax + 1, dtype=np.float64)
     _check(load().cpl_g_table(int(pmax), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def probe_fp64(n_blocks, iters, sink, stream=None):
+    """cpl_probe_fp64: launch the FP64 FMA throughput probe on torch's current
+    stream (or `stream`); `sink` is a device float64 tensor.  Returns the
+    launch's FLOP count; time it with CUDA events on the same stream."""
+    import torch
+    st = torch.cuda.current_stream(sink.device).cuda_stream if stream is None else stream
+    flop = ctypes.c_double(0.0)
+    _check(load().cpl_probe_fp64(int(n_blocks), int(iters), ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flop),
+                                 ctypes.c_void_p(st)))
+    return flop.value
 
 
 def h_table(pmax):

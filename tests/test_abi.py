@@ -163,6 +163,19 @@ def test_output_size_and_validation(lib):
     assert _status(lambda: coupling.output_size(10001, 1, coupling.TT, precision=coupling.DF32)) == 2
 
 
+def test_probe_argument_errors(lib):
+    import ctypes
+    flop = ctypes.c_double(0.0)
+    sink = ctypes.c_double(0.0)
+    L = coupling.load()
+    assert L.cpl_probe_fp64(0, 10, ctypes.byref(sink), ctypes.byref(flop), None) == 1
+    assert L.cpl_probe_fp64(10, 0, ctypes.byref(sink), ctypes.byref(flop), None) == 1
+    assert L.cpl_probe_fp64(10, 10, None, ctypes.byref(flop), None) == 1
+    assert L.cpl_probe_fp64(10, 10, ctypes.byref(sink), None, None) == 1
+    assert L.cpl_probe_fp64(1 << 21, 10, ctypes.byref(sink), ctypes.byref(flop), None) == 2
+    assert flop.value == 0.0
+
+
 def test_ctx_create_without_gpu_fails_cleanly(lib):
     try:
         import torch
