@@ -118,7 +118,9 @@ struct MxPrepAArgs {
     const float *gh, *gl;          // g table as double-float
     const int *l3cap;              // [nsrc] last l3 with nonzero weight
     int nsrc;
-    int alpha_mask;                // which A variants to build (bit alpha)
+    int alpha_mask;                // which A variants the request uses (bit alpha)
+    const int *src_role;           // [nsrc] role bits per source: a row group builds only the
+                                   // variants its sources' contractions read
     uint8_t *Aimg;
     int16_t *eA, *emaxA;
     MxLayout L;

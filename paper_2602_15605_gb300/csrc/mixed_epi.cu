@@ -50,6 +50,30 @@ __device__ __forceinline__ void pair_coeffs(const void *coef, int l1, int l2, xd
     qB[2] = xdf_mul(T1[8], T2[11]);                 //  C e1^2
 }
 
+// The same coefficients without renormalising each product: mantissa
+// (T1 T2 mantissas, |h| in [1, 4)) and the summed exponents.  The dense
+// epilogue's frame sums take the exponent of every term anyway.
+__device__ __forceinline__ xdf xdf_mul_raw(const xdf &a, const xdf &b) {
+    const dfl m = df_mul(dfl{a.h, a.l}, dfl{b.h, b.l});
+    return {m.h, m.l, a.e + b.e};
+}
+__device__ __forceinline__ void pair_coeffs_raw(const void *coef, int l1, int l2, xdf (&c)[12]) {
+    const xdf *T1 = reinterpret_cast<const xdf *>(coef) + (size_t)l1 * MX_COEF_N;
+    const xdf *T2 = reinterpret_cast<const xdf *>(coef) + (size_t)l2 * MX_COEF_N + MX_COEF_A;
+    c[0] = xdf_mul_raw(T1[0], T2[0]);              //  r c0
+    c[1] = xdf_neg(xdf_mul_raw(T1[1], T2[1]));     // -r c1
+    c[2] = xdf_neg(xdf_mul_raw(T1[1], T2[2]));     // -r c2
+    c[3] = xdf_mul_raw(T1[2], T2[3]);              //  r^2 c0^2
+    c[4] = xdf_neg(xdf_mul_raw(T1[3], T2[4]));     // -2 r^2 c0 c1
+    c[5] = xdf_neg(xdf_mul_raw(T1[3], T2[5]));     // -2 r^2 c0 c2
+    c[6] = xdf_mul_raw(T1[4], T2[6]);              //  r^2 c1^2
+    c[7] = xdf_mul_raw(T1[5], T2[7]);              //  2 r^2 c1 c2
+    c[8] = xdf_mul_raw(T1[4], T2[8]);              //  r^2 c2^2
+    c[9] = xdf_mul_raw(T1[6], T2[9]);              //  C e0^2
+    c[10] = xdf_neg(xdf_mul_raw(T1[7], T2[10]));   // -2 C e0 e1
+    c[11] = xdf_mul_raw(T1[8], T2[11]);            //  C e1^2
+}
+
 // Binned-output epilogue.  One thread per pair (parity, i, j), i fastest
 // across the block (the GEMM output is column-major, so the reads coalesce);
 // each pair's band-power contributions are added to the output with FP64
@@ -139,8 +163,9 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
 // l1 = l2 - d) are runs of 16 consecutive elements.  Each thread forms its pair's 12 combination
 // coefficients once in extended double-float and keeps them in registers;
 // per row source it combines the contractions in one exponent frame per
-// spectrum, converts the (2 l2 + 1) and (2 l1 + 1) multiples to FP64 with
-// integer operations, and stages them in shared memory for row-wise writes.
+// spectrum, converts each spectrum to FP64 with integer operations, scales it
+// by (2 l2 + 1) and (2 l1 + 1) in FP64, and stages the two values in shared
+// memory for row-wise writes.  Blocks that hold no valid pair return at once.
 constexpr int EB_I = 8, EB_J = 16, EB_P = 2 * EB_I * EB_J, EB_T = EB_P;
 
 struct Term {
@@ -148,36 +173,33 @@ struct Term {
     int x;   // exponent of the unit
 };
 
-// sum_t m_t 2^(x_t) in one frame: returns (dd, exponent)
+// sum_t m_t 2^(x_t) in one frame: returns (dd, exponent).  The frame E is the
+// largest term's exponent; terms below 2^-90 of 2^E are dropped (even after
+// the expansion's cancellation, at most 2^7, they lie far below FP64's
+// rounding of the result), which keeps every shift k = x_t - E inside FP32's
+// normal exponent range (|m_t| < 2^34 and normal), so one multiplication by
+// 2^k scales each part.
 template <int N>
 __device__ __forceinline__ xdf frame_sum(const Term (&t)[N]) {
     int E = -1000000;
+    int lg[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q)
-        if (t[q].m.h != 0.0f) E = max(E, t[q].x + ilogbf_fast(fabsf(t[q].m.h)));
+    for (int q = 0; q < N; ++q) {
+        lg[q] = ilogbf_fast(fabsf(t[q].m.h));
+        if (t[q].m.h != 0.0f) E = max(E, t[q].x + lg[q]);
+    }
     if (E == -1000000) return {0.f, 0.f, 0};
     dfl s = {0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-        if (t[q].m.h == 0.0f) continue;
-        const int k = t[q].x - E;           // the term's magnitude is 2^(k + ilogb m) <= 1
-        if (k < -230) continue;
-        s = df_add(s, dfl{scale2(t[q].m.h, k), scale2(t[q].m.l, k)});
+        if (t[q].m.h == 0.0f || t[q].x + lg[q] - E < -90) continue;
+        const float f = pow2f(t[q].x - E);
+        s = df_add(s, dfl{t[q].m.h * f, t[q].m.l * f});
     }
     return {s.h, s.l, E};
 }
 
 __device__ __forceinline__ Term term(xdf c, dfl m, int e) { return {df_mul(dfl{c.h, c.l}, m), c.e + e}; }
-
-__device__ __forceinline__ double times_int(xdf v, int f) {
-    // v * f for a small positive integer f, then FP64
-    const float ff = (float)f;
-    const float p = v.h * ff;
-    float e = fmaf(v.h, ff, -p);
-    e = fmaf(v.l, ff, e);
-    const dfl q = df_quick(p, e);
-    return xdf_to_double(xdf{q.h, q.l, v.e});
-}
 
 // Shared memory of one block: the staged rows of M, and the pair
 // coefficients (kept out of registers so that more blocks fit an SM).
@@ -187,7 +209,7 @@ struct EpiSmem {
     int cfe[12][EB_T];
 };
 
-__global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a) {
+__global__ void __launch_bounds__(EB_T, 4) k_mixed_epilogue_dense(const MxEpiArgs a) {
     extern __shared__ __align__(16) uint8_t epi_smem[];
     EpiSmem &sm = *reinterpret_cast<EpiSmem *>(epi_smem);
     const MxLayout &L = a.L;
@@ -198,20 +220,22 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
     const int i = i0 + ii, j = j0 + jj;
     const int l1 = j - i, l2 = i + j + pi;
     const bool valid = !(l1 < L1min || l2 > a.lmax || l1 > l2);
+    // a block without a valid pair (l1 = j - i >= L1min and l2 = i + j + pi <= lmax
+    // fail for all of its i, j) has nothing to write
+    if (j0 + EB_J - 1 - i0 < L1min || i0 + j0 > a.lmax) return;
 
     // ---- coefficients of this thread's pair (TE[0..2], EE[3..8], EE->BB[9..11])
     if (valid) {
-        xdf qTE[3], qEE[6], qB[3];
-        pair_coeffs(a.coef, l1, l2, qTE, qEE, qB);
-        const xdf *c[12] = {&qTE[0], &qTE[1], &qTE[2], &qEE[0], &qEE[1], &qEE[2],
-                            &qEE[3], &qEE[4], &qEE[5], &qB[0], &qB[1], &qB[2]};
+        xdf c[12];
+        pair_coeffs_raw(a.coef, l1, l2, c);
 #pragma unroll
         for (int x = 0; x < 12; ++x) {
-            sm.cfh[x][q] = c[x]->h;
-            sm.cfl[x][q] = c[x]->l;
-            sm.cfe[x][q] = c[x]->e;
+            sm.cfh[x][q] = c[x].h;
+            sm.cfl[x][q] = c[x].l;
+            sm.cfe[x][q] = c[x].e;
         }
     }
+    const double f12 = 2.0 * l2 + 1.0, f21 = 2.0 * l1 + 1.0;   // M[l1][l2] and the mirror M[l2][l1]
 
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const long long ncols = (long long)L.NC_B * MX_BJ;
@@ -299,8 +323,9 @@ __global__ void __launch_bounds__(EB_T) k_mixed_epilogue_dense(const MxEpiArgs a
 #pragma unroll
             for (int x = 0; x < 5; ++x) {
                 if (!(role & bits[x])) continue;
-                sm.stage[x][0][q] = times_int(X[x], 2 * l2 + 1);
-                sm.stage[x][1][q] = times_int(X[x], 2 * l1 + 1);
+                const double v = xdf_to_double(X[x]);
+                sm.stage[x][0][q] = v * f12;
+                sm.stage[x][1][q] = v * f21;
             }
         }
         __syncthreads();

@@ -496,6 +496,7 @@ cpl_status run_plan(cpl_ctx *c, MxPlan &P, cudaStream_t st) {
             pa.gh = gh;
             pa.gl = gl;
             pa.l3cap = cap;
+            pa.src_role = reinterpret_cast<const int *>(meta + J.m_src) + J.nsrc;
             pa.nsrc = J.nsrc;
             pa.alpha_mask = J.alpha_mask;
             pa.Aimg = base + J.o_Aimg;

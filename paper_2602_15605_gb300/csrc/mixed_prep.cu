@@ -77,8 +77,9 @@ __device__ __forceinline__ int warp_max(int v) {
 // mantissas with an exponent (the weight keeps its own exponent because
 // window spectra reach below the FP32 range): x = val 2^(e - ilogb(val) - 1)
 // relative to value_exp.  vex[q] = EXP_ZERO for a zero value.
-__device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, const float *Al, const int *Ae,
-                                         int cap, int i, int k, int pi, dfl (&val)[MX_NA], int (&vex)[MX_NA]) {
+__device__ __forceinline__ void a_values(const MxPrepAArgs &a, int vmask, const float *Ah, const float *Al,
+                                         const int *Ae, int cap, int i, int k, int pi, dfl (&val)[MX_NA],
+                                         int (&vex)[MX_NA]) {
 #pragma unroll
     for (int q = 0; q < MX_NA; ++q) {
         val[q] = {0.f, 0.f};
@@ -86,7 +87,7 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
     }
     // even sweep: l3 = 2k + pi, a0 = A(l3) g(i+k+pi) g(k-i), v = (2k+2i+2pi+1)(2k-2i)
     const int l3e = 2 * k + pi;
-    if ((a.alpha_mask & 7) && k >= i && l3e <= cap && Ah[l3e] != 0.f) {
+    if ((vmask & 7) && k >= i && l3e <= cap && Ah[l3e] != 0.f) {
         const dfl A = {Ah[l3e], Al[l3e]};
         const dfl g1 = {a.gh[i + k + pi], a.gl[i + k + pi]};
         const dfl g2 = {a.gh[k - i], a.gl[k - i]};
@@ -94,7 +95,7 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
         const int e = Ae[l3e];
         val[0] = a0;
         vex[0] = a0.h != 0.f ? value_exp(a0, e) : EXP_ZERO;
-        if (k > i && (a.alpha_mask & 6)) {
+        if (k > i && (vmask & 6)) {
             const dfl v = df_int_prod(2 * k + 2 * i + 2 * pi + 1, 2 * k - 2 * i);
             const dfl a0v = df_mul(a0, v);
             const dfl a0v2 = df_mul(a0v, v);
@@ -106,7 +107,7 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
     }
     // odd sweep: l3 = 2k + 1 - pi, a1 v = A(l3) g(i+k+1) g(k-i-pi) (2i+2k+2)(2k+1-2i-2pi)
     const int l3o = 2 * k + 1 - pi;
-    if ((a.alpha_mask & 8) && k >= i + pi && l3o <= cap && Ah[l3o] != 0.f) {
+    if ((vmask & 8) && k >= i + pi && l3o <= cap && Ah[l3o] != 0.f) {
         const dfl A = {Ah[l3o], Al[l3o]};
         const dfl g1 = {a.gh[i + k + 1], a.gl[i + k + 1]};
         const dfl g2 = {a.gh[k - i - pi], a.gl[k - i - pi]};
@@ -119,6 +120,25 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
     }
 }
 
+// Variants of the A operand that the contractions of a source with these role
+// bits read (mx_alpha of its products): a0 always, a0 v from TE on, a0 v^2
+// with EE, a1 v with the odd sweep.
+__device__ __forceinline__ int variants_of_role(int role) {
+    if (role & (kEE | kEEBB | kEB)) return (role & (kEEBB | kEB)) ? 15 : 7;
+    if (role & kTE) return 3;
+    if (role & kTT) return 1;
+    return 0;
+}
+
+// Packed FP32 pairs (sm_100+ f32x2 instructions): two values per instruction.
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
+    return *reinterpret_cast<float2 *>(&r);
+}
+
 // One block per (parity, row group, row block, octet of 8 tile rows): the 8
 // rows belong to one source (BI >= 8) and are 8 consecutive values of i.
 // Thread (warp w, lane) owns tile row 8 o + (lane & 7) and the 8 consecutive
@@ -128,7 +148,9 @@ __device__ __forceinline__ void a_values(const MxPrepAArgs &a, const float *Ah, 
 // shared memory (each thread its own 8 x 4 slots) and finds the row maxima
 // of the exponents (shuffles over the 4 lanes of a row, then shared memory
 // over the 8 warps); pass 2 writes the limbs of the kept values (a value's
-// shift against the row maximum needs only its weight's exponent).
+// shift against the row maximum needs only its weight's exponent), two values
+// per packed instruction.  A block builds only the variants that the
+// contractions of its row group's sources read.
 template <int S>
 __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     constexpr int NW = 256 / 32;
@@ -153,6 +175,10 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     const long long nrows = (long long)L.NRG * L.NB * MX_ROWS;
     const bool live = s < a.nsrc;
     const int cap = live ? a.l3cap[s] : -1;
+    int vmask = 0;   // the same for the whole block (its rows lie in one row group)
+    for (int x = 0; x < L.SRC; ++x)
+        if (rg * L.SRC + x < a.nsrc) vmask |= variants_of_role(a.src_role[rg * L.SRC + x]);
+    vmask &= a.alpha_mask;
     const float *Ah = a.Ah + (size_t)(live ? s : 0) * a.a_stride;
     const float *Al = a.Al + (size_t)(live ? s : 0) * a.a_stride;
     const int *Ae = a.Ae + (size_t)(live ? s : 0) * a.a_stride;
@@ -172,9 +198,10 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
         for (int m = 0; m < 8; ++m) {
             dfl val[MX_NA];
             int vex[MX_NA];
-            a_values(a, Ah, Al, Ae, cap, i, k0 + m, pi, val, vex);
+            a_values(a, vmask, Ah, Al, Ae, cap, i, k0 + m, pi, val, vex);
 #pragma unroll
             for (int q = 0; q < MX_NA; ++q) {
+                if (!((vmask >> q) & 1)) continue;
                 bmax[q] = max(bmax[q], vex[q]);
                 kept[(m * MX_NA + q) * 256 + tid] = make_float2(val[q].h, val[q].l);
             }
@@ -194,7 +221,7 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
 #pragma unroll
             for (int x = 0; x < NW; ++x) E[q] = max(E[q], wmax[buf][x][q8][q]);
             emax[q] = max(emax[q], E[q]);
-            if (w == 0 && kg == 0 && ((a.alpha_mask >> q) & 1))
+            if (w == 0 && kg == 0 && ((vmask >> q) & 1))
                 a.eA[(((long long)pi * MX_NA + q) * nrows + row_global) * L.NSB + sb] = (int16_t)E[q];
         }
         // ---- pass 2: limbs of the 8 values, one 16-byte store per limb and variant
@@ -202,28 +229,40 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
         if (kb < L.fA * b || kb >= L.NKBA) continue;
 #pragma unroll
         for (int q = 0; q < MX_NA; ++q) {
-            if (!((a.alpha_mask >> q) & 1)) continue;
+            if (!((vmask >> q) & 1)) continue;
             uint32_t pk[S][4];
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const float2 kv = kept[(m * MX_NA + q) * 256 + tid];
-                dfl y = {0.f, 0.f};
-                if (kv.x != 0.f && E[q] != EXP_ZERO) {
-                    // y = x 2^(7 - E), x = val 2^(vex - ilogb(val) - 1) = val 2^(weight exponent)
-                    const int l3 = q < 3 ? 2 * (k0 + m) + pi : 2 * (k0 + m) + 1 - pi;
-                    const int sh = Ae[l3] + 7 - E[q];
-                    y.h = scale2(kv.x, sh);
-                    y.l = scale2(kv.y, sh);
+            for (int mp = 0; mp < 4; ++mp) {
+                // values m = 2 mp (x lane, low half of each word) and 2 mp + 1 (y lane)
+                float yv[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+                for (int x = 0; x < 2; ++x) {
+                    const int m = 2 * mp + x;
+                    const float2 kv = kept[(m * MX_NA + q) * 256 + tid];
+                    if (kv.x != 0.f && E[q] != EXP_ZERO) {
+                        // y = x 2^(7 - E), x = val 2^(vex - ilogb(val) - 1) = val 2^(weight exponent)
+                        const int l3 = q < 3 ? 2 * (k0 + m) + pi : 2 * (k0 + m) + 1 - pi;
+                        const int sh = Ae[l3] + 7 - E[q];
+                        yv[x][0] = scale2(kv.x, sh);
+                        yv[x][1] = scale2(kv.y, sh);
+                    }
                 }
+                float2 yh = make_float2(yv[0][0], yv[1][0]), yl = make_float2(yv[0][1], yv[1][1]);
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
-                    const float l = rintf(y.h);
-                    const dfl z = df_two_sum(y.h - l, y.l);
-                    y.h = z.h * 256.0f;
-                    y.l = z.l * 256.0f;
-                    const uint32_t bits = __bfloat16_as_ushort(__float2bfloat16_rn(l * pow2f(-8 * t)));
-                    if (m & 1) pk[t][m >> 1] |= bits << 16;
-                    else pk[t][m >> 1] = bits;
+                    // digit l = rint(yh); the rest (yh - l) + yl by a fast two-sum, which is
+                    // exact here: yh - l is exact, and when it is nonzero it is at least
+                    // ulp(yh) >= 2 |yl|
+                    const float2 l = make_float2(rintf(yh.x), rintf(yh.y));
+                    const float2 d = f2sub(yh, l);
+                    const float2 sm = __fadd2_rn(d, yl);
+                    const float2 er = f2sub(yl, f2sub(sm, d));
+                    yh = __fmul2_rn(sm, make_float2(256.0f, 256.0f));
+                    yl = __fmul2_rn(er, make_float2(256.0f, 256.0f));
+                    const float sc = pow2f(-8 * t);
+                    const float2 lv = __fmul2_rn(l, make_float2(sc, sc));
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(lv.x, lv.y);   // .x in the low half
+                    pk[t][mp] = *reinterpret_cast<const uint32_t *>(&b2);
                 }
             }
             uint8_t *img = a.Aimg + mx_a_off(L, pi, q, rg, b, kb, 0) + mx_img_off(r, k0 % L.KB, L.KB);
@@ -235,7 +274,7 @@ __global__ void __launch_bounds__(256) k_prep_a(const MxPrepAArgs a) {
     if (w == 0 && kg == 0) {
 #pragma unroll
         for (int q = 0; q < MX_NA; ++q)
-            if ((a.alpha_mask >> q) & 1) a.emaxA[((long long)pi * MX_NA + q) * nrows + row_global] = (int16_t)emax[q];
+            if ((vmask >> q) & 1) a.emaxA[((long long)pi * MX_NA + q) * nrows + row_global] = (int16_t)emax[q];
     }
 }
 
