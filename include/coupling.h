@@ -477,16 +477,16 @@ cpl_status cpl_cov_gaussian(cpl_ctx *ctx, int lmax, int lmin, const cpl_cov_term
 /*
  * FP64 pipe throughput probe: the measured denominator of the plain path's
  * roofline (the paper's GPU comparison is an FP64 measurement, Sec. 4.2).
- * Launches n_blocks blocks of 256 threads on `stream`; every thread updates
- * a 4 x 4 tile of accumulators acc[r][c] = fma(x[r], y[c], acc[r][c]), all
- * operands in registers, 4 x iters times (64 x iters fused multiply-adds,
- * no memory traffic).  *flop (host) receives
- * the floating-point operations the launch performs (an FMA counts 2):
- * 2 * 64 * iters * 256 * n_blocks.  The caller times the launch with events
+ * Launches n_blocks blocks of 256 threads on `stream`; every thread runs
+ * 1024 x iters fused multiply-adds: a 4 x 4 tile of accumulators
+ * acc[r][c] = fma(a[r], b[c], acc[r][c]) whose operands it loads from a
+ * 32-deep shared-memory panel, as the contraction kernels do (no global
+ * memory traffic).  *flop (host) receives the floating-point operations the
+ * launch performs (an FMA counts 2): 2 * 1024 * iters * 256 * n_blocks.  The caller times the launch with events
  * on `stream`.  `sink` is a device double the kernel could write (it never
  * does; the condition keeps the sums from being optimised away).
  * Errors: CPL_ERR_ARG for n_blocks < 1, iters < 1 or a NULL pointer,
- * CPL_ERR_RANGE for n_blocks > 2^20 or iters > 2^24, CPL_ERR_CUDA if the
+ * CPL_ERR_RANGE for n_blocks > 2^20 or iters > 2^20, CPL_ERR_CUDA if the
  * launch fails.
  */
 cpl_status cpl_probe_fp64(int n_blocks, int iters, double *sink, double *flop, void *stream);

@@ -81,6 +81,11 @@ __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t ad, uint64_t bd, 
                    "=r"(r[7])                                                                      \
                  : "r"(addr))
 
+#define TMEM_LD4(addr, r)                                                                    \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"                   \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])                                  \
+                 : "r"(addr))
+
 constexpr int TQ = 4;                      // ticket ring slots
 
 // Packed FP32 pairs (sm_100+ f32x2 instructions): the drain handles two
@@ -390,51 +395,44 @@ __global__ void __launch_bounds__(NTH, 1) k_mixed_gemm(const MxGemmArgs a) {
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 // order >= 3 first: once it is in registers its accumulator is
-                // released, and the MMAs of the next block start on it
-                {
-                    uint32_t r3[32];
+                // released, and the MMAs of the next block start on it; its
+                // values join the low parts below (one update of the shared
+                // low part per element and block)
+                uint32_t r3[32];
 #pragma unroll
-                    for (int g = 0; g < 4; ++g) TMEM_LD8(lane_addr + 3 * MX_BJ + (uint32_t)(c0 + 8 * g), (r3 + 8 * g));
+                for (int g = 0; g < 4; ++g) TMEM_LD8(lane_addr + 3 * MX_BJ + (uint32_t)(c0 + 8 * g), (r3 + 8 * g));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar::arrive(s_acce3);
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    uint32_t r0[4], r1[4], r2[4];
+                    const uint32_t col = (uint32_t)(c0 + 4 * g);
+                    TMEM_LD4(lane_addr + col, r0);
+                    TMEM_LD4(lane_addr + MX_BJ + col, r1);
+                    TMEM_LD4(lane_addr + 2 * MX_BJ + col, r2);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                    __syncwarp();
-                    if (lane == 0) mbar::arrive(s_acce3);
-#pragma unroll
-                    for (int x = 0; x < 32; x += 2) {
-                        const int cp = (c0 + x) / 2;
-                        // scale of this block relative to the element's frame (0 if negligible)
-                        const float2 F = __fmul2_rn(fa2, sh.fcol[cp]);
-                        float2 &ls = Ls[cp * LPAD + row];
-                        ls = __fadd2_rn(ls, __fmul2_rn(u2f2(r3[x], r3[x + 1]), F));
-                    }
-                }
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    uint32_t r0[8], r1[8], r2[8];
-                    const uint32_t col = (uint32_t)(c0 + 8 * g);
-                    TMEM_LD8(lane_addr + col, r0);
-                    TMEM_LD8(lane_addr + MX_BJ + col, r1);
-                    TMEM_LD8(lane_addr + 2 * MX_BJ + col, r2);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (g == 3) {
+                    if (g == 7) {
                         // orders 0-2 are in registers: release their accumulators
                         asm volatile("tcgen05.fence::before_thread_sync;");
                         __syncwarp();
                         if (lane == 0) mbar::arrive(s_acce012);
                     }
 #pragma unroll
-                    for (int x = 0; x < 8; x += 2) {
-                        const int cp = (c0 + 8 * g + x) / 2;   // column pair
+                    for (int x = 0; x < 4; x += 2) {
+                        const int cp = (c0 + 4 * g + x) / 2;   // column pair
+                        // scale of this block relative to the element's frame (0 if negligible)
                         const float2 F = __fmul2_rn(fa2, sh.fcol[cp]);
                         // block value: orders 0, 1 and 2 summed exactly (two two-sums:
                         // with decaying operands order 2 can reach 2^-8 of order 0, so
                         // it must not be folded into the residue of the first sum);
-                        // the residues are then added in FP32
+                        // the residues and order >= 3 are then added in FP32
                         const dfl2 v01 = two_sum2(u2f2(r0[x], r0[x + 1]), u2f2(r1[x], r1[x + 1]));
                         const dfl2 v = two_sum2(v01.h, u2f2(r2[x], r2[x + 1]));
-                        const float2 vlo = __fadd2_rn(v01.l, v.l);
-                        const dfl2 z = two_sum2(H[4 * g + x / 2], __fmul2_rn(v.h, F));
-                        H[4 * g + x / 2] = z.h;
+                        const float2 vlo = __fadd2_rn(__fadd2_rn(v01.l, v.l), u2f2(r3[4 * g + x], r3[4 * g + x + 1]));
+                        const dfl2 z = two_sum2(H[2 * g + x / 2], __fmul2_rn(v.h, F));
+                        H[2 * g + x / 2] = z.h;
                         float2 &ls = Ls[cp * LPAD + row];
                         ls = __fadd2_rn(ls, __fadd2_rn(z.l, __fmul2_rn(vlo, F)));
                     }
