@@ -57,9 +57,8 @@ __device__ __forceinline__ xdf xdf_mul_raw(const xdf &a, const xdf &b) {
     const dfl m = df_mul(dfl{a.h, a.l}, dfl{b.h, b.l});
     return {m.h, m.l, a.e + b.e};
 }
-__device__ __forceinline__ void pair_coeffs_raw(const void *coef, int l1, int l2, xdf (&c)[12]) {
-    const xdf *T1 = reinterpret_cast<const xdf *>(coef) + (size_t)l1 * MX_COEF_N;
-    const xdf *T2 = reinterpret_cast<const xdf *>(coef) + (size_t)l2 * MX_COEF_N + MX_COEF_A;
+// T1: the MX_COEF_A factors of l1, T2: the MX_COEF_B factors of l2.
+__device__ __forceinline__ void pair_coeffs_raw(const xdf *T1, const xdf *T2, xdf (&c)[12]) {
     c[0] = xdf_mul_raw(T1[0], T2[0]);              //  r c0
     c[1] = xdf_neg(xdf_mul_raw(T1[1], T2[1]));     // -r c1
     c[2] = xdf_neg(xdf_mul_raw(T1[1], T2[2]));     // -r c2
@@ -167,6 +166,7 @@ __global__ void __launch_bounds__(128) k_mixed_epilogue(const MxEpiArgs a) {
 // by (2 l2 + 1) and (2 l1 + 1) in FP64, and stages the two values in shared
 // memory for row-wise writes.  Blocks that hold no valid pair return at once.
 constexpr int EB_I = 8, EB_J = 16, EB_P = 2 * EB_I * EB_J, EB_T = EB_P;
+constexpr int EB_NL1 = EB_I + EB_J - 1, EB_NL2 = EB_I + EB_J;   // l1 and l2 values of a block
 
 struct Term {
     dfl m;   // mantissa
@@ -224,16 +224,36 @@ __global__ void __launch_bounds__(EB_T, 4) k_mixed_epilogue_dense(const MxEpiArg
     // fail for all of its i, j) has nothing to write
     if (j0 + EB_J - 1 - i0 < L1min || i0 + j0 > a.lmax) return;
 
-    // ---- coefficients of this thread's pair (TE[0..2], EE[3..8], EE->BB[9..11])
-    if (valid) {
-        xdf c[12];
-        pair_coeffs_raw(a.coef, l1, l2, c);
-#pragma unroll
-        for (int x = 0; x < 12; ++x) {
-            sm.cfh[x][q] = c[x].h;
-            sm.cfl[x][q] = c[x].l;
-            sm.cfe[x][q] = c[x].e;
+    // ---- the block's per-l factors, staged in shared memory (coalesced rows of
+    // the table instead of 21 gathers per thread), in the stage buffer, which
+    // the source loop only uses later: l1 = j - i spans EB_NL1 values, l2 =
+    // i + j + pi EB_NL2
+    {
+        xdf *T1s = reinterpret_cast<xdf *>(&sm.stage[0][0][0]);
+        xdf *T2s = T1s + EB_NL1 * MX_COEF_A;
+        const xdf *tab = reinterpret_cast<const xdf *>(a.coef);
+        const int l1lo = j0 - i0 - (EB_I - 1), l2lo = i0 + j0;
+        for (int e = q; e < EB_NL1 * MX_COEF_A; e += EB_T) {
+            const int l = l1lo + e / MX_COEF_A;
+            if (l >= 0 && l <= a.lmax) T1s[e] = tab[(size_t)l * MX_COEF_N + e % MX_COEF_A];
         }
+        for (int e = q; e < EB_NL2 * MX_COEF_B; e += EB_T) {
+            const int l = l2lo + e / MX_COEF_B;
+            if (l <= a.lmax) T2s[e] = tab[(size_t)l * MX_COEF_N + MX_COEF_A + e % MX_COEF_B];
+        }
+        __syncthreads();
+        // ---- coefficients of this thread's pair (TE[0..2], EE[3..8], EE->BB[9..11])
+        if (valid) {
+            xdf c[12];
+            pair_coeffs_raw(T1s + (l1 - l1lo) * MX_COEF_A, T2s + (l2 - l2lo) * MX_COEF_B, c);
+#pragma unroll
+            for (int x = 0; x < 12; ++x) {
+                sm.cfh[x][q] = c[x].h;
+                sm.cfl[x][q] = c[x].l;
+                sm.cfe[x][q] = c[x].e;
+            }
+        }
+        __syncthreads();   // the stage buffer is free again
     }
     const double f12 = 2.0 * l2 + 1.0, f21 = 2.0 * l1 + 1.0;   // M[l1][l2] and the mirror M[l2][l1]
 

@@ -142,6 +142,27 @@ def test_five_limbs_faster_variant(ctx):
     assert max(errs.values()) <= 5e-9, errs
 
 
+def test_four_and_five_limbs_across_scale_blocks(ctx):
+    # mixed_slices = 4 and 5 run the 32-k stage variant of the GEMM (two stages,
+    # the order >= 3 products of one stage issued ahead of orders 0-2); l_max
+    # 700 gives items of up to three 256-k scale blocks.  Bounds: 4 limbs keep
+    # ~32 bits (measured ~1e-7), 5 limbs ~40 (the 5e-9 above)
+    lmax = 700
+    W = np.stack([windows.mask_like(lmax, seed=70 + q) for q in range(2)])
+    d = dev(W)
+    l1, l2 = sample_pairs(lmax, n_random=4000, band=3)
+    ref, sab = oracle.coupling_pairs(l1, l2, W, W, W, coupling.ALL)
+    import torch
+    a = torch.as_tensor(l1 - 2, device="cuda", dtype=torch.long)
+    b = torch.as_tensor(l2 - 2, device="cuda", dtype=torch.long)
+    for S, bound in ((4, 1e-6), (5, 5e-9)):
+        M = ctx.build(lmax, d, d, d, coupling.ALL, precision=coupling.MIXED_BF16, slices=S)
+        ctx.sync()
+        errs = per_spectrum(M[:, :, a, b].cpu().numpy(), ref, sab, ALLN)
+        print("mixed s=%d 700 x 2:" % S, errs)
+        assert max(errs.values()) <= bound, (S, errs)
+
+
 def test_two_windows_row_shape(ctx):
     # two windows per role: GEMM tiles of 2 sources x 64 i-values
     lmax = 333
