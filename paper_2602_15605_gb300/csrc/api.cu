@@ -723,6 +723,69 @@ cpl_status build_one(cpl_ctx *c, const cpl_request *r, double *out, cudaStream_t
     return build_fp64(c, r, out, st);
 }
 
+// Contractions a window-role group's GEMM runs (the separable products of its spectra).
+int group_products(unsigned spectra) {
+    if (spectra & (kEE | kEEBB | kEB)) return (spectra & (kEEBB | kEB)) ? 9 : 6;
+    if (spectra & kTE) return 3;
+    return 1;
+}
+
+// cpl_build_host for a mixed-precision dense request whose windows form
+// several role groups, into page-locked out_host: one build per group
+// (a request of the group's spectra and window), most contractions first,
+// each into its own region of the output staging buffer; once a group's
+// build is done its spectrum planes are copied to their places in out_host
+// on the copy stream (one strided copy per plane over the windows) while
+// the later groups compute.  The caller synchronises st; the copy stream is
+// synchronised here.
+cpl_status build_mixed_host_split(cpl_ctx *c, const cpl_request *rd, double *out_host, cudaStream_t st) {
+    std::vector<Group> groups = window_groups(rd);
+    std::stable_sort(groups.begin(), groups.end(), [](const Group &a, const Group &b) {
+        return group_products(a.spectra) > group_products(b.spectra);
+    });
+    if (!c->copy_stream) CPL_CUDA_TRY(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    while (c->copy_ev.size() < groups.size()) {
+        cudaEvent_t e;
+        CPL_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->copy_ev.push_back(e);
+    }
+    const size_t plane = (size_t)(rd->lmax - rd->lmin + 1) * (size_t)(rd->lmax - rd->lmin + 1);
+    const int nspec = spec_count(rd->spectra);
+    const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
+    double *stage = c->stage_out.as<double>();
+    size_t used = 0;   // doubles of the staging buffer taken by earlier groups
+    cpl_status s;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const Group &G = groups[gi];
+        cpl_request sub = *rd;
+        sub.spectra = G.spectra;
+        sub.W_tt = (G.spectra & kTT) ? G.W : nullptr;
+        sub.W_tp = (G.spectra & kTE) ? G.W : nullptr;
+        sub.W_pp = (G.spectra & (kEE | kEEBB | kEB)) ? G.W : nullptr;
+        const int nsub = spec_count(G.spectra);
+        double *dst = stage + used;
+        if ((s = build_one(c, &sub, dst, st)) != CPL_OK) {
+            (void)cudaStreamSynchronize(c->copy_stream);
+            return s;
+        }
+        CPL_CUDA_TRY(cudaEventRecord(c->copy_ev[gi], st));
+        CPL_CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->copy_ev[gi], 0));
+        for (int b = 0; b < 5; ++b) {
+            if (!(G.spectra & bits[b])) continue;
+            const int ss = spec_slot(G.spectra, bits[b]), fs = spec_slot(rd->spectra, bits[b]);
+            // plane ss of every window of the group's output to plane fs of out_host
+            CPL_CUDA_TRY(cudaMemcpy2DAsync(out_host + (size_t)fs * plane, sizeof(double) * plane * nspec,
+                                           dst + (size_t)ss * plane, sizeof(double) * plane * nsub,
+                                           sizeof(double) * plane, rd->n_windows, cudaMemcpyDeviceToHost,
+                                           c->copy_stream));
+        }
+        used += (size_t)rd->n_windows * nsub * plane;
+    }
+    const cudaError_t e = cudaStreamSynchronize(c->copy_stream);
+    if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));
+    return CPL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -931,7 +994,12 @@ cpl_status cpl_build_host(cpl_ctx *c, const cpl_request *r, double *out_host) {
     cudaPointerAttributes pa;
     bool pinned = cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
     cudaGetLastError();
-    if (rd.precision == CPL_MIXED_BF16 || !pinned) {
+    if (rd.precision == CPL_MIXED_BF16 && pinned && !rd.bin_edges && window_groups(&rd).size() > 1) {
+        // one build per window-role group, the group with the most contractions
+        // first; each group's matrices travel to the host on the copy stream
+        // while the later groups compute
+        if ((s = build_mixed_host_split(c, &rd, out_host, st)) != CPL_OK) return s;
+    } else if (rd.precision == CPL_MIXED_BF16 || !pinned) {
         if ((s = build_one(c, &rd, c->stage_out.as<double>(), st)) != CPL_OK) return s;
         CPL_CUDA_TRY(cudaMemcpyAsync(out_host, c->stage_out.ptr, ob, cudaMemcpyDeviceToHost, st));
     } else {

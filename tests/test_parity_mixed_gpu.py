@@ -163,6 +163,30 @@ def test_four_and_five_limbs_across_scale_blocks(ctx):
         assert max(errs.values()) <= bound, (S, errs)
 
 
+@pytest.mark.parametrize("shared_tt_pp", [False, True])
+def test_build_host_pinned_split_matches_device(ctx, shared_tt_pp):
+    # page-locked output of a mixed build with several window-role groups: one
+    # build per group, each group's planes copied to their places while the
+    # later groups compute (two windows; with W^TT = W^PP the groups are
+    # {TT, EE, EE->BB, EB} and {TE}, whose planes interleave in the output)
+    import torch
+    lmax = 257
+    Wt, Wc, Wp = (np.stack([windows.mask_like(lmax, seed=s + q) for q in range(2)]) for s in (90, 91, 92))
+    if shared_tt_pp:
+        Wp = Wt
+    dWt, dWc = dev(Wt), dev(Wc)
+    dWp = dWt if shared_tt_pp else dev(Wp)
+    Md = ctx.build(lmax, dWt, dWc, dWp, coupling.ALL, precision=coupling.MIXED_BF16).cpu().numpy()
+    pinned = torch.full(Md.shape, -1.0, dtype=torch.float64, pin_memory=True).numpy()
+    Mh = ctx.build_host(lmax, Wt, Wc, Wt if shared_tt_pp else Wp, coupling.ALL, precision=coupling.MIXED_BF16,
+                        out=pinned)
+    # the per-source limb contractions do not depend on which sources share a
+    # GEMM, so the split build is bit-identical to the single one
+    assert np.array_equal(Md, Mh)
+    pageable = ctx.build_host(lmax, Wt, Wc, Wt if shared_tt_pp else Wp, coupling.ALL, precision=coupling.MIXED_BF16)
+    assert np.array_equal(pageable, Mh)
+
+
 def test_two_windows_row_shape(ctx):
     # two windows per role: GEMM tiles of 2 sources x 64 i-values
     lmax = 333
