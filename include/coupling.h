@@ -223,7 +223,14 @@ cpl_status cpl_plan_info_fp64(const cpl_request *r, cpl_plan_info *info);
  * is a host buffer of cpl_output_size doubles.  The library copies the
  * windows to the device, builds, copies the result back and returns when
  * `out_host` is filled (synchronous).  Staging memory is owned by the
- * context and reused across calls.
+ * context and reused across calls.  When `out_host` is page-locked the
+ * device-to-host copies overlap the build: for CPL_FP64 and CPL_DF32 each
+ * kernel variant's output blocks travel while the later variants run; for a
+ * dense CPL_MIXED_BF16 request whose windows form several role groups (for
+ * instance separate W^TT, W^TP, W^PP) each group is built as a request of
+ * its own, most contractions first, and its planes travel while the later
+ * groups compute.  The result is the same as cpl_build's (bit for bit in the
+ * dense cases).
  */
 cpl_status cpl_build_host(cpl_ctx *ctx, const cpl_request *r, double *out_host);
 
