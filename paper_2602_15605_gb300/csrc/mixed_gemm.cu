@@ -115,7 +115,7 @@ __device__ __forceinline__ float pow2_or_zero(int e) { return e < -126 ? 0.0f : 
 // Stages at the start of a scale block whose order >= 3 products are issued
 // before the accumulators of orders 0-2 are free again (see the MMA issuer).
 template <int S>
-__host__ __device__ constexpr int mx_npre() { return S >= 6 ? 2 : 1; }
+__host__ __device__ constexpr int mx_npre() { return S >= 6 ? 3 : 1; }
 
 struct Shared {
     uint64_t full[3], empty[3], acc_full, acc_empty3, acc_empty012, done;
