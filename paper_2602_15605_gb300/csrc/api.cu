@@ -734,10 +734,10 @@ int group_products(unsigned spectra) {
 // several role groups, into page-locked out_host: one build per group
 // (a request of the group's spectra and window), most contractions first,
 // each into its own region of the output staging buffer; once a group's
-// build is done its spectrum planes are copied to their places in out_host
-// on the copy stream (one strided copy per plane over the windows) while
-// the later groups compute.  The caller synchronises st; the copy stream is
-// synchronised here.
+// build is done on the GPU its spectrum planes are copied to their places in
+// out_host on the copy stream (one strided copy per plane over the windows)
+// while the later groups compute.  The caller synchronises st; the copy
+// stream is synchronised here.
 cpl_status build_mixed_host_split(cpl_ctx *c, const cpl_request *rd, double *out_host, cudaStream_t st) {
     std::vector<Group> groups = window_groups(rd);
     std::stable_sort(groups.begin(), groups.end(), [](const Group &a, const Group &b) {
@@ -753,8 +753,11 @@ cpl_status build_mixed_host_split(cpl_ctx *c, const cpl_request *rd, double *out
     const int nspec = spec_count(rd->spectra);
     const unsigned bits[5] = {kTT, kTE, kEE, kEEBB, kEB};
     double *stage = c->stage_out.as<double>();
-    size_t used = 0;   // doubles of the staging buffer taken by earlier groups
     cpl_status s;
+    // every group's build is queued (and can fail, e.g. on an allocation)
+    // before any copy is: on an error the host buffer stays untouched
+    std::vector<size_t> first(groups.size());   // each group's offset in the staging buffer (doubles)
+    size_t used = 0;
     for (size_t gi = 0; gi < groups.size(); ++gi) {
         const Group &G = groups[gi];
         cpl_request sub = *rd;
@@ -762,13 +765,17 @@ cpl_status build_mixed_host_split(cpl_ctx *c, const cpl_request *rd, double *out
         sub.W_tt = (G.spectra & kTT) ? G.W : nullptr;
         sub.W_tp = (G.spectra & kTE) ? G.W : nullptr;
         sub.W_pp = (G.spectra & (kEE | kEEBB | kEB)) ? G.W : nullptr;
-        const int nsub = spec_count(G.spectra);
-        double *dst = stage + used;
-        if ((s = build_one(c, &sub, dst, st)) != CPL_OK) {
-            (void)cudaStreamSynchronize(c->copy_stream);
-            return s;
-        }
+        first[gi] = used;
+        if ((s = build_one(c, &sub, stage + used, st)) != CPL_OK) return s;
         CPL_CUDA_TRY(cudaEventRecord(c->copy_ev[gi], st));
+        used += (size_t)rd->n_windows * spec_count(G.spectra) * plane;
+    }
+    // the copies of a group wait for its build only, so they run while the
+    // later groups compute
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const Group &G = groups[gi];
+        const int nsub = spec_count(G.spectra);
+        const double *dst = stage + first[gi];
         CPL_CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->copy_ev[gi], 0));
         for (int b = 0; b < 5; ++b) {
             if (!(G.spectra & bits[b])) continue;
@@ -779,7 +786,6 @@ cpl_status build_mixed_host_split(cpl_ctx *c, const cpl_request *rd, double *out
                                            sizeof(double) * plane, rd->n_windows, cudaMemcpyDeviceToHost,
                                            c->copy_stream));
         }
-        used += (size_t)rd->n_windows * nsub * plane;
     }
     const cudaError_t e = cudaStreamSynchronize(c->copy_stream);
     if (e != cudaSuccess) return fail(CPL_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(e));

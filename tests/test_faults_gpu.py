@@ -69,6 +69,41 @@ def test_mixed_allocation_failures():
     assert n >= 6   # tables, double-float tables, B cache (3), arena, error word, ticket, plan metadata
 
 
+def test_mixed_host_split_allocation_failures():
+    # cpl_build_host into page-locked memory with three window-role groups:
+    # one build per group, copies overlapped with the later groups.  A failure
+    # in any group's build must leave the host buffer untouched (every build is
+    # queued before any copy), and the context must recover.
+    import torch
+    lmax = 120
+    Wt, Wc, Wp = (windows.mask_like(lmax, seed=s) for s in (11, 12, 13))
+    c = coupling.Context(0)
+    ref = c.build(lmax, dev(Wt), dev(Wc), dev(Wp), coupling.ALL, precision=coupling.MIXED_BF16).cpu().numpy()
+    c.close()
+    failures = 0
+    for n in range(1, 40):
+        c = coupling.Context(0)
+        try:
+            c.inject_alloc_failure(n)
+            host = torch.full(ref.shape, 7.0, dtype=torch.float64, pin_memory=True).numpy()
+            try:
+                c.build_host(lmax, Wt, Wc, Wp, coupling.ALL, precision=coupling.MIXED_BF16, out=host)
+                ok = True
+            except coupling.CouplingError as e:
+                ok = False
+                assert e.status == 3, e          # CPL_ERR_OOM
+                assert np.all(host == 7.0)       # untouched
+                failures += 1
+            c.inject_alloc_failure(0)
+            c.build_host(lmax, Wt, Wc, Wp, coupling.ALL, precision=coupling.MIXED_BF16, out=host)
+            assert np.array_equal(host, ref), n
+        finally:
+            c.close()
+        if ok:
+            break
+    assert failures >= 5   # staging, tables, B cache, arena, plan metadata of the group builds
+
+
 def test_df32_allocation_failures():
     lmax = 90
     Wt, Wc, Wp = (dev(windows.gaussian_taper(lmax, s)) for s in (6, 7, 8))
