@@ -46,6 +46,7 @@ namespace {
 constexpr int DC_THREADS = 512;
 constexpr int DC_WARPS = DC_THREADS / 32;
 constexpr int IR_ITMAX = 30;
+constexpr int IR_RB = 8;          // right-hand sides per pass of a residual thread
 constexpr double EPS64 = 1.1102230246251565e-16;   // 2^-53
 
 // One system: K = K1 (+ or -) K2 and b = P[f1] (+ or -) P[f2] by kind.
@@ -72,8 +73,24 @@ struct Scratch {           // static shared scalars of the block reductions
     double pv;
     int piv;
     double wnorm[2][DC_WARPS];            // per-warp |K|_inf and max |K_ij| candidates
-    unsigned long long wkey[2][DC_WARPS]; // per-warp pivot keys of the refined solver (2 buffers)
+    unsigned long long pkey[2][DC_WARPS]; // per-warp pivot keys of the refined solver's panel (2 buffers)
+    float prow[32], krow[32];             // the panel's pivot row and the row it replaces
 };
+
+// a[m] and a[m] = v for a run-time m, without indexing the register array
+// (which would place it in local memory)
+template <int N>
+__device__ __forceinline__ float pick(const float (&a)[N], int m) {
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < N; ++q) v = q == m ? a[q] : v;
+    return v;
+}
+template <int N>
+__device__ __forceinline__ void put(float (&a)[N], int m, float v) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) a[q] = q == m ? v : a[q];
+}
 
 __device__ __forceinline__ void argmax_combine(double &v, int &i, double v2, int i2) {
     if (v2 > v || (v2 == v && i2 < i)) {
@@ -129,143 +146,77 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// The largest of the DC_WARPS per-warp keys (every thread reads them all).
-__device__ __forceinline__ unsigned long long max_of_warps(const unsigned long long *w) {
-    unsigned long long v = 0ull;
-#pragma unroll
-    for (int q = 0; q < DC_WARPS; ++q) v = w[q] > v ? w[q] : v;
-    return v;
-}
-
-// FP32 LU + FP64 iterative refinement for n <= 32 NC.  Returns true with the
-// solution in xs[r * n + i] when every right-hand side met the stopping
-// rule; false sends the system to the FP64 solver.
-//
-// GB300 runs FP64 arithmetic, comparisons and conversions at 1/64 of the
-// FP32 rate, so besides the residual's n^2 FMAs per right-hand side the
-// solver spends no FP64 instruction per matrix element: K is rounded to FP32
-// unscaled (an entry outside FP32's range becomes inf or 0 and the
-// factorisation falls back), |K|_inf comes from FP32 row sums, maxima are
-// taken on the bit patterns of non-negative doubles, and the residual runs
-// one thread per row so no FP64 reduction is needed.  For kind 1 and 2 the
-// FP64 matrix K1 +- K2 is formed once into Kc (global scratch).
-//
-// The factorisation is LAPACK's right-looking blocked LU with 32-column
-// panels, on the system padded to np = 32 NC with identity rows and columns
+// The refined solver's factorisation: LAPACK's right-looking blocked LU
+// with 32-column panels of fl32(K) in L (row-major, ld = np + 4), on the
+// system padded to np = 32 NC with identity rows and columns
 // (the padding never pivots and leaves the n x n factors unchanged):
-//   panel: 32 elimination steps on its columns, each pivot found while the
-//          previous step updates that column -- the lane that owns it offers
-//          (|a|, ~row) as one 64-bit key; each warp leaves its largest key
-//          in shared memory and every thread takes the largest of those
-//          after the barrier (largest |a|, lowest row on ties, independent of
-//          timing) -- with the row swaps applied to full rows (two barriers a
-//          step);
+//   panel: 32 elimination steps on its columns with the panel in registers
+//          (warp w holds rows w + 16 m, lane = column).  Each pivot is found
+//          while the previous step updates that column: the lane that owns
+//          it offers (|a|, ~row) as one 64-bit key over its warp's rows, and
+//          every thread takes the largest of the 16 keys after the barrier
+//          (largest |a|, lowest row on ties, independent of timing).  The
+//          pivot row and the row it replaces pass through shared memory, the
+//          rest of the two rows is swapped in place, and each row's
+//          multiplier reaches its warp's lanes by a shuffle: two barriers a
+//          step and no shared-memory traffic per element (with the panel in
+//          shared memory every element's load, update and store sat on the
+//          step's critical path, ~2.8k clocks a step at n = 160);
 //   U12 = L11^-1 A12: one thread per column, the 32 unknowns in registers;
 //   A22 -= L21 U12: register tiles of 4 x 4, 32-deep, float4 shared loads.
-// perm[i] is the original row now at position i.
+// perm[i] is the original row now at position i, dinv[k] = 1 / U_kk.  Its
+// own function (not inlined) so that the panel's registers are allocated
+// apart from the refinement's arrays.  Returns false on a zero or non-finite
+// pivot.
 template <int NC>
-__device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, unsigned char *base,
-                                           const IrLayout &lay, Scratch &sc) {
+__device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &sc) {
     constexpr int NP = 32 * NC;
     constexpr int LDF = NP + 4;
-    constexpr int G2 = NC <= 4 ? 4 : (NC <= 8 ? 2 : 1);   // rows per group in the fill
+    constexpr int RPW = NP / DC_WARPS;   // panel rows per warp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int kind = S.kind;
-    const double *K1 = S.K1, *K2 = S.K2;
-    const double *P1 = S.P + (size_t)S.f1 * n, *P2 = S.P + (size_t)S.f2 * n;
-    const size_t pstride = (size_t)S.nf * n;
-    const double *Kr = kind ? Kc : K1;   // the FP64 matrix of the residuals
-    int *perm = reinterpret_cast<int *>(base + lay.perm);
-    float *dinv = reinterpret_cast<float *>(base + lay.dinv);
-    double *xs = reinterpret_cast<double *>(base + lay.x);
-    double *rs = reinterpret_cast<double *>(base + lay.r);
-    unsigned long long *xn = reinterpret_cast<unsigned long long *>(base + lay.xn);   // [2][R] bits of max |x|
-    unsigned long long *rn = reinterpret_cast<unsigned long long *>(base + lay.rn);   // [2][warp][R] bits of max |r|
-
-    // L = fl32(K) padded with identity (Kc = K1 +- K2 on the way), FP32 row sums of |L|
-    float wrow = 0.f;
-    for (int i0 = warp; i0 < NP; i0 += G2 * DC_WARPS) {
-        double v[G2][NC];
-#pragma unroll
-        for (int g = 0; g < G2; ++g) {
-            const int i = i0 + g * DC_WARPS;
-#pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                const int j = lane + 32 * m;
-                v[g][m] = (i < n && j < n) ? __ldg(K1 + (size_t)i * n + j) : (i == j ? 1.0 : 0.0);
-            }
-        }
-        if (kind) {
-#pragma unroll
-            for (int g = 0; g < G2; ++g) {
-                const int i = i0 + g * DC_WARPS;
-#pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    const int j = lane + 32 * m;
-                    if (i < n && j < n) {
-                        const double w = __ldg(K2 + (size_t)i * n + j);
-                        v[g][m] = kind == 1 ? v[g][m] + w : v[g][m] - w;
-                        Kc[(size_t)i * n + j] = v[g][m];
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < G2; ++g) {
-            const int i = i0 + g * DC_WARPS;
-            float rsum = 0.f;
-#pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                const int j = lane + 32 * m;
-                const float f = (float)v[g][m];
-                if (i < NP) L[(size_t)i * LDF + j] = f;
-                if (i < n) rsum += fabsf(f);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
-            wrow = fmaxf(wrow, rsum);
-        }
-    }
-    if (lane == 0) sc.wnorm[0][warp] = (double)wrow;
-    for (int i = tid; i < NP; i += DC_THREADS) perm[i] = i;
-    for (int idx = tid; idx < R * n; idx += DC_THREADS) {
-        const int r = idx / n, i = idx - r * n;
-        const double u = P1[r * pstride + i], w = P2[r * pstride + i];
-        xs[idx] = 0.0;
-        rs[idx] = kind == 0 ? u : (kind == 1 ? u + w : u - w);
-    }
-    __syncthreads();
-    float amax = 0.f;
-#pragma unroll
-    for (int q = 0; q < DC_WARPS; ++q) amax = fmaxf(amax, (float)sc.wnorm[0][q]);
-    if (!(amax > 0.f && amax <= 3.4028234663852886e38f)) return false;
-    const double anrm = (double)amax;
-
-    // blocked FP32 factorisation: L U = rows perm[0..np-1] of the padded fl32(K)
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
         const int k0 = 32 * c;
-        {
+        // the panel in registers: warp w holds rows w + DC_WARPS m, lane =
+        // column k0 + lane
+        float a[RPW];
+#pragma unroll
+        for (int m = 0; m < RPW; ++m) a[m] = L[(size_t)(warp + DC_WARPS * m) * LDF + k0 + lane];
+        if (lane == 0) {   // pivot key of column k0 over this warp's rows >= k0
             unsigned long long best = 0ull;
-            for (int i = k0 + tid; i < NP; i += DC_THREADS) {
-                const unsigned long long q = pivot_key(L[(size_t)i * LDF + k0], i);
-                best = q > best ? q : best;
+#pragma unroll
+            for (int m = 0; m < RPW; ++m) {
+                const int i = warp + DC_WARPS * m;
+                const unsigned long long q = pivot_key(a[m], i);
+                if (i >= k0) best = q > best ? q : best;
             }
-            best = warp_max_u64(best);
-            if (lane == 0) sc.wkey[k0 & 1][warp] = best;
+            sc.pkey[0][warp] = best;
         }
         __syncthreads();
         for (int t = 0; t < 32; ++t) {
             const int k = k0 + t;
-            const unsigned long long kk = max_of_warps(sc.wkey[k & 1]);
+            unsigned long long kk = 0ull;
+#pragma unroll
+            for (int q = 0; q < DC_WARPS; ++q) kk = sc.pkey[t & 1][q] > kk ? sc.pkey[t & 1][q] : kk;
             const int p = (int)(0xFFFFFFFFu - (unsigned)(kk & 0xFFFFFFFFull));
             const float pv = __uint_as_float((unsigned)(kk >> 32));
-            if (!(pv > 0.f && pv <= 3.4028234663852886e38f)) return false;
+            if (!(pv > 0.f && pv <= 3.4028234663852886e38f)) return false;   // the same decision in every thread
+            const int wk = k % DC_WARPS, mk = k / DC_WARPS, wp = p % DC_WARPS, mp = p / DC_WARPS;
+            // rows p and k of the panel through shared memory
+            if (warp == wp) sc.prow[lane] = pick(a, mp);
+            if (warp == wk && p != k) sc.krow[lane] = pick(a, mk);
+            __syncthreads();
+            const float pr = sc.prow[lane];   // the pivot row's entry in this lane's column
             if (p != k) {
-                for (int j = tid; j < NP; j += DC_THREADS) {
-                    const float tmp = L[(size_t)k * LDF + j];
-                    L[(size_t)k * LDF + j] = L[(size_t)p * LDF + j];
-                    L[(size_t)p * LDF + j] = tmp;
+                if (warp == wk) put(a, mk, pr);
+                if (warp == wp) put(a, mp, sc.krow[lane]);
+                // the rest of rows k and p (the factors left of the panel, the
+                // trailing columns right of it) in place
+                for (int j = tid; j < NP - 32; j += DC_THREADS) {
+                    const int col = j < k0 ? j : j + 32;
+                    const float tmp = L[(size_t)k * LDF + col];
+                    L[(size_t)k * LDF + col] = L[(size_t)p * LDF + col];
+                    L[(size_t)p * LDF + col] = tmp;
                 }
                 if (tid == 0) {
                     const int tmp = perm[k];
@@ -273,41 +224,33 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
                     perm[p] = tmp;
                 }
             }
-            __syncthreads();
-            const float rinv = 1.0f / L[(size_t)k * LDF + k];
+            const float rinv = 1.0f / sc.prow[t];
             if (tid == 0) dinv[k] = rinv;
-            const float pkv = L[(size_t)k * LDF + k0 + lane];
-            unsigned long long kbest = 0ull;   // lane t + 1: best key of column k + 1 over this warp's rows
-            for (int i0 = k + 1 + warp; i0 < NP; i0 += 4 * DC_WARPS) {
-                float a[4], l[4];
+            // rows below k: the multiplier l = a_ik / a_kk replaces a_ik (lane
+            // t), the columns right of it take a_ij - l a_kj; lane t + 1 keeps
+            // the pivot key of column k + 1 over this warp's rows
+            unsigned long long kbest = 0ull;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const int i = i0 + g * DC_WARPS;
-                    const int ii = i < NP ? i : k;
-                    l[g] = L[(size_t)ii * LDF + k] * rinv;
-                    a[g] = L[(size_t)ii * LDF + k0 + lane];
-                }
-                __syncwarp();
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const int i = i0 + g * DC_WARPS;
-                    if (i < NP) {
-                        if (lane > t) {
-                            const float u = fmaf(-l[g], pkv, a[g]);
-                            L[(size_t)i * LDF + k0 + lane] = u;
-                            if (lane == t + 1) {
-                                const unsigned long long q = pivot_key(u, i);
-                                kbest = q > kbest ? q : kbest;
-                            }
-                        } else if (lane == t) {
-                            L[(size_t)i * LDF + k] = l[g];
-                        }
-                    }
+            for (int m = 0; m < RPW; ++m) {
+                const int i = warp + DC_WARPS * m;
+                const float l = __shfl_sync(0xffffffffu, a[m], t) * rinv;
+                if (i > k) {
+                    const float u = fmaf(-l, pr, a[m]);
+                    if (lane > t) a[m] = u;
+                    else if (lane == t) a[m] = l;
+                    const unsigned long long q = pivot_key(u, i);
+                    if (lane == t + 1) kbest = q > kbest ? q : kbest;
                 }
             }
-            if (lane == t + 1) sc.wkey[(k + 1) & 1][warp] = kbest;
+            if (t < 31 && lane == t + 1) sc.pkey[(t + 1) & 1][warp] = kbest;
             __syncthreads();
         }
+#pragma unroll
+        for (int m = 0; m < RPW; ++m) {
+            const int i = warp + DC_WARPS * m;
+            if (i >= k0) L[(size_t)i * LDF + k0 + lane] = a[m];
+        }
+        __syncthreads();
         if (c + 1 == NC) break;
         // U12 = L11^-1 A12, one thread per column of A12
         const int j1 = k0 + 32, ncol = NP - j1;
@@ -360,12 +303,113 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
         }
         __syncthreads();
     }
+    return true;
+}
+
+// FP32 LU + FP64 iterative refinement for n <= 32 NC.  Returns true with the
+// solution in xs[r * n + i] when every right-hand side met the stopping
+// rule; false sends the system to the FP64 solver.
+//
+// GB300 runs FP64 arithmetic, comparisons and conversions at 1/64 of the
+// FP32 rate, so besides the residual's n^2 FMAs per right-hand side the
+// solver spends no FP64 instruction per matrix element: K is rounded to FP32
+// unscaled (an entry outside FP32's range becomes inf or 0 and the
+// factorisation falls back), |K|_inf comes from FP32 row sums, maxima are
+// taken on the bit patterns of non-negative doubles, and each residual
+// element is one thread's sum, so no FP64 reduction is needed.  For kind 1
+// and 2 the FP64 matrix K1 +- K2 is formed once into Kc (global scratch).
+// The factorisation is lu_fp32's.
+template <int NC>
+__device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, unsigned char *base,
+                                           const IrLayout &lay, Scratch &sc) {
+    constexpr int NP = 32 * NC;
+    constexpr int LDF = NP + 4;
+    constexpr int G2 = NC <= 4 ? 4 : (NC <= 8 ? 2 : 1);   // rows per group in the fill
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kind = S.kind;
+    const double *K1 = S.K1, *K2 = S.K2;
+    const double *P1 = S.P + (size_t)S.f1 * n, *P2 = S.P + (size_t)S.f2 * n;
+    const size_t pstride = (size_t)S.nf * n;
+    const double *Kr = kind ? Kc : K1;   // the FP64 matrix of the residuals
+    int *perm = reinterpret_cast<int *>(base + lay.perm);
+    float *dinv = reinterpret_cast<float *>(base + lay.dinv);
+    double *xs = reinterpret_cast<double *>(base + lay.x);
+    double *rs = reinterpret_cast<double *>(base + lay.r);
+    unsigned long long *xn = reinterpret_cast<unsigned long long *>(base + lay.xn);   // [2][R] bits of max |x|
+    unsigned long long *rn = reinterpret_cast<unsigned long long *>(base + lay.rn);   // [3][R] bits of max |r|
+
+    // L = fl32(K) padded with identity (Kc = K1 +- K2 on the way), FP32 row sums of |L|
+    float wrow = 0.f;
+    for (int i0 = warp; i0 < NP; i0 += G2 * DC_WARPS) {
+        double v[G2][NC];
+#pragma unroll
+        for (int g = 0; g < G2; ++g) {
+            const int i = i0 + g * DC_WARPS;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const int j = lane + 32 * m;
+                v[g][m] = (i < n && j < n) ? __ldg(K1 + (size_t)i * n + j) : (i == j ? 1.0 : 0.0);
+            }
+        }
+        if (kind) {
+#pragma unroll
+            for (int g = 0; g < G2; ++g) {
+                const int i = i0 + g * DC_WARPS;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const int j = lane + 32 * m;
+                    if (i < n && j < n) {
+                        const double w = __ldg(K2 + (size_t)i * n + j);
+                        v[g][m] = kind == 1 ? v[g][m] + w : v[g][m] - w;
+                        Kc[(size_t)i * n + j] = v[g][m];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G2; ++g) {
+            const int i = i0 + g * DC_WARPS;
+            float rsum = 0.f;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const int j = lane + 32 * m;
+                const float f = (float)v[g][m];
+                if (i < NP) L[(size_t)i * LDF + j] = f;
+                if (i < n) rsum += fabsf(f);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+            wrow = fmaxf(wrow, rsum);
+        }
+    }
+    if (lane == 0) sc.wnorm[0][warp] = (double)wrow;
+    for (int i = tid; i < NP; i += DC_THREADS) perm[i] = i;
+    for (int r = tid; r < R; r += DC_THREADS) rn[r] = 0ull;
+    for (int idx = tid; idx < R * n; idx += DC_THREADS) {
+        const int r = idx / n, i = idx - r * n;
+        const double u = P1[r * pstride + i], w = P2[r * pstride + i];
+        xs[idx] = 0.0;
+        rs[idx] = kind == 0 ? u : (kind == 1 ? u + w : u - w);
+    }
+    __syncthreads();
+    float amax = 0.f;
+#pragma unroll
+    for (int q = 0; q < DC_WARPS; ++q) amax = fmaxf(amax, (float)sc.wnorm[0][q]);
+    if (!(amax > 0.f && amax <= 3.4028234663852886e38f)) return false;
+    const double anrm = (double)amax;
+
+    // blocked FP32 factorisation: L U = rows perm[0..np-1] of the padded fl32(K)
+    if (!lu_fp32<NC>(L, perm, dinv, sc)) return false;
 
     // refinement: it = 0 is the first solve from x = 0
     const double cte = anrm * EPS64 * sqrt((double)n);
     for (int it = 0; it <= IR_ITMAX; ++it) {
         unsigned long long *xnb = xn + (it & 1) * R;
-        unsigned long long *rnb = rn + (size_t)(it & 1) * DC_WARPS * R;
+        // bits of max |r| per right-hand side, three buffers: this
+        // iteration's was zeroed before the last barrier of the previous
+        // one, the next one's (last read two iterations ago) is zeroed now
+        unsigned long long *rnb = rn + (size_t)(it % 3) * R;
+        for (int r = tid; r < R; r += DC_THREADS) rn[(size_t)((it + 1) % 3) * R + r] = 0ull;
         // x += K^-1 r through the FP32 factors, one warp per right-hand side,
         // y in registers (lane owns rows lane + 32 m), pivots broadcast by shuffles
         for (int r = warp; r < R; r += DC_WARPS) {
@@ -437,39 +481,69 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
             if (lane == 0) xnb[r] = (m0 != m0) ? 0x7ff8000000000000ull : xb;   // a NaN residual never converges
         }
         __syncthreads();
-        // r = b - K x in FP64, one thread per row (no cross-lane FP64 reduction)
-        for (int r = 0; r < R; ++r) {
-            unsigned long long best = 0ull;
-            const double *xr = xs + (size_t)r * n;
-            for (int i = tid; i < n; i += DC_THREADS) {
-                const double *kr = Kr + (size_t)i * n;
-                double acc = 0.0;
+        // r = b - K x in FP64: thread (g, i) takes row i of right-hand sides
+        // g, g + G, g + 2G, ... (G = DC_THREADS / n groups), IR_RB of them a
+        // pass, so a row of K is read ceil(R / (G IR_RB)) times instead of R;
+        // every sum runs over j in order (one FMA chain per element, the
+        // rounding of a plain dot product)
+        {
+            const int G = DC_THREADS / n;
+            const int g = tid / n, i = tid - g * n;
+            const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
+            const bool whole = g0 == g31 && g31 < G;   // the warp's lanes share their right-hand sides
+            const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
+            const double *kr = Kr + (size_t)i * n;
+            for (int q0 = 0; q0 < mine; q0 += IR_RB) {
+                const int nb = min(IR_RB, mine - q0);
+                const double *xb = xs + (size_t)(g + G * q0) * n;
+                const size_t xstride = (size_t)G * n;
+                double acc[IR_RB];
+#pragma unroll
+                for (int b = 0; b < IR_RB; ++b) acc[b] = 0.0;
                 int j = 0;
                 for (; j + 4 <= n; j += 4) {
                     const double k0 = __ldg(kr + j), k1 = __ldg(kr + j + 1), k2 = __ldg(kr + j + 2),
                                  k3 = __ldg(kr + j + 3);
-                    acc = fma(k0, xr[j], acc);
-                    acc = fma(k1, xr[j + 1], acc);
-                    acc = fma(k2, xr[j + 2], acc);
-                    acc = fma(k3, xr[j + 3], acc);
+#pragma unroll
+                    for (int b = 0; b < IR_RB; ++b) {
+                        if (b < nb) {
+                            const double *x = xb + b * xstride + j;
+                            acc[b] = fma(k0, x[0], acc[b]);
+                            acc[b] = fma(k1, x[1], acc[b]);
+                            acc[b] = fma(k2, x[2], acc[b]);
+                            acc[b] = fma(k3, x[3], acc[b]);
+                        }
+                    }
                 }
-                for (; j < n; ++j) acc = fma(__ldg(kr + j), xr[j], acc);
-                const double u = P1[r * pstride + i], w = P2[r * pstride + i];
-                const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - acc;
-                rs[(size_t)r * n + i] = rv;
-                const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
-                best = q > best ? q : best;   // NaN patterns exceed every number's
+                for (; j < n; ++j) {
+                    const double kv = __ldg(kr + j);
+#pragma unroll
+                    for (int b = 0; b < IR_RB; ++b)
+                        if (b < nb) acc[b] = fma(kv, xb[b * xstride + j], acc[b]);
+                }
+#pragma unroll
+                for (int b = 0; b < IR_RB; ++b) {
+                    if (b < nb) {
+                        const int r = g + G * (q0 + b);
+                        const double u = P1[r * pstride + i], w = P2[r * pstride + i];
+                        const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - acc[b];
+                        rs[(size_t)r * n + i] = rv;
+                        // bits of |r|: NaN patterns exceed every number's
+                        unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
+                        if (whole) {
+                            q = warp_max_u64(q);
+                            if (lane == 0) atomicMax(rnb + r, q);
+                        } else {
+                            atomicMax(rnb + r, q);
+                        }
+                    }
+                }
             }
-            best = warp_max_u64(best);
-            if (lane == 0) rnb[(size_t)warp * R + r] = best;
         }
         __syncthreads();
         bool conv = true;
         for (int r = 0; r < R && conv; ++r) {
-            unsigned long long mb = 0ull;
-#pragma unroll
-            for (int q = 0; q < DC_WARPS; ++q) mb = rnb[(size_t)q * R + r] > mb ? rnb[(size_t)q * R + r] : mb;
-            const double rmax = __longlong_as_double((long long)mb);
+            const double rmax = __longlong_as_double((long long)rnb[r]);
             const double xmax = __longlong_as_double((long long)xnb[r]);
             if (!(rmax <= xmax * cte)) conv = false;
         }

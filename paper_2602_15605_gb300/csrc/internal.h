@@ -211,7 +211,7 @@ CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
     s.x = o;    o += ir_align(sizeof(double) * (size_t)R * n);
     s.r = o;    o += ir_align(sizeof(double) * (size_t)R * n);
     s.xn = o;   o += ir_align(sizeof(double) * 2 * (size_t)R);
-    s.rn = o;   o += ir_align(sizeof(double) * 2 * 16 * (size_t)R);   // per-warp residual maxima, 2 buffers
+    s.rn = o;   o += ir_align(sizeof(double) * 3 * (size_t)R);        // residual maxima, 3 buffers
     s.total = o;
     return s;
 }
