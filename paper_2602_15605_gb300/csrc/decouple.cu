@@ -195,9 +195,7 @@ __device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &
         __syncthreads();
         for (int t = 0; t < 32; ++t) {
             const int k = k0 + t;
-            unsigned long long kk = 0ull;
-#pragma unroll
-            for (int q = 0; q < DC_WARPS; ++q) kk = sc.pkey[t & 1][q] > kk ? sc.pkey[t & 1][q] : kk;
+            const unsigned long long kk = warp_max_u64(lane < DC_WARPS ? sc.pkey[t & 1][lane] : 0ull);
             const int p = (int)(0xFFFFFFFFu - (unsigned)(kk & 0xFFFFFFFFull));
             const float pv = __uint_as_float((unsigned)(kk >> 32));
             if (!(pv > 0.f && pv <= 3.4028234663852886e38f)) return false;   // the same decision in every thread
@@ -233,8 +231,8 @@ __device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &
 #pragma unroll
             for (int m = 0; m < RPW; ++m) {
                 const int i = warp + DC_WARPS * m;
-                const float l = __shfl_sync(0xffffffffu, a[m], t) * rinv;
-                if (i > k) {
+                if (i > k) {   // the same in every lane: rows at or above k are skipped whole
+                    const float l = __shfl_sync(0xffffffffu, a[m], t) * rinv;
                     const float u = fmaf(-l, pr, a[m]);
                     if (lane > t) a[m] = u;
                     else if (lane == t) a[m] = l;
@@ -306,6 +304,221 @@ __device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &
     return true;
 }
 
+// x += K^-1 r through the FP32 factors of lu_fp32, for every right-hand
+// side: r is scaled by 2^-e (e the exponent of max |r|, so the FP32 values
+// neither overflow nor lose range), permuted into Y ([R][np] in shared
+// memory), and the two substitutions run blocked by 32 rows.  In each block
+// one warp per right-hand side (two at a time, interleaved) runs the block's
+// 32 dependent steps on values held in registers, taking each step's y_k by
+// a shuffle; then every thread applies the block to the rows below it (above
+// it on the way back), one (right-hand side, row) pair at a time.  Every y_i
+// receives the same FMAs in the same order as in an unblocked column sweep.
+// A right-hand side whose residual is 0 or not finite is left unchanged;
+// xnb[r] gets the bits of max |x| (NaN bits for a NaN residual, which never
+// converges).  The caller's barrier follows.
+constexpr int YE_SKIP = -0x7fffffff - 1;   // ye[r]: residual 0 or infinite, no correction
+constexpr int YE_NAN = YE_SKIP + 1;        // ye[r]: NaN residual
+template <int NC>
+__device__ __noinline__ void ir_correct(int n, int R, const float *L, const int *perm, const float *dinv, double *xs,
+                                        const double *rs, float *Y, int *ye, unsigned long long *xnb) {
+    constexpr int NP = 32 * NC;
+    constexpr int LDF = NP + 4;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int r = warp; r < R; r += DC_WARPS) {
+        const double *rr = rs + (size_t)r * n;
+        unsigned long long mb = 0ull;
+        for (int i = lane; i < n; i += 32) {
+            const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rr[i]));
+            mb = q > mb ? q : mb;
+        }
+        mb = warp_max_u64(mb);
+        const double m0 = __longlong_as_double((long long)mb);
+        const bool solve = m0 > 0.0 && m0 <= 1.7976931348623157e308;
+        int e = 0;
+        if (solve) frexp(m0, &e);
+        for (int i = lane; i < NP; i += 32) Y[(size_t)r * NP + i] = solve && i < n ? (float)ldexp(rr[perm[i]], -e) : 0.f;
+        if (lane == 0) ye[r] = solve ? e : (m0 != m0 ? YE_NAN : YE_SKIP);
+    }
+    __syncthreads();
+    const int nb = (n + 31) / 32;
+    // forward: L y = 2^-e P r (unit lower factor)
+    for (int c = 0; c < nb; ++c) {
+        const int b0 = 32 * c, i = b0 + lane, tn = min(32, n - b0);
+        for (int r = warp; r < R; r += 2 * DC_WARPS) {
+            const int r2 = r + DC_WARPS;
+            const bool s1 = ye[r] > YE_NAN, s2 = r2 < R && ye[r2] > YE_NAN;
+            float v1 = s1 ? Y[(size_t)r * NP + i] : 0.f, v2 = s2 ? Y[(size_t)r2 * NP + i] : 0.f;
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                if (t < tn) {
+                    const bool act = lane > t && i < n;
+                    const float lik = act ? L[(size_t)i * LDF + b0 + t] : 0.f;
+                    const float y1 = __shfl_sync(0xffffffffu, v1, t), y2 = __shfl_sync(0xffffffffu, v2, t);
+                    if (act) {
+                        v1 = fmaf(-lik, y1, v1);
+                        v2 = fmaf(-lik, y2, v2);
+                    }
+                }
+            }
+            if (s1) Y[(size_t)r * NP + i] = v1;
+            if (s2) Y[(size_t)r2 * NP + i] = v2;
+        }
+        __syncthreads();
+        const int r0 = b0 + 32, cnt = n - r0;
+        if (cnt > 0) {   // rows r0 .. n-1 take the block's 32 columns
+            for (int q = tid; q < R * cnt; q += DC_THREADS) {
+                const int r = q / cnt, ii = r0 + (q - r * cnt);
+                if (ye[r] <= YE_NAN) continue;
+                const float4 *Li = reinterpret_cast<const float4 *>(L + (size_t)ii * LDF + b0);
+                const float4 *yb = reinterpret_cast<const float4 *>(Y + (size_t)r * NP + b0);
+                float y = Y[(size_t)r * NP + ii];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float4 l4 = Li[t], y4 = yb[t];
+                    y = fmaf(-l4.x, y4.x, y);
+                    y = fmaf(-l4.y, y4.y, y);
+                    y = fmaf(-l4.z, y4.z, y);
+                    y = fmaf(-l4.w, y4.w, y);
+                }
+                Y[(size_t)r * NP + ii] = y;
+            }
+            __syncthreads();
+        }
+    }
+    // backward: U y = y (U_kk = 1 / dinv[k])
+    for (int c = nb - 1; c >= 0; --c) {
+        const int b0 = 32 * c, i = b0 + lane, tn = min(32, n - b0);
+        for (int r = warp; r < R; r += 2 * DC_WARPS) {
+            const int r2 = r + DC_WARPS;
+            const bool s1 = ye[r] > YE_NAN, s2 = r2 < R && ye[r2] > YE_NAN;
+            float v1 = s1 ? Y[(size_t)r * NP + i] : 0.f, v2 = s2 ? Y[(size_t)r2 * NP + i] : 0.f;
+#pragma unroll
+            for (int t = 31; t >= 0; --t) {
+                if (t < tn) {
+                    const float dk = dinv[b0 + t];
+                    const float uik = lane < t ? L[(size_t)i * LDF + b0 + t] : 0.f;
+                    const float y1 = __shfl_sync(0xffffffffu, v1, t) * dk, y2 = __shfl_sync(0xffffffffu, v2, t) * dk;
+                    if (lane == t) {
+                        v1 = y1;
+                        v2 = y2;
+                    } else if (lane < t) {
+                        v1 = fmaf(-uik, y1, v1);
+                        v2 = fmaf(-uik, y2, v2);
+                    }
+                }
+            }
+            if (s1) Y[(size_t)r * NP + i] = v1;
+            if (s2) Y[(size_t)r2 * NP + i] = v2;
+        }
+        __syncthreads();
+        if (b0 > 0) {   // rows 0 .. b0-1 take the block's columns, the last first
+            for (int q = tid; q < R * b0; q += DC_THREADS) {
+                const int r = q / b0, ii = q - r * b0;
+                if (ye[r] <= YE_NAN) continue;
+                const float *Li = L + (size_t)ii * LDF + b0;
+                const float *yb = Y + (size_t)r * NP + b0;
+                float y = Y[(size_t)r * NP + ii];
+                if (tn == 32) {
+                    const float4 *L4 = reinterpret_cast<const float4 *>(Li);
+                    const float4 *y4p = reinterpret_cast<const float4 *>(yb);
+#pragma unroll
+                    for (int t = 7; t >= 0; --t) {
+                        const float4 l4 = L4[t], y4 = y4p[t];
+                        y = fmaf(-l4.w, y4.w, y);
+                        y = fmaf(-l4.z, y4.z, y);
+                        y = fmaf(-l4.y, y4.y, y);
+                        y = fmaf(-l4.x, y4.x, y);
+                    }
+                } else {
+                    for (int t = tn - 1; t >= 0; --t) y = fmaf(-Li[t], yb[t], y);
+                }
+                Y[(size_t)r * NP + ii] = y;
+            }
+            __syncthreads();
+        }
+    }
+    // x += 2^e y
+    for (int r = warp; r < R; r += DC_WARPS) {
+        const int e = ye[r];
+        unsigned long long xb = 0ull;
+        for (int i = lane; i < n; i += 32) {
+            double xv = xs[(size_t)r * n + i];
+            if (e > YE_NAN) {
+                xv += ldexp((double)Y[(size_t)r * NP + i], e);
+                xs[(size_t)r * n + i] = xv;
+            }
+            const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(xv));
+            xb = q > xb ? q : xb;
+        }
+        xb = warp_max_u64(xb);
+        if (lane == 0) xnb[r] = e == YE_NAN ? 0x7ff8000000000000ull : xb;
+    }
+}
+
+// The refinement's residual r = b - K x in FP64, K_ij at Kt[j n + i]:
+// thread (g, i) takes row i of right-hand sides g, g + G, g + 2G, ...
+// (G = DC_THREADS / n groups), IR_RB of them a pass, so a row of K is read
+// ceil(R / (G IR_RB)) times instead of R.  Every sum runs over j in order
+// (one FMA chain per element, the rounding of a plain dot product); max |r|
+// per right-hand side goes into rnb as bits, by atomicMax.  Its own
+// function for its registers.
+__device__ __noinline__ void ir_residual(int n, int R, int kind, const double *Kt, const double *xs, double *rs,
+                                         const double *P1, const double *P2, size_t pstride, unsigned long long *rnb) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = DC_THREADS / n;
+    const int g = tid / n, i = tid - g * n;
+    const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
+    const bool whole = g0 == g31 && g31 < G;   // the warp's lanes share their right-hand sides
+    const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
+    const double *kt = Kt + i;   // K_ij = kt[j n]: a warp's lanes read consecutive rows
+    for (int q0 = 0; q0 < mine; q0 += IR_RB) {
+        const int nb = min(IR_RB, mine - q0);
+        const double *xb = xs + (size_t)(g + G * q0) * n;
+        const size_t xstride = (size_t)G * n;
+        double acc[IR_RB];
+#pragma unroll
+        for (int b = 0; b < IR_RB; ++b) acc[b] = 0.0;
+        int j = 0;
+        for (; j + 4 <= n; j += 4) {
+            const double k0 = kt[(size_t)j * n], k1 = kt[(size_t)(j + 1) * n], k2 = kt[(size_t)(j + 2) * n],
+                         k3 = kt[(size_t)(j + 3) * n];
+#pragma unroll
+            for (int b = 0; b < IR_RB; ++b) {
+                if (b < nb) {
+                    const double *x = xb + b * xstride + j;
+                    acc[b] = fma(k0, x[0], acc[b]);
+                    acc[b] = fma(k1, x[1], acc[b]);
+                    acc[b] = fma(k2, x[2], acc[b]);
+                    acc[b] = fma(k3, x[3], acc[b]);
+                }
+            }
+        }
+        for (; j < n; ++j) {
+            const double kv = kt[(size_t)j * n];
+#pragma unroll
+            for (int b = 0; b < IR_RB; ++b)
+                if (b < nb) acc[b] = fma(kv, xb[b * xstride + j], acc[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < IR_RB; ++b) {
+            if (b < nb) {
+                const int r = g + G * (q0 + b);
+                const double u = P1[r * pstride + i], w = P2[r * pstride + i];
+                const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - acc[b];
+                rs[(size_t)r * n + i] = rv;
+                // bits of |r|: NaN patterns exceed every number's
+                unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
+                if (whole) {
+                    q = warp_max_u64(q);
+                    if (lane == 0) atomicMax(rnb + r, q);
+                } else {
+                    atomicMax(rnb + r, q);
+                }
+            }
+        }
+    }
+}
+
 // FP32 LU + FP64 iterative refinement for n <= 32 NC.  Returns true with the
 // solution in xs[r * n + i] when every right-hand side met the stopping
 // rule; false sends the system to the FP64 solver.
@@ -316,8 +529,9 @@ __device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &
 // unscaled (an entry outside FP32's range becomes inf or 0 and the
 // factorisation falls back), |K|_inf comes from FP32 row sums, maxima are
 // taken on the bit patterns of non-negative doubles, and each residual
-// element is one thread's sum, so no FP64 reduction is needed.  For kind 1
-// and 2 the FP64 matrix K1 +- K2 is formed once into Kc (global scratch).
+// element is one thread's sum, so no FP64 reduction is needed.  The FP64
+// matrix (K1 +- K2 for kind 1 and 2) is copied once, transposed, into Kc
+// (global scratch), so that the residual's loads coalesce.
 // The factorisation is lu_fp32's.
 template <int NC>
 __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, unsigned char *base,
@@ -330,15 +544,17 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     const double *K1 = S.K1, *K2 = S.K2;
     const double *P1 = S.P + (size_t)S.f1 * n, *P2 = S.P + (size_t)S.f2 * n;
     const size_t pstride = (size_t)S.nf * n;
-    const double *Kr = kind ? Kc : K1;   // the FP64 matrix of the residuals
+    double *Kt = Kc;   // [j][i]: K_ij of the residuals (K1 +- K2 for kind 1 and 2), column by column
     int *perm = reinterpret_cast<int *>(base + lay.perm);
     float *dinv = reinterpret_cast<float *>(base + lay.dinv);
     double *xs = reinterpret_cast<double *>(base + lay.x);
     double *rs = reinterpret_cast<double *>(base + lay.r);
     unsigned long long *xn = reinterpret_cast<unsigned long long *>(base + lay.xn);   // [2][R] bits of max |x|
     unsigned long long *rn = reinterpret_cast<unsigned long long *>(base + lay.rn);   // [3][R] bits of max |r|
+    float *Y = reinterpret_cast<float *>(base + lay.y);     // [R][np] the correction's FP32 values
+    int *ye = reinterpret_cast<int *>(base + lay.ye);       // [R] their power-of-two scale
 
-    // L = fl32(K) padded with identity (Kc = K1 +- K2 on the way), FP32 row sums of |L|
+    // L = fl32(K) padded with identity (Kt = the FP64 K, transposed, on the way), FP32 row sums of |L|
     float wrow = 0.f;
     for (int i0 = warp; i0 < NP; i0 += G2 * DC_WARPS) {
         double v[G2][NC];
@@ -351,18 +567,18 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
                 v[g][m] = (i < n && j < n) ? __ldg(K1 + (size_t)i * n + j) : (i == j ? 1.0 : 0.0);
             }
         }
-        if (kind) {
 #pragma unroll
-            for (int g = 0; g < G2; ++g) {
-                const int i = i0 + g * DC_WARPS;
+        for (int g = 0; g < G2; ++g) {
+            const int i = i0 + g * DC_WARPS;
 #pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    const int j = lane + 32 * m;
-                    if (i < n && j < n) {
+            for (int m = 0; m < NC; ++m) {
+                const int j = lane + 32 * m;
+                if (i < n && j < n) {
+                    if (kind) {
                         const double w = __ldg(K2 + (size_t)i * n + j);
                         v[g][m] = kind == 1 ? v[g][m] + w : v[g][m] - w;
-                        Kc[(size_t)i * n + j] = v[g][m];
                     }
+                    Kt[(size_t)j * n + i] = v[g][m];
                 }
             }
         }
@@ -410,136 +626,10 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
         // one, the next one's (last read two iterations ago) is zeroed now
         unsigned long long *rnb = rn + (size_t)(it % 3) * R;
         for (int r = tid; r < R; r += DC_THREADS) rn[(size_t)((it + 1) % 3) * R + r] = 0ull;
-        // x += K^-1 r through the FP32 factors, one warp per right-hand side,
-        // y in registers (lane owns rows lane + 32 m), pivots broadcast by shuffles
-        for (int r = warp; r < R; r += DC_WARPS) {
-            const double *rr = rs + (size_t)r * n;
-            unsigned long long mb = 0ull;
-#pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                const int i = lane + 32 * m;
-                if (i < n) {
-                    const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rr[i]));
-                    mb = q > mb ? q : mb;
-                }
-            }
-            mb = warp_max_u64(mb);
-            const double m0 = __longlong_as_double((long long)mb);
-            unsigned long long xb = 0ull;
-            int e = 0;
-            float y[NC];
-            const bool solve = m0 > 0.0 && m0 <= 1.7976931348623157e308;
-            if (solve) {
-                frexp(m0, &e);
-#pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    const int i = lane + 32 * m;
-                    y[m] = i < n ? (float)ldexp(rr[perm[i]], -e) : 0.f;
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    for (int t = 0; t < 32; ++t) {
-                        const int k = 32 * c + t;
-                        if (k >= n) break;
-                        const float yk = __shfl_sync(0xffffffffu, y[c], t);
-#pragma unroll
-                        for (int m = c; m < NC; ++m) {
-                            const int i = lane + 32 * m;
-                            if (i > k && i < n) y[m] = fmaf(-L[(size_t)i * LDF + k], yk, y[m]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = NC - 1; c >= 0; --c) {
-                    for (int t = 31; t >= 0; --t) {
-                        const int k = 32 * c + t;
-                        if (k >= n) continue;
-                        const float yk = __shfl_sync(0xffffffffu, y[c], t) * dinv[k];
-                        if (lane == t) y[c] = yk;
-#pragma unroll
-                        for (int m = 0; m <= c; ++m) {
-                            const int i = lane + 32 * m;
-                            if (i < k) y[m] = fmaf(-L[(size_t)i * LDF + k], yk, y[m]);
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                const int i = lane + 32 * m;
-                if (i < n) {
-                    double xv = xs[(size_t)r * n + i];
-                    if (solve) {
-                        xv += ldexp((double)y[m], e);
-                        xs[(size_t)r * n + i] = xv;
-                    }
-                    const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(xv));
-                    xb = q > xb ? q : xb;
-                }
-            }
-            xb = warp_max_u64(xb);
-            if (lane == 0) xnb[r] = (m0 != m0) ? 0x7ff8000000000000ull : xb;   // a NaN residual never converges
-        }
+        // x += K^-1 r through the FP32 factors
+        ir_correct<NC>(n, R, L, perm, dinv, xs, rs, Y, ye, xnb);
         __syncthreads();
-        // r = b - K x in FP64: thread (g, i) takes row i of right-hand sides
-        // g, g + G, g + 2G, ... (G = DC_THREADS / n groups), IR_RB of them a
-        // pass, so a row of K is read ceil(R / (G IR_RB)) times instead of R;
-        // every sum runs over j in order (one FMA chain per element, the
-        // rounding of a plain dot product)
-        {
-            const int G = DC_THREADS / n;
-            const int g = tid / n, i = tid - g * n;
-            const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
-            const bool whole = g0 == g31 && g31 < G;   // the warp's lanes share their right-hand sides
-            const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
-            const double *kr = Kr + (size_t)i * n;
-            for (int q0 = 0; q0 < mine; q0 += IR_RB) {
-                const int nb = min(IR_RB, mine - q0);
-                const double *xb = xs + (size_t)(g + G * q0) * n;
-                const size_t xstride = (size_t)G * n;
-                double acc[IR_RB];
-#pragma unroll
-                for (int b = 0; b < IR_RB; ++b) acc[b] = 0.0;
-                int j = 0;
-                for (; j + 4 <= n; j += 4) {
-                    const double k0 = __ldg(kr + j), k1 = __ldg(kr + j + 1), k2 = __ldg(kr + j + 2),
-                                 k3 = __ldg(kr + j + 3);
-#pragma unroll
-                    for (int b = 0; b < IR_RB; ++b) {
-                        if (b < nb) {
-                            const double *x = xb + b * xstride + j;
-                            acc[b] = fma(k0, x[0], acc[b]);
-                            acc[b] = fma(k1, x[1], acc[b]);
-                            acc[b] = fma(k2, x[2], acc[b]);
-                            acc[b] = fma(k3, x[3], acc[b]);
-                        }
-                    }
-                }
-                for (; j < n; ++j) {
-                    const double kv = __ldg(kr + j);
-#pragma unroll
-                    for (int b = 0; b < IR_RB; ++b)
-                        if (b < nb) acc[b] = fma(kv, xb[b * xstride + j], acc[b]);
-                }
-#pragma unroll
-                for (int b = 0; b < IR_RB; ++b) {
-                    if (b < nb) {
-                        const int r = g + G * (q0 + b);
-                        const double u = P1[r * pstride + i], w = P2[r * pstride + i];
-                        const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - acc[b];
-                        rs[(size_t)r * n + i] = rv;
-                        // bits of |r|: NaN patterns exceed every number's
-                        unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
-                        if (whole) {
-                            q = warp_max_u64(q);
-                            if (lane == 0) atomicMax(rnb + r, q);
-                        } else {
-                            atomicMax(rnb + r, q);
-                        }
-                    }
-                }
-            }
-        }
+        ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb);
         __syncthreads();
         bool conv = true;
         for (int r = 0; r < R && conv; ++r) {
