@@ -161,7 +161,10 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 //          multiplier reaches its warp's lanes by a shuffle: two barriers a
 //          step and no shared-memory traffic per element (with the panel in
 //          shared memory every element's load, update and store sat on the
-//          step's critical path, ~2.8k clocks a step at n = 160);
+//          step's critical path, ~2.8k clocks a step at n = 160, against
+//          ~1.7k).  Measured slower: 8 warps with twice the rows each, and one
+//          barrier a step with every warp posting its candidate row (the
+//          extra selects and stores cost more than the barrier saved);
 //   U12 = L11^-1 A12: one thread per column, the 32 unknowns in registers;
 //   A22 -= L21 U12: register tiles of 4 x 4, 32-deep, float4 shared loads.
 // perm[i] is the original row now at position i, dinv[k] = 1 / U_kk.  Its
@@ -304,6 +307,46 @@ __device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &
     return true;
 }
 
+// The diagonal block's 32 dependent steps of the forward substitution for
+// one or two right-hand sides (v1, v2: this lane's row), with the row's
+// factors lk[t] in registers: step t takes y_t by a shuffle from lane t and
+// the rows below it (lanes > t, rows < n) subtract l_it y_t.
+template <bool TWO>
+__device__ __forceinline__ void fwd_chain(float &v1, float &v2, const float (&lk)[32], int lane, bool row_ok, int tn) {
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        if (t < tn) {
+            const bool act = lane > t && row_ok;
+            const float y1 = __shfl_sync(0xffffffffu, v1, t);
+            const float y2 = TWO ? __shfl_sync(0xffffffffu, v2, t) : 0.f;
+            if (act) {
+                v1 = fmaf(-lk[t], y1, v1);
+                if (TWO) v2 = fmaf(-lk[t], y2, v2);
+            }
+        }
+    }
+}
+// The backward counterpart: step t (from the last) scales y_t by 1 / U_tt
+// (dk[t]) on lane t and the rows above it (lanes < t) subtract u_it y_t.
+template <bool TWO>
+__device__ __forceinline__ void bwd_chain(float &v1, float &v2, const float (&uk)[32], const float (&dk)[32], int lane,
+                                          int tn) {
+#pragma unroll
+    for (int t = 31; t >= 0; --t) {
+        if (t < tn) {
+            const float y1 = __shfl_sync(0xffffffffu, v1, t) * dk[t];
+            const float y2 = TWO ? __shfl_sync(0xffffffffu, v2, t) * dk[t] : 0.f;
+            if (lane == t) {
+                v1 = y1;
+                if (TWO) v2 = y2;
+            } else if (lane < t) {
+                v1 = fmaf(-uk[t], y1, v1);
+                if (TWO) v2 = fmaf(-uk[t], y2, v2);
+            }
+        }
+    }
+}
+
 // x += K^-1 r through the FP32 factors of lu_fp32, for every right-hand
 // side: r is scaled by 2^-e (e the exponent of max |r|, so the FP32 values
 // neither overflow nor lose range), permuted into Y ([R][np] in shared
@@ -344,24 +387,26 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
     // forward: L y = 2^-e P r (unit lower factor)
     for (int c = 0; c < nb; ++c) {
         const int b0 = 32 * c, i = b0 + lane, tn = min(32, n - b0);
-        for (int r = warp; r < R; r += 2 * DC_WARPS) {
-            const int r2 = r + DC_WARPS;
-            const bool s1 = ye[r] > YE_NAN, s2 = r2 < R && ye[r2] > YE_NAN;
-            float v1 = s1 ? Y[(size_t)r * NP + i] : 0.f, v2 = s2 ? Y[(size_t)r2 * NP + i] : 0.f;
+        if (warp < R) {   // this row's 32 factors of the block, loaded once
+            float lk[32];
+            const float4 *l4 = reinterpret_cast<const float4 *>(L + (size_t)i * LDF + b0);
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-                if (t < tn) {
-                    const bool act = lane > t && i < n;
-                    const float lik = act ? L[(size_t)i * LDF + b0 + t] : 0.f;
-                    const float y1 = __shfl_sync(0xffffffffu, v1, t), y2 = __shfl_sync(0xffffffffu, v2, t);
-                    if (act) {
-                        v1 = fmaf(-lik, y1, v1);
-                        v2 = fmaf(-lik, y2, v2);
-                    }
-                }
+            for (int q = 0; q < 8; ++q) {
+                const float4 v = l4[q];
+                lk[4 * q] = v.x;
+                lk[4 * q + 1] = v.y;
+                lk[4 * q + 2] = v.z;
+                lk[4 * q + 3] = v.w;
             }
-            if (s1) Y[(size_t)r * NP + i] = v1;
-            if (s2) Y[(size_t)r2 * NP + i] = v2;
+            for (int r = warp; r < R; r += 2 * DC_WARPS) {
+                const int r2 = r + DC_WARPS;
+                const bool s1 = ye[r] > YE_NAN, s2 = r2 < R && ye[r2] > YE_NAN;
+                float v1 = s1 ? Y[(size_t)r * NP + i] : 0.f, v2 = s2 ? Y[(size_t)r2 * NP + i] : 0.f;
+                if (s2) fwd_chain<true>(v1, v2, lk, lane, i < n, tn);
+                else fwd_chain<false>(v1, v2, lk, lane, i < n, tn);
+                if (s1) Y[(size_t)r * NP + i] = v1;
+                if (s2) Y[(size_t)r2 * NP + i] = v2;
+            }
         }
         __syncthreads();
         const int r0 = b0 + 32, cnt = n - r0;
@@ -388,27 +433,31 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
     // backward: U y = y (U_kk = 1 / dinv[k])
     for (int c = nb - 1; c >= 0; --c) {
         const int b0 = 32 * c, i = b0 + lane, tn = min(32, n - b0);
-        for (int r = warp; r < R; r += 2 * DC_WARPS) {
-            const int r2 = r + DC_WARPS;
-            const bool s1 = ye[r] > YE_NAN, s2 = r2 < R && ye[r2] > YE_NAN;
-            float v1 = s1 ? Y[(size_t)r * NP + i] : 0.f, v2 = s2 ? Y[(size_t)r2 * NP + i] : 0.f;
+        if (warp < R) {   // this row's 32 factors of the block and the block's 1 / U_kk
+            float uk[32], dk[32];
+            const float4 *u4 = reinterpret_cast<const float4 *>(L + (size_t)i * LDF + b0);
+            const float4 *d4 = reinterpret_cast<const float4 *>(dinv + b0);
 #pragma unroll
-            for (int t = 31; t >= 0; --t) {
-                if (t < tn) {
-                    const float dk = dinv[b0 + t];
-                    const float uik = lane < t ? L[(size_t)i * LDF + b0 + t] : 0.f;
-                    const float y1 = __shfl_sync(0xffffffffu, v1, t) * dk, y2 = __shfl_sync(0xffffffffu, v2, t) * dk;
-                    if (lane == t) {
-                        v1 = y1;
-                        v2 = y2;
-                    } else if (lane < t) {
-                        v1 = fmaf(-uik, y1, v1);
-                        v2 = fmaf(-uik, y2, v2);
-                    }
-                }
+            for (int q = 0; q < 8; ++q) {
+                const float4 v = u4[q], d = d4[q];
+                uk[4 * q] = v.x;
+                uk[4 * q + 1] = v.y;
+                uk[4 * q + 2] = v.z;
+                uk[4 * q + 3] = v.w;
+                dk[4 * q] = d.x;
+                dk[4 * q + 1] = d.y;
+                dk[4 * q + 2] = d.z;
+                dk[4 * q + 3] = d.w;
             }
-            if (s1) Y[(size_t)r * NP + i] = v1;
-            if (s2) Y[(size_t)r2 * NP + i] = v2;
+            for (int r = warp; r < R; r += 2 * DC_WARPS) {
+                const int r2 = r + DC_WARPS;
+                const bool s1 = ye[r] > YE_NAN, s2 = r2 < R && ye[r2] > YE_NAN;
+                float v1 = s1 ? Y[(size_t)r * NP + i] : 0.f, v2 = s2 ? Y[(size_t)r2 * NP + i] : 0.f;
+                if (s2) bwd_chain<true>(v1, v2, uk, dk, lane, tn);
+                else bwd_chain<false>(v1, v2, uk, dk, lane, tn);
+                if (s1) Y[(size_t)r * NP + i] = v1;
+                if (s2) Y[(size_t)r2 * NP + i] = v2;
+            }
         }
         __syncthreads();
         if (b0 > 0) {   // rows 0 .. b0-1 take the block's columns, the last first
@@ -460,13 +509,47 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
 // (G = DC_THREADS / n groups), IR_RB of them a pass, so a row of K is read
 // ceil(R / (G IR_RB)) times instead of R.  Every sum runs over j in order
 // (one FMA chain per element, the rounding of a plain dot product); max |r|
-// per right-hand side goes into rnb as bits, by atomicMax.  Its own
-// function for its registers.
+// per right-hand side goes into rnb as bits, by atomicMax.  A single
+// right-hand side is summed in G slices instead (G chains of n / G FMAs, so
+// that all G n threads work).  Its own function for its registers.
 __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *Kt, const double *xs, double *rs,
-                                         const double *P1, const double *P2, size_t pstride, unsigned long long *rnb) {
+                                         const double *P1, const double *P2, size_t pstride, unsigned long long *rnb,
+                                         double *part) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int G = DC_THREADS / n;
     const int g = tid / n, i = tid - g * n;
+    if (R == 1 && G > 1) {
+        // one right-hand side: the G groups each sum a slice of j (whole
+        // multiples of 4) into part[g n + i], and thread (0, i) adds the
+        // slices in order -- the rounding of a sum in G pieces
+        const int seg = ((n + G - 1) / G + 3) & ~3;
+        if (g < G) {
+            const int j0 = min(n, g * seg), j1 = min(n, j0 + seg);
+            const double *kt = Kt + i;
+            double acc = 0.0;
+            int j = j0;
+            for (; j + 4 <= j1; j += 4) {
+                const double k0 = kt[(size_t)j * n], k1 = kt[(size_t)(j + 1) * n], k2 = kt[(size_t)(j + 2) * n],
+                             k3 = kt[(size_t)(j + 3) * n];
+                acc = fma(k0, xs[j], acc);
+                acc = fma(k1, xs[j + 1], acc);
+                acc = fma(k2, xs[j + 2], acc);
+                acc = fma(k3, xs[j + 3], acc);
+            }
+            for (; j < j1; ++j) acc = fma(kt[(size_t)j * n], xs[j], acc);
+            part[g * n + i] = acc;
+        }
+        __syncthreads();
+        if (g == 0) {
+            double acc = part[i];
+            for (int q = 1; q < G; ++q) acc += part[q * n + i];
+            const double u = P1[i], w = P2[i];
+            const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - acc;
+            rs[i] = rv;
+            atomicMax(rnb, (unsigned long long)__double_as_longlong(fabs(rv)));
+        }
+        return;
+    }
     const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
     const bool whole = g0 == g31 && g31 < G;   // the warp's lanes share their right-hand sides
     const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
@@ -553,6 +636,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     unsigned long long *rn = reinterpret_cast<unsigned long long *>(base + lay.rn);   // [3][R] bits of max |r|
     float *Y = reinterpret_cast<float *>(base + lay.y);     // [R][np] the correction's FP32 values
     int *ye = reinterpret_cast<int *>(base + lay.ye);       // [R] their power-of-two scale
+    double *part = reinterpret_cast<double *>(base + lay.part);   // [DC_THREADS] slices of a residual
 
     // L = fl32(K) padded with identity (Kt = the FP64 K, transposed, on the way), FP32 row sums of |L|
     float wrow = 0.f;
@@ -629,7 +713,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
         // x += K^-1 r through the FP32 factors
         ir_correct<NC>(n, R, L, perm, dinv, xs, rs, Y, ye, xnb);
         __syncthreads();
-        ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb);
+        ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb, part);
         __syncthreads();
         bool conv = true;
         for (int r = 0; r < R && conv; ++r) {

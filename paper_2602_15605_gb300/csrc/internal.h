@@ -197,7 +197,7 @@ constexpr int PT_ERR_RANGE = 0x1001;   // a tile's chunks are not covered by its
 constexpr int PT_ERR_WAIT = 0x1002;    // a bulk copy did not complete within the bounded wait
 CPL_HD inline int ir_ldf(int n) { return ir_np(n) + 4; }
 struct IrLayout {
-    size_t L, perm, dinv, x, r, xn, rn, y, ye, total;
+    size_t L, perm, dinv, x, r, xn, rn, y, ye, part, total;
 };
 CPL_HD inline size_t ir_align(size_t b) { return (b + 15) & ~(size_t)15; }
 CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
@@ -214,6 +214,7 @@ CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
     s.rn = o;   o += ir_align(sizeof(double) * 3 * (size_t)R);        // residual maxima, 3 buffers
     s.y = o;    o += ir_align(sizeof(float) * (size_t)R * np);        // the correction in FP32
     s.ye = o;   o += ir_align(sizeof(int) * (size_t)R);
+    s.part = o; o += ir_align(sizeof(double) * 512);                  // slices of a one-column residual
     s.total = o;
     return s;
 }
