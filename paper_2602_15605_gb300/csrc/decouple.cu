@@ -348,39 +348,36 @@ __device__ __forceinline__ void bwd_chain(float &v1, float &v2, const float (&uk
 }
 
 // x += K^-1 r through the FP32 factors of lu_fp32, for every right-hand
-// side: r is scaled by 2^-e (e the exponent of max |r|, so the FP32 values
-// neither overflow nor lose range), permuted into Y ([R][np] in shared
-// memory), and the two substitutions run blocked by 32 rows.  In each block
+// side: r is scaled by 2^-e (e the exponent of max |r|, whose bits are
+// rmax[r], so the FP32 values neither overflow nor lose range), permuted
+// into Y ([R][np] in shared memory), and the two substitutions run blocked
+// by 32 rows.  In each block
 // one warp per right-hand side (two at a time, interleaved) runs the block's
 // 32 dependent steps on values held in registers, taking each step's y_k by
 // a shuffle; then every thread applies the block to the rows below it (above
 // it on the way back), one (right-hand side, row) pair at a time.  Every y_i
 // receives the same FMAs in the same order as in an unblocked column sweep.
 // A right-hand side whose residual is 0 or not finite is left unchanged;
-// xnb[r] gets the bits of max |x| (NaN bits for a NaN residual, which never
-// converges).  The caller's barrier follows.
+// xnb[r] (zero on entry) gets the bits of max |x| (NaN bits for a NaN
+// residual, which never converges).  The caller's barrier follows.
 constexpr int YE_SKIP = -0x7fffffff - 1;   // ye[r]: residual 0 or infinite, no correction
 constexpr int YE_NAN = YE_SKIP + 1;        // ye[r]: NaN residual
 template <int NC>
 __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int *perm, const float *dinv, double *xs,
-                                        const double *rs, float *Y, int *ye, unsigned long long *xnb) {
+                                        const double *rs, const unsigned long long *rmax, float *Y, int *ye,
+                                        unsigned long long *xnb) {
     constexpr int NP = 32 * NC;
     constexpr int LDF = NP + 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int r = warp; r < R; r += DC_WARPS) {
-        const double *rr = rs + (size_t)r * n;
-        unsigned long long mb = 0ull;
-        for (int i = lane; i < n; i += 32) {
-            const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rr[i]));
-            mb = q > mb ? q : mb;
-        }
-        mb = warp_max_u64(mb);
-        const double m0 = __longlong_as_double((long long)mb);
+    // element by element (the FP64 scaling and conversions spread over all warps)
+    for (int q = tid; q < R * NP; q += DC_THREADS) {
+        const int r = q / NP, i = q - r * NP;
+        const double m0 = __longlong_as_double((long long)rmax[r]);
         const bool solve = m0 > 0.0 && m0 <= 1.7976931348623157e308;
         int e = 0;
         if (solve) frexp(m0, &e);
-        for (int i = lane; i < NP; i += 32) Y[(size_t)r * NP + i] = solve && i < n ? (float)ldexp(rr[perm[i]], -e) : 0.f;
-        if (lane == 0) ye[r] = solve ? e : (m0 != m0 ? YE_NAN : YE_SKIP);
+        Y[q] = solve && i < n ? (float)ldexp(rs[(size_t)r * n + perm[i]], -e) : 0.f;
+        if (i == 0) ye[r] = solve ? e : (m0 != m0 ? YE_NAN : YE_SKIP);
     }
     __syncthreads();
     const int nb = (n + 31) / 32;
@@ -486,21 +483,31 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
             __syncthreads();
         }
     }
-    // x += 2^e y
-    for (int r = warp; r < R; r += DC_WARPS) {
-        const int e = ye[r];
+    // x += 2^e y, element by element; max |x| per right-hand side into xnb
+    // (zero before the call) by atomicMax, a warp at a time where its lanes
+    // share the right-hand side
+    for (int q0 = warp * 32; q0 < R * n; q0 += DC_THREADS) {
+        const int q = q0 + lane;
+        const bool ok = q < R * n;
+        const int r = ok ? q / n : R - 1, i = q - r * n;
         unsigned long long xb = 0ull;
-        for (int i = lane; i < n; i += 32) {
-            double xv = xs[(size_t)r * n + i];
+        if (ok) {
+            const int e = ye[r];
+            double xv = xs[q];
             if (e > YE_NAN) {
                 xv += ldexp((double)Y[(size_t)r * NP + i], e);
-                xs[(size_t)r * n + i] = xv;
+                xs[q] = xv;
             }
-            const unsigned long long q = (unsigned long long)__double_as_longlong(fabs(xv));
-            xb = q > xb ? q : xb;
+            xb = e == YE_NAN ? 0x7ff8000000000000ull   // a NaN residual never converges
+                             : (unsigned long long)__double_as_longlong(fabs(xv));
         }
-        xb = warp_max_u64(xb);
-        if (lane == 0) xnb[r] = e == YE_NAN ? 0x7ff8000000000000ull : xb;
+        const int ra = __shfl_sync(0xffffffffu, r, 0), rb = __shfl_sync(0xffffffffu, r, 31);
+        if (ra == rb) {
+            xb = warp_max_u64(xb);
+            if (lane == 0) atomicMax(xnb + r, xb);
+        } else if (ok) {
+            atomicMax(xnb + r, xb);
+        }
     }
 }
 
@@ -684,7 +691,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     }
     if (lane == 0) sc.wnorm[0][warp] = (double)wrow;
     for (int i = tid; i < NP; i += DC_THREADS) perm[i] = i;
-    for (int r = tid; r < R; r += DC_THREADS) rn[r] = 0ull;
+    for (int r = tid; r < R; r += DC_THREADS) rn[r] = rn[2 * (size_t)R + r] = 0ull;
     for (int idx = tid; idx < R * n; idx += DC_THREADS) {
         const int r = idx / n, i = idx - r * n;
         const double u = P1[r * pstride + i], w = P2[r * pstride + i];
@@ -701,7 +708,21 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     // blocked FP32 factorisation: L U = rows perm[0..np-1] of the padded fl32(K)
     if (!lu_fp32<NC>(L, perm, dinv, sc)) return false;
 
-    // refinement: it = 0 is the first solve from x = 0
+    // refinement: it = 0 is the first solve from x = 0, scaled by max |b|
+    // (its bits into rn's third buffer, which the first correction reads)
+    for (int q0 = warp * 32; q0 < R * n; q0 += DC_THREADS) {
+        const int q = q0 + lane;
+        const bool ok = q < R * n;
+        const int r = ok ? q / n : R - 1;
+        unsigned long long b = ok ? (unsigned long long)__double_as_longlong(fabs(rs[q])) : 0ull;
+        if (__shfl_sync(0xffffffffu, r, 0) == __shfl_sync(0xffffffffu, r, 31)) {
+            b = warp_max_u64(b);
+            if (lane == 0) atomicMax(rn + 2 * (size_t)R + r, b);
+        } else if (ok) {
+            atomicMax(rn + 2 * (size_t)R + r, b);
+        }
+    }
+    __syncthreads();
     const double cte = anrm * EPS64 * sqrt((double)n);
     for (int it = 0; it <= IR_ITMAX; ++it) {
         unsigned long long *xnb = xn + (it & 1) * R;
@@ -709,9 +730,12 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
         // iteration's was zeroed before the last barrier of the previous
         // one, the next one's (last read two iterations ago) is zeroed now
         unsigned long long *rnb = rn + (size_t)(it % 3) * R;
-        for (int r = tid; r < R; r += DC_THREADS) rn[(size_t)((it + 1) % 3) * R + r] = 0ull;
+        for (int r = tid; r < R; r += DC_THREADS) {
+            rn[(size_t)((it + 1) % 3) * R + r] = 0ull;
+            xnb[r] = 0ull;   // last read two iterations ago
+        }
         // x += K^-1 r through the FP32 factors
-        ir_correct<NC>(n, R, L, perm, dinv, xs, rs, Y, ye, xnb);
+        ir_correct<NC>(n, R, L, perm, dinv, xs, rs, rn + (size_t)((it + 2) % 3) * R, Y, ye, xnb);
         __syncthreads();
         ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb, part);
         __syncthreads();
