@@ -1061,24 +1061,19 @@ cpl_status cpl_threej_m11(cpl_ctx *c, const int *j2, const int *j3, int n, doubl
     cudaStream_t st = (cudaStream_t)stream;
     int *d = c->threej_idx.as<int>();
     CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
-    // square roots of the tables and of the integers up to 2 (j2 + j3) + 4
-    const int nn = 2 * smax + 4;
-    if (c->sq_pmax != c->pmax || c->sq_nn < nn) {
-        const int np1 = c->pmax + 1, nn_b = std::max(nn, 2 * CPL_THREEJ_JMAX / 8);
+    // square roots of the g and h tables (five per entry), once per table size
+    const int np1 = c->pmax + 1;
+    if (c->sq_pmax != c->pmax) {
         c->sq_pmax = -1;
-        if ((s = c->sqrt_tab.ensure(sizeof(float2) * (2 * (size_t)np1 + nn_b), "square-root tables")) != CPL_OK)
-            return s;
-        float2 *sg = c->sqrt_tab.as<float2>();
-        CPL_CUDA_TRY(launch_sqrt_tables(c->g.as<double>(), c->h.as<double>(), np1, nn_b, sg, sg + np1, sg + 2 * np1, st));
+        if ((s = c->sqrt_tab.ensure(sizeof(float2) * 5 * (size_t)np1, "square-root tables")) != CPL_OK) return s;
+        CPL_CUDA_TRY(launch_sqrt_tables(c->g.as<double>(), c->h.as<double>(), np1, c->sqrt_tab.as<float2>(), st));
         c->sq_pmax = c->pmax;
-        c->sq_nn = nn_b;
     }
-    const float2 *sg = c->sqrt_tab.as<float2>(), *sh = sg + (c->pmax + 1), *sn = sg + 2 * (c->pmax + 1);
     CPL_CUDA_TRY(cudaMemcpyAsync(d, j2, sizeof(int) * n, cudaMemcpyHostToDevice, st));
     CPL_CUDA_TRY(cudaMemcpyAsync(d + n, j3, sizeof(int) * n, cudaMemcpyHostToDevice, st));
     {
         LaunchScope ls(c, "threej_m11", st);
-        CPL_CUDA_TRY(launch_threej_m11(sg, sh, sn, d, d + n, n, out, out_stride, st));
+        CPL_CUDA_TRY(launch_threej_m11(c->sqrt_tab.as<float2>(), np1, d, d + n, n, out, out_stride, st));
         ls.done(0.0, 8.0 * (double)n * (double)out_stride);
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));

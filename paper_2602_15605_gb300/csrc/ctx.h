@@ -107,8 +107,8 @@ struct cpl_ctx {
     DevBuf items;                // FP64 path: sweep table, caps, bins and work items of the last build
     DevBuf stage_w, stage_out;   // cpl_build_host staging
     DevBuf threej_idx;           // cpl_threej_m11: (j2, j3) of the last call
-    DevBuf sqrt_tab;             // cpl_threej_m11: sqrt g | sqrt h (pmax + 1 each) | sqrt n (sq_nn), FP32 pairs
-    int sq_pmax = -1, sq_nn = 0;
+    DevBuf sqrt_tab;             // cpl_threej_m11: five square-root tables of g and h (pmax + 1 each), FP32 pairs
+    int sq_pmax = -1;
     DevBuf df_tab;               // CPL_DF32: g | h as FP32 pairs (pmax + 1 each)
     int df_pmax = -1;
     DevBuf ptab_b;               // tabled FP64 kernel: B operand blocks (window independent)

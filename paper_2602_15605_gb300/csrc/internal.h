@@ -130,12 +130,11 @@ constexpr int PL_COEF_N = 11;
 void plain_coef_host(int n, std::vector<double> &out);
 cudaError_t launch_atab(const double *A, int a_stride, const int *l3cap, const double *g, const long long *aoff,
                         int n_win, int nib, int max_count, int nae, int odd, double *At, cudaStream_t st);
-// (j1 j2 j3; 0 -1 1) rows for device arrays j2, j3 from sqrt g, sqrt h, sqrt n
-// held as double-float (threej.cu)
-cudaError_t launch_sqrt_tables(const double *g, const double *h, int np1, int nn, float2 *sg, float2 *sh, float2 *sn,
-                               cudaStream_t st);
-cudaError_t launch_threej_m11(const float2 *sg, const float2 *sh, const float2 *sn, const int *j2, const int *j3,
-                              int n, double *out, long long stride, cudaStream_t st);
+// (j1 j2 j3; 0 -1 1) rows for device arrays j2, j3 from five square-root
+// tables of g and h (tab: 5 np1 FP32 pairs) held as double-float (threej.cu)
+cudaError_t launch_sqrt_tables(const double *g, const double *h, int np1, float2 *tab, cudaStream_t st);
+cudaError_t launch_threej_m11(const float2 *tab, int np1, const int *j2, const int *j3, int n, double *out,
+                              long long stride, cudaStream_t st);
 
 // Mode decoupling (decouple.cu): one CTA per n x n system of Eq. pseudo_cl.
 // kind 0: K = M[slot1], rhs = pcl[field1], out[field1] = x;
