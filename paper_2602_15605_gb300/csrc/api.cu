@@ -1057,7 +1057,9 @@ cpl_status cpl_threej_m11(cpl_ctx *c, const int *j2, const int *j3, int n, doubl
     cpl_status s;
     if ((s = select_device(c)) != CPL_OK) return s;
     if ((s = ensure_tables(c, smax + 1)) != CPL_OK) return s;
-    if ((s = c->threej_idx.ensure(sizeof(int) * 2 * (size_t)n, "3j indices")) != CPL_OK) return s;
+    // (j2, j3) of the rows, then their constants (16 bytes each)
+    if ((s = c->threej_idx.ensure(sizeof(int) * 2 * (size_t)n + 16 * (size_t)n + 16, "3j indices")) != CPL_OK)
+        return s;
     cudaStream_t st = (cudaStream_t)stream;
     int *d = c->threej_idx.as<int>();
     CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
@@ -1071,9 +1073,15 @@ cpl_status cpl_threej_m11(cpl_ctx *c, const int *j2, const int *j3, int n, doubl
     }
     CPL_CUDA_TRY(cudaMemcpyAsync(d, j2, sizeof(int) * n, cudaMemcpyHostToDevice, st));
     CPL_CUDA_TRY(cudaMemcpyAsync(d + n, j3, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    float4 *cst = reinterpret_cast<float4 *>(c->threej_idx.as<unsigned char>() + ((8 * (size_t)n + 15) & ~(size_t)15));
+    {
+        LaunchScope ls(c, "threej_consts", st);
+        CPL_CUDA_TRY(launch_threej_consts(d, d + n, n, cst, st));
+        ls.done(0.0, 24.0 * (double)n);
+    }
     {
         LaunchScope ls(c, "threej_m11", st);
-        CPL_CUDA_TRY(launch_threej_m11(c->sqrt_tab.as<float2>(), np1, d, d + n, n, out, out_stride, st));
+        CPL_CUDA_TRY(launch_threej_m11(c->sqrt_tab.as<float2>(), np1, d, d + n, n, cst, out, out_stride, st));
         ls.done(0.0, 8.0 * (double)n * (double)out_stride);
     }
     CPL_CUDA_TRY(cudaEventRecord(c->done, st));

@@ -133,8 +133,9 @@ cudaError_t launch_atab(const double *A, int a_stride, const int *l3cap, const d
 // (j1 j2 j3; 0 -1 1) rows for device arrays j2, j3 from five square-root
 // tables of g and h (tab: 5 np1 FP32 pairs) held as double-float (threej.cu)
 cudaError_t launch_sqrt_tables(const double *g, const double *h, int np1, float2 *tab, cudaStream_t st);
-cudaError_t launch_threej_m11(const float2 *tab, int np1, const int *j2, const int *j3, int n, double *out,
-                              long long stride, cudaStream_t st);
+cudaError_t launch_threej_consts(const int *j2, const int *j3, int n, float4 *cst, cudaStream_t st);
+cudaError_t launch_threej_m11(const float2 *tab, int np1, const int *j2, const int *j3, int n, const float4 *cst,
+                              double *out, long long stride, cudaStream_t st);
 
 // Mode decoupling (decouple.cu): one CTA per n x n system of Eq. pseudo_cl.
 // kind 0: K = M[slot1], rhs = pcl[field1], out[field1] = x;

@@ -89,24 +89,31 @@ __device__ __forceinline__ double m11(const SqrtTabs &T, int j1, int j2, int j3,
     return xdf_to_double(xdf{v.h, v.l, 0});
 }
 
+// Per-row constants of m11 in FP64, one thread per row (apart from the row
+// kernel, whose blocks would otherwise wait on one thread's FP64 square
+// roots and divisions): cst[q] = (ce.h, ce.l, so.h, so.l).
+__global__ void k_threej_consts(const int *__restrict__ j2s, const int *__restrict__ j3s, int n, float4 *cst) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const double d2 = j2s[q], d3 = j3s[q];
+    const dfl ce = dfl_of(sqrt((d2 + 1.0) * (d3 + 1.0) / (d2 * d3)) / (2.0 * (d2 + 1.0) * (d3 + 1.0)));
+    const dfl so = dfl_of(-0.5 / sqrt(d2 * (d2 + 1.0) * d3 * (d3 + 1.0)));
+    cst[q] = make_float4(ce.h, ce.l, so.h, so.l);
+}
+
 // One row (j2, j3) per block.  Each thread takes two neighbours j1, j1 + 1
 // (at every step all lanes of a warp have the same parity of J, so the two
 // formulas do not diverge) and stores them as one 16-byte pair; a row that
 // starts off a 16-byte boundary takes its first element alone.
 __global__ void __launch_bounds__(256) k_threej_m11(SqrtTabs T, const int *__restrict__ j2s,
-                                                    const int *__restrict__ j3s, double *out, long long stride) {
-    __shared__ dfl cst[2];
+                                                    const int *__restrict__ j3s, const float4 *__restrict__ cst,
+                                                    double *out, long long stride) {
     const int q = blockIdx.x;
     const int j2 = j2s[q], j3 = j3s[q];
     const int jmin = abs(j2 - j3), jmax = j2 + j3;
     double *row = out + (long long)q * stride;
-    if (threadIdx.x == 0) {   // per-row constants, in FP64 once
-        const double d2 = j2, d3 = j3;
-        cst[0] = dfl_of(sqrt((d2 + 1.0) * (d3 + 1.0) / (d2 * d3)) / (2.0 * (d2 + 1.0) * (d3 + 1.0)));
-        cst[1] = dfl_of(-0.5 / sqrt(d2 * (d2 + 1.0) * d3 * (d3 + 1.0)));
-    }
-    __syncthreads();
-    const dfl ce = cst[0], so = cst[1];
+    const float4 c4 = cst[q];
+    const dfl ce = {c4.x, c4.y}, so = {c4.z, c4.w};
     auto value = [&](long long idx) {
         const int j1 = jmin + (int)idx;
         return j1 > jmax ? 0.0 : m11(T, j1, j2, j3, ce, so);
@@ -133,11 +140,17 @@ cudaError_t launch_sqrt_tables(const double *g, const double *h, int np1, float2
     return cudaGetLastError();
 }
 
-cudaError_t launch_threej_m11(const float2 *tab, int np1, const int *j2, const int *j3, int n, double *out,
-                              long long stride, cudaStream_t st) {
+cudaError_t launch_threej_consts(const int *j2, const int *j3, int n, float4 *cst, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_threej_consts<<<(n + 255) / 256, 256, 0, st>>>(j2, j3, n, cst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_threej_m11(const float2 *tab, int np1, const int *j2, const int *j3, int n, const float4 *cst,
+                              double *out, long long stride, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const SqrtTabs T{tab, tab + np1, tab + 2 * np1, tab + 3 * np1, tab + 4 * np1};
-    k_threej_m11<<<n, 256, 0, st>>>(T, j2, j3, out, stride);
+    k_threej_m11<<<n, 256, 0, st>>>(T, j2, j3, cst, out, stride);
     return cudaGetLastError();
 }
 
