@@ -47,6 +47,7 @@ constexpr int DC_THREADS = 512;
 constexpr int DC_WARPS = DC_THREADS / 32;
 constexpr int IR_ITMAX = 30;
 constexpr int IR_RB = 8;          // right-hand sides per pass of a residual thread
+constexpr int IR_DF_MIN = 8;      // right-hand sides from which the first residual runs in double-float
 constexpr double EPS64 = 1.1102230246251565e-16;   // 2^-53
 
 // One system: K = K1 (+ or -) K2 and b = P[f1] (+ or -) P[f2] by kind.
@@ -307,6 +308,38 @@ __device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &
     return true;
 }
 
+// ldexp(x, k) with integer operations when x and the result are normal
+// doubles (then it only moves the exponent field, exactly as ldexp does),
+// else ldexp itself: GB300's FP64 pipe is the scarce one.
+__device__ __forceinline__ double ldexp_fast(double x, int k) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex != 0 && ex + k >= 1 && ex + k <= 2046) return __longlong_as_double(b + ((long long)k << 52));
+    return ldexp(x, k);
+}
+// The exponent frexp would give for finite m > 0, read from the bits for a
+// normal m.
+__device__ __forceinline__ int frexp_exp(double m) {
+    const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7ff);
+    if (ex != 0) return ex - 1022;
+    int e;
+    frexp(m, &e);
+    return e;
+}
+// (double) f * 2^k with integer operations when f and the result are
+// normal, else by conversion and ldexp.
+__device__ __forceinline__ double widen_scaled(float f, int k) {
+    const unsigned u = __float_as_uint(f);
+    const int ef = (int)((u >> 23) & 0xff);
+    const int ed = ef - 127 + 1023 + k;
+    if (ef != 0 && ef != 255 && ed >= 1 && ed <= 2046) {
+        const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)ed << 52) |
+                                     ((unsigned long long)(u & 0x7fffffu) << 29);
+        return __longlong_as_double((long long)b);
+    }
+    return ldexp((double)f, k);
+}
+
 // The diagonal block's 32 dependent steps of the forward substitution for
 // one or two right-hand sides (v1, v2: this lane's row), with the row's
 // factors lk[t] in registers: step t takes y_t by a shuffle from lane t and
@@ -375,8 +408,8 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
         const double m0 = __longlong_as_double((long long)rmax[r]);
         const bool solve = m0 > 0.0 && m0 <= 1.7976931348623157e308;
         int e = 0;
-        if (solve) frexp(m0, &e);
-        Y[q] = solve && i < n ? (float)ldexp(rs[(size_t)r * n + perm[i]], -e) : 0.f;
+        if (solve) e = frexp_exp(m0);
+        Y[q] = solve && i < n ? (float)ldexp_fast(rs[(size_t)r * n + perm[i]], -e) : 0.f;
         if (i == 0) ye[r] = solve ? e : (m0 != m0 ? YE_NAN : YE_SKIP);
     }
     __syncthreads();
@@ -495,7 +528,7 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
             const int e = ye[r];
             double xv = xs[q];
             if (e > YE_NAN) {
-                xv += ldexp((double)Y[(size_t)r * NP + i], e);
+                xv += widen_scaled(Y[(size_t)r * NP + i], e);
                 xs[q] = xv;
             }
             xb = e == YE_NAN ? 0x7ff8000000000000ull   // a NaN residual never converges
@@ -609,6 +642,101 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
     }
 }
 
+// fl32(v - f) for f = fl32(v), with integer operations: v - f is exact in
+// FP64 (at most half an FP32 ulp of v, so below 2^28 units of v's last
+// place), and its FP32 rounding is that of the integer difference of the
+// mantissas.  Returns 0 where v, f or the result is not a normal number;
+// the pair (f, 0) is then a coarser K, which only the first residual uses
+// (the refinement still ends on FP64 residuals).
+__device__ __forceinline__ float low_part(double v, float f) {
+    const long long bv = __double_as_longlong(v);
+    const int ev = (int)((bv >> 52) & 0x7ff);
+    const unsigned bf = __float_as_uint(f);
+    const int ef = (int)((bf >> 23) & 0xff);
+    const int sh = ef - ev + 925;   // f's mantissa in units of v's last place: << 29, or 30 after a carry
+    if (ev == 0 || ev == 0x7ff || ef == 0 || ef == 0xff || (sh != 29 && sh != 30)) return 0.f;
+    const long long mv = (bv & ((1ll << 52) - 1)) | (1ll << 52);
+    const long long mf = (long long)((bf & 0x7fffffu) | 0x800000u) << sh;
+    const int d = (int)(mv - mf);   // |d| <= 2^28
+    if (d == 0) return 0.f;
+    const unsigned bd = __float_as_uint(__int2float_rn(d));
+    const int ed = (int)((bd >> 23) & 0xff) + ev - 1075;   // scale by 2^(ev - 1075)
+    if (ed < 1 || ed > 254) return 0.f;
+    const unsigned r = (bd & 0x807fffffu) | ((unsigned)ed << 23);
+    return __uint_as_float(bv < 0 ? r ^ 0x80000000u : r);
+}
+
+// The first residual r = b - K x0 in double-float on the FP32 pipe, for
+// x0 = 2^e Y (the first correction from x = 0, exact in that form) and K
+// held as FP32 pairs Kf[j n + i] = (fl32(K_ij), fl32(K_ij - fl32(K_ij))):
+// each product K_ij Y_j as hi * y (exact with its fma error) plus lo * y,
+// summed over j in order with a two-sum on the high part; the sum is brought
+// to FP64 once per element.  Its error (~n 2^-48 |K| |x0|) is far below what
+// the first correction leaves (~cond(K) 2^-24 |x|), so the refinement takes
+// the same steps; the FP64 residuals that follow decide convergence.  The
+// threads are grouped as in ir_residual.
+__device__ __noinline__ void ir_residual_df(int n, int R, int NP, int kind, const float2 *Kf, const float *Y,
+                                            const int *ye, double *rs, const double *P1, const double *P2,
+                                            size_t pstride, unsigned long long *rnb) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = DC_THREADS / n;
+    const int g = tid / n, i = tid - g * n;
+    const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
+    const bool whole = g0 == g31 && g31 < G;
+    const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
+    const float2 *kf = Kf + i;
+    for (int q0 = 0; q0 < mine; q0 += IR_RB) {
+        const int nb = min(IR_RB, mine - q0);
+        const float *yb = Y + (size_t)(g + G * q0) * NP;
+        const size_t ystride = (size_t)G * NP;
+        float sh[IR_RB], sl[IR_RB];
+#pragma unroll
+        for (int b = 0; b < IR_RB; ++b) sh[b] = sl[b] = 0.f;
+        auto term = [&](float2 k, int j) {
+#pragma unroll
+            for (int b = 0; b < IR_RB; ++b) {
+                if (b < nb) {
+                    const float y = yb[b * ystride + j];
+                    const float p = k.x * y;
+                    const float pe = fmaf(k.x, y, -p);
+                    const float t = sh[b] + p;
+                    const float bb = t - sh[b];
+                    const float err = (sh[b] - (t - bb)) + (p - bb);
+                    sh[b] = t;
+                    sl[b] += err + fmaf(k.y, y, pe);
+                }
+            }
+        };
+        int j = 0;
+        for (; j + 8 <= n; j += 8) {   // eight loads in flight, then their terms in order
+            float2 k[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) k[u] = kf[(size_t)(j + u) * n];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) term(k[u], j + u);
+        }
+        for (; j < n; ++j) term(kf[(size_t)j * n], j);
+#pragma unroll
+        for (int b = 0; b < IR_RB; ++b) {
+            if (b < nb) {
+                const int r = g + G * (q0 + b);
+                const int e = ye[r];
+                const double kx = e > YE_NAN ? widen_scaled(sh[b], e) + widen_scaled(sl[b], e) : 0.0;
+                const double u = P1[r * pstride + i], w = P2[r * pstride + i];
+                const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - kx;
+                rs[(size_t)r * n + i] = rv;
+                unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
+                if (whole) {
+                    q = warp_max_u64(q);
+                    if (lane == 0) atomicMax(rnb + r, q);
+                } else {
+                    atomicMax(rnb + r, q);
+                }
+            }
+        }
+    }
+}
+
 // FP32 LU + FP64 iterative refinement for n <= 32 NC.  Returns true with the
 // solution in xs[r * n + i] when every right-hand side met the stopping
 // rule; false sends the system to the FP64 solver.
@@ -624,7 +752,7 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
 // (global scratch), so that the residual's loads coalesce.
 // The factorisation is lu_fp32's.
 template <int NC>
-__device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, unsigned char *base,
+__device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, float2 *Kf, unsigned char *base,
                                            const IrLayout &lay, Scratch &sc) {
     constexpr int NP = 32 * NC;
     constexpr int LDF = NP + 4;
@@ -705,6 +833,13 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     if (!(amax > 0.f && amax <= 3.4028234663852886e38f)) return false;
     const double anrm = (double)amax;
 
+    if (Kf) {   // K as FP32 pairs for a double-float first residual, from fl32(K) in L and K in Kt
+        for (int q = tid; q < n * n; q += DC_THREADS) {
+            const int j = q / n, i = q - j * n;
+            const float f = L[(size_t)i * LDF + j];
+            Kf[q] = make_float2(f, low_part(Kt[q], f));
+        }
+    }
     // blocked FP32 factorisation: L U = rows perm[0..np-1] of the padded fl32(K)
     if (!lu_fp32<NC>(L, perm, dinv, sc)) return false;
 
@@ -737,9 +872,14 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
         // x += K^-1 r through the FP32 factors
         ir_correct<NC>(n, R, L, perm, dinv, xs, rs, rn + (size_t)((it + 2) % 3) * R, Y, ye, xnb);
         __syncthreads();
-        ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb, part);
+        // the first residual in double-float when there are many right-hand
+        // sides (its error, ~n 2^-48 |K| |x|, is far below the first
+        // correction's own); it never decides convergence
+        const bool df = Kf && it == 0;
+        if (df) ir_residual_df(n, R, NP, kind, Kf, Y, ye, rs, P1, P2, pstride, rnb);
+        else ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb, part);
         __syncthreads();
-        bool conv = true;
+        bool conv = !df;
         for (int r = 0; r < R && conv; ++r) {
             const double rmax = __longlong_as_double((long long)rnb[r]);
             const double xmax = __longlong_as_double((long long)xnb[r]);
@@ -750,21 +890,21 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     return false;
 }
 
-__device__ bool solve_refined_n(const SysView &S, int n, int R, float *L, double *Kc, unsigned char *base,
+__device__ bool solve_refined_n(const SysView &S, int n, int R, float *L, double *Kc, float2 *Kf, unsigned char *base,
                                 const IrLayout &lay, Scratch &sc) {
     switch ((n + 31) / 32) {
-        case 1: return solve_refined<1>(S, n, R, L, Kc, base, lay, sc);
-        case 2: return solve_refined<2>(S, n, R, L, Kc, base, lay, sc);
-        case 3: return solve_refined<3>(S, n, R, L, Kc, base, lay, sc);
-        case 4: return solve_refined<4>(S, n, R, L, Kc, base, lay, sc);
-        case 5: return solve_refined<5>(S, n, R, L, Kc, base, lay, sc);
-        case 6: return solve_refined<6>(S, n, R, L, Kc, base, lay, sc);
-        case 7: return solve_refined<7>(S, n, R, L, Kc, base, lay, sc);
-        case 8: return solve_refined<8>(S, n, R, L, Kc, base, lay, sc);
-        case 9: case 10: return solve_refined<10>(S, n, R, L, Kc, base, lay, sc);
-        case 11: case 12: return solve_refined<12>(S, n, R, L, Kc, base, lay, sc);
-        case 13: case 14: return solve_refined<14>(S, n, R, L, Kc, base, lay, sc);
-        case 15: case 16: return solve_refined<16>(S, n, R, L, Kc, base, lay, sc);
+        case 1: return solve_refined<1>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 2: return solve_refined<2>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 3: return solve_refined<3>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 4: return solve_refined<4>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 5: return solve_refined<5>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 6: return solve_refined<6>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 7: return solve_refined<7>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 8: return solve_refined<8>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 9: case 10: return solve_refined<10>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 11: case 12: return solve_refined<12>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 13: case 14: return solve_refined<14>(S, n, R, L, Kc, Kf, base, lay, sc);
+        case 15: case 16: return solve_refined<16>(S, n, R, L, Kc, Kf, base, lay, sc);
         default: return false;
     }
 }
@@ -834,12 +974,16 @@ __global__ void __launch_bounds__(DC_THREADS, 1) k_decouple(DecoupleArgs a) {
     const int tid = threadIdx.x;
     const int n = a.n, ld = a.ld, R = a.n_rhs, nf = a.n_fields;
     // workspace slice: the refined solver's FP64 K1 +- K2 (n^2, rounded up to
-    // 16 bytes), then its FP32 factors when they are not in shared memory;
-    // the FP64 solver's augmented matrix from the start when it is not
+    // 16 bytes), then its FP32 factors when they are not in shared memory,
+    // then K as FP32 pairs for a double-float first residual; the FP64
+    // solver's augmented matrix from the start when it is not
     double *slice = a.ws ? a.ws + (size_t)blockIdx.x * a.ws_stride : nullptr;
     const IrLayout lay = ir_layout(n, R, !a.l_in_ws);
     double *Kc = slice;
-    float *L = a.l_in_ws ? reinterpret_cast<float *>(slice + (((size_t)n * n + 1) & ~(size_t)1))
+    const size_t kc_d = ((size_t)n * n + 1) & ~(size_t)1;                        // doubles of Kc
+    const size_t f32_d = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;   // doubles of the FP32 factors
+    float2 *Kf = a.df_first ? reinterpret_cast<float2 *>(slice + kc_d + f32_d) : nullptr;
+    float *L = a.l_in_ws ? reinterpret_cast<float *>(slice + kc_d)
                          : reinterpret_cast<float *>(dsm + lay.L);
     double *A = a.direct_in_ws ? slice : reinterpret_cast<double *>(dsm);
     const double *xs = reinterpret_cast<const double *>(dsm + lay.x);
@@ -856,7 +1000,7 @@ __global__ void __launch_bounds__(DC_THREADS, 1) k_decouple(DecoupleArgs a) {
         S.nf = nf;
         S.n = n;
 
-        const bool refined = a.refine && solve_refined_n(S, n, R, L, Kc, dsm, lay, sc);
+        const bool refined = a.refine && solve_refined_n(S, n, R, L, Kc, Kf, dsm, lay, sc);
         __syncthreads();   // the FP64 solver reuses the refinement's shared memory
         const int bad = refined ? 0 : solve_fp64(S, n, ld, R, A, sc);
 
@@ -972,12 +1116,15 @@ cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, cons
     const int grid = (int)std::min<long long>(a.n_sys, (long long)nsm * std::max(bps, 1));
     if (a.direct_in_ws || a.refine) {
         // one slice per CTA: the refined solver's FP64 K1 +- K2 (n^2 doubles,
-        // whole 16-byte units) and, when not in shared memory, its padded FP32
-        // factors; or the FP64 solver's augmented matrix -- the larger, even
+        // whole 16-byte units), when not in shared memory its padded FP32
+        // factors, and from IR_DF_MIN right-hand sides K as FP32 pairs; or the
+        // FP64 solver's augmented matrix -- the larger, even
         const size_t kc = ((size_t)n * n + 1) & ~(size_t)1;
         const size_t f32 = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;
+        a.df_first = a.refine && n_rhs >= IR_DF_MIN;
+        const size_t kf = a.df_first ? (size_t)n * n : 0;   // FP32 pairs of K for the first residual
         const size_t fp64 = a.direct_in_ws ? (size_t)n * a.ld : 0;
-        a.ws_stride = (std::max(a.refine ? kc + f32 : 0, fp64) + 1) & ~(size_t)1;
+        a.ws_stride = (std::max(a.refine ? kc + f32 + kf : 0, fp64) + 1) & ~(size_t)1;
         CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
         if ((s = c->dec_ws.ensure(sizeof(double) * a.ws_stride * grid, "decoupling workspace")) != CPL_OK) return s;
         a.ws = c->dec_ws.as<double>();

@@ -152,6 +152,7 @@ struct DecoupleArgs {
     int refine;             // FP32 LU + FP64 iterative refinement first (FP64 LU on failure)
     int l_in_ws;            // refinement: FP32 factors in the workspace slice instead of shared memory
     int direct_in_ws;       // FP64 LU: augmented matrix in the workspace slice instead of shared memory
+    int df_first;           // refinement: the first residual in double-float (FP32 pairs of K after the factors)
     double *ws;             // global workspace, ws_stride doubles per CTA (NULL when unused)
     size_t ws_stride;
 };
