@@ -19,7 +19,9 @@
 //   against 128 for FP32, so the O(n^3) factorisation runs in FP32 on
 //   K 2^-e (a power-of-two scale, exact) and the answer is brought to FP64
 //   accuracy by iterative refinement: x += K^-1 r with the FP32 factors,
-//   r = b - K x in FP64 from the FP64 matrix, until
+//   r = b - K x in FP64 from the FP64 matrix (from 8 right-hand sides only
+//   the first; each later residual is the previous one minus K times the
+//   update x received, in double-float on the FP32 pipe), until
 //   max|r| <= max|x| |K|_inf eps sqrt(n) for every right-hand side (the
 //   stopping rule of LAPACK's mixed-precision dsgesv, at most 30 steps).
 //   Each right-hand side is scaled by a power of two before it is rounded to
@@ -33,6 +35,8 @@
 // Matrices live in shared memory when they fit, else in a per-CTA slice of a
 // global workspace (L2-resident at these sizes).  Every reduction has a fixed
 // order, so results are deterministic.
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include <algorithm>
@@ -47,7 +51,8 @@ constexpr int DC_THREADS = 512;
 constexpr int DC_WARPS = DC_THREADS / 32;
 constexpr int IR_ITMAX = 30;
 constexpr int IR_RB = 8;          // right-hand sides per pass of a residual thread
-constexpr int IR_DF_MIN = 8;      // right-hand sides from which the first residual runs in double-float
+constexpr int IR_INC_MIN = 8;     // right-hand sides from which the residuals after the first are double-float updates
+static_assert(IR_INC_MIN > 1, "the update errors share shared memory with the one-column residual's slices");
 constexpr double EPS64 = 1.1102230246251565e-16;   // 2^-53
 
 // One system: K = K1 (+ or -) K2 and b = P[f1] (+ or -) P[f2] by kind.
@@ -392,13 +397,16 @@ __device__ __forceinline__ void bwd_chain(float &v1, float &v2, const float (&uk
 // receives the same FMAs in the same order as in an unblocked column sweep.
 // A right-hand side whose residual is 0 or not finite is left unchanged;
 // xnb[r] (zero on entry) gets the bits of max |x| (NaN bits for a NaN
-// residual, which never converges).  The caller's barrier follows.
+// residual, which never converges).  With E (incremental residuals), the
+// rounding error of each FP64 update x + 2^e y is kept: the update actually
+// applied is 2^e (y - E), which the next residual subtracts.  The caller's
+// barrier follows.
 constexpr int YE_SKIP = -0x7fffffff - 1;   // ye[r]: residual 0 or infinite, no correction
 constexpr int YE_NAN = YE_SKIP + 1;        // ye[r]: NaN residual
 template <int NC>
 __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int *perm, const float *dinv, double *xs,
                                         const double *rs, const unsigned long long *rmax, float *Y, int *ye,
-                                        unsigned long long *xnb) {
+                                        unsigned long long *xnb, __nv_bfloat16 *E) {
     constexpr int NP = 32 * NC;
     constexpr int LDF = NP + 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -528,8 +536,24 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
             const int e = ye[r];
             double xv = xs[q];
             if (e > YE_NAN) {
-                xv += widen_scaled(Y[(size_t)r * NP + i], e);
+                const double d = widen_scaled(Y[(size_t)r * NP + i], e);
+                const double s = xv + d;
+                if (E) {
+                    // the exact rounding error of s = x + d (a fast two-sum
+                    // with the larger magnitude first, compared on the bits),
+                    // in units of 2^e, to BF16: it is at most 2^-53 |x|, and
+                    // 8 bits of it leave the tracked update within 2^-61 |x|
+                    const long long bx = __double_as_longlong(xv) & 0x7fffffffffffffffll;
+                    const long long bd = __double_as_longlong(d) & 0x7fffffffffffffffll;
+                    const double big = bx >= bd ? xv : d, small = bx >= bd ? d : xv;
+                    const double err = small - (s - big);
+                    const bool zero = (__double_as_longlong(err) & 0x7fffffffffffffffll) == 0;
+                    E[(size_t)r * NP + i] = __float2bfloat16_rn(zero ? 0.f : __double2float_rn(ldexp_fast(err, -e)));
+                }
+                xv = s;
                 xs[q] = xv;
+            } else if (E) {
+                E[(size_t)r * NP + i] = __float2bfloat16_rn(0.f);
             }
             xb = e == YE_NAN ? 0x7ff8000000000000ull   // a NaN residual never converges
                              : (unsigned long long)__double_as_longlong(fabs(xv));
@@ -646,8 +670,9 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
 // FP64 (at most half an FP32 ulp of v, so below 2^28 units of v's last
 // place), and its FP32 rounding is that of the integer difference of the
 // mantissas.  Returns 0 where v, f or the result is not a normal number;
-// the pair (f, 0) is then a coarser K, which only the first residual uses
-// (the refinement still ends on FP64 residuals).
+// the pair (f, 0) is then a coarser K_ij, which only the residual updates
+// use: there it multiplies a correction of order cond(K) 2^-24 |x|, and an
+// entry below FP32's normal range is far below |K|_inf.
 __device__ __forceinline__ float low_part(double v, float f) {
     const long long bv = __double_as_longlong(v);
     const int ev = (int)((bv >> 52) & 0x7ff);
@@ -666,18 +691,21 @@ __device__ __forceinline__ float low_part(double v, float f) {
     return __uint_as_float(bv < 0 ? r ^ 0x80000000u : r);
 }
 
-// The first residual r = b - K x0 in double-float on the FP32 pipe, for
-// x0 = 2^e Y (the first correction from x = 0, exact in that form) and K
-// held as FP32 pairs Kf[j n + i] = (fl32(K_ij), fl32(K_ij - fl32(K_ij))):
-// each product K_ij Y_j as hi * y (exact with its fma error) plus lo * y,
-// summed over j in order with a two-sum on the high part; the sum is brought
-// to FP64 once per element.  Its error (~n 2^-48 |K| |x0|) is far below what
-// the first correction leaves (~cond(K) 2^-24 |x|), so the refinement takes
-// the same steps; the FP64 residuals that follow decide convergence.  The
-// threads are grouped as in ir_residual.
-__device__ __noinline__ void ir_residual_df(int n, int R, int NP, int kind, const float2 *Kf, const float *Y,
-                                            const int *ye, double *rs, const double *P1, const double *P2,
-                                            size_t pstride, unsigned long long *rnb) {
+// A residual update on the FP32 pipe in double-float: r <- r - K 2^e (Y - E)
+// for the update 2^e (Y - E) that the last correction applied to x (Y its
+// FP32 values, E the rounding errors of the FP64 additions in BF16, both in
+// units of 2^e), with K held as FP32 pairs Kf[j n + i] = (fl32(K_ij),
+// fl32(K_ij - fl32(K_ij))): each product K_ij Y_j as hi * y (exact with its
+// fma error) plus lo * y, summed over j in order with a two-sum on the high
+// part, minus hi * E_j in the low part; the sum is brought to FP64 once per
+// element.  Its error, ~n 2^-48 |K| |2^e Y|, is far below FP64's rounding of
+// |K| |x| once the first correction has been applied (|2^e Y| ~ cond(K)
+// 2^-24 |x| and less after every step), so r stays the residual of the FP64
+// x as closely as an FP64 residual would.  The threads are grouped as in
+// ir_residual.
+__device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 *Kf, const float *Y,
+                                             const __nv_bfloat16 *E, const int *ye, double *rs,
+                                             unsigned long long *rnb) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int G = DC_THREADS / n;
     const int g = tid / n, i = tid - g * n;
@@ -688,42 +716,67 @@ __device__ __noinline__ void ir_residual_df(int n, int R, int NP, int kind, cons
     for (int q0 = 0; q0 < mine; q0 += IR_RB) {
         const int nb = min(IR_RB, mine - q0);
         const float *yb = Y + (size_t)(g + G * q0) * NP;
+        const __nv_bfloat16 *eb = E + (size_t)(g + G * q0) * NP;
         const size_t ystride = (size_t)G * NP;
         float sh[IR_RB], sl[IR_RB];
 #pragma unroll
         for (int b = 0; b < IR_RB; ++b) sh[b] = sl[b] = 0.f;
-        auto term = [&](float2 k, int j) {
+        auto term = [&](float2 k, float y, float ev, int b) {
+            const float p = k.x * y;
+            const float pe = fmaf(k.x, y, -p);
+            const float t = sh[b] + p;
+            const float bb = t - sh[b];
+            const float err = (sh[b] - (t - bb)) + (p - bb);
+            sh[b] = t;
+            sl[b] = fmaf(-k.x, ev, sl[b] + (err + fmaf(k.y, y, pe)));
+        };
+        // eight columns of K a step, the next eight loading while these are used
+        const int n8 = n & ~7;
+        float2 k[8];
+        if (n8 > 0) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) k[u] = kf[(size_t)u * n];
+        }
+        int j = 0;
+        for (; j < n8; j += 8) {
+            float2 kc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) kc[u] = k[u];
+            if (j + 8 < n8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) k[u] = kf[(size_t)(j + 8 + u) * n];
+            }
 #pragma unroll
             for (int b = 0; b < IR_RB; ++b) {
-                if (b < nb) {
-                    const float y = yb[b * ystride + j];
-                    const float p = k.x * y;
-                    const float pe = fmaf(k.x, y, -p);
-                    const float t = sh[b] + p;
-                    const float bb = t - sh[b];
-                    const float err = (sh[b] - (t - bb)) + (p - bb);
-                    sh[b] = t;
-                    sl[b] += err + fmaf(k.y, y, pe);
+                if (b < nb) {   // Y and E rows start 16-byte aligned (NP a multiple of 32, j of 8)
+                    const float4 y0 = *reinterpret_cast<const float4 *>(yb + b * ystride + j);
+                    const float4 y1 = *reinterpret_cast<const float4 *>(yb + b * ystride + j + 4);
+                    const uint4 e8 = *reinterpret_cast<const uint4 *>(eb + b * ystride + j);
+                    // BF16 to FP32: the 16 bits are the top of the FP32 pattern
+                    term(kc[0], y0.x, __uint_as_float(e8.x << 16), b);
+                    term(kc[1], y0.y, __uint_as_float(e8.x & 0xffff0000u), b);
+                    term(kc[2], y0.z, __uint_as_float(e8.y << 16), b);
+                    term(kc[3], y0.w, __uint_as_float(e8.y & 0xffff0000u), b);
+                    term(kc[4], y1.x, __uint_as_float(e8.z << 16), b);
+                    term(kc[5], y1.y, __uint_as_float(e8.z & 0xffff0000u), b);
+                    term(kc[6], y1.z, __uint_as_float(e8.w << 16), b);
+                    term(kc[7], y1.w, __uint_as_float(e8.w & 0xffff0000u), b);
                 }
             }
-        };
-        int j = 0;
-        for (; j + 8 <= n; j += 8) {   // eight loads in flight, then their terms in order
-            float2 k[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) k[u] = kf[(size_t)(j + u) * n];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) term(k[u], j + u);
         }
-        for (; j < n; ++j) term(kf[(size_t)j * n], j);
+        for (; j < n; ++j) {
+            const float2 kv = kf[(size_t)j * n];
+#pragma unroll
+            for (int b = 0; b < IR_RB; ++b)
+                if (b < nb) term(kv, yb[b * ystride + j], __bfloat162float(eb[b * ystride + j]), b);
+        }
 #pragma unroll
         for (int b = 0; b < IR_RB; ++b) {
             if (b < nb) {
                 const int r = g + G * (q0 + b);
                 const int e = ye[r];
                 const double kx = e > YE_NAN ? widen_scaled(sh[b], e) + widen_scaled(sl[b], e) : 0.0;
-                const double u = P1[r * pstride + i], w = P2[r * pstride + i];
-                const double rv = (kind == 0 ? u : (kind == 1 ? u + w : u - w)) - kx;
+                const double rv = rs[(size_t)r * n + i] - kx;
                 rs[(size_t)r * n + i] = rv;
                 unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
                 if (whole) {
@@ -752,8 +805,8 @@ __device__ __noinline__ void ir_residual_df(int n, int R, int NP, int kind, cons
 // (global scratch), so that the residual's loads coalesce.
 // The factorisation is lu_fp32's.
 template <int NC>
-__device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, float2 *Kf, unsigned char *base,
-                                           const IrLayout &lay, Scratch &sc) {
+__device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, float2 *Kf,
+                                           unsigned char *base, const IrLayout &lay, Scratch &sc) {
     constexpr int NP = 32 * NC;
     constexpr int LDF = NP + 4;
     constexpr int G2 = NC <= 4 ? 4 : (NC <= 8 ? 2 : 1);   // rows per group in the fill
@@ -771,6 +824,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     unsigned long long *rn = reinterpret_cast<unsigned long long *>(base + lay.rn);   // [3][R] bits of max |r|
     float *Y = reinterpret_cast<float *>(base + lay.y);     // [R][np] the correction's FP32 values
     int *ye = reinterpret_cast<int *>(base + lay.ye);       // [R] their power-of-two scale
+    __nv_bfloat16 *E = reinterpret_cast<__nv_bfloat16 *>(base + lay.e);   // [R][np] rounding errors of the updates
     double *part = reinterpret_cast<double *>(base + lay.part);   // [DC_THREADS] slices of a residual
 
     // L = fl32(K) padded with identity (Kt = the FP64 K, transposed, on the way), FP32 row sums of |L|
@@ -811,6 +865,8 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
                 const float f = (float)v[g][m];
                 if (i < NP) L[(size_t)i * LDF + j] = f;
                 if (i < n) rsum += fabsf(f);
+                // K as FP32 pairs for the double-float residual updates, transposed as Kt
+                if (Kf && i < n && j < n) Kf[(size_t)j * n + i] = make_float2(f, low_part(v[g][m], f));
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
@@ -833,13 +889,6 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     if (!(amax > 0.f && amax <= 3.4028234663852886e38f)) return false;
     const double anrm = (double)amax;
 
-    if (Kf) {   // K as FP32 pairs for a double-float first residual, from fl32(K) in L and K in Kt
-        for (int q = tid; q < n * n; q += DC_THREADS) {
-            const int j = q / n, i = q - j * n;
-            const float f = L[(size_t)i * LDF + j];
-            Kf[q] = make_float2(f, low_part(Kt[q], f));
-        }
-    }
     // blocked FP32 factorisation: L U = rows perm[0..np-1] of the padded fl32(K)
     if (!lu_fp32<NC>(L, perm, dinv, sc)) return false;
 
@@ -869,17 +918,17 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
             rn[(size_t)((it + 1) % 3) * R + r] = 0ull;
             xnb[r] = 0ull;   // last read two iterations ago
         }
-        // x += K^-1 r through the FP32 factors
-        ir_correct<NC>(n, R, L, perm, dinv, xs, rs, rn + (size_t)((it + 2) % 3) * R, Y, ye, xnb);
+        // with many right-hand sides, only the first residual b - K x runs
+        // in FP64; each later one is the previous minus K times the update
+        // the correction applied, in double-float on the FP32 pipe
+        const bool inc = Kf && it > 0;
+        // x += K^-1 r through the FP32 factors (from x = 0 at it = 0, exact)
+        ir_correct<NC>(n, R, L, perm, dinv, xs, rs, rn + (size_t)((it + 2) % 3) * R, Y, ye, xnb, inc ? E : nullptr);
         __syncthreads();
-        // the first residual in double-float when there are many right-hand
-        // sides (its error, ~n 2^-48 |K| |x|, is far below the first
-        // correction's own); it never decides convergence
-        const bool df = Kf && it == 0;
-        if (df) ir_residual_df(n, R, NP, kind, Kf, Y, ye, rs, P1, P2, pstride, rnb);
+        if (inc) ir_residual_inc(n, R, NP, Kf, Y, E, ye, rs, rnb);
         else ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb, part);
         __syncthreads();
-        bool conv = !df;
+        bool conv = true;
         for (int r = 0; r < R && conv; ++r) {
             const double rmax = __longlong_as_double((long long)rnb[r]);
             const double xmax = __longlong_as_double((long long)xnb[r]);
@@ -975,14 +1024,14 @@ __global__ void __launch_bounds__(DC_THREADS, 1) k_decouple(DecoupleArgs a) {
     const int n = a.n, ld = a.ld, R = a.n_rhs, nf = a.n_fields;
     // workspace slice: the refined solver's FP64 K1 +- K2 (n^2, rounded up to
     // 16 bytes), then its FP32 factors when they are not in shared memory,
-    // then K as FP32 pairs for a double-float first residual; the FP64
-    // solver's augmented matrix from the start when it is not
+    // then K as FP32 pairs for the residual updates; the FP64 solver's
+    // augmented matrix from the start when it is not in shared memory
     double *slice = a.ws ? a.ws + (size_t)blockIdx.x * a.ws_stride : nullptr;
     const IrLayout lay = ir_layout(n, R, !a.l_in_ws);
     double *Kc = slice;
     const size_t kc_d = ((size_t)n * n + 1) & ~(size_t)1;                        // doubles of Kc
     const size_t f32_d = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;   // doubles of the FP32 factors
-    float2 *Kf = a.df_first ? reinterpret_cast<float2 *>(slice + kc_d + f32_d) : nullptr;
+    float2 *Kf = a.df_inc ? reinterpret_cast<float2 *>(slice + kc_d + f32_d) : nullptr;
     float *L = a.l_in_ws ? reinterpret_cast<float *>(slice + kc_d)
                          : reinterpret_cast<float *>(dsm + lay.L);
     double *A = a.direct_in_ws ? slice : reinterpret_cast<double *>(dsm);
@@ -1117,12 +1166,12 @@ cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, cons
     if (a.direct_in_ws || a.refine) {
         // one slice per CTA: the refined solver's FP64 K1 +- K2 (n^2 doubles,
         // whole 16-byte units), when not in shared memory its padded FP32
-        // factors, and from IR_DF_MIN right-hand sides K as FP32 pairs; or the
+        // factors, and from IR_INC_MIN right-hand sides K as FP32 pairs; or the
         // FP64 solver's augmented matrix -- the larger, even
         const size_t kc = ((size_t)n * n + 1) & ~(size_t)1;
         const size_t f32 = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;
-        a.df_first = a.refine && n_rhs >= IR_DF_MIN;
-        const size_t kf = a.df_first ? (size_t)n * n : 0;   // FP32 pairs of K for the first residual
+        a.df_inc = a.refine && n_rhs >= IR_INC_MIN;
+        const size_t kf = a.df_inc ? (size_t)n * n : 0;   // FP32 pairs of K for the residual updates
         const size_t fp64 = a.direct_in_ws ? (size_t)n * a.ld : 0;
         a.ws_stride = (std::max(a.refine ? kc + f32 + kf : 0, fp64) + 1) & ~(size_t)1;
         CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));

@@ -152,7 +152,8 @@ struct DecoupleArgs {
     int refine;             // FP32 LU + FP64 iterative refinement first (FP64 LU on failure)
     int l_in_ws;            // refinement: FP32 factors in the workspace slice instead of shared memory
     int direct_in_ws;       // FP64 LU: augmented matrix in the workspace slice instead of shared memory
-    int df_first;           // refinement: the first residual in double-float (FP32 pairs of K after the factors)
+    int df_inc;             // refinement: residuals after the first as double-float updates (FP32 pairs of K
+                            // and the updates' rounding errors after the factors)
     double *ws;             // global workspace, ws_stride doubles per CTA (NULL when unused)
     size_t ws_stride;
 };
@@ -198,7 +199,7 @@ constexpr int PT_ERR_RANGE = 0x1001;   // a tile's chunks are not covered by its
 constexpr int PT_ERR_WAIT = 0x1002;    // a bulk copy did not complete within the bounded wait
 CPL_HD inline int ir_ldf(int n) { return ir_np(n) + 4; }
 struct IrLayout {
-    size_t L, perm, dinv, x, r, xn, rn, y, ye, part, total;
+    size_t L, perm, dinv, x, r, xn, rn, y, e, ye, part, total;
 };
 CPL_HD inline size_t ir_align(size_t b) { return (b + 15) & ~(size_t)15; }
 CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
@@ -215,7 +216,11 @@ CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
     s.rn = o;   o += ir_align(sizeof(double) * 3 * (size_t)R);        // residual maxima, 3 buffers
     s.y = o;    o += ir_align(sizeof(float) * (size_t)R * np);        // the correction in FP32
     s.ye = o;   o += ir_align(sizeof(int) * (size_t)R);
-    s.part = o; o += ir_align(sizeof(double) * 512);                  // slices of a one-column residual
+    // one region for two uses that never meet: the slices of a one-column
+    // residual (one right-hand side), and the BF16 rounding errors [R][np] of
+    // the updates x received (residual updates, from 8 right-hand sides)
+    s.part = s.e = o;
+    o += ir_align(2 * (size_t)R * np > sizeof(double) * 512 ? 2 * (size_t)R * np : sizeof(double) * 512);
     s.total = o;
     return s;
 }

@@ -179,6 +179,36 @@ def test_refined_and_fp64_solvers_agree(ctx):
     print("refined:", check(M, pcl[:, :1], one, sp, ref), "fp64:", check(M, pcl[:, :1], many[:, :1], sp, ref))
 
 
+@pytest.mark.parametrize("cond", [1e5, 1e6])
+def test_many_rhs_residual_updates(ctx, cond):
+    # From 8 right-hand sides only the first residual is formed in FP64; the
+    # later ones are updates r - K d in double-float.  Matrices with a set
+    # condition number (U diag(s) V^T, s log-spaced) make the refinement take
+    # several update steps (cond 2^-24 per step); one right-hand side is
+    # zero (no correction), one tiny.  The answer must meet the forward and
+    # backward bars, and agree with the single-right-hand-side solves (FP64
+    # residuals throughout) to the forward bar.
+    n, R = 96, 32
+    rng = np.random.default_rng(int(np.log10(cond)))
+    M = np.empty((1, 1, n, n))
+    U, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    V, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    M[0, 0] = (U * np.logspace(0, -np.log10(cond), n)) @ V.T
+    pcl = rng.normal(size=(1, R, 1, n))
+    pcl[0, 3] = 0.0
+    pcl[0, 7] *= 1e-250
+    got, info = run(ctx, M, pcl, coupling.TT)
+    assert np.all(info == 0)
+    assert np.all(got[0, 3] == 0.0)
+    ref = dc.decouple(M, pcl, coupling.TT)
+    print("cond %.0e:" % cond, check(M, pcl, got, coupling.TT, ref))
+    kappa = np.linalg.cond(M[0, 0], np.inf)
+    for r in (0, 7, 31):
+        one, _ = run(ctx, M, np.ascontiguousarray(pcl[:, r:r + 1]), coupling.TT)
+        fe = np.max(np.abs(one[0, 0] - got[0, r])) / np.max(np.abs(one[0, 0]))
+        assert fe <= 8 * n * EPS * kappa, (r, fe)
+
+
 def test_singular_systems_report_info(ctx):
     n = 12
     sp = coupling.TT | coupling.EE | coupling.EEBB
