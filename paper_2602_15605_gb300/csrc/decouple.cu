@@ -313,15 +313,6 @@ __device__ __noinline__ bool lu_fp32(float *L, int *perm, float *dinv, Scratch &
     return true;
 }
 
-// ldexp(x, k) with integer operations when x and the result are normal
-// doubles (then it only moves the exponent field, exactly as ldexp does),
-// else ldexp itself: GB300's FP64 pipe is the scarce one.
-__device__ __forceinline__ double ldexp_fast(double x, int k) {
-    const long long b = __double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex != 0 && ex + k >= 1 && ex + k <= 2046) return __longlong_as_double(b + ((long long)k << 52));
-    return ldexp(x, k);
-}
 // The exponent frexp would give for finite m > 0, read from the bits for a
 // normal m.
 __device__ __forceinline__ int frexp_exp(double m) {
@@ -343,6 +334,21 @@ __device__ __forceinline__ double widen_scaled(float f, int k) {
         return __longlong_as_double((long long)b);
     }
     return ldexp((double)f, k);
+}
+// fl32(v 2^k) with integer operations (round to nearest even at the 29th
+// fraction bit; a carry into the exponent field is the correct result) when
+// v and the result are normal, else by ldexp and conversion.
+__device__ __forceinline__ float narrow_scaled(double v, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const int ef = ex - 1023 + 127 + k;
+    if (ex != 0 && ex != 0x7ff && ef >= 1 && ef <= 253) {
+        const unsigned long long m = b & 0x000fffffffffffffull;
+        const unsigned long long rnd = m + 0x0fffffffull + ((m >> 29) & 1ull);
+        const unsigned f = ((unsigned)ef << 23) + (unsigned)(rnd >> 29);
+        return __uint_as_float(f | ((unsigned)(b >> 32) & 0x80000000u));
+    }
+    return (float)ldexp(v, k);
 }
 
 // The diagonal block's 32 dependent steps of the forward substitution for
@@ -399,10 +405,106 @@ __device__ __forceinline__ void bwd_chain(float &v1, float &v2, const float (&uk
 // xnb[r] (zero on entry) gets the bits of max |x| (NaN bits for a NaN
 // residual, which never converges).  With E (incremental residuals), the
 // rounding error of each FP64 update x + 2^e y is kept: the update actually
-// applied is 2^e (y - E), which the next residual subtracts.  The caller's
-// barrier follows.
+// applied is 2^e (y - E), which the next residual subtracts.  From
+// IR_BLK_MIN right-hand sides the block updates run in blk_update_fwd and
+// blk_update_bwd.  The caller's barrier follows.
 constexpr int YE_SKIP = -0x7fffffff - 1;   // ye[r]: residual 0 or infinite, no correction
 constexpr int YE_NAN = YE_SKIP + 1;        // ye[r]: NaN residual
+constexpr int IR_OB = 4;                    // right-hand sides per thread in the blocked updates
+constexpr int IR_BLK_MIN = 16;              // right-hand sides from which the block updates are blocked
+
+// Rows r0 .. r0 + cnt - 1 of every right-hand side take the forward block's
+// 32 columns b0 .. b0 + 31.  A thread takes one row and up to IR_OB
+// right-hand sides, the row's 32 factors loaded once (consecutive threads:
+// consecutive rows of the same right-hand sides, whose y are broadcast).
+// Each y_i receives its FMAs in column order, as in the one-pair-a-thread
+// loop that serves fewer right-hand sides.  A function of its own, so that
+// its registers do not crowd the dependent chains beside it.
+__device__ __noinline__ void blk_update_fwd(int R, int NP, int LDF, int b0, int r0, int cnt, const float *L, float *Y,
+                                            const int *ye) {
+    const int tid = threadIdx.x;
+    const int ngr = (R + IR_OB - 1) / IR_OB;
+    for (int q = tid; q < ngr * cnt; q += DC_THREADS) {
+        const int rg = q / cnt, ii = r0 + (q - rg * cnt);
+        float lr[32];
+        const float4 *Li = reinterpret_cast<const float4 *>(L + (size_t)ii * LDF + b0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const float4 l4 = Li[t];
+            lr[4 * t] = l4.x;
+            lr[4 * t + 1] = l4.y;
+            lr[4 * t + 2] = l4.z;
+            lr[4 * t + 3] = l4.w;
+        }
+#pragma unroll
+        for (int u = 0; u < IR_OB; ++u) {
+            const int r = rg * IR_OB + u;
+            if (r >= R || ye[r] <= YE_NAN) continue;
+            const float4 *yb = reinterpret_cast<const float4 *>(Y + (size_t)r * NP + b0);
+            float y = Y[(size_t)r * NP + ii];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float4 y4 = yb[t];
+                y = fmaf(-lr[4 * t], y4.x, y);
+                y = fmaf(-lr[4 * t + 1], y4.y, y);
+                y = fmaf(-lr[4 * t + 2], y4.z, y);
+                y = fmaf(-lr[4 * t + 3], y4.w, y);
+            }
+            Y[(size_t)r * NP + ii] = y;
+        }
+    }
+}
+
+// Rows 0 .. b0 - 1 of every right-hand side take the backward block's
+// columns b0 .. b0 + tn - 1, the last first; blocked over right-hand sides
+// as in blk_update_fwd.
+__device__ __noinline__ void blk_update_bwd(int R, int NP, int LDF, int b0, int tn, const float *L, float *Y,
+                                            const int *ye) {
+    const int tid = threadIdx.x;
+    const int ngr = (R + IR_OB - 1) / IR_OB;
+    for (int q = tid; q < ngr * b0; q += DC_THREADS) {
+        const int rg = q / b0, ii = q - rg * b0;
+        const float *Li = L + (size_t)ii * LDF + b0;
+        if (tn == 32) {
+            float lr[32];
+            const float4 *L4 = reinterpret_cast<const float4 *>(Li);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const float4 l4 = L4[t];
+                lr[4 * t] = l4.x;
+                lr[4 * t + 1] = l4.y;
+                lr[4 * t + 2] = l4.z;
+                lr[4 * t + 3] = l4.w;
+            }
+#pragma unroll
+            for (int u = 0; u < IR_OB; ++u) {
+                const int r = rg * IR_OB + u;
+                if (r >= R || ye[r] <= YE_NAN) continue;
+                const float4 *y4p = reinterpret_cast<const float4 *>(Y + (size_t)r * NP + b0);
+                float y = Y[(size_t)r * NP + ii];
+#pragma unroll
+                for (int t = 7; t >= 0; --t) {
+                    const float4 y4 = y4p[t];
+                    y = fmaf(-lr[4 * t + 3], y4.w, y);
+                    y = fmaf(-lr[4 * t + 2], y4.z, y);
+                    y = fmaf(-lr[4 * t + 1], y4.y, y);
+                    y = fmaf(-lr[4 * t], y4.x, y);
+                }
+                Y[(size_t)r * NP + ii] = y;
+            }
+        } else {
+            for (int u = 0; u < IR_OB; ++u) {
+                const int r = rg * IR_OB + u;
+                if (r >= R || ye[r] <= YE_NAN) continue;
+                const float *yb = Y + (size_t)r * NP + b0;
+                float y = Y[(size_t)r * NP + ii];
+                for (int t = tn - 1; t >= 0; --t) y = fmaf(-Li[t], yb[t], y);
+                Y[(size_t)r * NP + ii] = y;
+            }
+        }
+    }
+}
+
 template <int NC>
 __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int *perm, const float *dinv, double *xs,
                                         const double *rs, const unsigned long long *rmax, float *Y, int *ye,
@@ -413,12 +515,19 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
     // element by element (the FP64 scaling and conversions spread over all warps)
     for (int q = tid; q < R * NP; q += DC_THREADS) {
         const int r = q / NP, i = q - r * NP;
-        const double m0 = __longlong_as_double((long long)rmax[r]);
-        const bool solve = m0 > 0.0 && m0 <= 1.7976931348623157e308;
+        // max |r| from its bits: positive and finite, or 0 / inf (no
+        // correction), or a NaN pattern (above the infinity's)
+        const unsigned long long mb = rmax[r];
+        const bool solve = mb != 0ull && mb < 0x7ff0000000000000ull;
         int e = 0;
-        if (solve) e = frexp_exp(m0);
-        Y[q] = solve && i < n ? (float)ldexp_fast(rs[(size_t)r * n + perm[i]], -e) : 0.f;
-        if (i == 0) ye[r] = solve ? e : (m0 != m0 ? YE_NAN : YE_SKIP);
+        if (solve) e = frexp_exp(__longlong_as_double((long long)mb));
+        float yv = 0.f;
+        if (solve && i < n) {
+            const double rv = rs[(size_t)r * n + perm[i]];
+            yv = narrow_scaled(rv, -e);
+        }
+        Y[q] = yv;
+        if (i == 0) ye[r] = solve ? e : (mb > 0x7ff0000000000000ull ? YE_NAN : YE_SKIP);
     }
     __syncthreads();
     const int nb = (n + 31) / 32;
@@ -449,21 +558,25 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
         __syncthreads();
         const int r0 = b0 + 32, cnt = n - r0;
         if (cnt > 0) {   // rows r0 .. n-1 take the block's 32 columns
-            for (int q = tid; q < R * cnt; q += DC_THREADS) {
-                const int r = q / cnt, ii = r0 + (q - r * cnt);
-                if (ye[r] <= YE_NAN) continue;
-                const float4 *Li = reinterpret_cast<const float4 *>(L + (size_t)ii * LDF + b0);
-                const float4 *yb = reinterpret_cast<const float4 *>(Y + (size_t)r * NP + b0);
-                float y = Y[(size_t)r * NP + ii];
+            if (R >= IR_BLK_MIN) {
+                blk_update_fwd(R, NP, LDF, b0, r0, cnt, L, Y, ye);
+            } else {   // few right-hand sides: one (right-hand side, row) a thread
+                for (int q = tid; q < R * cnt; q += DC_THREADS) {
+                    const int r = q / cnt, ii = r0 + (q - r * cnt);
+                    if (ye[r] <= YE_NAN) continue;
+                    const float4 *Li = reinterpret_cast<const float4 *>(L + (size_t)ii * LDF + b0);
+                    const float4 *yb = reinterpret_cast<const float4 *>(Y + (size_t)r * NP + b0);
+                    float y = Y[(size_t)r * NP + ii];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const float4 l4 = Li[t], y4 = yb[t];
-                    y = fmaf(-l4.x, y4.x, y);
-                    y = fmaf(-l4.y, y4.y, y);
-                    y = fmaf(-l4.z, y4.z, y);
-                    y = fmaf(-l4.w, y4.w, y);
+                    for (int t = 0; t < 8; ++t) {
+                        const float4 l4 = Li[t], y4 = yb[t];
+                        y = fmaf(-l4.x, y4.x, y);
+                        y = fmaf(-l4.y, y4.y, y);
+                        y = fmaf(-l4.z, y4.z, y);
+                        y = fmaf(-l4.w, y4.w, y);
+                    }
+                    Y[(size_t)r * NP + ii] = y;
                 }
-                Y[(size_t)r * NP + ii] = y;
             }
             __syncthreads();
         }
@@ -499,27 +612,31 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
         }
         __syncthreads();
         if (b0 > 0) {   // rows 0 .. b0-1 take the block's columns, the last first
-            for (int q = tid; q < R * b0; q += DC_THREADS) {
-                const int r = q / b0, ii = q - r * b0;
-                if (ye[r] <= YE_NAN) continue;
-                const float *Li = L + (size_t)ii * LDF + b0;
-                const float *yb = Y + (size_t)r * NP + b0;
-                float y = Y[(size_t)r * NP + ii];
-                if (tn == 32) {
-                    const float4 *L4 = reinterpret_cast<const float4 *>(Li);
-                    const float4 *y4p = reinterpret_cast<const float4 *>(yb);
+            if (R >= IR_BLK_MIN) {
+                blk_update_bwd(R, NP, LDF, b0, tn, L, Y, ye);
+            } else {
+                for (int q = tid; q < R * b0; q += DC_THREADS) {
+                    const int r = q / b0, ii = q - r * b0;
+                    if (ye[r] <= YE_NAN) continue;
+                    const float *Li = L + (size_t)ii * LDF + b0;
+                    const float *yb = Y + (size_t)r * NP + b0;
+                    float y = Y[(size_t)r * NP + ii];
+                    if (tn == 32) {
+                        const float4 *L4 = reinterpret_cast<const float4 *>(Li);
+                        const float4 *y4p = reinterpret_cast<const float4 *>(yb);
 #pragma unroll
-                    for (int t = 7; t >= 0; --t) {
-                        const float4 l4 = L4[t], y4 = y4p[t];
-                        y = fmaf(-l4.w, y4.w, y);
-                        y = fmaf(-l4.z, y4.z, y);
-                        y = fmaf(-l4.y, y4.y, y);
-                        y = fmaf(-l4.x, y4.x, y);
+                        for (int t = 7; t >= 0; --t) {
+                            const float4 l4 = L4[t], y4 = y4p[t];
+                            y = fmaf(-l4.w, y4.w, y);
+                            y = fmaf(-l4.z, y4.z, y);
+                            y = fmaf(-l4.y, y4.y, y);
+                            y = fmaf(-l4.x, y4.x, y);
+                        }
+                    } else {
+                        for (int t = tn - 1; t >= 0; --t) y = fmaf(-Li[t], yb[t], y);
                     }
-                } else {
-                    for (int t = tn - 1; t >= 0; --t) y = fmaf(-Li[t], yb[t], y);
+                    Y[(size_t)r * NP + ii] = y;
                 }
-                Y[(size_t)r * NP + ii] = y;
             }
             __syncthreads();
         }
@@ -548,7 +665,7 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
                     const double big = bx >= bd ? xv : d, small = bx >= bd ? d : xv;
                     const double err = small - (s - big);
                     const bool zero = (__double_as_longlong(err) & 0x7fffffffffffffffll) == 0;
-                    E[(size_t)r * NP + i] = __float2bfloat16_rn(zero ? 0.f : __double2float_rn(ldexp_fast(err, -e)));
+                    E[(size_t)r * NP + i] = __float2bfloat16_rn(zero ? 0.f : narrow_scaled(err, -e));
                 }
                 xv = s;
                 xs[q] = xv;
@@ -702,10 +819,14 @@ __device__ __forceinline__ float low_part(double v, float f) {
 // |K| |x| once the first correction has been applied (|2^e Y| ~ cond(K)
 // 2^-24 |x| and less after every step), so r stays the residual of the FP64
 // x as closely as an FP64 residual would.  The threads are grouped as in
-// ir_residual.
+// ir_residual; one call is the pass over a thread's right-hand sides
+// q0 .. q0 + W - 1 (W = 8, or 4 for a short last pass); the slots of a pass
+// beyond its right-hand sides read the zero rows Z (Y) and ZE (E), whose
+// terms leave the sums unchanged, so the pass runs without branches.
+template <int W>
 __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 *Kf, const float *Y,
-                                             const __nv_bfloat16 *E, const int *ye, double *rs,
-                                             unsigned long long *rnb) {
+                                             const __nv_bfloat16 *E, const float *Z, const __nv_bfloat16 *ZE,
+                                             const int *ye, double *rs, unsigned long long *rnb, int q0) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int G = DC_THREADS / n;
     const int g = tid / n, i = tid - g * n;
@@ -713,14 +834,15 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
     const bool whole = g0 == g31 && g31 < G;
     const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
     const float2 *kf = Kf + i;
-    for (int q0 = 0; q0 < mine; q0 += IR_RB) {
-        const int nb = min(IR_RB, mine - q0);
+    const int n8 = n & ~7;
+    if (q0 < mine) {
+        const int nb = min(W, mine - q0);
         const float *yb = Y + (size_t)(g + G * q0) * NP;
         const __nv_bfloat16 *eb = E + (size_t)(g + G * q0) * NP;
         const size_t ystride = (size_t)G * NP;
-        float sh[IR_RB], sl[IR_RB];
+        float sh[W], sl[W];
 #pragma unroll
-        for (int b = 0; b < IR_RB; ++b) sh[b] = sl[b] = 0.f;
+        for (int b = 0; b < W; ++b) sh[b] = sl[b] = 0.f;
         auto term = [&](float2 k, float y, float ev, int b) {
             const float p = k.x * y;
             const float pe = fmaf(k.x, y, -p);
@@ -731,7 +853,6 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
             sl[b] = fmaf(-k.x, ev, sl[b] + (err + fmaf(k.y, y, pe)));
         };
         // eight columns of K a step, the next eight loading while these are used
-        const int n8 = n & ~7;
         float2 k[8];
         if (n8 > 0) {
 #pragma unroll
@@ -747,31 +868,35 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
                 for (int u = 0; u < 8; ++u) k[u] = kf[(size_t)(j + 8 + u) * n];
             }
 #pragma unroll
-            for (int b = 0; b < IR_RB; ++b) {
-                if (b < nb) {   // Y and E rows start 16-byte aligned (NP a multiple of 32, j of 8)
-                    const float4 y0 = *reinterpret_cast<const float4 *>(yb + b * ystride + j);
-                    const float4 y1 = *reinterpret_cast<const float4 *>(yb + b * ystride + j + 4);
-                    const uint4 e8 = *reinterpret_cast<const uint4 *>(eb + b * ystride + j);
-                    // BF16 to FP32: the 16 bits are the top of the FP32 pattern
-                    term(kc[0], y0.x, __uint_as_float(e8.x << 16), b);
-                    term(kc[1], y0.y, __uint_as_float(e8.x & 0xffff0000u), b);
-                    term(kc[2], y0.z, __uint_as_float(e8.y << 16), b);
-                    term(kc[3], y0.w, __uint_as_float(e8.y & 0xffff0000u), b);
-                    term(kc[4], y1.x, __uint_as_float(e8.z << 16), b);
-                    term(kc[5], y1.y, __uint_as_float(e8.z & 0xffff0000u), b);
-                    term(kc[6], y1.z, __uint_as_float(e8.w << 16), b);
-                    term(kc[7], y1.w, __uint_as_float(e8.w & 0xffff0000u), b);
-                }
+            for (int b = 0; b < W; ++b) {
+                // Y and E rows start 16-byte aligned (NP a multiple of 32, j of 8)
+                const float *yr = (b < nb ? yb + b * ystride : Z) + j;
+                const __nv_bfloat16 *er = (b < nb ? eb + b * ystride : ZE) + j;
+                const float4 y0 = *reinterpret_cast<const float4 *>(yr);
+                const float4 y1 = *reinterpret_cast<const float4 *>(yr + 4);
+                const uint4 e8 = *reinterpret_cast<const uint4 *>(er);
+                // BF16 to FP32: the 16 bits are the top of the FP32 pattern
+                term(kc[0], y0.x, __uint_as_float(e8.x << 16), b);
+                term(kc[1], y0.y, __uint_as_float(e8.x & 0xffff0000u), b);
+                term(kc[2], y0.z, __uint_as_float(e8.y << 16), b);
+                term(kc[3], y0.w, __uint_as_float(e8.y & 0xffff0000u), b);
+                term(kc[4], y1.x, __uint_as_float(e8.z << 16), b);
+                term(kc[5], y1.y, __uint_as_float(e8.z & 0xffff0000u), b);
+                term(kc[6], y1.z, __uint_as_float(e8.w << 16), b);
+                term(kc[7], y1.w, __uint_as_float(e8.w & 0xffff0000u), b);
             }
         }
         for (; j < n; ++j) {
             const float2 kv = kf[(size_t)j * n];
 #pragma unroll
-            for (int b = 0; b < IR_RB; ++b)
-                if (b < nb) term(kv, yb[b * ystride + j], __bfloat162float(eb[b * ystride + j]), b);
+            for (int b = 0; b < W; ++b) {
+                const float *yr = b < nb ? yb + b * ystride : Z;
+                const __nv_bfloat16 *er = b < nb ? eb + b * ystride : ZE;
+                term(kv, yr[j], __bfloat162float(er[j]), b);
+            }
         }
 #pragma unroll
-        for (int b = 0; b < IR_RB; ++b) {
+        for (int b = 0; b < W; ++b) {
             if (b < nb) {
                 const int r = g + G * (q0 + b);
                 const int e = ye[r];
@@ -825,6 +950,8 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     float *Y = reinterpret_cast<float *>(base + lay.y);     // [R][np] the correction's FP32 values
     int *ye = reinterpret_cast<int *>(base + lay.ye);       // [R] their power-of-two scale
     __nv_bfloat16 *E = reinterpret_cast<__nv_bfloat16 *>(base + lay.e);   // [R][np] rounding errors of the updates
+    float *Z = reinterpret_cast<float *>(base + lay.z);     // [np] zeros, then [np] BF16 zeros
+    __nv_bfloat16 *ZE = reinterpret_cast<__nv_bfloat16 *>(Z + ir_np(n));
     double *part = reinterpret_cast<double *>(base + lay.part);   // [DC_THREADS] slices of a residual
 
     // L = fl32(K) padded with identity (Kt = the FP64 K, transposed, on the way), FP32 row sums of |L|
@@ -875,6 +1002,8 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     }
     if (lane == 0) sc.wnorm[0][warp] = (double)wrow;
     for (int i = tid; i < NP; i += DC_THREADS) perm[i] = i;
+    if (Kf)
+        for (int i = tid; i < NP + NP / 2; i += DC_THREADS) Z[i] = 0.f;   // the zero rows of Y and E
     for (int r = tid; r < R; r += DC_THREADS) rn[r] = rn[2 * (size_t)R + r] = 0ull;
     for (int idx = tid; idx < R * n; idx += DC_THREADS) {
         const int r = idx / n, i = idx - r * n;
@@ -925,7 +1054,13 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
         // x += K^-1 r through the FP32 factors (from x = 0 at it = 0, exact)
         ir_correct<NC>(n, R, L, perm, dinv, xs, rs, rn + (size_t)((it + 2) % 3) * R, Y, ye, xnb, inc ? E : nullptr);
         __syncthreads();
-        if (inc) ir_residual_inc(n, R, NP, Kf, Y, E, ye, rs, rnb);
+        if (inc) {
+            const int per = (R + DC_THREADS / n - 1) / (DC_THREADS / n);   // right-hand sides per thread
+            for (int q0 = 0; q0 < per; q0 += 8) {
+                if (per - q0 > 4) ir_residual_inc<8>(n, R, NP, Kf, Y, E, Z, ZE, ye, rs, rnb, q0);
+                else ir_residual_inc<4>(n, R, NP, Kf, Y, E, Z, ZE, ye, rs, rnb, q0);
+            }
+        }
         else ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb, part);
         __syncthreads();
         bool conv = true;

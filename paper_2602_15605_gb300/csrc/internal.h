@@ -199,7 +199,7 @@ constexpr int PT_ERR_RANGE = 0x1001;   // a tile's chunks are not covered by its
 constexpr int PT_ERR_WAIT = 0x1002;    // a bulk copy did not complete within the bounded wait
 CPL_HD inline int ir_ldf(int n) { return ir_np(n) + 4; }
 struct IrLayout {
-    size_t L, perm, dinv, x, r, xn, rn, y, e, ye, part, total;
+    size_t L, perm, dinv, x, r, xn, rn, y, z, e, ye, part, total;
 };
 CPL_HD inline size_t ir_align(size_t b) { return (b + 15) & ~(size_t)15; }
 CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
@@ -215,6 +215,7 @@ CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
     s.xn = o;   o += ir_align(sizeof(double) * 2 * (size_t)R);
     s.rn = o;   o += ir_align(sizeof(double) * 3 * (size_t)R);        // residual maxima, 3 buffers
     s.y = o;    o += ir_align(sizeof(float) * (size_t)R * np);        // the correction in FP32
+    s.z = o;    o += ir_align(6 * np);                                // a zero row of y and of the update errors
     s.ye = o;   o += ir_align(sizeof(int) * (size_t)R);
     // one region for two uses that never meet: the slices of a one-column
     // residual (one right-hand side), and the BF16 rounding errors [R][np] of
