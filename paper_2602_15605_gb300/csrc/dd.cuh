@@ -166,6 +166,19 @@ __device__ __forceinline__ xdf xdf_scale_int(xdf a, long long k) { return xdf_mu
 // FP64 value of a (truncating below 2^-52 relative), built with integer
 // operations only (the FP64 pipe is the scarce one).  Handles FP64
 // subnormals and zero.
+// (double) f from the bits for a normal f, 0 for a zero or subnormal f.
+__device__ __forceinline__ double df_widen_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0x000fffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+// FP64 of a double-float value: both parts widened from their bits and added
+// once, i.e. the correctly rounded h + l (a low part below FP32's normal
+// range, at most 2^-126 in absolute value, is dropped).
+__device__ __forceinline__ double df_to_double(dfl a) { return df_widen_bits(a.h) + df_widen_bits(a.l); }
+
 __device__ __forceinline__ double xdf_to_double(xdf a) {
     if (a.h == 0.0f) return 0.0;
     const unsigned long long sign = (a.h < 0.0f) ? (1ull << 63) : 0ull;

@@ -12,8 +12,9 @@
 // h table):  X = (-1)^p sqrt(g(p - j1) g(p - j2) g(p - j3) h(p)),
 // h(p) = 1 / ((2p + 1) g(p)).  The square roots are taken once per table
 // entry (k_sqrt_tables, held as FP32 pairs), and an element is four or five
-// double-float products on the FP32 pipe, converted to FP64 with integer
-// operations: GB300's FP64 pipe would otherwise bound the kernel.  (With
+// double-float products on the FP32 pipe, converted to FP64 by widening both
+// parts from their bits and one FP64 addition: GB300's FP64 pipe would
+// otherwise bound the kernel.  (With
 // separate roots of the integer factors and the bracket of the even case
 // formed as 1 - (J+2)(J_{-++}+1) / (2 (j2+1)(j3+1)) in double-float, an
 // element took seven or eight products and a sum: 0.113 ms instead of
@@ -85,8 +86,8 @@ __device__ __forceinline__ double m11(const SqrtTabs &T, int j1, int j2, int j3,
         v = df_mul(so, x);
         if (p & 1) v = df_neg(v);
     }
-    // FP64 from the pair with integer operations (the FP64 pipe stays idle)
-    return xdf_to_double(xdf{v.h, v.l, 0});
+    // FP64 from the pair: its parts widened from their bits, one FP64 addition
+    return df_to_double(v);
 }
 
 // Per-row constants of m11 in FP64, one thread per row (apart from the row
