@@ -179,7 +179,29 @@ __device__ __forceinline__ double df_widen_bits(float f) {
 // range, at most 2^-126 in absolute value, is dropped).
 __device__ __forceinline__ double df_to_double(dfl a) { return df_widen_bits(a.h) + df_widen_bits(a.l); }
 
+// (double) f * 2^k from the bits, for a normal f whose scaled exponent stays
+// above FP64's normal range's bottom (else 0).
+__device__ __forceinline__ double xdf_widen_bits(float f, int k) {
+    const unsigned u = __float_as_uint(f);
+    const int ef = (int)((u >> 23) & 0xffu);
+    const int fd = ef + 896 + k;
+    if (ef == 0 || fd < 1) return 0.0;
+    const unsigned hi = (u & 0x80000000u) | ((unsigned)fd << 20) | ((u >> 3) & 0x000fffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+// FP64 of (h + l) 2^e, h and l a normalised double-float pair: where h 2^e
+// is a normal double at least 2^-960 in magnitude, both parts are widened
+// from their bits and added once (the correctly rounded value; a low part
+// that falls below FP64's normal range is far below its rounding); else the
+// mantissa assembly of xdf_to_double_slow.
+__device__ __forceinline__ double xdf_to_double_slow(xdf a);
 __device__ __forceinline__ double xdf_to_double(xdf a) {
+    const int eh = (int)((__float_as_uint(a.h) >> 23) & 0xffu);
+    const int fh = eh + 896 + a.e;
+    if (eh != 0 && eh != 255 && fh > 63 && fh < 2047) return xdf_widen_bits(a.h, a.e) + xdf_widen_bits(a.l, a.e);
+    return xdf_to_double_slow(a);
+}
+__device__ __forceinline__ double xdf_to_double_slow(xdf a) {
     if (a.h == 0.0f) return 0.0;
     const unsigned long long sign = (a.h < 0.0f) ? (1ull << 63) : 0ull;
     const float ah = fabsf(a.h);
