@@ -685,7 +685,15 @@ __device__ __noinline__ void ir_correct(int n, int R, const float *L, const int 
     }
 }
 
-// The refinement's residual r = b - K x in FP64, K_ij at Kt[j n + i]:
+// Layouts of K's copies for the residuals, in groups of consecutive columns:
+// the FP64 copy Kt as [j / 4][i][j % 4], the FP32 pairs Kf as [j / 8][i][j % 8].
+// A warp's lanes (consecutive rows i) read 4 or 8 columns each as one
+// contiguous run, and the fill's warps (consecutive columns j of one row)
+// write 4 or 8 neighbours into one run.
+__device__ __forceinline__ size_t kt_idx(int n, int i, int j) { return ((size_t)(j >> 2) * n + i) * 4 + (j & 3); }
+__device__ __forceinline__ size_t kf_idx(int n, int i, int j) { return ((size_t)(j >> 3) * n + i) * 8 + (j & 7); }
+
+// The refinement's residual r = b - K x in FP64, K_ij at Kt[kt_idx(n, i, j)]:
 // thread (g, i) takes row i of right-hand sides g, g + G, g + 2G, ...
 // (G = DC_THREADS / n groups), IR_RB of them a pass, so a row of K is read
 // ceil(R / (G IR_RB)) times instead of R.  Every sum runs over j in order
@@ -706,18 +714,18 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
         const int seg = ((n + G - 1) / G + 3) & ~3;
         if (g < G) {
             const int j0 = min(n, g * seg), j1 = min(n, j0 + seg);
-            const double *kt = Kt + i;
             double acc = 0.0;
             int j = j0;
             for (; j + 4 <= j1; j += 4) {
-                const double k0 = kt[(size_t)j * n], k1 = kt[(size_t)(j + 1) * n], k2 = kt[(size_t)(j + 2) * n],
-                             k3 = kt[(size_t)(j + 3) * n];
+                const double2 *kp = reinterpret_cast<const double2 *>(Kt + kt_idx(n, i, j));
+                const double2 ka = kp[0], kb = kp[1];
+                const double k0 = ka.x, k1 = ka.y, k2 = kb.x, k3 = kb.y;
                 acc = fma(k0, xs[j], acc);
                 acc = fma(k1, xs[j + 1], acc);
                 acc = fma(k2, xs[j + 2], acc);
                 acc = fma(k3, xs[j + 3], acc);
             }
-            for (; j < j1; ++j) acc = fma(kt[(size_t)j * n], xs[j], acc);
+            for (; j < j1; ++j) acc = fma(Kt[kt_idx(n, i, j)], xs[j], acc);
             part[g * n + i] = acc;
         }
         __syncthreads();
@@ -734,7 +742,6 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
     const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
     const bool whole = g0 == g31 && g31 < G;   // the warp's lanes share their right-hand sides
     const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
-    const double *kt = Kt + i;   // K_ij = kt[j n]: a warp's lanes read consecutive rows
     for (int q0 = 0; q0 < mine; q0 += IR_RB) {
         const int nb = min(IR_RB, mine - q0);
         const double *xb = xs + (size_t)(g + G * q0) * n;
@@ -744,8 +751,9 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
         for (int b = 0; b < IR_RB; ++b) acc[b] = 0.0;
         int j = 0;
         for (; j + 4 <= n; j += 4) {
-            const double k0 = kt[(size_t)j * n], k1 = kt[(size_t)(j + 1) * n], k2 = kt[(size_t)(j + 2) * n],
-                         k3 = kt[(size_t)(j + 3) * n];
+            const double2 *kp = reinterpret_cast<const double2 *>(Kt + kt_idx(n, i, j));
+            const double2 ka = kp[0], kb = kp[1];
+            const double k0 = ka.x, k1 = ka.y, k2 = kb.x, k3 = kb.y;
 #pragma unroll
             for (int b = 0; b < IR_RB; ++b) {
                 if (b < nb) {
@@ -758,7 +766,7 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
             }
         }
         for (; j < n; ++j) {
-            const double kv = kt[(size_t)j * n];
+            const double kv = Kt[kt_idx(n, i, j)];
 #pragma unroll
             for (int b = 0; b < IR_RB; ++b)
                 if (b < nb) acc[b] = fma(kv, xb[b * xstride + j], acc[b]);
@@ -811,7 +819,7 @@ __device__ __forceinline__ float low_part(double v, float f) {
 // A residual update on the FP32 pipe in double-float: r <- r - K 2^e (Y - E)
 // for the update 2^e (Y - E) that the last correction applied to x (Y its
 // FP32 values, E the rounding errors of the FP64 additions in BF16, both in
-// units of 2^e), with K held as FP32 pairs Kf[j n + i] = (fl32(K_ij),
+// units of 2^e), with K held as FP32 pairs Kf[kf_idx(n, i, j)] = (fl32(K_ij),
 // fl32(K_ij - fl32(K_ij))): each product K_ij Y_j as hi * y (exact with its
 // fma error) plus lo * y, summed over j in order with a two-sum on the high
 // part, minus hi * E_j in the low part; the sum is brought to FP64 once per
@@ -833,7 +841,6 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
     const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
     const bool whole = g0 == g31 && g31 < G;
     const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
-    const float2 *kf = Kf + i;
     const int n8 = n & ~7;
     if (q0 < mine) {
         const int nb = min(W, mine - q0);
@@ -856,7 +863,11 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
         float2 k[8];
         if (n8 > 0) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) k[u] = kf[(size_t)u * n];
+            for (int u = 0; u < 4; ++u) {
+                const float4 v = reinterpret_cast<const float4 *>(Kf + kf_idx(n, i, 0))[u];
+                k[2 * u] = make_float2(v.x, v.y);
+                k[2 * u + 1] = make_float2(v.z, v.w);
+            }
         }
         int j = 0;
         for (; j < n8; j += 8) {
@@ -865,7 +876,11 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
             for (int u = 0; u < 8; ++u) kc[u] = k[u];
             if (j + 8 < n8) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) k[u] = kf[(size_t)(j + 8 + u) * n];
+                for (int u = 0; u < 4; ++u) {
+                    const float4 v = reinterpret_cast<const float4 *>(Kf + kf_idx(n, i, j + 8))[u];
+                    k[2 * u] = make_float2(v.x, v.y);
+                    k[2 * u + 1] = make_float2(v.z, v.w);
+                }
             }
 #pragma unroll
             for (int b = 0; b < W; ++b) {
@@ -887,7 +902,7 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
             }
         }
         for (; j < n; ++j) {
-            const float2 kv = kf[(size_t)j * n];
+            const float2 kv = Kf[kf_idx(n, i, j)];
 #pragma unroll
             for (int b = 0; b < W; ++b) {
                 const float *yr = b < nb ? yb + b * ystride : Z;
@@ -926,8 +941,9 @@ __device__ __noinline__ void ir_residual_inc(int n, int R, int NP, const float2 
 // factorisation falls back), |K|_inf comes from FP32 row sums, maxima are
 // taken on the bit patterns of non-negative doubles, and each residual
 // element is one thread's sum, so no FP64 reduction is needed.  The FP64
-// matrix (K1 +- K2 for kind 1 and 2) is copied once, transposed, into Kc
-// (global scratch), so that the residual's loads coalesce.
+// matrix (K1 +- K2 for kind 1 and 2) is copied once into Kc (global
+// scratch) in groups of 4 columns (kt_idx), so that the residual's loads
+// coalesce.
 // The factorisation is lu_fp32's.
 template <int NC>
 __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float *L, double *Kc, float2 *Kf,
@@ -940,7 +956,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     const double *K1 = S.K1, *K2 = S.K2;
     const double *P1 = S.P + (size_t)S.f1 * n, *P2 = S.P + (size_t)S.f2 * n;
     const size_t pstride = (size_t)S.nf * n;
-    double *Kt = Kc;   // [j][i]: K_ij of the residuals (K1 +- K2 for kind 1 and 2), column by column
+    double *Kt = Kc;   // K_ij of the residuals (K1 +- K2 for kind 1 and 2) at kt_idx(n, i, j)
     int *perm = reinterpret_cast<int *>(base + lay.perm);
     float *dinv = reinterpret_cast<float *>(base + lay.dinv);
     double *xs = reinterpret_cast<double *>(base + lay.x);
@@ -954,7 +970,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     __nv_bfloat16 *ZE = reinterpret_cast<__nv_bfloat16 *>(Z + ir_np(n));
     double *part = reinterpret_cast<double *>(base + lay.part);   // [DC_THREADS] slices of a residual
 
-    // L = fl32(K) padded with identity (Kt = the FP64 K, transposed, on the way), FP32 row sums of |L|
+    // L = fl32(K) padded with identity (Kt = the FP64 K in column groups, on the way), FP32 row sums of |L|
     float wrow = 0.f;
     for (int i0 = warp; i0 < NP; i0 += G2 * DC_WARPS) {
         double v[G2][NC];
@@ -978,7 +994,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
                         const double w = __ldg(K2 + (size_t)i * n + j);
                         v[g][m] = kind == 1 ? v[g][m] + w : v[g][m] - w;
                     }
-                    Kt[(size_t)j * n + i] = v[g][m];
+                    Kt[kt_idx(n, i, j)] = v[g][m];
                 }
             }
         }
@@ -992,8 +1008,8 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
                 const float f = (float)v[g][m];
                 if (i < NP) L[(size_t)i * LDF + j] = f;
                 if (i < n) rsum += fabsf(f);
-                // K as FP32 pairs for the double-float residual updates, transposed as Kt
-                if (Kf && i < n && j < n) Kf[(size_t)j * n + i] = make_float2(f, low_part(v[g][m], f));
+                // K as FP32 pairs for the double-float residual updates, in groups of 8 columns
+                if (Kf && i < n && j < n) Kf[kf_idx(n, i, j)] = make_float2(f, low_part(v[g][m], f));
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
@@ -1164,7 +1180,7 @@ __global__ void __launch_bounds__(DC_THREADS, 1) k_decouple(DecoupleArgs a) {
     double *slice = a.ws ? a.ws + (size_t)blockIdx.x * a.ws_stride : nullptr;
     const IrLayout lay = ir_layout(n, R, !a.l_in_ws);
     double *Kc = slice;
-    const size_t kc_d = ((size_t)n * n + 1) & ~(size_t)1;                        // doubles of Kc
+    const size_t kc_d = (size_t)((n + 3) / 4) * 4 * n;                           // doubles of Kc (whole column groups)
     const size_t f32_d = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;   // doubles of the FP32 factors
     float2 *Kf = a.df_inc ? reinterpret_cast<float2 *>(slice + kc_d + f32_d) : nullptr;
     float *L = a.l_in_ws ? reinterpret_cast<float *>(slice + kc_d)
@@ -1303,10 +1319,10 @@ cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, cons
         // whole 16-byte units), when not in shared memory its padded FP32
         // factors, and from IR_INC_MIN right-hand sides K as FP32 pairs; or the
         // FP64 solver's augmented matrix -- the larger, even
-        const size_t kc = ((size_t)n * n + 1) & ~(size_t)1;
+        const size_t kc = (size_t)((n + 3) / 4) * 4 * n;   // whole groups of 4 columns
         const size_t f32 = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;
         a.df_inc = a.refine && n_rhs >= IR_INC_MIN;
-        const size_t kf = a.df_inc ? (size_t)n * n : 0;   // FP32 pairs of K for the residual updates
+        const size_t kf = a.df_inc ? (size_t)((n + 7) / 8) * 8 * n : 0;   // FP32 pairs of K, whole groups of 8
         const size_t fp64 = a.direct_in_ws ? (size_t)n * a.ld : 0;
         a.ws_stride = (std::max(a.refine ? kc + f32 + kf : 0, fp64) + 1) & ~(size_t)1;
         CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));
