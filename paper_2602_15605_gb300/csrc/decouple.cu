@@ -20,8 +20,10 @@
 //   K 2^-e (a power-of-two scale, exact) and the answer is brought to FP64
 //   accuracy by iterative refinement: x += K^-1 r with the FP32 factors,
 //   r = b - K x in FP64 from the FP64 matrix (from 8 right-hand sides only
-//   the first; each later residual is the previous one minus K times the
-//   update x received, in double-float on the FP32 pipe), until
+//   the first, and that one on the FP64 and FP32 pipes at once, some
+//   right-hand sides as FP64 chains and the others as error-free
+//   triple-float products; each later residual is the previous one minus K
+//   times the update x received, in double-float on the FP32 pipe), until
 //   max|r| <= max|x| |K|_inf eps sqrt(n) for every right-hand side (the
 //   stopping rule of LAPACK's mixed-precision dsgesv, at most 30 steps).
 //   Each right-hand side is scaled by a power of two before it is rounded to
@@ -791,29 +793,169 @@ __device__ __noinline__ void ir_residual(int n, int R, int kind, const double *K
     }
 }
 
-// fl32(v - f) for f = fl32(v), with integer operations: v - f is exact in
-// FP64 (at most half an FP32 ulp of v, so below 2^28 units of v's last
-// place), and its FP32 rounding is that of the integer difference of the
-// mantissas.  Returns 0 where v, f or the result is not a normal number;
-// the pair (f, 0) is then a coarser K_ij, which only the residual updates
-// use: there it multiplies a correction of order cond(K) 2^-24 |x|, and an
-// entry below FP32's normal range is far below |K|_inf.
-__device__ __forceinline__ float low_part(double v, float f) {
+
+// Kl = fl32(v - f) and the rest Kll = v - f - Kl for f = fl32(v), with
+// integer operations: v - f is exact in FP64 (at most half an FP32 ulp of v,
+// so below 2^28 units of v's last place), the difference d of the mantissas
+// rounds to FP32 as Kl, and d minus that rounding (at most 5 bits) is Kll,
+// so v = f + Kl + Kll exactly.  Both are 0 where v, f or a result is not a
+// normal number: the parts are then coarser, by at most FP32's smallest
+// normal number (2^-126) times |x| per entry; the solver uses them only when
+// |K|_inf >= 2^-40, where that stays far below |K|_inf 2^-53 |x|.
+__device__ __forceinline__ float scaled_int_float(float x, int k, bool neg) {
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xff) + k;
+    if (x == 0.f || e < 1 || e > 254) return 0.f;
+    const unsigned r = (b & 0x807fffffu) | ((unsigned)e << 23);
+    return __uint_as_float(neg ? r ^ 0x80000000u : r);
+}
+__device__ __forceinline__ void low_parts(double v, float f, float &l, float &ll) {
+    l = ll = 0.f;
     const long long bv = __double_as_longlong(v);
     const int ev = (int)((bv >> 52) & 0x7ff);
     const unsigned bf = __float_as_uint(f);
     const int ef = (int)((bf >> 23) & 0xff);
-    const int sh = ef - ev + 925;   // f's mantissa in units of v's last place: << 29, or 30 after a carry
-    if (ev == 0 || ev == 0x7ff || ef == 0 || ef == 0xff || (sh != 29 && sh != 30)) return 0.f;
+    const int sh = ef - ev + 925;
+    if (ev == 0 || ev == 0x7ff || ef == 0 || ef == 0xff || (sh != 29 && sh != 30)) return;
     const long long mv = (bv & ((1ll << 52) - 1)) | (1ll << 52);
     const long long mf = (long long)((bf & 0x7fffffu) | 0x800000u) << sh;
     const int d = (int)(mv - mf);   // |d| <= 2^28
-    if (d == 0) return 0.f;
-    const unsigned bd = __float_as_uint(__int2float_rn(d));
-    const int ed = (int)((bd >> 23) & 0xff) + ev - 1075;   // scale by 2^(ev - 1075)
-    if (ed < 1 || ed > 254) return 0.f;
-    const unsigned r = (bd & 0x807fffffu) | ((unsigned)ed << 23);
-    return __uint_as_float(bv < 0 ? r ^ 0x80000000u : r);
+    const float dh = __int2float_rn(d);
+    const int dl = d - __float2int_rn(dh);
+    l = scaled_int_float(dh, ev - 1075, bv < 0);
+    ll = scaled_int_float(__int2float_rn(dl), ev - 1075, bv < 0);
+}
+
+// The first residual r = b - K x0 of many right-hand sides on both of the
+// SM's pipes at once.  x0 = 2^e Y (the first correction, exact in FP32).  In
+// one pass over j a thread forms NF of its right-hand sides as FP64 FMA
+// chains from K's FP64 copy Kt (as ir_residual does) and NT of them as
+// error-free triple-float products on the FP32 pipe: K = Kh + Kl + Kll
+// exactly (Kf and Kll), each Kh y and Kl y with its fma error, and the sum
+// cascaded over three levels -- two-sums on the first two, the third level
+// holding terms below 2^-48 of the first -- so that its error stays near
+// 2^-70 of sum |K_ij y_j|, below what an FP64 FMA chain leaves.  The three
+// levels reach FP64 as r = ((b - S1) - S2) - S3.  Slots beyond a thread's
+// right-hand sides read zero rows (ZD for x, Z for Y).  FP64 issues 2 FMAs
+// per clock per SM and FP32 64 times that, so with NF : NT near 5 : 6 the
+// two pipes finish together, in about half the time of an all-FP64 residual.
+template <int NF, int NT>
+__device__ __noinline__ void ir_residual_first(int n, int R, int NP, int kind, const double *Kt, const float2 *Kf,
+                                               const float *Kll, const double *xs, const float *Y, const int *ye,
+                                               const double *ZD, const float *Z, double *rs, const double *P1,
+                                               const double *P2, size_t pstride, unsigned long long *rnb, int q0) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = DC_THREADS / n;
+    const int g = tid / n, i = tid - g * n;
+    const int g0 = __shfl_sync(0xffffffffu, g, 0), g31 = __shfl_sync(0xffffffffu, g, 31);
+    const bool whole = g0 == g31 && g31 < G;
+    const int mine = g < G && g < R ? (R - g + G - 1) / G : 0;
+    if (q0 >= mine) return;
+    const int nb = min(NF + NT, mine - q0);
+    // row of slot b: x (FP64) for b < NF, Y (FP32) after; zero rows past nb
+    const double *xb = xs + (size_t)(g + G * q0) * n;
+    const float *yb = Y + (size_t)(g + G * (q0 + NF)) * NP;
+    const size_t xstride = (size_t)G * n, ystride = (size_t)G * NP;
+#define XROW(b) ((b) < nb ? xb + (b) * xstride : ZD)
+#define YROW(b) (NF + (b) < nb ? yb + (b) * ystride : Z)
+    double acc[NF > 0 ? NF : 1];
+    float s1[NT > 0 ? NT : 1], s2[NT > 0 ? NT : 1], s3[NT > 0 ? NT : 1];
+#pragma unroll
+    for (int b = 0; b < NF; ++b) acc[b] = 0.0;
+#pragma unroll
+    for (int b = 0; b < NT; ++b) s1[b] = s2[b] = s3[b] = 0.f;
+    auto two_sum = [](float a, float b, float &s, float &e) {
+        s = a + b;
+        const float bb = s - a;
+        e = (a - (s - bb)) + (b - bb);
+    };
+    auto term3 = [&](float kh, float kl, float kll, float y, int b) {
+        const float p1 = kh * y, q1 = fmaf(kh, y, -p1);
+        const float p2 = kl * y, q2 = fmaf(kl, y, -p2);
+        float t1, t2, t3, t4;
+        two_sum(s1[b], p1, s1[b], t1);
+        two_sum(s2[b], t1, s2[b], t2);
+        two_sum(s2[b], q1, s2[b], t3);
+        two_sum(s2[b], p2, s2[b], t4);
+        s3[b] += ((t2 + t3) + (t4 + q2)) + kll * y;
+    };
+    // four columns a step (one group of Kt, half a group of Kf and Kll)
+    const int n4 = n & ~3;
+    int j = 0;
+    for (; j < n4; j += 4) {
+        double kd[4];
+        float2 kf[4];
+        float kq[4];
+        if (NF > 0) {
+            const double2 *p = reinterpret_cast<const double2 *>(Kt + kt_idx(n, i, j));
+            const double2 v0 = p[0], v1 = p[1];
+            kd[0] = v0.x;
+            kd[1] = v0.y;
+            kd[2] = v1.x;
+            kd[3] = v1.y;
+        }
+        if (NT > 0) {
+            const float4 *p = reinterpret_cast<const float4 *>(Kf + kf_idx(n, i, j));
+            const float4 v0 = p[0], v1 = p[1];
+            kf[0] = make_float2(v0.x, v0.y);
+            kf[1] = make_float2(v0.z, v0.w);
+            kf[2] = make_float2(v1.x, v1.y);
+            kf[3] = make_float2(v1.z, v1.w);
+            const float4 q = *reinterpret_cast<const float4 *>(Kll + kf_idx(n, i, j));
+            kq[0] = q.x;
+            kq[1] = q.y;
+            kq[2] = q.z;
+            kq[3] = q.w;
+        }
+#pragma unroll
+        for (int b = 0; b < NF; ++b) {   // x rows start at r n doubles: 8-byte loads
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[b] = fma(kd[u], XROW(b)[j + u], acc[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < NT; ++b) {
+            const float4 y4 = *reinterpret_cast<const float4 *>(YROW(b) + j);
+            term3(kf[0].x, kf[0].y, kq[0], y4.x, b);
+            term3(kf[1].x, kf[1].y, kq[1], y4.y, b);
+            term3(kf[2].x, kf[2].y, kq[2], y4.z, b);
+            term3(kf[3].x, kf[3].y, kq[3], y4.w, b);
+        }
+    }
+    for (; j < n; ++j) {
+        const double kv = Kt[kt_idx(n, i, j)];
+        const float2 kfv = Kf[kf_idx(n, i, j)];
+        const float kqv = Kll[kf_idx(n, i, j)];
+#pragma unroll
+        for (int b = 0; b < NF; ++b) acc[b] = fma(kv, XROW(b)[j], acc[b]);
+#pragma unroll
+        for (int b = 0; b < NT; ++b) term3(kfv.x, kfv.y, kqv, YROW(b)[j], b);
+    }
+#undef XROW
+#undef YROW
+#pragma unroll
+    for (int b = 0; b < NF + NT; ++b) {
+        if (b < nb) {
+            const int r = g + G * (q0 + b);
+            const double u = P1[r * pstride + i], w = P2[r * pstride + i];
+            const double bv = kind == 0 ? u : (kind == 1 ? u + w : u - w);
+            double rv;
+            if (b < NF) {
+                rv = bv - acc[b < NF ? b : 0];
+            } else {
+                const int bt = b >= NF ? b - NF : 0, e = ye[r];
+                rv = e > YE_NAN ? ((bv - widen_scaled(s1[bt], e)) - widen_scaled(s2[bt], e)) - widen_scaled(s3[bt], e)
+                                : bv;
+            }
+            rs[(size_t)r * n + i] = rv;
+            unsigned long long q = (unsigned long long)__double_as_longlong(fabs(rv));
+            if (whole) {
+                q = warp_max_u64(q);
+                if (lane == 0) atomicMax(rnb + r, q);
+            } else {
+                atomicMax(rnb + r, q);
+            }
+        }
+    }
 }
 
 // A residual update on the FP32 pipe in double-float: r <- r - K 2^e (Y - E)
@@ -966,8 +1108,11 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     float *Y = reinterpret_cast<float *>(base + lay.y);     // [R][np] the correction's FP32 values
     int *ye = reinterpret_cast<int *>(base + lay.ye);       // [R] their power-of-two scale
     __nv_bfloat16 *E = reinterpret_cast<__nv_bfloat16 *>(base + lay.e);   // [R][np] rounding errors of the updates
-    float *Z = reinterpret_cast<float *>(base + lay.z);     // [np] zeros, then [np] BF16 zeros
+    float *Z = reinterpret_cast<float *>(base + lay.z);     // [np] zeros, [np] BF16 zeros, [np] FP64 zeros
     __nv_bfloat16 *ZE = reinterpret_cast<__nv_bfloat16 *>(Z + ir_np(n));
+    const double *ZD = reinterpret_cast<const double *>(Z + ir_np(n) + ir_np(n) / 2);
+    // the exact third FP32 part of K for the first residual, after the pairs
+    float *Kll = Kf ? reinterpret_cast<float *>(Kf + (size_t)((n + 7) / 8) * 8 * n) : nullptr;
     double *part = reinterpret_cast<double *>(base + lay.part);   // [DC_THREADS] slices of a residual
 
     // L = fl32(K) padded with identity (Kt = the FP64 K in column groups, on the way), FP32 row sums of |L|
@@ -1009,7 +1154,12 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
                 if (i < NP) L[(size_t)i * LDF + j] = f;
                 if (i < n) rsum += fabsf(f);
                 // K as FP32 pairs for the double-float residual updates, in groups of 8 columns
-                if (Kf && i < n && j < n) Kf[kf_idx(n, i, j)] = make_float2(f, low_part(v[g][m], f));
+                if (Kf && i < n && j < n) {
+                    float kl, kll;
+                    low_parts(v[g][m], f, kl, kll);
+                    Kf[kf_idx(n, i, j)] = make_float2(f, kl);
+                    Kll[kf_idx(n, i, j)] = kll;
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
@@ -1019,7 +1169,7 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     if (lane == 0) sc.wnorm[0][warp] = (double)wrow;
     for (int i = tid; i < NP; i += DC_THREADS) perm[i] = i;
     if (Kf)
-        for (int i = tid; i < NP + NP / 2; i += DC_THREADS) Z[i] = 0.f;   // the zero rows of Y and E
+        for (int i = tid; i < 3 * NP + NP / 2; i += DC_THREADS) Z[i] = 0.f;   // the zero rows of Y, E and x
     for (int r = tid; r < R; r += DC_THREADS) rn[r] = rn[2 * (size_t)R + r] = 0ull;
     for (int idx = tid; idx < R * n; idx += DC_THREADS) {
         const int r = idx / n, i = idx - r * n;
@@ -1033,6 +1183,9 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
     for (int q = 0; q < DC_WARPS; ++q) amax = fmaxf(amax, (float)sc.wnorm[0][q]);
     if (!(amax > 0.f && amax <= 3.4028234663852886e38f)) return false;
     const double anrm = (double)amax;
+    // the FP32-pipe residuals (first residual and updates) need K's FP32
+    // parts to carry it exactly; below this norm they would not
+    const bool many = Kf && amax >= 0x1p-40f;
 
     // blocked FP32 factorisation: L U = rows perm[0..np-1] of the padded fl32(K)
     if (!lu_fp32<NC>(L, perm, dinv, sc)) return false;
@@ -1066,11 +1219,31 @@ __device__ __noinline__ bool solve_refined(const SysView &S, int n, int R, float
         // with many right-hand sides, only the first residual b - K x runs
         // in FP64; each later one is the previous minus K times the update
         // the correction applied, in double-float on the FP32 pipe
-        const bool inc = Kf && it > 0;
+        const bool inc = many && it > 0;
         // x += K^-1 r through the FP32 factors (from x = 0 at it = 0, exact)
         ir_correct<NC>(n, R, L, perm, dinv, xs, rs, rn + (size_t)((it + 2) % 3) * R, Y, ye, xnb, inc ? E : nullptr);
         __syncthreads();
-        if (inc) {
+        if (many && !inc) {
+            // the first residual of many right-hand sides on the FP64 and FP32 pipes at once
+            const int per = (R + DC_THREADS / n - 1) / (DC_THREADS / n);   // right-hand sides per thread
+            if (per <= 5) {
+                ir_residual(n, R, kind, Kt, xs, rs, P1, P2, pstride, rnb, part);
+            } else {
+                for (int q0 = 0; q0 < per;) {
+                    const int rem = per - q0;
+                    if (rem >= 10) {
+                        ir_residual_first<5, 6>(n, R, NP, kind, Kt, Kf, Kll, xs, Y, ye, ZD, Z, rs, P1, P2, pstride, rnb, q0);
+                        q0 += 11;
+                    } else if (rem >= 6) {
+                        ir_residual_first<4, 5>(n, R, NP, kind, Kt, Kf, Kll, xs, Y, ye, ZD, Z, rs, P1, P2, pstride, rnb, q0);
+                        q0 += 9;
+                    } else {
+                        ir_residual_first<4, 0>(n, R, NP, kind, Kt, Kf, Kll, xs, Y, ye, ZD, Z, rs, P1, P2, pstride, rnb, q0);
+                        q0 += 4;
+                    }
+                }
+            }
+        } else if (inc) {
             const int per = (R + DC_THREADS / n - 1) / (DC_THREADS / n);   // right-hand sides per thread
             for (int q0 = 0; q0 < per; q0 += 8) {
                 if (per - q0 > 4) ir_residual_inc<8>(n, R, NP, Kf, Y, E, Z, ZE, ye, rs, rnb, q0);
@@ -1322,7 +1495,8 @@ cpl_status cpl_decouple(cpl_ctx *c, int n, int n_windows, unsigned spectra, cons
         const size_t kc = (size_t)((n + 3) / 4) * 4 * n;   // whole groups of 4 columns
         const size_t f32 = a.l_in_ws ? ((size_t)ir_np(n) * ir_ldf(n) + 1) / 2 : 0;
         a.df_inc = a.refine && n_rhs >= IR_INC_MIN;
-        const size_t kf = a.df_inc ? (size_t)((n + 7) / 8) * 8 * n : 0;   // FP32 pairs of K, whole groups of 8
+        // FP32 pairs of K and its exact third parts, whole groups of 8 columns (8 n doubles, then 4 n)
+        const size_t kf = a.df_inc ? (size_t)((n + 7) / 8) * 12 * n : 0;
         const size_t fp64 = a.direct_in_ws ? (size_t)n * a.ld : 0;
         a.ws_stride = (std::max(a.refine ? kc + f32 + kf : 0, fp64) + 1) & ~(size_t)1;
         CPL_CUDA_TRY(cudaStreamWaitEvent(st, c->done, 0));

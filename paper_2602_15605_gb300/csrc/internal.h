@@ -215,7 +215,7 @@ CPL_HD inline IrLayout ir_layout(int n, int R, bool l_in_smem) {
     s.xn = o;   o += ir_align(sizeof(double) * 2 * (size_t)R);
     s.rn = o;   o += ir_align(sizeof(double) * 3 * (size_t)R);        // residual maxima, 3 buffers
     s.y = o;    o += ir_align(sizeof(float) * (size_t)R * np);        // the correction in FP32
-    s.z = o;    o += ir_align(6 * np);                                // a zero row of y and of the update errors
+    s.z = o;    o += ir_align(14 * np);                               // zero rows of y (FP32), the update errors (BF16), x (FP64)
     s.ye = o;   o += ir_align(sizeof(int) * (size_t)R);
     // one region for two uses that never meet: the slices of a one-column
     // residual (one right-hand side), and the BF16 rounding errors [R][np] of

@@ -179,17 +179,20 @@ def test_refined_and_fp64_solvers_agree(ctx):
     print("refined:", check(M, pcl[:, :1], one, sp, ref), "fp64:", check(M, pcl[:, :1], many[:, :1], sp, ref))
 
 
-@pytest.mark.parametrize("cond", [1e5, 1e6])
-def test_many_rhs_residual_updates(ctx, cond):
-    # From 8 right-hand sides only the first residual is formed in FP64; the
-    # later ones are updates r - K d in double-float.  Matrices with a set
-    # condition number (U diag(s) V^T, s log-spaced) make the refinement take
-    # several update steps (cond 2^-24 per step); one right-hand side is
-    # zero (no correction), one tiny.  The answer must meet the forward and
-    # backward bars, and agree with the single-right-hand-side solves (FP64
-    # residuals throughout) to the forward bar.
-    n, R = 96, 32
-    rng = np.random.default_rng(int(np.log10(cond)))
+@pytest.mark.parametrize("n,cond", [(96, 1e5), (96, 1e6), (160, 1e5)])
+def test_many_rhs_residual_updates(ctx, n, cond):
+    # From 8 right-hand sides the first residual runs on the FP64 and FP32
+    # pipes at once (FP64 chains for some right-hand sides, error-free
+    # triple-float products for the others: 4 + 5 of them a thread at
+    # n = 96, 5 + 6 at n = 160), and the later ones are updates r - K d in
+    # double-float.  Matrices with a set condition number (U diag(s) V^T, s
+    # log-spaced) make the refinement take several update steps (cond 2^-24
+    # per step); one right-hand side is zero (no correction), one tiny.  The
+    # answer must meet the forward and backward bars, and agree with the
+    # single-right-hand-side solves (FP64 residuals throughout) to the
+    # forward bar.
+    R = 32
+    rng = np.random.default_rng(int(np.log10(cond)) + n)
     M = np.empty((1, 1, n, n))
     U, _ = np.linalg.qr(rng.normal(size=(n, n)))
     V, _ = np.linalg.qr(rng.normal(size=(n, n)))
