@@ -212,6 +212,28 @@ def test_many_rhs_residual_updates(ctx, n, cond):
         assert fe <= 8 * n * EPS * kappa, (r, fe)
 
 
+def test_many_rhs_tiny_norm_uses_fp64_residuals(ctx):
+    # Below |K|_inf = 2^-40 the FP32 parts of K no longer carry it exactly,
+    # so the solver keeps every residual in FP64 there: a coupling matrix
+    # scaled by 1e-20 with 32 right-hand sides meets the bars, and its
+    # solution scales exactly with 1 / scale against the unscaled solve.
+    lmax = 161
+    W = windows.mask_like(lmax, seed=41)
+    M = oracle.coupling_dense(lmax, W, W, W, coupling.TT)[0]
+    rng = np.random.default_rng(9)
+    pcl = rng.uniform(0.1, 1.0, size=(1, 32, 1, lmax - 1))
+    scale = 1e-20
+    got, info = run(ctx, M * scale, pcl, coupling.TT)
+    assert np.all(info == 0)
+    ref = dc.decouple(M * scale, pcl, coupling.TT)
+    print("tiny norm:", check(M * scale, pcl, got, coupling.TT, ref))
+    one, _ = run(ctx, M, pcl, coupling.TT)
+    n = lmax - 1
+    kappa = np.linalg.cond(M[0, 0], np.inf)
+    fe = np.max(np.abs(got * scale - one)) / np.max(np.abs(one))
+    assert fe <= 8 * n * EPS * kappa, fe
+
+
 def test_singular_systems_report_info(ctx):
     n = 12
     sp = coupling.TT | coupling.EE | coupling.EEBB
