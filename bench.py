@@ -763,9 +763,10 @@ def run_ours(args, rank, world, local):
                              "peak_source": FP64_PEAK["source"],
                              "achieved_counts": "FP64-equivalent flops of the direct solve (2n^3/3 + 2 n^2 n_rhs "
                                                 "per system) / median event time; the refined solver runs the "
-                                                "factorisation in FP32 and only the residuals in FP64; one CTA "
-                                                "per system (80 of 152 SMs), a chain of n dependent "
-                                                "elimination steps"}}
+                                                "factorisation in FP32 and the residuals at FP64 accuracy (from 8 "
+                                                "right-hand sides the first on the FP64 and FP32 pipes, the later "
+                                                "ones as double-float updates); one CTA per system (80 of 152 "
+                                                "SMs), a chain of n dependent elimination steps"}}
             del pcl, dout
         del Mb, db
 
