@@ -14,7 +14,8 @@ Printed JSON line (rank 0):
   e2e          the same metric through cpl_build_host (pinned host windows in,
                pinned host matrix out; H2D and D2H copies inside the timed region)
   roofline     dominant kernel's algorithmic FLOP / its event-timed duration
-               against the FP64 pipe peak (2 FMA/clk/SM x 152 SMs x 2.07 GHz)
+               against the FP64 rate the library's FMA probe measures in the same
+               run (fp64_peak; the nominal 2 FMA/clk/SM x 152 SMs x 2.07 GHz beside it)
   cpu_baseline the CPU oracle (Schulten-Gordon recursion + direct sum) on a
                bounded random sample of pairs of the same workload
   cov          cpl_cov_gaussian (TT + EE terms, l_max = 3000) with squared-mask
@@ -24,6 +25,12 @@ Printed JSON line (rank 0):
   decouple     cpl_decouple on the binned matrices of 16 band-limited windows
                (l_max = 8000, 160 bins): event time per call for 1 and 32
                right-hand sides
+  mixed        the same workload in mixed precision (tcgen05 limb GEMMs), its
+               error against the FP64 arm, its own roofline and e2e
+  batch        8 ragged jobs (l_max 1000 - 10000, 4 windows each) as one
+               cpl_build_batch (a CUDA-graph replay) per step, mixed precision
+  large_lmax   TT at l_max = 20000, FP64, with and without the operand tables
+  threej_m11   (j1 j2 j3; 0 -1 1) rows for 4096 (j2, j3) pairs
 Multi-GPU (torchrun): every rank builds an independent problem of the same
 size (weak scaling; no data-path collective), the step time is the max over
 ranks, and value counts the elements of all ranks.
