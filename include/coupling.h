@@ -425,9 +425,14 @@ cpl_status cpl_threej_m11(cpl_ctx *ctx, const int *j2, const int *j3, int n, dou
  * Each system is solved by Gaussian elimination with partial pivoting; the
  * EE/BB system is split exactly into (K^EE +- K^EEBB) systems.  With few
  * right-hand sides (n_rhs <= 2n/9, n <= 512) the factorisation runs in FP32
- * and iterative refinement with FP64 residuals brings every solution to
- * max|pcl - K C| <= max|C| |K|_inf 2^-53 sqrt(n) (the stopping rule of
- * LAPACK's dsgesv); a system whose FP32 factors fail (a zero pivot, entries
+ * and iterative refinement with residuals of FP64 accuracy brings every
+ * solution to max|pcl - K C| <= max|C| |K|_inf 2^-53 sqrt(n) (the stopping
+ * rule of LAPACK's dsgesv).  From 8 right-hand sides (and |K|_inf >= 2^-40)
+ * the first residual runs partly as exact triple-FP32 products (where a
+ * thread of the solver holds more than 5 right-hand sides) and each
+ * later one is the previous residual minus K times the update the solution
+ * received, in FP32 pairs; with fewer every residual is an FP64 product.
+ * A system whose FP32 factors fail (a zero pivot, entries
  * outside FP32's range, no convergence in 30 steps) and every system with
  * more right-hand sides is solved in FP64.  Results are deterministic.
  * Asynchronous on `stream`; CPL_ERR_ARG / CPL_ERR_RANGE for invalid
